@@ -1,0 +1,416 @@
+"""Benchmark: NTBC inference (Mblocks/s) and 4k-material encode time on one GB300 per rank.
+
+Workload (default): the 4096^2 material with diffuse + normal (BC1) and roughness + AO
+(BC4) textures and crack overlay, 12 grid levels 16..2048, 8-bit QAT grids,
+3 x 64 SELU MLPs, FP16 inference weights. Synthetic, seeded (no dataset exists here).
+
+One timed step = one NTBC inference pass over the whole material (all 4 textures,
+1,048,576 block positions, 4,194,304 texture blocks) through the C ABI, inputs
+resident in HBM; the L2 is flushed (256 MiB write) between timed iterations, each
+iteration bracketed by its own CUDA events on the launching stream.
+Also reported: the encode (training) time per step and the full-schedule encode
+seconds extrapolated from the measured steps, the same metric end to end with host
+buffers (model blob H2D, blocks D2H), the plain FP32 PyTorch path on the same GPU,
+and the CPU oracle on a bounded sample (cpu_baseline).
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FULL_MAIN_STEPS = 20000
+FULL_QAT_STEPS = 2000
+BATCH_TEXELS = 1 << 18
+FORMATS = [1, 1, 4, 4]
+METRIC = "NTBC infer Mblocks/s (4k material, 4 textures) + 4k-material encode s, vs plain FP32 GPU, at decoded-PSNR parity"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--train-steps", type=int, default=1000, help="main-phase encode steps actually run")
+    ap.add_argument("--side", type=int, default=4096)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# workload setup
+# ----------------------------------------------------------------------------
+
+def build_workload(nt, torch, side, seed, dev):
+    mat = synth.material_4k(seed=seed, side=side)
+    w = nt.configs.WORKLOADS["mat4k"]
+    desc = nt.configs.desc_for(w, mat.formats, side=side)
+    cres, eres = nt.configs.res_lists(desc)
+    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
+    tex_d = [torch.from_numpy(t.ravel()).to(dev) for t in mat.textures]
+    nblk = (side // 4) ** 2
+    refs = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in mat.formats]
+    return mat, desc, p0, tex_d, refs
+
+
+def time_events(torch, fn, iters, flush=None, stream=None):
+    """Per-iteration CUDA-event timing on the launching stream; optional L2 flush between."""
+    times = []
+    for _ in range(iters):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def psnr_list(nt, obc, torch, mat, blocks, side):
+    out = []
+    for t, fmt in enumerate(mat.formats):
+        b = blocks[t].cpu().numpy().reshape(-1, 8)
+        out.append(round(obc.psnr(obc.decode(fmt, b, side, side), mat.textures[t]), 3))
+    return out
+
+
+def cpu_oracle_inference(nt, desc, flat_params, grid_bits, budget_s=12.0, seed=0):
+    """Time the FP64 oracle's NTBC inference on a bounded sample of blocks (single thread)."""
+    from oracle import ntbc as ont
+    params = nt.configs.unflatten(desc, flat_params)
+    p16 = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
+    for k in ("color_mlp", "endpoint_mlp"):
+        p16[k] = [(W.astype(np.float16).astype(np.float64), b.astype(np.float16).astype(np.float64)) for W, b in params[k]]
+    cres, eres = nt.configs.res_lists(desc)
+    od = ont.ModelDesc(desc.width, desc.height, [desc.formats[i] for i in range(desc.n_textures)], cres, eres,
+                       hidden_layers=desc.hidden_layers, activation="selu" if desc.activation == 0 else "relu")
+    codes, sc, zr = ont.export_grid(params["color_grid"] + params["endpoint_grid"], grid_bits)
+    deq = ont.dequantize_grid(codes, sc, zr)
+    nc = desc.color_levels
+    rng = np.random.default_rng(seed)
+    n = 64
+    t0 = time.perf_counter()
+    ont.infer_blocks(od, p16, block_ids=rng.choice(od.n_blocks, n, replace=False), color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    per_block = (time.perf_counter() - t0) / n
+    n = int(max(64, min(od.n_blocks, budget_s / max(per_block, 1e-9))))
+    ids = np.sort(rng.choice(od.n_blocks, n, replace=False))
+    t0 = time.perf_counter()
+    ont.infer_blocks(od, p16, block_ids=ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    dt = time.perf_counter() - t0
+    return n, dt
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ----------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import paper_2407_09543_gb300 as nt
+    side = args.side
+    w = nt.configs.WORKLOADS["mat4k"]
+    desc = nt.configs.desc_for(w, FORMATS, side=side)
+    cres, eres = nt.configs.res_lists(desc)
+    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
+    params = synth.random_params_like(p0, seed=1)
+    flat = nt.configs.flatten(desc, params)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rates = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        n, dt = cpu_oracle_inference(nt, desc, flat, 8, budget_s=budget, seed=i)
+        if i >= args.warmup:
+            rates.append(n * len(FORMATS) / dt / 1e6)
+            samples.append(n)
+    value = float(np.mean(rates))
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mblocks/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * (desc.width // 4) ** 2 * len(FORMATS) / (value * 1e6),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"mat4k {side}x{side}, 4 textures (2 BC1 + 2 BC4), 12 levels 16..2048 u8, 3x64 SELU",
+                   "l2": "oracle on CPU", "parallelism": "single process, CPU"},
+        "cpu_baseline": {"value": value, "unit": "Mblocks/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{int(np.mean(samples))} random blocks of the 4k material per step (FP64 numpy)"},
+        "e2e": {"value": value, "unit": "Mblocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2407_09543_gb300 as nt
+    from oracle import bc as obc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    stream = torch.cuda.current_stream()
+    side = args.side
+    nblk = (side // 4) ** 2
+    tex_blocks = nblk * len(FORMATS)
+
+    mat, desc, p0, tex_d, refs = build_workload(nt, torch, side, seed=rank, dev=dev)
+
+    # ---- reference BC targets (timed separately)
+    for t, fmt in enumerate(mat.formats):
+        nt.bc_reference_encode(fmt, tex_d[t], side, side, refs[t])
+    torch.cuda.synchronize()
+    ref_ms = time_events(torch, lambda: [nt.bc_reference_encode(f, tex_d[t], side, side, refs[t])
+                                         for t, f in enumerate(mat.formats)], 3)
+    ref_psnr = psnr_list(nt, obc, torch, mat, refs, side)
+
+    # ---- encode (training) on the GPU: measured steps, full schedule extrapolated
+    model = nt.Model(desc)
+    flat0 = torch.from_numpy(nt.configs.flatten(desc, p0)).to(dev)
+    model.set_params(flat0)
+    model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+    untrained = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in FORMATS]
+    model.infer_to_bc(untrained)
+    untrained_psnr = psnr_list(nt, obc, torch, mat, untrained, side)
+    material = nt.Material.make(side, side, mat.formats, tex_d, refs)
+    main_steps = args.train_steps
+    cfg = nt.TrainConfig.make(steps=main_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1, grid_bits=8, seed=rank)
+    total_steps = main_steps + int(np.ceil(0.1 * main_steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    last_losses = model.train(material, cfg)
+    train_s = time.perf_counter() - t0
+    ms_per_train_step = 1e3 * train_s / total_steps
+    encode_full_s = ms_per_train_step * (FULL_MAIN_STEPS + FULL_QAT_STEPS) / 1e3
+    model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+
+    # ---- inference timing (device-resident inputs)
+    outs = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in FORMATS]
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def infer():
+        model.infer_to_bc(outs)
+
+    for _ in range(args.warmup):
+        flush()
+        infer()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = time_events(torch, infer, args.steps, flush=flush)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ours_psnr = psnr_list(nt, obc, torch, mat, outs, side)
+    value = world * tex_blocks / (ms * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers: blob H2D, infer, blocks D2H
+    blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
+    model.save(blob)
+    host_out = [torch.empty(nblk * 8, dtype=torch.uint8).pin_memory() for _ in FORMATS]
+    e2e_model = nt.Model(desc)
+
+    def e2e():
+        e2e_model.load(blob)
+        e2e_model.infer_to_bc(outs)
+        for h, d in zip(host_out, outs):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e()
+    torch.cuda.synchronize()
+    e2e_times = time_events(torch, e2e, args.steps, flush=flush)
+    e2e_ms = float(np.mean(e2e_times))
+    e2e_value = world * tex_blocks / (e2e_ms * 1e-3) / 1e6
+    e2e_psnr = psnr_list(nt, obc, torch, mat, host_out, side)
+
+    # ---- roofline of the inference kernel (FP32 SIMT form: FMA-pipe bound)
+    flops_per_pos = 2 * (desc.color_levels * 2 * 64 + 64 * 64 * 2 + 64 * nt.ntbc_model_layout(desc).out_color) * 16 \
+        + 2 * (desc.endpoint_levels * 2 * 64 + 64 * 64 * 2 + 64 * nt.ntbc_model_layout(desc).out_endpoint)
+    achieved_tflops = flops_per_pos * nblk / (ms * 1e-3) / 1e12
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12        # FP32 FMA lanes x 2 FLOP x max SM clock
+    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 3), "peak": round(fp32_peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / fp32_peak, 4), "traffic": None,
+                "kernel": "infer_simt_kernel<MODE_PACK>", "peak_kind": "FP32 FMA pipe: 152 SM x 128 lanes x 2 x 2.07 GHz"}
+
+    # ---- plain FP32 PyTorch path on the same GPU and weights
+    plain = None
+    if not args.no_plain:
+        from baseline import plain_fp32 as pf
+        flat = torch.empty(model.n_params, device=dev)
+        model.get_params(flat)
+        params = nt.configs.unflatten(desc, flat.cpu().numpy())
+        cres, eres = nt.configs.res_lists(desc)
+        pm = pf.PlainModel(side, side, mat.formats, cres, eres, params, "selu", dev)
+        qf = pf._qat_fn(8)
+        with torch.no_grad():
+            grids = ([qf(g) for g in pm.color_grid], [qf(g) for g in pm.endpoint_grid])
+        for W, b in pm.color_mlp + pm.endpoint_mlp:
+            with torch.no_grad():
+                W.copy_(W.half().float())
+                b.copy_(b.half().float())
+        pf.infer_to_bc(pm, grids=grids)
+        torch.cuda.synchronize()
+        p_times = time_events(torch, lambda: pf.infer_to_bc(pm, grids=grids), 2, flush=flush)
+        p_ms = float(np.mean(p_times))
+        p_outs = pf.infer_to_bc(pm, grids=grids)
+        plain_psnr = psnr_list(nt, obc, torch, mat, [o.reshape(-1) for o in p_outs], side)
+        # training step of the plain path
+        ref_e = [torch.from_numpy(obc.reference_endpoints(f, r.cpu().numpy().reshape(-1, 8))).float().to(dev)
+                 for f, r in zip(mat.formats, refs)]
+        texs = [torch.from_numpy(t).to(dev) for t in mat.textures]
+        trainer = pf.PlainTrainer(pm, FULL_MAIN_STEPS + FULL_QAT_STEPS)
+        ids = torch.randint(0, nblk, (BATCH_TEXELS // 16,), device=dev)
+        for _ in range(2):
+            trainer.step(texs, ref_e, ids)
+        torch.cuda.synchronize()
+        pt = time_events(torch, lambda: trainer.step(texs, ref_e, ids), 5)
+        p_train_ms = float(np.mean(pt))
+        plain = {"infer_value": round(tex_blocks / (p_ms * 1e-3) / 1e6, 3), "unit": "Mblocks/s",
+                 "infer_ms": round(p_ms, 3), "psnr_db": plain_psnr,
+                 "train_ms_per_step": round(p_train_ms, 3),
+                 "encode_s_extrapolated": round(p_train_ms * (FULL_MAIN_STEPS + FULL_QAT_STEPS) / 1e3, 1)}
+
+    # ---- CPU oracle on a bounded sample
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        flat = torch.empty(model.n_params, device=dev)
+        model.get_params(flat)
+        n, dt = cpu_oracle_inference(nt, desc, flat.cpu().numpy(), 8, budget_s=12.0)
+        cpu = {"value": round(n * len(FORMATS) / dt / 1e6, 6), "unit": "Mblocks/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} random blocks of the 4k material, FP64 numpy, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mblocks/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (SIMT; FP16-rounded weights, u8 grids)", "data": "synthetic",
+        "config": {"workload": f"mat4k {side}x{side}, 4 textures (2 BC1 + 2 BC4), 12 levels 16..2048 u8 QAT, "
+                               f"3x64 SELU, FP16 weights", "texture_blocks": tex_blocks, "block_positions": nblk,
+                   "l2": "flushed (256 MiB write) between timed iterations", "parallelism": f"replicas x{world}"},
+        "block_positions_per_s_M": round(nblk * world / (ms * 1e-3) / 1e6, 3),
+        "psnr_db": {"ntbc": ours_psnr, "untrained": untrained_psnr, "reference_bc": ref_psnr,
+                    "e2e": e2e_psnr, "plain_fp32": plain["psnr_db"] if plain else None},
+        "encode": {"ms_per_step": round(ms_per_train_step, 3), "steps_run": total_steps,
+                   "batch_texels": BATCH_TEXELS, "measured_s": round(train_s, 2),
+                   "full_schedule_s_extrapolated": round(encode_full_s, 1),
+                   "full_schedule_steps": FULL_MAIN_STEPS + FULL_QAT_STEPS,
+                   "last_losses": [round(x, 6) for x in last_losses],
+                   "reference_bc_encode_ms": round(float(np.mean(ref_ms)), 3)},
+        "plain_fp32_gpu": plain,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 3), "unit": "Mblocks/s", "ms_per_step": round(e2e_ms, 4),
+                "h2d_bytes_per_step": int(blob.numel()), "d2h_bytes_per_step": int(nblk * 8 * len(FORMATS))},
+        "clocks": clk,
+        "gpu_launches": args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

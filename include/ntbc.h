@@ -1,0 +1,290 @@
+/*
+ * ntbc.h -- C ABI of the GB300 (sm_103a) implementation of Neural Texture Block
+ * Compression (Fujieda & Harada, "Neural Texture Block Compression", 2024).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an ntbc_status; NTBC_OK is 0. On failure the calling
+ *     thread's message is available from ntbc_last_error(). Nothing throws,
+ *     aborts or traps.
+ *   - Arguments are validated on the host before any launch; invalid shapes or
+ *     pointers give NTBC_EINVAL and launch nothing.
+ *   - Data pointers are DEVICE pointers owned by the caller unless the comment
+ *     says "host". `stream` is a cudaStream_t (NULL = legacy default stream);
+ *     calls are asynchronous on it unless the comment says otherwise.
+ *   - Textures are row-major uint8: RGB8 (3 bytes per texel) for BC1, R8 for BC4,
+ *     pitch = width * channels. Width and height are positive multiples of 4.
+ *   - Compressed textures are (width/4)*(height/4) blocks of 8 bytes in
+ *     row-major block order (Sec. 1: "BC1 and BC4 compress each block to 8 bytes").
+ *     Within a block texel i = 4*y + x. BC1: bytes 0-1 colour0, 2-3 colour1
+ *     (little-endian RGB565, R in bits 15..11), bytes 4-7 little-endian u32 with
+ *     texel i's 2-bit code in bits 2i..2i+1. BC4: byte 0 r0, byte 1 r1, bytes 2-7
+ *     little-endian 48-bit field with texel i's 3-bit code in bits 3i..3i+2.
+ */
+#ifndef NTBC_H
+#define NTBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NTBC_OK = 0,
+    NTBC_EINVAL = 1,        /* bad argument; nothing was launched */
+    NTBC_ENOMEM = 2,        /* device allocation failed */
+    NTBC_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+    NTBC_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    NTBC_ENONFINITE = 5,    /* training produced a non-finite loss */
+    NTBC_EUNSUPPORTED = 6   /* valid request outside what the kernels implement */
+} ntbc_status;
+
+enum { NTBC_BC1 = 1, NTBC_BC4 = 4 };
+enum { NTBC_ACT_SELU = 0, NTBC_ACT_RELU = 1 };
+enum { NTBC_PREC_FP32 = 0, NTBC_PREC_FP16 = 1 };
+
+#define NTBC_MAX_TEXTURES 8
+#define NTBC_MAX_LEVELS 16
+#define NTBC_MAX_MLP_LAYERS 4
+#define NTBC_HIDDEN_WIDTH 64
+
+/* Returns the calling thread's message for the last failed call ("" if none). */
+const char* ntbc_last_error(void);
+
+/* ABI version; bumps whenever a struct layout or signature changes. */
+int ntbc_abi_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* BC1 / BC4 codec                                                            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Reference BC encoder (stands in for the Compressonator encoder that produces
+ * the training targets and the "Ref. BC" quality bar, Sec. 3.2 and Sec. 5.1).
+ * BC1: principal-axis range fit (integer covariance, 8 FP64 power iterations,
+ * extreme-projection texels as endpoints), RGB565 quantisation, exhaustive
+ * per-texel code choice, colour0 > colour1. BC4: best of the 8-value mode over
+ * [min, max] and the 6-value mode over the texels other than 0 and 255.
+ * Deterministic; bit-exact with the CPU oracle.
+ *   fmt     NTBC_BC1 or NTBC_BC4
+ *   texels  device, w*h*3 (BC1) or w*h (BC4) bytes, row-major
+ *   blocks  device, (w/4)*(h/4)*8 bytes, written
+ */
+ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h,
+                                uint8_t* blocks, void* stream);
+
+/*
+ * Decoder (the "existing BC decompression" of Sec. 5.4): blocks -> texels with
+ * the integer palette (interpolants rounded to nearest; BC1 colour0 <= colour1
+ * selects the 3-colour mode, BC4 r0 <= r1 the 6-value mode with 0 and 255).
+ *   blocks  device, (w/4)*(h/4)*8 bytes
+ *   texels  device, w*h*3 (BC1) or w*h (BC4) bytes, written
+ */
+ntbc_status bc_decode(int fmt, const uint8_t* blocks, int w, int h,
+                      uint8_t* texels, void* stream);
+
+/*
+ * Steps a6-a8 of NTBC inference on given network outputs (Sec. 3.2, Fig. NTBC
+ * (a)): quantise predicted endpoints (floor(e*31+0.5), G *63, BC4 *255, FP32),
+ * order BC1 colour0 > colour1 by swapping (equal: all codes 0) or take the BC4
+ * mode from r0 > r1, build the integer palette / 255, pick per texel the code of
+ * least squared FP32 distance (ties: lowest code), pack.
+ *   e_hat   device float [n][2*C]  (e0 then e1; C = 3 for BC1, 1 for BC4)
+ *   c_hat   device float [n][16][C] predicted texel colours in [0, 1]
+ *   blocks  device, n*8 bytes, written
+ */
+ntbc_status ntbc_outputs_to_bc(int fmt, const float* e_hat, const float* c_hat, int n,
+                               uint8_t* blocks, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Model                                                                      */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Architecture of one NTBC model (Sec. 3.2, Sec. 4.4, Sec. 5.1): an endpoint
+ * network over block coordinates and a colour network over texel coordinates,
+ * each a multi-resolution 2D feature grid (dense res x res x features per level,
+ * bilinear, corner aligned) followed by an MLP with `hidden_layers` hidden layers
+ * of 64 units and sigmoid outputs. The textures of the material share one model
+ * (aggressive packaging); the conservative packaging is two models.
+ */
+typedef struct {
+    int width, height;                     /* texels of every texture of the material */
+    int n_textures;                        /* 1..NTBC_MAX_TEXTURES */
+    int formats[NTBC_MAX_TEXTURES];        /* NTBC_BC1 / NTBC_BC4, material order */
+    int color_levels;                      /* 1..NTBC_MAX_LEVELS */
+    int color_res[NTBC_MAX_LEVELS];        /* per-level resolution, >= 2 */
+    int endpoint_levels;
+    int endpoint_res[NTBC_MAX_LEVELS];
+    int features;                          /* features per level (2) */
+    int hidden_layers;                     /* 1..3 */
+    int hidden_width;                      /* must be 64 */
+    int activation;                        /* NTBC_ACT_SELU / NTBC_ACT_RELU */
+} ntbc_model_desc;
+
+typedef struct { size_t offset, count; } ntbc_span;   /* in floats */
+
+/*
+ * Flat FP32 parameter layout: colour-grid levels (each [res][res][features],
+ * row = y), endpoint-grid levels, colour MLP (per layer W [out][in] then b
+ * [out]), endpoint MLP. in/out: MLP input (features*levels) and output sizes
+ * (colour 3 per BC1 + 1 per BC4 texture; endpoint twice that: e0 then e1 per
+ * texture, in material order).
+ */
+typedef struct {
+    size_t total;
+    ntbc_span color_grid[NTBC_MAX_LEVELS];
+    ntbc_span endpoint_grid[NTBC_MAX_LEVELS];
+    ntbc_span color_w[NTBC_MAX_MLP_LAYERS], color_b[NTBC_MAX_MLP_LAYERS];
+    ntbc_span endpoint_w[NTBC_MAX_MLP_LAYERS], endpoint_b[NTBC_MAX_MLP_LAYERS];
+    int in_color, out_color, in_endpoint, out_endpoint;
+    size_t grid_floats;                    /* colour + endpoint grid floats (a prefix) */
+} ntbc_layout;
+
+/* Host-only: validate desc and fill the layout. No device work. */
+ntbc_status ntbc_model_layout(const ntbc_model_desc* desc, ntbc_layout* out);
+
+/*
+ * Grid level resolutions res_l = floor(n_min * (n_max/n_min)^(l/(levels-1)) + 0.5)
+ * (geometric ladder from the coarsest to the finest resolution, Sec. 4.4).
+ * Host-only. out: host int[levels].
+ */
+ntbc_status ntbc_level_resolutions(int levels, int n_min, int n_max, int* out);
+
+typedef struct ntbc_model ntbc_model;      /* opaque, library-owned device state */
+
+/* Allocate a model (FP32 master parameters on the current device, zeroed). */
+ntbc_status ntbc_model_create(const ntbc_model_desc* desc, ntbc_model** out);
+void ntbc_model_free(ntbc_model* model);
+/* Device pointer and float count of the FP32 master parameters (layout above). */
+ntbc_status ntbc_model_params(ntbc_model* model, float** params, size_t* count);
+/*
+ * Copy `count` floats (must equal layout.total) of FP32 master parameters from
+ * device `src` into the model, or from the model into device `dst`. Async.
+ */
+ntbc_status ntbc_model_set_params(ntbc_model* model, const float* src, size_t count, void* stream);
+ntbc_status ntbc_model_get_params(const ntbc_model* model, float* dst, size_t count, void* stream);
+
+/*
+ * Build the inference form (Sec. 3.3): with grid_bits 8 or 4 every grid level is
+ * quantised as in QAT (range [min(0,min), max(0,max)], s = range/(2^b-1),
+ * z = round(-alpha/s), q = clamp(round(r/s)+z), FP32 decisions) and stored as one
+ * code per byte plus (s, z) per level; grid_bits 0 keeps FP32 grids.
+ * weight_prec NTBC_PREC_FP16 rounds MLP weights and biases to half precision
+ * (round to nearest even); NTBC_PREC_FP32 keeps them.
+ */
+ntbc_status ntbc_model_export(ntbc_model* model, int grid_bits, int weight_prec, void* stream);
+
+/*
+ * Read back the exported grid: codes (device, grid_floats bytes, same element
+ * order as the grid part of the layout), scales and zeros (device float
+ * [color_levels + endpoint_levels]).
+ */
+ntbc_status ntbc_model_exported_grid(const ntbc_model* model, uint8_t* codes, float* scales,
+                                     float* zeros, void* stream);
+
+/* Size in bytes of the stored model blob of the current export (host-only query). */
+ntbc_status ntbc_model_blob_size(const ntbc_model* model, size_t* size);
+
+/*
+ * Stored model blob (the on-disk form the paper loads at texture-load time):
+ * exported grid codes (or FP32 grid), per-level (s, z), MLP weights in the
+ * export precision. ntbc_model_save copies device -> host `blob` (host,
+ * blob_size bytes; synchronises the stream); ntbc_model_load copies host `blob`
+ * (pinned host memory recommended) -> the model's device buffers, asynchronously.
+ */
+ntbc_status ntbc_model_save(const ntbc_model* model, uint8_t* blob, size_t size, void* stream);
+ntbc_status ntbc_model_load(ntbc_model* model, const uint8_t* blob, size_t size, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Inference (Sec. 3.2, Fig. NTBC (a); Sec. 5.4)                              */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * NTBC inference to BC blocks for every texture of the model's material, in one
+ * fused launch: grid lookup + dequantisation, endpoint MLP per block, colour MLP
+ * per texel, endpoint quantisation, per-texel argmax of -||c_hat - p_n||, index
+ * packing and 8-byte block stores. Uses the exported form (ntbc_model_export).
+ *   blocks_out  host array of n_textures DEVICE pointers, each (w/4)*(h/4)*8 bytes
+ */
+ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out, void* stream);
+
+/*
+ * Raw network outputs (pre-quantisation) of the exported model at given blocks:
+ *   block_ids  device int32 [n]
+ *   e_hat      device float [n][out_endpoint]
+ *   c_hat      device float [n][16][out_color]  (texel i = 4y + x of each block)
+ */
+ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int n,
+                         float* e_hat, float* c_hat, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Training (Sec. 3.2 losses and straight-through argmax; Sec. 3.3 QAT;        */
+/* Sec. 4.4 Adam + schedule)                                                 */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int width, height, n_textures;
+    int formats[NTBC_MAX_TEXTURES];
+    const uint8_t* texels[NTBC_MAX_TEXTURES];       /* device, source textures */
+    const uint8_t* ref_blocks[NTBC_MAX_TEXTURES];   /* device, reference BC blocks (targets) */
+} ntbc_material;
+
+typedef struct {
+    long steps;                 /* main-phase steps S */
+    int batch_texels;           /* texels per step (multiple of 16: whole blocks) */
+    float qat_fraction;         /* extra ceil(fraction*S) QAT steps; 0 disables QAT */
+    int grid_bits;              /* QAT bit width (8 or 4) */
+    float lr_grid, lr_mlp;      /* peak learning rates (0.01, 0.005) */
+    float temperature;          /* softmax temperature T (0.01) */
+    int warmup;                 /* linear warm-up steps (10) */
+    uint64_t seed;              /* Philox key of the batch sampler */
+} ntbc_train_config;
+
+/*
+ * Losses and gradients of one training step on the given blocks (all 16
+ * texels of each), for the current FP32 master parameters.
+ *   block_ids  device int32 [n_blocks]
+ *   qat_bits   0 (float grids) or the QAT width (fake-quantised grids, STE)
+ *   grads      device float [layout.total], overwritten with d loss / d params
+ *              (endpoint parameters: of L_e + L_cd; colour: of L_c + L_cd)
+ *   losses     device float [6]: L_e, L_cd(endpoint), L_c, L_cd(colour),
+ *              L_endpoint, L_color
+ */
+ntbc_status ntbc_train_grads(ntbc_model* model, const ntbc_material* mat, const int32_t* block_ids,
+                             int n_blocks, int qat_bits, float temperature, float* grads,
+                             float* losses, void* stream);
+
+/*
+ * One dense Adam step (beta 0.9/0.999, eps 1e-15, bias correction) on the FP32
+ * master parameters with learning rate lr_grid / lr_mlp scaled by the warm-up +
+ * cosine schedule at `step` of `total_steps`. Adam moments are library-owned
+ * and start at zero at step 0.
+ */
+ntbc_status ntbc_adam_step(ntbc_model* model, const float* grads, long step, long total_steps,
+                           const ntbc_train_config* cfg, void* stream);
+
+/*
+ * Philox4x32-10 batch sampler: ids[i] = (word * n_blocks) >> 32 with word
+ * (i mod 4) of philox(counter = (i/4, step, 0, 0), key = (seed lo, seed hi)).
+ *   ids  device int32 [n]
+ */
+ntbc_status ntbc_sample_blocks(uint64_t seed, long step, int n, int n_blocks, int32_t* ids, void* stream);
+
+/*
+ * Full encode (Fig. NTBC (b)): S main steps then ceil(qat_fraction*S) QAT steps,
+ * each sampling batch_texels/16 blocks, computing gradients and taking an Adam
+ * step, all on device; the per-step launches are captured once in a CUDA graph.
+ * The model's parameters must be initialised (ntbc_model_params) by the caller.
+ * Synchronises the stream at the end. losses_out: host float[6] of the last
+ * step (may be NULL). NTBC_ENONFINITE if the last loss is not finite.
+ */
+ntbc_status ntbc_train(ntbc_model* model, const ntbc_material* mat, const ntbc_train_config* cfg,
+                       float* losses_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTBC_H */

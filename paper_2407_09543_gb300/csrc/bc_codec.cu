@@ -1,0 +1,365 @@
+// BC1 / BC4 reference encoder, decoder and the output-to-block stage of NTBC
+// inference; host error plumbing of the library.
+//
+// Format: Sec. 2.1 (8-byte blocks, RGB565 + 2-bit codes, 8-bit + 3-bit codes,
+// palettes of Eq. palette / Eq. weightBC4). The reference encoder stands in for
+// the Compressonator encoder of Sec. 5.1 and is bit-exact with the CPU oracle:
+// its FP64 arithmetic uses explicit round-to-nearest intrinsics (no fused
+// multiply-add) in the same order as the oracle's.
+#include <cstdlib>
+#include <cstring>
+
+#include "ntbc_internal.cuh"
+
+namespace ntbc {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+ntbc_status fail(ntbc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+ntbc_status cuda_fail(cudaError_t err, const char* what) {
+    if (err == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(NTBC_ENOMEM, "%s: %s", what, cudaGetErrorString(err));
+    }
+    return fail(NTBC_ECUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+bool fault_injected(const char* what) {
+    const char* env = std::getenv("NTBC_FAULT");
+    return env && std::strstr(env, what) != nullptr;
+}
+
+ntbc_status device_alloc(void** ptr, size_t bytes, const char* what) {
+    *ptr = nullptr;
+    if (fault_injected("alloc")) return fail(NTBC_ENOMEM, "injected allocation failure: %s", what);
+    if (bytes == 0) return NTBC_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(NTBC_ENOMEM, "cudaMalloc(%zu) for %s: %s", bytes, what, cudaGetErrorString(e));
+    }
+    return NTBC_OK;
+}
+
+ntbc_status check_texture_args(int fmt, const void* a, const void* b, int w, int h) {
+    if (fmt != NTBC_BC1 && fmt != NTBC_BC4) return fail(NTBC_EINVAL, "format must be NTBC_BC1 or NTBC_BC4, got %d", fmt);
+    if (w <= 0 || h <= 0 || (w & 3) || (h & 3))
+        return fail(NTBC_EINVAL, "width and height must be positive multiples of 4, got %dx%d", w, h);
+    if ((long long)w * h > (1LL << 30)) return fail(NTBC_EINVAL, "texture too large (%dx%d)", w, h);
+    if (!a || !b) return fail(NTBC_EINVAL, "null data pointer");
+    return NTBC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reference encoder
+// ---------------------------------------------------------------------------
+
+constexpr int kPowerIterations = 8;
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+
+__global__ void bc1_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, uint8_t* __restrict__ out) {
+    int bw = w >> 2, bh = h >> 2;
+    long long nb = (long long)bw * bh;
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int bx = (int)(b % bw), by = (int)(b / bw);
+    int x[16][3];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint8_t* p = tex + ((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * 3;
+        x[i][0] = p[0];
+        x[i][1] = p[1];
+        x[i][2] = p[2];
+    }
+    // integer covariance of 16 * deviation
+    int s[3] = {0, 0, 0}, mn[3] = {255, 255, 255}, mx[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            s[c] += x[i][c];
+            mn[c] = min(mn[c], x[i][c]);
+            mx[c] = max(mx[c], x[i][c]);
+        }
+    long long cov[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            long long acc = 0;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc += (long long)(16 * x[i][j] - s[j]) * (16 * x[i][k] - s[k]);
+            cov[j][k] = acc;
+        }
+    double C[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) C[j][k] = (double)cov[j][k];
+    int widest = 0;
+    int r0 = mx[0] - mn[0], r1 = mx[1] - mn[1], r2 = mx[2] - mn[2];
+    if (r1 > r0) widest = 1;
+    if (r2 > (widest == 0 ? r0 : r1)) widest = 2;
+    double v[3] = {(double)r0, (double)r1, (double)r2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (c != widest && cov[widest][c] < 0) v[c] = -v[c];
+    bool live = true;
+    for (int it = 0; it < kPowerIterations; ++it) {
+        double wv[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) wv[j] = dadd(dadd(dmul(C[j][0], v[0]), dmul(C[j][1], v[1])), dmul(C[j][2], v[2]));
+        double m = fmax(fmax(fabs(wv[0]), fabs(wv[1])), fabs(wv[2]));
+        live = live && (m > 0.0);
+        if (live) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[j] = __ddiv_rn(wv[j], m);
+        }
+    }
+    int imax = 0, imin = 0;
+    double pmax = 0.0, pmin = 0.0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        double p = dadd(dadd(dmul((double)x[i][0], v[0]), dmul((double)x[i][1], v[1])), dmul((double)x[i][2], v[2]));
+        if (i == 0 || p > pmax) {
+            pmax = p;
+            imax = i;
+        }
+        if (i == 0 || p < pmin) {
+            pmin = p;
+            imin = i;
+        }
+    }
+    auto q565 = [&](int i) -> uint32_t {
+        return (uint32_t)(((x[i][0] * 31 + 127) / 255) << 11) | (uint32_t)(((x[i][1] * 63 + 127) / 255) << 5) |
+               (uint32_t)((x[i][2] * 31 + 127) / 255);
+    };
+    uint32_t c0 = q565(imax), c1 = q565(imin);
+    if (c0 < c1) {
+        uint32_t t = c0;
+        c0 = c1;
+        c1 = t;
+    }
+    uint32_t idx = 0;
+    if (c0 != c1) {
+        int pal[4][3];
+        bc1_palette(c0, c1, pal);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            int best = 0, bestd = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                int dr = x[i][0] - pal[k][0], dg = x[i][1] - pal[k][1], db = x[i][2] - pal[k][2];
+                int d = dr * dr + dg * dg + db * db;
+                if (k == 0 || d < bestd) {
+                    bestd = d;
+                    best = k;
+                }
+            }
+            idx |= (uint32_t)best << (2 * i);
+        }
+    }
+    store_block(out + b * 8, c0 | (c1 << 16), idx);
+}
+
+__device__ __forceinline__ void bc4_codes(const int x[16], int r0, int r1, uint64_t& idx, int& sse) {
+    int pal[8];
+    bc4_palette(r0, r1, pal);
+    idx = 0;
+    sse = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        int best = 0, bestd = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int d = abs(x[i] - pal[k]);
+            if (k == 0 || d < bestd) {
+                bestd = d;
+                best = k;
+            }
+        }
+        idx |= (uint64_t)best << (3 * i);
+        sse += bestd * bestd;
+    }
+}
+
+__global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, uint8_t* __restrict__ out) {
+    int bw = w >> 2, bh = h >> 2;
+    long long nb = (long long)bw * bh;
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int bx = (int)(b % bw), by = (int)(b / bw);
+    int x[16];
+    int mx = 0, mn = 255, lo = 256, hi = -1;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        x[i] = tex[(long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)];
+        mx = max(mx, x[i]);
+        mn = min(mn, x[i]);
+        if (x[i] != 0 && x[i] != 255) {
+            lo = min(lo, x[i]);
+            hi = max(hi, x[i]);
+        }
+    }
+    int r0, r1;
+    uint64_t idx;
+    if (mx == mn) {
+        r0 = r1 = mx;
+        idx = 0;
+    } else {
+        if (hi < 0) {
+            lo = 0;
+            hi = 255;
+        }
+        uint64_t ia, ib;
+        int sa, sb;
+        bc4_codes(x, mx, mn, ia, sa);
+        bc4_codes(x, lo, hi, ib, sb);
+        if (sa <= sb) {
+            r0 = mx;
+            r1 = mn;
+            idx = ia;
+        } else {
+            r0 = lo;
+            r1 = hi;
+            idx = ib;
+        }
+    }
+    uint32_t wlo = (uint32_t)r0 | ((uint32_t)r1 << 8) | (uint32_t)((idx & 0xFFFF) << 16);
+    uint32_t whi = (uint32_t)(idx >> 16);
+    store_block(out + b * 8, wlo, whi);
+}
+
+// ---------------------------------------------------------------------------
+// decoder: one thread per block, 16 texels written
+// ---------------------------------------------------------------------------
+
+__global__ void bc_decode_kernel(int fmt, const uint8_t* __restrict__ blocks, int w, int h, uint8_t* __restrict__ tex) {
+    int bw = w >> 2, bh = h >> 2;
+    long long nb = (long long)bw * bh;
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int bx = (int)(b % bw), by = (int)(b / bw);
+    uint2 blk = *reinterpret_cast<const uint2*>(blocks + b * 8);
+    if (fmt == NTBC_BC1) {
+        int pal[4][3];
+        bc1_palette(blk.x & 0xFFFF, blk.x >> 16, pal);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            int code = (blk.y >> (2 * i)) & 3;
+            uint8_t* p = tex + ((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * 3;
+            p[0] = (uint8_t)pal[code][0];
+            p[1] = (uint8_t)pal[code][1];
+            p[2] = (uint8_t)pal[code][2];
+        }
+    } else {
+        int pal[8];
+        bc4_palette(blk.x & 0xFF, (blk.x >> 8) & 0xFF, pal);
+        uint64_t idx = (uint64_t)(blk.x >> 16) | ((uint64_t)blk.y << 16);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            int code = (int)((idx >> (3 * i)) & 7);
+            tex[(long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)] = (uint8_t)pal[code];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// outputs -> blocks (steps a6-a8) for given network outputs
+// ---------------------------------------------------------------------------
+
+__global__ void outputs_to_bc_kernel(int fmt, const float* __restrict__ e_hat, const float* __restrict__ c_hat,
+                                     int n, uint8_t* __restrict__ out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    BlockPalette bp;
+    if (fmt == NTBC_BC1) {
+        float e[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) e[k] = e_hat[(long long)b * 6 + k];
+        make_palette_bc1(e, bp);
+        uint32_t idx = 0;
+        const float* c = c_hat + (long long)b * 48;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) idx |= (uint32_t)choose_code_bc1(bp, c[3 * i], c[3 * i + 1], c[3 * i + 2]) << (2 * i);
+        store_block(out + (long long)b * 8, bp.ep, idx);
+    } else {
+        float e[2] = {e_hat[(long long)b * 2], e_hat[(long long)b * 2 + 1]};
+        make_palette_bc4(e, bp);
+        uint64_t idx = 0;
+        const float* c = c_hat + (long long)b * 16;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) idx |= (uint64_t)choose_code_bc4(bp, c[i]) << (3 * i);
+        store_block(out + (long long)b * 8, bp.ep | (uint32_t)((idx & 0xFFFF) << 16), (uint32_t)(idx >> 16));
+    }
+}
+
+}  // namespace ntbc
+
+using namespace ntbc;
+
+extern "C" {
+
+const char* ntbc_last_error(void) { return g_last_error.c_str(); }
+
+int ntbc_abi_version(void) { return 1; }
+
+ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h, uint8_t* blocks, void* stream) {
+    clear_error();
+    ntbc_status st = check_texture_args(fmt, texels, blocks, w, h);
+    if (st != NTBC_OK) return st;
+    long long nb = (long long)(w / 4) * (h / 4);
+    int threads = 128;
+    unsigned grid = (unsigned)((nb + threads - 1) / threads);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (fmt == NTBC_BC1)
+        bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, blocks);
+    else
+        bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, blocks);
+    NTBC_CHECK_LAUNCH("bc_reference_encode");
+    return NTBC_OK;
+}
+
+ntbc_status bc_decode(int fmt, const uint8_t* blocks, int w, int h, uint8_t* texels, void* stream) {
+    clear_error();
+    ntbc_status st = check_texture_args(fmt, blocks, texels, w, h);
+    if (st != NTBC_OK) return st;
+    long long nb = (long long)(w / 4) * (h / 4);
+    int threads = 128;
+    unsigned grid = (unsigned)((nb + threads - 1) / threads);
+    bc_decode_kernel<<<grid, threads, 0, (cudaStream_t)stream>>>(fmt, blocks, w, h, texels);
+    NTBC_CHECK_LAUNCH("bc_decode");
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_outputs_to_bc(int fmt, const float* e_hat, const float* c_hat, int n, uint8_t* blocks, void* stream) {
+    clear_error();
+    if (fmt != NTBC_BC1 && fmt != NTBC_BC4) return fail(NTBC_EINVAL, "format must be NTBC_BC1 or NTBC_BC4");
+    if (n < 0) return fail(NTBC_EINVAL, "negative block count");
+    if (n == 0) return NTBC_OK;
+    if (!e_hat || !c_hat || !blocks) return fail(NTBC_EINVAL, "null data pointer");
+    int threads = 128;
+    outputs_to_bc_kernel<<<(n + threads - 1) / threads, threads, 0, (cudaStream_t)stream>>>(fmt, e_hat, c_hat, n, blocks);
+    NTBC_CHECK_LAUNCH("ntbc_outputs_to_bc");
+    return NTBC_OK;
+}
+
+}  // extern "C"

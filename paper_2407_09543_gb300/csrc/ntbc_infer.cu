@@ -1,0 +1,302 @@
+// NTBC inference to BC blocks (Sec. 3.2, Fig. NTBC (a); Sec. 5.4): one fused
+// launch performs the grid lookup and dequantisation, the endpoint MLP per
+// block, the colour MLP per texel, endpoint quantisation, the per-texel argmax
+// of -||c_hat - p_n|| and the packing into 8-byte blocks.
+//
+// This translation unit holds the FP32 SIMT form of the fused kernel: one
+// thread owns one block (its endpoint network and its 16 texels), the weights
+// of the running network sit in shared memory and each thread keeps a private
+// column of shared memory for the 64 hidden activations.
+#include "ntbc_internal.cuh"
+#include "ntbc_kernels.cuh"
+
+namespace ntbc {
+
+constexpr int kInPad = kMaxIn;          // layer-0 rows padded to 32 inputs
+constexpr int kSimtThreads = 128;
+constexpr int kPalFloats = 12;          // per texture: BC1 4x3, BC4 8
+
+// Shared-memory image of one network's weights: layer 0 [64][32] zero padded,
+// hidden layers [64][64], output [out][64], then the biases.
+struct WeightImage {
+    int w[NTBC_MAX_MLP_LAYERS], b[NTBC_MAX_MLP_LAYERS], cols[NTBC_MAX_MLP_LAYERS];
+    int floats;
+};
+
+static WeightImage weight_image(const NetView& nv) {
+    WeightImage wi;
+    int off = 0;
+    for (int l = 0; l < nv.n_layers; ++l) {
+        wi.cols[l] = l == 0 ? kInPad : kHidden;
+        wi.w[l] = off;
+        off += nv.layer_out[l] * wi.cols[l];
+    }
+    for (int l = 0; l < nv.n_layers; ++l) {
+        wi.b[l] = off;
+        off += nv.layer_out[l];
+    }
+    wi.floats = (off + 3) & ~3;
+    return wi;
+}
+
+__device__ void load_weight_image(const NetView& nv, const WeightImage& wi, const float* __restrict__ params,
+                                  float* __restrict__ img) {
+    for (int l = 0; l < nv.n_layers; ++l) {
+        int rows = nv.layer_out[l], in = nv.layer_in[l], cols = wi.cols[l];
+        for (int i = threadIdx.x; i < rows * cols; i += blockDim.x) {
+            int r = i / cols, c = i % cols;
+            img[wi.w[l] + i] = c < in ? params[nv.w_off[l] + (long long)r * in + c] : 0.f;
+        }
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) img[wi.b[l] + i] = params[nv.b_off[l] + i];
+    }
+}
+
+// Evaluate the MLP of one sample. x0: layer-0 input (32, zero padded). The hidden
+// activations live in the thread's shared-memory column col[k * stride]; the
+// sigmoid outputs are written to col[0 .. out).
+__device__ void mlp_eval(const NetView& nv, const WeightImage& wi, const float* __restrict__ img, int act,
+                         const float (&x0)[kInPad], float* col, int stride) {
+    // layer 0
+    {
+        const float* W = img + wi.w[0];
+        const float* B = img + wi.b[0];
+        bool last = nv.n_layers == 1;
+        int rows = nv.layer_out[0];
+#pragma unroll 1
+        for (int o = 0; o < rows; ++o) {
+            const float4* w4 = reinterpret_cast<const float4*>(W + o * kInPad);
+            float acc = B[o];
+#pragma unroll
+            for (int i = 0; i < kInPad / 4; ++i) {
+                float4 w = w4[i];
+                acc = fmaf(w.x, x0[4 * i], acc);
+                acc = fmaf(w.y, x0[4 * i + 1], acc);
+                acc = fmaf(w.z, x0[4 * i + 2], acc);
+                acc = fmaf(w.w, x0[4 * i + 3], acc);
+            }
+            col[o * stride] = last ? sigmoid_f(acc) : act_f(acc, act);
+        }
+    }
+    for (int l = 1; l < nv.n_layers; ++l) {
+        float x[kHidden];
+#pragma unroll
+        for (int i = 0; i < kHidden; ++i) x[i] = col[i * stride];
+        const float* W = img + wi.w[l];
+        const float* B = img + wi.b[l];
+        bool last = l + 1 == nv.n_layers;
+        int rows = nv.layer_out[l];
+#pragma unroll 1
+        for (int o = 0; o < rows; ++o) {
+            const float4* w4 = reinterpret_cast<const float4*>(W + o * kHidden);
+            float acc = B[o];
+#pragma unroll
+            for (int i = 0; i < kHidden / 4; ++i) {
+                float4 w = w4[i];
+                acc = fmaf(w.x, x[4 * i], acc);
+                acc = fmaf(w.y, x[4 * i + 1], acc);
+                acc = fmaf(w.z, x[4 * i + 2], acc);
+                acc = fmaf(w.w, x[4 * i + 3], acc);
+            }
+            col[o * stride] = last ? sigmoid_f(acc) : act_f(acc, act);
+        }
+    }
+}
+
+struct OutPtrs {
+    uint8_t* p[NTBC_MAX_TEXTURES];
+};
+
+// MODE_PACK: write BC blocks; MODE_RAW: write e_hat / c_hat of the listed blocks
+enum { MODE_PACK = 0, MODE_RAW = 1 };
+
+template <int MODE>
+__global__ void __launch_bounds__(kSimtThreads)
+infer_simt_kernel(ModelView mv, const float* __restrict__ params, GridSrc csrc, GridSrc esrc, WeightImage wic,
+                  WeightImage wie, OutPtrs outs, const int32_t* __restrict__ ids, int n, float* __restrict__ e_out,
+                  float* __restrict__ c_out) {
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    const int stride = blockDim.x;
+    int wfloats = max(wic.floats, wie.floats);
+    float* img = smem;
+    float* colbase = smem + wfloats;                              // [64][stride]
+    float* palbase = colbase + kHidden * stride;                  // [T][12][stride]
+    uint32_t* epbase = reinterpret_cast<uint32_t*>(palbase + mv.n_textures * kPalFloats * stride);
+    const int tid = threadIdx.x;
+    float* col = colbase + tid;
+    int idx_in = blockIdx.x * blockDim.x + tid;
+    bool valid = idx_in < n;
+    int b = valid ? (ids ? ids[idx_in] : idx_in) : 0;
+    int bx = b % mv.bw, by = b / mv.bw;
+
+    // ---- endpoint network (per block)
+    load_weight_image(mv.endpoint, wie, params, img);
+    __syncthreads();
+    if (valid) {
+        float x0[kInPad];
+        float feats[kInPad];
+        grid_features(mv.endpoint, esrc, ((float)bx + 0.5f) / (float)mv.bw, ((float)by + 0.5f) / (float)mv.bh, feats);
+#pragma unroll
+        for (int i = 0; i < kInPad; ++i) x0[i] = i < mv.endpoint.in_dim ? feats[i] : 0.f;
+        mlp_eval(mv.endpoint, wie, img, mv.activation, x0, col, stride);
+        if (MODE == MODE_RAW) {
+            for (int o = 0; o < mv.endpoint.out_dim; ++o) e_out[(long long)idx_in * mv.endpoint.out_dim + o] = col[o * stride];
+        } else {
+            for (int t = 0; t < mv.n_textures; ++t) {
+                BlockPalette bp;
+                float e[6];
+                int eo = mv.eoff[t];
+                float* pal = palbase + t * kPalFloats * stride + tid;
+                if (mv.formats[t] == NTBC_BC1) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) e[k] = col[(eo + k) * stride];
+                    make_palette_bc1(e, bp);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) pal[(k * 3 + ch) * stride] = bp.pal[k][ch];
+                    epbase[t * stride + tid] = bp.ep;
+                } else {
+                    e[0] = col[eo * stride];
+                    e[1] = col[(eo + 1) * stride];
+                    make_palette_bc4(e, bp);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) pal[k * stride] = bp.pal[k][0];
+                    epbase[t * stride + tid] = bp.ep;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- colour network (per texel) + argmax + pack
+    load_weight_image(mv.color, wic, params, img);
+    __syncthreads();
+    if (!valid) return;
+    uint64_t idx[NTBC_MAX_TEXTURES];
+#pragma unroll
+    for (int t = 0; t < NTBC_MAX_TEXTURES; ++t) idx[t] = 0;
+    for (int i = 0; i < 16; ++i) {
+        int x = 4 * bx + (i & 3), y = 4 * by + (i >> 2);
+        float x0[kInPad];
+        float feats[kInPad];
+        grid_features(mv.color, csrc, ((float)x + 0.5f) / (float)mv.width, ((float)y + 0.5f) / (float)mv.height, feats);
+#pragma unroll
+        for (int k = 0; k < kInPad; ++k) x0[k] = k < mv.color.in_dim ? feats[k] : 0.f;
+        mlp_eval(mv.color, wic, img, mv.activation, x0, col, stride);
+        if (MODE == MODE_RAW) {
+            for (int o = 0; o < mv.color.out_dim; ++o)
+                c_out[((long long)idx_in * 16 + i) * mv.color.out_dim + o] = col[o * stride];
+            continue;
+        }
+#pragma unroll
+        for (int t = 0; t < NTBC_MAX_TEXTURES; ++t) {
+            if (t >= mv.n_textures) break;
+            const float* pal = palbase + t * kPalFloats * stride + tid;
+            int co = mv.coff[t];
+            BlockPalette bp;
+            int code;
+            if (mv.formats[t] == NTBC_BC1) {
+                uint32_t ep = epbase[t * stride + tid];
+                bp.solid = (ep & 0xFFFFu) == (ep >> 16);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) bp.pal[k][ch] = pal[(k * 3 + ch) * stride];
+                code = choose_code_bc1(bp, col[co * stride], col[(co + 1) * stride], col[(co + 2) * stride]);
+                idx[t] |= (uint64_t)code << (2 * i);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) bp.pal[k][0] = pal[k * stride];
+                code = choose_code_bc4(bp, col[co * stride]);
+                idx[t] |= (uint64_t)code << (3 * i);
+            }
+        }
+    }
+    if (MODE == MODE_PACK) {
+#pragma unroll
+        for (int t = 0; t < NTBC_MAX_TEXTURES; ++t) {
+            if (t >= mv.n_textures) break;
+            uint32_t ep = epbase[t * stride + tid];
+            uint8_t* dst = outs.p[t] + (long long)b * 8;
+            if (mv.formats[t] == NTBC_BC1) {
+                store_block(dst, ep, (uint32_t)idx[t]);       // equal colours carry all-zero codes
+            } else {
+                store_block(dst, ep | (uint32_t)((idx[t] & 0xFFFF) << 16), (uint32_t)(idx[t] >> 16));
+            }
+        }
+    }
+}
+
+static size_t simt_smem_bytes(const ModelView& mv, const WeightImage& wic, const WeightImage& wie, int threads) {
+    size_t wf = (size_t)std::max(wic.floats, wie.floats);
+    return (wf + (size_t)kHidden * threads + (size_t)mv.n_textures * kPalFloats * threads) * sizeof(float) +
+           (size_t)mv.n_textures * threads * sizeof(uint32_t);
+}
+
+static ntbc_status grid_sources(const ntbc_model* m, GridSrc& csrc, GridSrc& esrc) {
+    if (m->grid_bits < 0) return fail(NTBC_EINVAL, "model has not been exported (call ntbc_model_export or ntbc_model_load)");
+    memset(&csrc, 0, sizeof(csrc));
+    memset(&esrc, 0, sizeof(esrc));
+    if (m->grid_bits > 0) {
+        csrc.codes = m->qgrid;
+        esrc.codes = m->qgrid;
+        csrc.scale = m->qscale;
+        csrc.zero = m->qzero;
+        esrc.scale = m->qscale + m->desc.color_levels;
+        esrc.zero = m->qzero + m->desc.color_levels;
+    } else {
+        csrc.f32 = m->infer_params;
+        esrc.f32 = m->infer_params;
+    }
+    return NTBC_OK;
+}
+
+template <int MODE>
+static ntbc_status launch_simt(const ntbc_model* m, const OutPtrs& outs, const int32_t* ids, int n, float* e_out,
+                               float* c_out, cudaStream_t s) {
+    GridSrc csrc, esrc;
+    ntbc_status st = grid_sources(m, csrc, esrc);
+    if (st != NTBC_OK) return st;
+    ModelView mv = make_view(m->desc, m->layout);
+    WeightImage wic = weight_image(mv.color), wie = weight_image(mv.endpoint);
+    int threads = kSimtThreads;
+    size_t smem = simt_smem_bytes(mv, wic, wie, threads);
+    NTBC_CHECK_CUDA(cudaFuncSetAttribute(infer_simt_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = (n + threads - 1) / threads;
+    infer_simt_kernel<MODE><<<grid, threads, smem, s>>>(mv, m->infer_params, csrc, esrc, wic, wie, outs, ids, n, e_out, c_out);
+    NTBC_CHECK_LAUNCH("ntbc inference (SIMT)");
+    return NTBC_OK;
+}
+
+}  // namespace ntbc
+
+using namespace ntbc;
+
+extern "C" {
+
+ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, void* stream) {
+    clear_error();
+    if (!m || !blocks_out) return fail(NTBC_EINVAL, "null argument");
+    OutPtrs outs;
+    memset(&outs, 0, sizeof(outs));
+    for (int t = 0; t < m->desc.n_textures; ++t) {
+        if (!blocks_out[t]) return fail(NTBC_EINVAL, "null output pointer for texture %d", t);
+        if (reinterpret_cast<uintptr_t>(blocks_out[t]) & 7) return fail(NTBC_EINVAL, "output %d not 8-byte aligned", t);
+        outs.p[t] = blocks_out[t];
+    }
+    int n = (m->desc.width / 4) * (m->desc.height / 4);
+    return launch_simt<MODE_PACK>(m, outs, nullptr, n, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+ntbc_status ntbc_forward(const ntbc_model* m, const int32_t* block_ids, int n, float* e_hat, float* c_hat, void* stream) {
+    clear_error();
+    if (!m || !block_ids || !e_hat || !c_hat) return fail(NTBC_EINVAL, "null argument");
+    if (n < 0) return fail(NTBC_EINVAL, "negative count");
+    if (n == 0) return NTBC_OK;
+    OutPtrs outs;
+    memset(&outs, 0, sizeof(outs));
+    return launch_simt<MODE_RAW>(m, outs, block_ids, n, e_hat, c_hat, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,862 @@
+// NTBC training (encode): batch sampling, forward of both networks, the losses
+// L_endpoint = L_e + L_cd and L_color = L_c + L_cd (Sec. 3.2, Eq. lossNTBC_e /
+// lossNTBC_c) with the straight-through argmax (Eq. softmax, App. A), the hand-
+// written backward (MLP weight / input gradients, grid scatter-add), QAT fake
+// quantisation of the grids (Sec. 3.3) and dense Adam with warm-up + cosine
+// schedule (Sec. 4.4).
+//
+// Layout: every activation buffer is feature-major, [unit][sample], so that
+// consecutive threads (samples) touch consecutive addresses. The colour network
+// runs on 16 samples per sampled block (all its texels), the endpoint network on
+// one sample per block.
+#include <cmath>
+#include <cstring>
+
+#include "ntbc_internal.cuh"
+#include "ntbc_kernels.cuh"
+
+namespace ntbc {
+
+constexpr double kAdamB1 = 0.9, kAdamB2 = 0.999;
+constexpr float kAdamEps = 1e-15f;
+constexpr float kNormGuard = 1e-6f;
+
+struct StepState {
+    long long step;          // current step index (0-based)
+    float lr_grid, lr_mlp;   // scheduled learning rates of this step
+    float bc1, bc2;          // Adam bias corrections 1 - beta^(step+1)
+    int qat;                 // 1 while the QAT phase fake-quantises the grids
+};
+
+struct NetBuffers {
+    int cap;                 // sample capacity
+    float* X;                // [32][cap] grid features
+    float* A[3];             // [64][cap] hidden activations (post-activation)
+    float* Y;                // [out][cap] sigmoid outputs
+    float* D0;               // [64][cap] deltas (ping)
+    float* D1;               // [64][cap] deltas (pong)
+};
+
+}  // namespace ntbc
+
+struct ntbc_train_state {
+    int cap_blocks = 0;
+    ntbc::NetBuffers color{}, endpoint{};
+    int32_t* ids = nullptr;
+    float* grads = nullptr;
+    double* loss_acc = nullptr;       // [6]
+    float* losses = nullptr;          // [6]
+    ntbc::StepState* st = nullptr;
+    float* qscale = nullptr;          // [levels] QAT scale / zero of this step
+    float* qzero = nullptr;
+    unsigned* qmm = nullptr;
+    int* qat_flag = nullptr;          // points at st->qat
+};
+
+namespace ntbc {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al. 2011)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        if (r < 9) {
+            k.x += W0;
+            k.y += W1;
+        }
+    }
+    return c;
+}
+
+__global__ void sample_kernel(uint64_t seed, const StepState* __restrict__ st, long long explicit_step, int n,
+                              int n_blocks, int32_t* __restrict__ ids) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long step = st ? st->step : explicit_step;
+    uint4 w = philox4x32_10(make_uint4((uint32_t)(i >> 2), (uint32_t)step, 0u, 0u),
+                            make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    uint32_t word = (i & 3) == 0 ? w.x : (i & 3) == 1 ? w.y : (i & 3) == 2 ? w.z : w.w;
+    ids[i] = (int32_t)(((uint64_t)word * (uint64_t)n_blocks) >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// step bookkeeping: schedule, bias corrections, QAT phase flag
+// ---------------------------------------------------------------------------
+
+__global__ void step_begin_kernel(StepState* st, long long explicit_step, long long main_steps, long long total_steps,
+                                  float lr_grid, float lr_mlp, int warmup, int qat_bits) {
+    if (threadIdx.x != 0) return;
+    long long t = explicit_step >= 0 ? explicit_step : st->step;
+    st->step = t;
+    double f;
+    if (t < warmup) {
+        f = (double)(t + 1) / warmup;
+    } else {
+        long long span = total_steps - warmup > 0 ? total_steps - warmup : 1;
+        f = 0.5 * (1.0 + cos(3.14159265358979323846 * (double)(t - warmup) / (double)span));
+    }
+    st->lr_grid = (float)(lr_grid * f);
+    st->lr_mlp = (float)(lr_mlp * f);
+    st->bc1 = (float)(1.0 - pow(kAdamB1, (double)(t + 1)));
+    st->bc2 = (float)(1.0 - pow(kAdamB2, (double)(t + 1)));
+    st->qat = (qat_bits > 0 && t >= main_steps) ? 1 : 0;
+}
+
+__global__ void step_end_kernel(StepState* st) {
+    if (threadIdx.x == 0) st->step += 1;
+}
+
+__global__ void set_qat_kernel(StepState* st, int on) {
+    if (threadIdx.x == 0) st->qat = on;
+}
+
+// ---------------------------------------------------------------------------
+// batch gather of grid features
+// ---------------------------------------------------------------------------
+
+// sample k of the colour network is texel (k & 15) of block ids[k >> 4];
+// sample k of the endpoint network is block ids[k]
+__device__ __forceinline__ void sample_coords(const ModelView& mv, bool color, const int32_t* ids, int k, float& u,
+                                              float& v, int& x, int& y) {
+    if (color) {
+        int b = ids[k >> 4], i = k & 15;
+        x = 4 * (b % mv.bw) + (i & 3);
+        y = 4 * (b / mv.bw) + (i >> 2);
+        u = ((float)x + 0.5f) / (float)mv.width;
+        v = ((float)y + 0.5f) / (float)mv.height;
+    } else {
+        int b = ids[k];
+        x = b % mv.bw;
+        y = b / mv.bw;
+        u = ((float)x + 0.5f) / (float)mv.bw;
+        v = ((float)y + 0.5f) / (float)mv.bh;
+    }
+}
+
+__global__ void gather_kernel(ModelView mv, bool color, GridSrc src, const int32_t* __restrict__ ids, int B,
+                              float* __restrict__ X) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B) return;
+    const NetView& nv = color ? mv.color : mv.endpoint;
+    float u, v;
+    int x, y;
+    sample_coords(mv, color, ids, k, u, v, x, y);
+    float f[kMaxIn];
+    grid_features(nv, src, u, v, f);
+#pragma unroll
+    for (int i = 0; i < kMaxIn; ++i)
+        if (i < nv.in_dim) X[(long long)i * B + k] = f[i];
+}
+
+// ---------------------------------------------------------------------------
+// dense layers
+// ---------------------------------------------------------------------------
+
+// Y[o][k] = act(b[o] + sum_i W[o][i] X[i][k]); act: 0 SELU, 1 ReLU, 2 sigmoid
+template <int IN_PAD>
+__global__ void dense_fwd_kernel(const float* __restrict__ X, int in, int B, const float* __restrict__ W,
+                                 const float* __restrict__ bias, int out, int act, float* __restrict__ Y) {
+    __shared__ __align__(16) float Ws[kHidden * IN_PAD];
+    __shared__ float bs[kHidden];
+    for (int i = threadIdx.x; i < out * IN_PAD; i += blockDim.x) {
+        int r = i / IN_PAD, c = i % IN_PAD;
+        Ws[i] = c < in ? W[r * in + c] : 0.f;
+    }
+    for (int i = threadIdx.x; i < out; i += blockDim.x) bs[i] = bias[i];
+    __syncthreads();
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B) return;
+    float x[IN_PAD];
+#pragma unroll
+    for (int i = 0; i < IN_PAD; ++i) x[i] = i < in ? X[(long long)i * B + k] : 0.f;
+#pragma unroll 1
+    for (int o = 0; o < out; ++o) {
+        const float4* w4 = reinterpret_cast<const float4*>(Ws + o * IN_PAD);
+        float acc = bs[o];
+#pragma unroll
+        for (int i = 0; i < IN_PAD / 4; ++i) {
+            float4 w = w4[i];
+            acc = fmaf(w.x, x[4 * i], acc);
+            acc = fmaf(w.y, x[4 * i + 1], acc);
+            acc = fmaf(w.z, x[4 * i + 2], acc);
+            acc = fmaf(w.w, x[4 * i + 3], acc);
+        }
+        Y[(long long)o * B + k] = act == 2 ? sigmoid_f(acc) : act_f(acc, act);
+    }
+}
+
+// Dprev[i][k] = (sum_o W[o][i] D[o][k]) * act'(Aprev[i][k])   (no factor when Aprev == null)
+__global__ void dense_bwd_data_kernel(const float* __restrict__ D, int out, int B, const float* __restrict__ W, int in,
+                                      const float* __restrict__ Aprev, int act, float* __restrict__ Dprev) {
+    __shared__ __align__(16) float WT[kHidden * kHidden];    // [i][o], o padded to 64
+    for (int j = threadIdx.x; j < in * kHidden; j += blockDim.x) {
+        int i = j / kHidden, o = j % kHidden;
+        WT[j] = o < out ? W[o * in + i] : 0.f;
+    }
+    __syncthreads();
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B) return;
+    float d[kHidden];
+#pragma unroll
+    for (int o = 0; o < kHidden; ++o) d[o] = o < out ? D[(long long)o * B + k] : 0.f;
+#pragma unroll 1
+    for (int i = 0; i < in; ++i) {
+        const float4* w4 = reinterpret_cast<const float4*>(WT + i * kHidden);
+        float acc = 0.f;
+#pragma unroll
+        for (int o = 0; o < kHidden / 4; ++o) {
+            float4 w = w4[o];
+            acc = fmaf(w.x, d[4 * o], acc);
+            acc = fmaf(w.y, d[4 * o + 1], acc);
+            acc = fmaf(w.z, d[4 * o + 2], acc);
+            acc = fmaf(w.w, d[4 * o + 3], acc);
+        }
+        if (Aprev) acc *= act_grad_from_out(Aprev[(long long)i * B + k], act);
+        Dprev[(long long)i * B + k] = acc;
+    }
+}
+
+// dW[o][i] += sum_k D[o][k] A[i][k], db[o] += sum_k D[o][k] over this CTA's chunk of samples
+constexpr int kWgChunk = 2048;
+constexpr int kWgTile = 32;
+
+__global__ void __launch_bounds__(256) dense_bwd_weight_kernel(const float* __restrict__ D, int out,
+                                                               const float* __restrict__ A, int in, int B,
+                                                               float* __restrict__ dW, float* __restrict__ db) {
+    __shared__ float Ds[kHidden][kWgTile + 1];
+    __shared__ float As[kHidden][kWgTile + 1];
+    int ob = threadIdx.x / 16, ib = threadIdx.x % 16;   // 4 x 4 tile of (o, i)
+    float acc[4][4] = {};
+    float bacc[4] = {};
+    long long k0 = (long long)blockIdx.x * kWgChunk;
+    long long k1 = min((long long)B, k0 + kWgChunk);
+    for (long long kt = k0; kt < k1; kt += kWgTile) {
+        for (int j = threadIdx.x; j < kHidden * kWgTile; j += blockDim.x) {
+            int r = j / kWgTile, c = j % kWgTile;
+            long long k = kt + c;
+            bool ok = k < k1;
+            Ds[r][c] = (r < out && ok) ? D[(long long)r * B + k] : 0.f;
+            As[r][c] = (r < in && ok) ? A[(long long)r * B + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int c = 0; c < kWgTile; ++c) {
+            float d[4], a[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                d[j] = Ds[4 * ob + j][c];
+                a[j] = As[4 * ib + j][c];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                bacc[p] += d[p];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(d[p], a[q], acc[p][q]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        int o = 4 * ob + p;
+        if (o >= out) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int i = 4 * ib + q;
+            if (i < in) atomicAdd(&dW[o * in + i], acc[p][q]);
+        }
+        if (ib == 0) atomicAdd(&db[o], bacc[p]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// losses with the straight-through argmax
+// ---------------------------------------------------------------------------
+
+// linear-order float palette P_n = a_n e0 + b_n e1 + const_n (Eq. palette / Eq. weightBC4)
+__device__ __forceinline__ int palette_coeffs(int fmt, bool eight, float a[8], float b[8], float c[8]) {
+    if (fmt == NTBC_BC1) {
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            float w = (float)n / 3.f;
+            a[n] = 1.f - w;
+            b[n] = w;
+            c[n] = 0.f;
+        }
+        return 4;
+    }
+    if (eight) {
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            float w = (float)n / 7.f;
+            a[n] = 1.f - w;
+            b[n] = w;
+            c[n] = 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            bool interp = n >= 1 && n <= 6;
+            float w = interp ? (float)(n - 1) / 5.f : 0.f;
+            a[n] = interp ? 1.f - w : 0.f;
+            b[n] = interp ? w : 0.f;
+            c[n] = n == 7 ? 1.f : 0.f;
+        }
+    }
+    return 8;
+}
+
+// decoded reference endpoints in [0, 1] (stored order) of block b of texture t
+__device__ __forceinline__ void ref_endpoints(int fmt, const uint8_t* blocks, int b, float e0[3], float e1[3]) {
+    uint32_t lo = *reinterpret_cast<const uint32_t*>(blocks + (long long)b * 8);
+    if (fmt == NTBC_BC1) {
+        int r, g, bb;
+        expand565(lo & 0xFFFF, r, g, bb);
+        e0[0] = r / 255.f; e0[1] = g / 255.f; e0[2] = bb / 255.f;
+        expand565(lo >> 16, r, g, bb);
+        e1[0] = r / 255.f; e1[1] = g / 255.f; e1[2] = bb / 255.f;
+    } else {
+        e0[0] = (float)(lo & 0xFF) / 255.f;
+        e1[0] = (float)((lo >> 8) & 0xFF) / 255.f;
+    }
+}
+
+__device__ __forceinline__ float texel_value(const uint8_t* tex, int fmt, int w, int x, int y, int ch) {
+    int C = fmt == NTBC_BC1 ? 3 : 1;
+    return (float)tex[((long long)y * w + x) * C + ch] / 255.f;
+}
+
+struct TexPtrs {
+    const uint8_t* texels[NTBC_MAX_TEXTURES];
+    const uint8_t* blocks[NTBC_MAX_TEXTURES];
+};
+
+__device__ __forceinline__ void block_reduce_add(double* acc, float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, (double)v);
+}
+
+// Softmax-expectation backward of the hard decode dec = P_{argmax d}:
+// g_d[n] = (1/T) sigma_n sum_c g_dec[c] (P[n][c] - sum_i sigma_i P[i][c])
+__device__ __forceinline__ void ste_grad(int K, int C, const float d[8], const float P[8][3], const float g_dec[3],
+                                         float T, float g_d[8]) {
+    float m = d[0];
+    for (int n = 1; n < K; ++n) m = fmaxf(m, d[n]);
+    float sig[8], sum = 0.f;
+    for (int n = 0; n < K; ++n) {
+        sig[n] = expf((d[n] - m) / T);
+        sum += sig[n];
+    }
+    float pbar[3] = {0.f, 0.f, 0.f};
+    for (int n = 0; n < K; ++n) {
+        sig[n] /= sum;
+        for (int c = 0; c < C; ++c) pbar[c] += sig[n] * P[n][c];
+    }
+    for (int n = 0; n < K; ++n) {
+        float s = 0.f;
+        for (int c = 0; c < C; ++c) s += g_dec[c] * (P[n][c] - pbar[c]);
+        g_d[n] = sig[n] * s / T;
+    }
+}
+
+// colour network: per texel sample, L_c + L_cd with distances from c_hat to the
+// reference palette; writes D[o][k] = dL/dz_out (through the sigmoid)
+__global__ void color_loss_kernel(ModelView mv, TexPtrs tp, const int32_t* __restrict__ ids, int B,
+                                  const float* __restrict__ Y, float T, float* __restrict__ D, double* __restrict__ acc) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = k < B;
+    float lc = 0.f, lcd = 0.f;
+    if (ok) {
+        int b = ids[k >> 4], i = k & 15;
+        int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
+        float n_el = (float)B * (float)mv.color.out_dim;
+        for (int t = 0; t < mv.n_textures; ++t) {
+            int fmt = mv.formats[t], C = fmt == NTBC_BC1 ? 3 : 1, co = mv.coff[t];
+            float c[3], ch[3], e0[3], e1[3], g[3];
+            for (int q = 0; q < C; ++q) {
+                c[q] = texel_value(tp.texels[t], fmt, mv.width, x, y, q);
+                ch[q] = Y[(long long)(co + q) * B + k];
+            }
+            ref_endpoints(fmt, tp.blocks[t], b, e0, e1);
+            float A[8], Bc[8], Cc[8], P[8][3], d[8], nrm[8];
+            int K = palette_coeffs(fmt, e0[0] > e1[0], A, Bc, Cc);
+            int best = 0;
+            for (int n = 0; n < K; ++n) {
+                float s = 0.f;
+                for (int q = 0; q < C; ++q) {
+                    P[n][q] = A[n] * e0[q] + Bc[n] * e1[q] + Cc[n];
+                    float df = ch[q] - P[n][q];
+                    s += df * df;
+                }
+                nrm[n] = sqrtf(s);
+                d[n] = -nrm[n];
+                if (d[n] > d[best]) best = n;
+            }
+            float g_dec[3];
+            for (int q = 0; q < C; ++q) {
+                float r = c[q] - P[best][q];
+                lcd += r * r;
+                g_dec[q] = -2.f * r / n_el;
+                float e = ch[q] - c[q];
+                lc += e * e;
+                g[q] = 2.f * e / n_el;
+            }
+            float g_d[8];
+            ste_grad(K, C, d, P, g_dec, T, g_d);
+            for (int n = 0; n < K; ++n) {
+                float inv = 1.f / fmaxf(nrm[n], kNormGuard);
+                for (int q = 0; q < C; ++q) g[q] -= g_d[n] * (ch[q] - P[n][q]) * inv;
+            }
+            for (int q = 0; q < C; ++q) D[(long long)(co + q) * B + k] = g[q] * ch[q] * (1.f - ch[q]);
+        }
+    }
+    float n_el = (float)B * (float)mv.color.out_dim;
+    block_reduce_add(&acc[2], lc / n_el);
+    block_reduce_add(&acc[3], lcd / n_el);
+}
+
+// endpoint network: per block sample, L_e + L_cd with distances from the block's
+// texel colours to the palette of the predicted (unquantised) endpoints, decoded
+// with the reference endpoints
+__global__ void endpoint_loss_kernel(ModelView mv, TexPtrs tp, const int32_t* __restrict__ ids, int Bn,
+                                     const float* __restrict__ Y, float T, float* __restrict__ D,
+                                     double* __restrict__ acc) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = k < Bn;
+    float le = 0.f, lcd = 0.f;
+    if (ok) {
+        int b = ids[k];
+        int bx = b % mv.bw, by = b / mv.bw;
+        float n_e = (float)Bn * (float)mv.endpoint.out_dim;
+        float n_cd = (float)Bn * 16.f * (float)mv.color.out_dim;
+        for (int t = 0; t < mv.n_textures; ++t) {
+            int fmt = mv.formats[t], C = fmt == NTBC_BC1 ? 3 : 1, eo = mv.eoff[t];
+            float eh0[3], eh1[3], e0[3], e1[3], g0[3], g1[3];
+            ref_endpoints(fmt, tp.blocks[t], b, e0, e1);
+            for (int q = 0; q < C; ++q) {
+                eh0[q] = Y[(long long)(eo + q) * Bn + k];
+                eh1[q] = Y[(long long)(eo + C + q) * Bn + k];
+                float r0 = eh0[q] - e0[q], r1 = eh1[q] - e1[q];
+                le += r0 * r0 + r1 * r1;
+                g0[q] = 2.f * r0 / n_e;
+                g1[q] = 2.f * r1 / n_e;
+            }
+            float Ah[8], Bh[8], Ch[8], Ar[8], Br[8], Cr[8];
+            int K = palette_coeffs(fmt, eh0[0] > eh1[0], Ah, Bh, Ch);
+            palette_coeffs(fmt, e0[0] > e1[0], Ar, Br, Cr);
+            float Ph[8][3], Pr[8][3];
+            for (int n = 0; n < K; ++n)
+                for (int q = 0; q < C; ++q) {
+                    Ph[n][q] = Ah[n] * eh0[q] + Bh[n] * eh1[q] + Ch[n];
+                    Pr[n][q] = Ar[n] * e0[q] + Br[n] * e1[q] + Cr[n];
+                }
+            for (int i = 0; i < 16; ++i) {
+                int x = 4 * bx + (i & 3), y = 4 * by + (i >> 2);
+                float c[3];
+                for (int q = 0; q < C; ++q) c[q] = texel_value(tp.texels[t], fmt, mv.width, x, y, q);
+                float d[8], nrm[8];
+                int best = 0;
+                for (int n = 0; n < K; ++n) {
+                    float s = 0.f;
+                    for (int q = 0; q < C; ++q) {
+                        float df = c[q] - Ph[n][q];
+                        s += df * df;
+                    }
+                    nrm[n] = sqrtf(s);
+                    d[n] = -nrm[n];
+                    if (d[n] > d[best]) best = n;
+                }
+                float g_dec[3];
+                for (int q = 0; q < C; ++q) {
+                    float r = c[q] - Pr[best][q];
+                    lcd += r * r;
+                    g_dec[q] = -2.f * r / n_cd;
+                }
+                float g_d[8];
+                ste_grad(K, C, d, Pr, g_dec, T, g_d);
+                for (int n = 0; n < K; ++n) {
+                    float inv = 1.f / fmaxf(nrm[n], kNormGuard);
+                    for (int q = 0; q < C; ++q) {
+                        float gp = g_d[n] * (c[q] - Ph[n][q]) * inv;    // d d_n / d p_n = (c - p_n)/||.||
+                        g0[q] += Ah[n] * gp;
+                        g1[q] += Bh[n] * gp;
+                    }
+                }
+            }
+            for (int q = 0; q < C; ++q) {
+                D[(long long)(eo + q) * Bn + k] = g0[q] * eh0[q] * (1.f - eh0[q]);
+                D[(long long)(eo + C + q) * Bn + k] = g1[q] * eh1[q] * (1.f - eh1[q]);
+            }
+        }
+    }
+    float n_e = (float)Bn * (float)mv.endpoint.out_dim;
+    float n_cd = (float)Bn * 16.f * (float)mv.color.out_dim;
+    block_reduce_add(&acc[0], le / n_e);
+    block_reduce_add(&acc[1], lcd / n_cd);
+}
+
+__global__ void loss_finalize_kernel(const double* __restrict__ acc, float* __restrict__ losses) {
+    if (threadIdx.x != 0) return;
+    losses[0] = (float)acc[0];
+    losses[1] = (float)acc[1];
+    losses[2] = (float)acc[2];
+    losses[3] = (float)acc[3];
+    losses[4] = (float)(acc[0] + acc[1]);
+    losses[5] = (float)(acc[2] + acc[3]);
+}
+
+// ---------------------------------------------------------------------------
+// grid scatter-add (bilinear adjoint), with the QAT straight-through mask
+// ---------------------------------------------------------------------------
+
+__global__ void grid_scatter_kernel(ModelView mv, bool color, const int32_t* __restrict__ ids, int B,
+                                    const float* __restrict__ G, GridSrc src, float* __restrict__ ggrad) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B) return;
+    const NetView& nv = color ? mv.color : mv.endpoint;
+    float u, v;
+    int x, y;
+    sample_coords(mv, color, ids, k, u, v, x, y);
+    int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+    for (int l = 0; l < nv.levels; ++l) {
+        Bilinear bl = bilinear_at(nv.res[l], u, v);
+        float g0 = G[(long long)(2 * l) * B + k], g1 = G[(long long)(2 * l + 1) * B + k];
+        long long o = nv.grid_off[l] + bl.base;
+        long long corner[4] = {o, o + 2, o + bl.row, o + bl.row + 2};
+        float w[4] = {bl.w00, bl.w01, bl.w10, bl.w11};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float2 add = make_float2(w[j] * g0, w[j] * g1);
+            if (qat_bits > 0) {
+                float s = src.scale[l], z = src.zero[l], qm = (float)((1 << qat_bits) - 1);
+                float2 r = *reinterpret_cast<const float2*>(src.f32 + corner[j]);
+                float q0 = roundf(__fdiv_rn(r.x, s)) + z, q1 = roundf(__fdiv_rn(r.y, s)) + z;
+                if (q0 < 0.f || q0 > qm) add.x = 0.f;
+                if (q1 < 0.f || q1 > qm) add.y = 0.f;
+            }
+            atomicAdd(reinterpret_cast<float2*>(ggrad + corner[j]), add);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adam (dense)
+// ---------------------------------------------------------------------------
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, long long grid_floats, const StepState* __restrict__ st) {
+    float lr_g = st->lr_grid, lr_m = st->lr_mlp, bc1 = st->bc1, bc2 = st->bc2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = 0.9f * m[i] + 0.1f * gi;
+        float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float lr = i < grid_floats ? lr_g : lr_m;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + kAdamEps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static void free_net(NetBuffers& nb) {
+    cudaFree(nb.X);
+    for (int l = 0; l < 3; ++l) cudaFree(nb.A[l]);
+    cudaFree(nb.Y);
+    cudaFree(nb.D0);
+    cudaFree(nb.D1);
+    memset(&nb, 0, sizeof(nb));
+}
+
+void ntbc_train_release(ntbc_model* m) {
+    ntbc_train_state* ts = m->train;
+    if (!ts) return;
+    free_net(ts->color);
+    free_net(ts->endpoint);
+    cudaFree(ts->ids);
+    cudaFree(ts->grads);
+    cudaFree(ts->loss_acc);
+    cudaFree(ts->st);
+    cudaFree(ts->qscale);
+    delete ts;
+    m->train = nullptr;
+}
+
+static ntbc_status alloc_net(NetBuffers& nb, int cap, int out_dim) {
+    nb.cap = cap;
+    ntbc_status st = device_alloc((void**)&nb.X, (size_t)kMaxIn * cap * sizeof(float), "features");
+    for (int l = 0; l < 3 && st == NTBC_OK; ++l) st = device_alloc((void**)&nb.A[l], (size_t)kHidden * cap * sizeof(float), "activations");
+    if (st == NTBC_OK) st = device_alloc((void**)&nb.Y, (size_t)out_dim * cap * sizeof(float), "outputs");
+    if (st == NTBC_OK) st = device_alloc((void**)&nb.D0, (size_t)kHidden * cap * sizeof(float), "deltas");
+    if (st == NTBC_OK) st = device_alloc((void**)&nb.D1, (size_t)kHidden * cap * sizeof(float), "deltas");
+    return st;
+}
+
+static ntbc_status ensure_train_state(ntbc_model* m, int n_blocks) {
+    ntbc_train_state* ts = m->train;
+    if (ts && ts->cap_blocks >= n_blocks) return NTBC_OK;
+    int levels = m->desc.color_levels + m->desc.endpoint_levels;
+    float* grads_keep = nullptr;
+    if (ts) {
+        free_net(ts->color);
+        free_net(ts->endpoint);
+        cudaFree(ts->ids);
+        ts->ids = nullptr;
+    } else {
+        ts = new ntbc_train_state();
+        m->train = ts;
+        ntbc_status st = device_alloc((void**)&ts->grads, m->layout.total * sizeof(float), "gradients");
+        if (st == NTBC_OK) st = device_alloc((void**)&ts->loss_acc, 6 * sizeof(double) + 6 * sizeof(float), "losses");
+        if (st == NTBC_OK) st = device_alloc((void**)&ts->st, sizeof(StepState), "step state");
+        if (st == NTBC_OK) st = device_alloc((void**)&ts->qscale, levels * (2 * sizeof(float) + 2 * sizeof(unsigned)), "QAT scales");
+        if (st != NTBC_OK) {
+            ntbc_train_release(m);
+            return st;
+        }
+        ts->losses = reinterpret_cast<float*>(ts->loss_acc + 6);
+        ts->qzero = ts->qscale + levels;
+        ts->qmm = reinterpret_cast<unsigned*>(ts->qscale + 2 * levels);
+        ts->qat_flag = &ts->st->qat;
+        NTBC_CHECK_CUDA(cudaMemset(ts->st, 0, sizeof(StepState)));
+    }
+    (void)grads_keep;
+    ts->cap_blocks = n_blocks;
+    const ntbc_layout& L = m->layout;
+    ntbc_status st = alloc_net(ts->color, n_blocks * 16, L.out_color);
+    if (st == NTBC_OK) st = alloc_net(ts->endpoint, n_blocks, L.out_endpoint);
+    if (st == NTBC_OK) st = device_alloc((void**)&ts->ids, (size_t)n_blocks * sizeof(int32_t), "batch ids");
+    if (st != NTBC_OK) ntbc_train_release(m);
+    return st;
+}
+
+static ntbc_status ensure_adam(ntbc_model* m) {
+    if (m->adam_m) return NTBC_OK;
+    size_t bytes = m->layout.total * sizeof(float);
+    ntbc_status st = device_alloc((void**)&m->adam_m, bytes, "Adam m");
+    if (st == NTBC_OK) st = device_alloc((void**)&m->adam_v, bytes, "Adam v");
+    if (st != NTBC_OK) return st;
+    NTBC_CHECK_CUDA(cudaMemset(m->adam_m, 0, bytes));
+    NTBC_CHECK_CUDA(cudaMemset(m->adam_v, 0, bytes));
+    return NTBC_OK;
+}
+
+static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static ntbc_status check_material(const ntbc_model* m, const ntbc_material* mat) {
+    if (!mat) return fail(NTBC_EINVAL, "null material");
+    if (mat->width != m->desc.width || mat->height != m->desc.height || mat->n_textures != m->desc.n_textures)
+        return fail(NTBC_EINVAL, "material does not match the model (size or texture count)");
+    for (int t = 0; t < mat->n_textures; ++t) {
+        if (mat->formats[t] != m->desc.formats[t]) return fail(NTBC_EINVAL, "texture %d: format differs from the model", t);
+        if (!mat->texels[t] || !mat->ref_blocks[t]) return fail(NTBC_EINVAL, "texture %d: null texels or reference blocks", t);
+    }
+    return NTBC_OK;
+}
+
+// one network's forward + loss + backward on the gathered batch
+static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const TexPtrs& tp, const int32_t* ids, int B,
+                           GridSrc src, float T, float* grads, double* acc, cudaStream_t s) {
+    ntbc_train_state* ts = m->train;
+    NetBuffers& nb = color ? ts->color : ts->endpoint;
+    const NetView& nv = color ? mv.color : mv.endpoint;
+    const int thr = 128;
+    unsigned g = blocks_for(B, thr);
+    gather_kernel<<<g, thr, 0, s>>>(mv, color, src, ids, B, nb.X);
+    const float* prev = nb.X;
+    int nl = nv.n_layers;
+    for (int l = 0; l < nl; ++l) {
+        bool last = l + 1 == nl;
+        float* outbuf = last ? nb.Y : nb.A[l];
+        int act = last ? 2 : mv.activation;
+        if (l == 0)
+            dense_fwd_kernel<kMaxIn><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, m->params + nv.w_off[l], m->params + nv.b_off[l], nv.layer_out[l], act, outbuf);
+        else
+            dense_fwd_kernel<kHidden><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, m->params + nv.w_off[l], m->params + nv.b_off[l], nv.layer_out[l], act, outbuf);
+        prev = outbuf;
+    }
+    float* D = nb.D0;
+    float* Dn = nb.D1;
+    if (color)
+        color_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
+    else
+        endpoint_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
+    unsigned gw = blocks_for(B, kWgChunk);
+    for (int l = nl - 1; l >= 0; --l) {
+        const float* Ain = l == 0 ? nb.X : nb.A[l - 1];
+        dense_bwd_weight_kernel<<<gw, 256, 0, s>>>(D, nv.layer_out[l], Ain, nv.layer_in[l], B, grads + nv.w_off[l], grads + nv.b_off[l]);
+        dense_bwd_data_kernel<<<g, thr, 0, s>>>(D, nv.layer_out[l], B, m->params + nv.w_off[l], nv.layer_in[l],
+                                                 l == 0 ? nullptr : nb.A[l - 1], mv.activation, Dn);
+        float* t = D;
+        D = Dn;
+        Dn = t;
+    }
+    grid_scatter_kernel<<<g, thr, 0, s>>>(mv, color, ids, B, D, src, grads);
+    NTBC_CHECK_LAUNCH(color ? "colour network step" : "endpoint network step");
+    return NTBC_OK;
+}
+
+static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const int32_t* ids, int nb, int qat_bits,
+                                bool dynamic_qat, float T, float* grads, cudaStream_t s) {
+    ntbc_train_state* ts = m->train;
+    ModelView mv = make_view(m->desc, m->layout);
+    TexPtrs tp;
+    memset(&tp, 0, sizeof(tp));
+    for (int t = 0; t < mat->n_textures; ++t) {
+        tp.texels[t] = mat->texels[t];
+        tp.blocks[t] = mat->ref_blocks[t];
+    }
+    GridSrc csrc, esrc;
+    memset(&csrc, 0, sizeof(csrc));
+    csrc.f32 = m->params;
+    csrc.qat_bits = qat_bits;
+    csrc.qat_active = dynamic_qat ? ts->qat_flag : nullptr;
+    esrc = csrc;
+    if (qat_bits > 0) {
+        LevelTable lt = level_table(m->desc, m->layout);
+        ntbc_status st = launch_level_scale_zero(m->params, lt, qat_bits, ts->qmm, ts->qscale, ts->qzero, s);
+        if (st != NTBC_OK) return st;
+        csrc.scale = ts->qscale;
+        csrc.zero = ts->qzero;
+        esrc.scale = ts->qscale + m->desc.color_levels;
+        esrc.zero = ts->qzero + m->desc.color_levels;
+    }
+    NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
+    NTBC_CHECK_CUDA(cudaMemsetAsync(ts->loss_acc, 0, 6 * sizeof(double), s));
+    ntbc_status st = run_net(m, mv, true, tp, ids, nb * 16, csrc, T, grads, ts->loss_acc, s);
+    if (st == NTBC_OK) st = run_net(m, mv, false, tp, ids, nb, esrc, T, grads, ts->loss_acc, s);
+    if (st != NTBC_OK) return st;
+    loss_finalize_kernel<<<1, 32, 0, s>>>(ts->loss_acc, ts->losses);
+    NTBC_CHECK_LAUNCH("loss finalize");
+    return NTBC_OK;
+}
+
+static ntbc_status adam_launch(ntbc_model* m, const float* grads, cudaStream_t s) {
+    long long n = (long long)m->layout.total;
+    unsigned g = (unsigned)std::min<long long>(blocks_for(n, 256), 152LL * 16);
+    adam_kernel<<<g, 256, 0, s>>>(m->params, grads, m->adam_m, m->adam_v, n, (long long)m->layout.grid_floats, m->train->st);
+    NTBC_CHECK_LAUNCH("adam");
+    return NTBC_OK;
+}
+
+}  // namespace ntbc
+
+using namespace ntbc;
+
+extern "C" {
+
+ntbc_status ntbc_sample_blocks(uint64_t seed, long step, int n, int n_blocks, int32_t* ids, void* stream) {
+    clear_error();
+    if (!ids || n < 0 || n_blocks <= 0) return fail(NTBC_EINVAL, "need ids, n >= 0 and n_blocks > 0");
+    if (n == 0) return NTBC_OK;
+    sample_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(seed, nullptr, step, n, n_blocks, ids);
+    NTBC_CHECK_LAUNCH("sample blocks");
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_train_grads(ntbc_model* m, const ntbc_material* mat, const int32_t* block_ids, int n_blocks,
+                             int qat_bits, float temperature, float* grads, float* losses, void* stream) {
+    clear_error();
+    if (!m || !block_ids || !grads) return fail(NTBC_EINVAL, "null argument");
+    ntbc_status st = check_material(m, mat);
+    if (st != NTBC_OK) return st;
+    if (n_blocks <= 0) return fail(NTBC_EINVAL, "need at least one block");
+    if (qat_bits != 0 && qat_bits != 8 && qat_bits != 4) return fail(NTBC_EINVAL, "qat_bits must be 0, 4 or 8");
+    if (!(temperature > 0.f)) return fail(NTBC_EINVAL, "temperature must be positive");
+    st = ensure_train_state(m, n_blocks);
+    if (st != NTBC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = grads_on_ids(m, mat, block_ids, n_blocks, qat_bits, false, temperature, grads, s);
+    if (st != NTBC_OK) return st;
+    if (losses) NTBC_CHECK_CUDA(cudaMemcpyAsync(losses, m->train->losses, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_adam_step(ntbc_model* m, const float* grads, long step, long total_steps, const ntbc_train_config* cfg,
+                           void* stream) {
+    clear_error();
+    if (!m || !grads || !cfg) return fail(NTBC_EINVAL, "null argument");
+    if (step < 0 || total_steps <= 0 || step >= total_steps) return fail(NTBC_EINVAL, "step outside [0, total_steps)");
+    ntbc_status st = ensure_train_state(m, 1);
+    if (st == NTBC_OK) st = ensure_adam(m);
+    if (st != NTBC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (step == 0) {
+        NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), s));
+        NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), s));
+    }
+    step_begin_kernel<<<1, 32, 0, s>>>(m->train->st, step, total_steps, total_steps, cfg->lr_grid, cfg->lr_mlp, cfg->warmup, 0);
+    NTBC_CHECK_LAUNCH("step begin");
+    return adam_launch(m, grads, s);
+}
+
+ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, float* losses_out,
+                       void* stream) {
+    clear_error();
+    if (!m || !cfg) return fail(NTBC_EINVAL, "null argument");
+    ntbc_status st = check_material(m, mat);
+    if (st != NTBC_OK) return st;
+    if (cfg->steps <= 0 || cfg->batch_texels < 16 || (cfg->batch_texels & 15))
+        return fail(NTBC_EINVAL, "need steps > 0 and batch_texels a positive multiple of 16");
+    if (cfg->qat_fraction < 0.f || (cfg->qat_fraction > 0.f && cfg->grid_bits != 8 && cfg->grid_bits != 4))
+        return fail(NTBC_EINVAL, "QAT needs grid_bits 8 or 4");
+    if (!(cfg->temperature > 0.f) || cfg->warmup < 0) return fail(NTBC_EINVAL, "bad temperature or warm-up");
+    int nb = cfg->batch_texels / 16;
+    int n_blocks = (m->desc.width / 4) * (m->desc.height / 4);
+    long long qat_steps = cfg->qat_fraction > 0.f ? (long long)std::ceil((double)cfg->qat_fraction * (double)cfg->steps) : 0;
+    long long total = cfg->steps + qat_steps;
+    int qbits = qat_steps > 0 ? cfg->grid_bits : 0;
+    st = ensure_train_state(m, nb);
+    if (st == NTBC_OK) st = ensure_adam(m);
+    if (st != NTBC_OK) return st;
+    ntbc_train_state* ts = m->train;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t cap;
+    NTBC_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    NTBC_CHECK_CUDA(cudaStreamSynchronize(s));
+    NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), cap));
+    NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), cap));
+    NTBC_CHECK_CUDA(cudaMemsetAsync(ts->st, 0, sizeof(StepState), cap));
+    // capture one step; every quantity that changes per step lives in StepState
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    NTBC_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    step_begin_kernel<<<1, 32, 0, cap>>>(ts->st, -1, cfg->steps, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup, qbits);
+    sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, 0, nb, n_blocks, ts->ids);
+    st = grads_on_ids(m, mat, ts->ids, nb, qbits, true, cfg->temperature, ts->grads, cap);
+    if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap);
+    step_end_kernel<<<1, 32, 0, cap>>>(ts->st);
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (st != NTBC_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        return st != NTBC_OK ? st : cuda_fail(ce, "cudaStreamEndCapture");
+    }
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    for (long long t = 0; t < total && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec, cap);
+    cudaError_t se = cudaStreamSynchronize(cap);
+    cudaGraphExecDestroy(exec);
+    cudaStreamDestroy(cap);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphLaunch");
+    if (se != cudaSuccess) return cuda_fail(se, "training steps");
+    float host_losses[6];
+    NTBC_CHECK_CUDA(cudaMemcpy(host_losses, ts->losses, sizeof(host_losses), cudaMemcpyDeviceToHost));
+    if (losses_out) memcpy(losses_out, host_losses, sizeof(host_losses));
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(host_losses[i])) return fail(NTBC_ENONFINITE, "non-finite loss after training");
+    return NTBC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+"""GPU parity of NTBC inference against the FP64 oracle network on the same weights.
+
+Bars: pre-quantisation outputs within 1e-3 relative of the FP64 oracle; at most
+0.1% of endpoint or index fields differ after quantisation (a field flips only
+where FP32 and FP64 outputs straddle a rounding or argmax boundary); decoded
+PSNR within 0.05 dB; exported grid codes bit-exact (FP32 decisions on both sides).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import bc as obc, ntbc as ont
+
+nt = pytest.importorskip("paper_2407_09543_gb300")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+RTOL = 1e-3
+
+
+def make_case(side=64, kinds=("sine_rgb", "sine_r"), levels=3, lo=4, hi=16, hidden=2, act="selu", seed=0,
+              height=None):
+    mat = synth.make_material(f"inf{side}", side, list(kinds), seed)
+    h = height or side
+    acti = nt.ACT_SELU if act == "selu" else nt.ACT_RELU
+    desc = nt.configs.model_desc(mat.formats, side, levels, lo, hi, hidden, acti, height=h)
+    cres, eres = nt.configs.res_lists(desc)
+    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
+    params = synth.random_params_like(p0, seed=seed + 1)
+    odesc = ont.ModelDesc(side, h, mat.formats, cres, eres, hidden_layers=hidden, activation=act)
+    return mat, desc, odesc, params
+
+
+def gpu_model(desc, params, grid_bits=0, weight_prec=0):
+    m = nt.Model(desc)
+    m.set_params(torch.from_numpy(nt.configs.flatten(desc, params)).to(DEV))
+    m.export(grid_bits=grid_bits, weight_prec=weight_prec)
+    return m
+
+
+def gpu_forward(model, ids):
+    lay = model.layout
+    t = torch.from_numpy(np.asarray(ids, np.int32)).to(DEV)
+    e = torch.empty(len(ids), lay.out_endpoint, device=DEV)
+    c = torch.empty(len(ids), 16, lay.out_color, device=DEV)
+    model.forward(t, e, c)
+    torch.cuda.synchronize()
+    return e.cpu().numpy().astype(np.float64), c.cpu().numpy().astype(np.float64)
+
+
+def gpu_blocks(model, desc):
+    n = (desc.width // 4) * (desc.height // 4)
+    outs = [torch.empty(n * 8, dtype=torch.uint8, device=DEV) for _ in range(desc.n_textures)]
+    model.infer_to_bc(outs)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy().reshape(-1, 8) for o in outs]
+
+
+def field_mismatch(fmt, a, b):
+    """(mismatched endpoint + index fields, total fields)."""
+    if fmt == 1:
+        a0, a1, ac = obc.bc1_unpack(a)
+        b0, b1, bc_ = obc.bc1_unpack(b)
+    else:
+        a0, a1, ac = obc.bc4_unpack(a)
+        b0, b1, bc_ = obc.bc4_unpack(b)
+    mism = int((a0 != b0).sum() + (a1 != b1).sum() + (ac != bc_).sum())
+    return mism, a0.size * 18
+
+
+def oracle_params_fp16(params):
+    out = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
+    for k in ("color_mlp", "endpoint_mlp"):
+        out[k] = [(W.astype(np.float16).astype(np.float64), b.astype(np.float16).astype(np.float64)) for W, b in params[k]]
+    return out
+
+
+@pytest.mark.parametrize("act,hidden", [("selu", 2), ("relu", 2), ("selu", 3), ("selu", 1)])
+def test_forward_fp32_matches_oracle(act, hidden):
+    mat, desc, odesc, params = make_case(act=act, hidden=hidden)
+    model = gpu_model(desc, params)
+    ids = np.arange(odesc.n_blocks)
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, params, ids)
+    np.testing.assert_allclose(e, er, rtol=RTOL, atol=1e-6)
+    np.testing.assert_allclose(c, cr, rtol=RTOL, atol=1e-6)
+
+
+def check_blocks(mat, desc, odesc, got, ref):
+    total_m, total_f = 0, 0
+    for t, fmt in enumerate(mat.formats):
+        m, f = field_mismatch(fmt, got[t], ref[t])
+        total_m += m
+        total_f += f
+        dec_g = obc.decode(fmt, got[t], desc.width, desc.height)
+        dec_r = obc.decode(fmt, ref[t], desc.width, desc.height)
+        src = mat.textures[t][:desc.height]
+        assert abs(obc.psnr(dec_g, src) - obc.psnr(dec_r, src)) <= 0.05
+    assert total_m <= 0.001 * total_f, (total_m, total_f)
+
+
+@pytest.mark.parametrize("side,height", [(64, 64), (264, 132)])
+def test_infer_to_bc_fp32(side, height):
+    mat, desc, odesc, params = make_case(side=side, height=height, levels=4, lo=4, hi=32)
+    model = gpu_model(desc, params)
+    check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ont.infer_blocks(odesc, params))
+
+
+def test_export_u8_codes_bit_exact_and_inference():
+    mat, desc, odesc, params = make_case(side=128, levels=4, lo=8, hi=64, hidden=3)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    lay = model.layout
+    levels = desc.color_levels + desc.endpoint_levels
+    codes = torch.empty(lay.grid_floats, dtype=torch.uint8, device=DEV)
+    sc = torch.empty(levels, device=DEV)
+    zr = torch.empty(levels, device=DEV)
+    model.exported_grid(codes, sc, zr)
+    torch.cuda.synchronize()
+    oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 8)
+    np.testing.assert_array_equal(sc.cpu().numpy(), os_)
+    np.testing.assert_array_equal(zr.cpu().numpy(), oz)
+    np.testing.assert_array_equal(codes.cpu().numpy(), np.concatenate([c.ravel() for c in oc]))
+    deq = ont.dequantize_grid(oc, os_, oz)
+    nc = desc.color_levels
+    p16 = oracle_params_fp16(params)
+    ids = np.arange(odesc.n_blocks)
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p16, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    np.testing.assert_allclose(e, er, rtol=RTOL, atol=1e-6)
+    np.testing.assert_allclose(c, cr, rtol=RTOL, atol=1e-6)
+    ref = ont.infer_blocks(odesc, p16, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ref)
+
+
+def test_blob_roundtrip_reproduces_blocks():
+    mat, desc, odesc, params = make_case(side=64, levels=3, lo=4, hi=16)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    before = gpu_blocks(model, desc)
+    blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
+    model.save(blob)
+    other = nt.Model(desc)
+    other.load(blob)
+    after = gpu_blocks(other, desc)
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_full_size_4k_sampled():
+    # the 4096^2 four-texture workload in the launch configuration the benchmark times;
+    # the oracle evaluates a seeded sample of blocks one by one
+    w = nt.configs.WORKLOADS["mat4k"]
+    formats = [1, 1, 4, 4]
+    desc = nt.configs.desc_for(w, formats)
+    cres, eres = nt.configs.res_lists(desc)
+    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 3)
+    params = synth.random_params_like(p0, seed=4)
+    odesc = ont.ModelDesc(4096, 4096, formats, cres, eres, hidden_layers=3, activation="selu")
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 8)
+    deq = ont.dequantize_grid(oc, os_, oz)
+    nc = desc.color_levels
+    p16 = oracle_params_fp16(params)
+    ids = np.sort(np.random.default_rng(0).choice(odesc.n_blocks, 400, replace=False))
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p16, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    np.testing.assert_allclose(e, er, rtol=RTOL, atol=1e-6)
+    np.testing.assert_allclose(c, cr, rtol=RTOL, atol=1e-6)
+    got = gpu_blocks(model, desc)
+    ref = ont.infer_blocks(odesc, p16, block_ids=ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    total_m = total_f = 0
+    for t, fmt in enumerate(formats):
+        m, f = field_mismatch(fmt, got[t][ids], ref[t])
+        total_m += m
+        total_f += f
+    assert total_m <= 0.001 * total_f
