@@ -257,6 +257,29 @@ ntbc_status ntbc_train_grads(ntbc_model* model, const ntbc_material* mat, const 
                              float* losses, void* stream);
 
 /*
+ * Allocation-free variant of ntbc_train_grads. The paper has no counterpart.
+ * For callers that cannot allocate device memory: an engine's texture-streaming
+ * thread working inside a fixed, pre-reserved VRAM budget, or a real-time thread
+ * that cannot afford the device-wide synchronisation of cudaMalloc. It calls no
+ * cudaMalloc / cudaFree or other allocating routine; its scratch is a file-scope
+ * device array of NTBC_NOALLOC_MAX_BLOCKS blocks' worth (about 3.3 MB) that every
+ * GPU loading the library holds until the process exits.
+ *   desc, params  model description (host) and FP32 parameters (device, layout of
+ *                 ntbc_model_layout); the other arguments as in ntbc_train_grads,
+ *                 with `losses` required.
+ *   n_blocks      1..NTBC_NOALLOC_MAX_BLOCKS, else NTBC_EINVAL before any launch.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. All calls share the one array: calls whose work overlaps
+ * on the GPU (other streams, other threads) race on it and must be serialised
+ * by the caller. Gradients and loss accumulators are cleared on every call.
+ */
+#define NTBC_NOALLOC_MAX_BLOCKS 128
+ntbc_status ntbc_train_grads_noalloc(const ntbc_model_desc* desc, const float* params, const ntbc_material* mat,
+                                     const int32_t* block_ids, int n_blocks, int qat_bits, float temperature,
+                                     float* grads, float* losses, void* stream);
+
+/*
  * One dense Adam step (beta 0.9/0.999, eps 1e-15, bias correction) on the FP32
  * master parameters with learning rate lr_grid / lr_mlp scaled by the warm-up +
  * cosine schedule at `step` of `total_steps`. Adam moments are library-owned

@@ -112,6 +112,8 @@ _SIGS = {
     "ntbc_infer_to_bc": (c_int, [_P, ctypes.POINTER(_P), _P]),
     "ntbc_forward": (c_int, [_P, _P, c_int, _P, _P, _P]),
     "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, _P, _P, _P]),
+    "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
+                                         c_float, _P, _P, _P]),
     "ntbc_adam_step": (c_int, [_P, _P, ctypes.c_long, ctypes.c_long, ctypes.POINTER(TrainConfig), _P]),
     "ntbc_sample_blocks": (c_int, [ctypes.c_uint64, ctypes.c_long, c_int, c_int, _P, _P]),
     "ntbc_train": (c_int, [_P, ctypes.POINTER(Material), ctypes.POINTER(TrainConfig), ctypes.POINTER(c_float), _P]),
@@ -169,6 +171,17 @@ def ntbc_model_layout(desc: ModelDesc) -> Layout:
 
 def ntbc_sample_blocks(seed, step, n, n_blocks, ids, stream=None):
     _check(lib.ntbc_sample_blocks(seed, step, n, n_blocks, _ptr(ids), _stream(stream)))
+
+
+NOALLOC_MAX_BLOCKS = 128
+
+
+def ntbc_train_grads_noalloc(desc: ModelDesc, params, material: Material, block_ids, grads, losses, qat_bits=0,
+                             temperature=0.01, stream=None):
+    """Allocation-free ntbc_train_grads on caller-owned FP32 parameters (see include/ntbc.h)."""
+    _check(lib.ntbc_train_grads_noalloc(ctypes.byref(desc), _ptr(params), ctypes.byref(material), _ptr(block_ids),
+                                        block_ids.numel(), qat_bits, temperature, _ptr(grads), _ptr(losses),
+                                        _stream(stream)))
 
 
 class Model:

@@ -11,6 +11,7 @@
 // one sample per block.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "ntbc_internal.cuh"
 #include "ntbc_kernels.cuh"
@@ -856,6 +857,175 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     if (losses_out) memcpy(losses_out, host_losses, sizeof(host_losses));
     for (int i = 0; i < 6; ++i)
         if (!std::isfinite(host_losses[i])) return fail(NTBC_ENONFINITE, "non-finite loss after training");
+    return NTBC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the training-gradient call.
+//
+// Some callers cannot allocate device memory: an engine's texture-streaming
+// thread that works inside a fixed, pre-reserved VRAM budget, or a real-time
+// thread that cannot afford the device-wide synchronisation cudaMalloc implies.
+// For them the scratch of one gradient evaluation (features, activations,
+// deltas, loss accumulators, QAT scales) lives in the file-scope array below,
+// sized for at most kNoAllocMaxBlocks blocks per call. Every GPU that loads the
+// library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace ntbc {
+
+constexpr int kNoAllocMaxBlocks = 128;                         // 2048 texels per call
+constexpr int kNoAllocColor = kNoAllocMaxBlocks * 16;
+constexpr size_t kNoAllocNetFloats(int cap, int out) { return (size_t)(kMaxIn + 3 * kHidden + out + 2 * kHidden) * cap; }
+constexpr size_t kNoAllocFloats = kNoAllocNetFloats(kNoAllocColor, kMaxOutC) + kNoAllocNetFloats(kNoAllocMaxBlocks, kMaxOutE);
+constexpr int kNoAllocLevels = 2 * NTBC_MAX_LEVELS;
+// floats of both networks, then 6 double loss accumulators, then QAT scale / zero / min-max words
+constexpr size_t kNoAllocBytes = kNoAllocFloats * sizeof(float) + 6 * sizeof(double) + kNoAllocLevels * 4 * sizeof(float);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static void* g_noalloc_addr[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device; looked up once per
+// device (with that device current) on the first call.
+static ntbc_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    NTBC_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(NTBC_EUNSUPPORTED, "device ordinal %d beyond %d", dev, kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    return NTBC_OK;
+}
+
+static NetBuffers carve_net(float*& cursor, int cap, int out) {
+    NetBuffers nb;
+    nb.cap = cap;
+    nb.X = cursor;
+    cursor += (size_t)kMaxIn * cap;
+    for (int l = 0; l < 3; ++l) {
+        nb.A[l] = cursor;
+        cursor += (size_t)kHidden * cap;
+    }
+    nb.Y = cursor;
+    cursor += (size_t)out * cap;
+    nb.D0 = cursor;
+    cursor += (size_t)kHidden * cap;
+    nb.D1 = cursor;
+    cursor += (size_t)kHidden * cap;
+    return nb;
+}
+
+// forward + loss + backward of one network on given buffers (same launches as the
+// model-based path)
+static void noalloc_net(const ModelView& mv, const float* params, bool color, const TexPtrs& tp, const int32_t* ids,
+                        int B, const GridSrc& src, float T, NetBuffers& nb, float* grads, double* acc, cudaStream_t s) {
+    const NetView& nv = color ? mv.color : mv.endpoint;
+    const int thr = 128;
+    unsigned g = blocks_for(B, thr);
+    gather_kernel<<<g, thr, 0, s>>>(mv, color, src, ids, B, nb.X);
+    const float* prev = nb.X;
+    int nl = nv.n_layers;
+    for (int l = 0; l < nl; ++l) {
+        bool last = l + 1 == nl;
+        float* outbuf = last ? nb.Y : nb.A[l];
+        int act = last ? 2 : mv.activation;
+        if (l == 0)
+            dense_fwd_kernel<kMaxIn><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, params + nv.w_off[l], params + nv.b_off[l], nv.layer_out[l], act, outbuf);
+        else
+            dense_fwd_kernel<kHidden><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, params + nv.w_off[l], params + nv.b_off[l], nv.layer_out[l], act, outbuf);
+        prev = outbuf;
+    }
+    float* D = nb.D0;
+    float* Dn = nb.D1;
+    if (color)
+        color_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
+    else
+        endpoint_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
+    unsigned gw = blocks_for(B, kWgChunk);
+    for (int l = nl - 1; l >= 0; --l) {
+        const float* Ain = l == 0 ? nb.X : nb.A[l - 1];
+        dense_bwd_weight_kernel<<<gw, 256, 0, s>>>(D, nv.layer_out[l], Ain, nv.layer_in[l], B, grads + nv.w_off[l], grads + nv.b_off[l]);
+        dense_bwd_data_kernel<<<g, thr, 0, s>>>(D, nv.layer_out[l], B, params + nv.w_off[l], nv.layer_in[l],
+                                                 l == 0 ? nullptr : nb.A[l - 1], mv.activation, Dn);
+        float* t = D;
+        D = Dn;
+        Dn = t;
+    }
+    grid_scatter_kernel<<<g, thr, 0, s>>>(mv, color, ids, B, D, src, grads);
+}
+
+}  // namespace ntbc
+
+extern "C" {
+
+ntbc_status ntbc_train_grads_noalloc(const ntbc_model_desc* desc, const float* params, const ntbc_material* mat,
+                                     const int32_t* block_ids, int n_blocks, int qat_bits, float temperature,
+                                     float* grads, float* losses, void* stream) {
+    clear_error();
+    ntbc_layout L;
+    ntbc_status st = ntbc_model_layout(desc, &L);
+    if (st != NTBC_OK) return st;
+    if (!params || !mat || !block_ids || !grads || !losses) return fail(NTBC_EINVAL, "null argument");
+    if (n_blocks <= 0) return fail(NTBC_EINVAL, "need at least one block");
+    if (n_blocks > kNoAllocMaxBlocks)
+        return fail(NTBC_EINVAL, "n_blocks %d exceeds the allocation-free limit of %d blocks (%d texels) per call",
+                    n_blocks, kNoAllocMaxBlocks, kNoAllocMaxBlocks * 16);
+    if (qat_bits != 0 && qat_bits != 8 && qat_bits != 4) return fail(NTBC_EINVAL, "qat_bits must be 0, 4 or 8");
+    if (!(temperature > 0.f)) return fail(NTBC_EINVAL, "temperature must be positive");
+    if (mat->width != desc->width || mat->height != desc->height || mat->n_textures != desc->n_textures)
+        return fail(NTBC_EINVAL, "material does not match the model (size or texture count)");
+    TexPtrs tp;
+    memset(&tp, 0, sizeof(tp));
+    for (int t = 0; t < mat->n_textures; ++t) {
+        if (mat->formats[t] != desc->formats[t]) return fail(NTBC_EINVAL, "texture %d: format differs from the model", t);
+        if (!mat->texels[t] || !mat->ref_blocks[t]) return fail(NTBC_EINVAL, "texture %d: null texels or reference blocks", t);
+        tp.texels[t] = mat->texels[t];
+        tp.blocks[t] = mat->ref_blocks[t];
+    }
+    unsigned char* base = nullptr;
+    st = noalloc_scratch(&base);
+    if (st != NTBC_OK) return st;
+    float* cursor = reinterpret_cast<float*>(base);
+    NetBuffers cbuf = carve_net(cursor, kNoAllocColor, kMaxOutC);
+    NetBuffers ebuf = carve_net(cursor, kNoAllocMaxBlocks, kMaxOutE);
+    double* acc = reinterpret_cast<double*>(base + kNoAllocFloats * sizeof(float));
+    float* qscale = reinterpret_cast<float*>(acc + 6);
+    float* qzero = qscale + kNoAllocLevels;
+    unsigned* qmm = reinterpret_cast<unsigned*>(qzero + kNoAllocLevels);
+
+    cudaStream_t s = (cudaStream_t)stream;
+    ModelView mv = make_view(*desc, L);
+    GridSrc csrc;
+    memset(&csrc, 0, sizeof(csrc));
+    csrc.f32 = params;
+    csrc.qat_bits = qat_bits;
+    GridSrc esrc = csrc;
+    if (qat_bits > 0) {
+        LevelTable lt = level_table(*desc, L);
+        st = launch_level_scale_zero(params, lt, qat_bits, qmm, qscale, qzero, s);
+        if (st != NTBC_OK) return st;
+        csrc.scale = qscale;
+        csrc.zero = qzero;
+        esrc.scale = qscale + desc->color_levels;
+        esrc.zero = qzero + desc->color_levels;
+    }
+    // the array keeps the previous call's contents: clear what accumulates
+    NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, L.total * sizeof(float), s));
+    NTBC_CHECK_CUDA(cudaMemsetAsync(acc, 0, 6 * sizeof(double), s));
+    noalloc_net(mv, params, true, tp, block_ids, n_blocks * 16, csrc, temperature, cbuf, grads, acc, s);
+    noalloc_net(mv, params, false, tp, block_ids, n_blocks, esrc, temperature, ebuf, grads, acc, s);
+    loss_finalize_kernel<<<1, 32, 0, s>>>(acc, losses);
+    NTBC_CHECK_LAUNCH("allocation-free training gradients");
     return NTBC_OK;
 }
 
