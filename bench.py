@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16")
+    ap.add_argument("--quick", action="store_true",
+                    help="inference only on random-init weights (no material, training, plain path or oracle)")
     return ap.parse_args()
 
 
@@ -219,6 +222,34 @@ def run_reference(args):
     return 0
 
 
+def run_quick(args):
+    """Inference-only timing on random-init 4k weights (for profiling captures)."""
+    import torch
+    import paper_2407_09543_gb300 as nt
+    dev = torch.device("cuda", 0)
+    side = args.side
+    nblk = (side // 4) ** 2
+    w = nt.configs.WORKLOADS["mat4k"]
+    desc = nt.configs.desc_for(w, FORMATS, side=side)
+    cres, eres = nt.configs.res_lists(desc)
+    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
+    params = synth.random_params_like(p0, seed=1)
+    model = nt.Model(desc)
+    model.set_params(torch.from_numpy(nt.configs.flatten(desc, params)).to(dev))
+    model.export(grid_bits=8, weight_prec=args.prec)
+    outs = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in FORMATS]
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        model.infer_to_bc(outs)
+    torch.cuda.synchronize()
+    times = time_events(torch, lambda: model.infer_to_bc(outs), args.steps, flush=lambda: flush_buf.fill_(1))
+    ms = float(np.mean(times))
+    print(json.dumps({"mode": "quick", "prec": args.prec, "workload": f"mat4k {side}x{side} random-init", "ms_per_step": round(ms, 4),
+                      "value": round(nblk * len(FORMATS) / (ms * 1e-3) / 1e6, 3), "unit": "Mblocks/s",
+                      "times_ms": [round(t, 4) for t in times]}), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
@@ -227,6 +258,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.quick:
+        return run_quick(args)
     import torch
     import paper_2407_09543_gb300 as nt
     from oracle import bc as obc

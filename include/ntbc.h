@@ -42,7 +42,16 @@ typedef enum {
 
 enum { NTBC_BC1 = 1, NTBC_BC4 = 4 };
 enum { NTBC_ACT_SELU = 0, NTBC_ACT_RELU = 1 };
-enum { NTBC_PREC_FP32 = 0, NTBC_PREC_FP16 = 1 };
+/*
+ * Inference precision (the stored MLP weights are FP16 for the two FP16 modes):
+ *   NTBC_PREC_FP32       FP32 weights and arithmetic (SIMT kernel)
+ *   NTBC_PREC_FP16       FP16 weights on tensor cores (tcgen05, FP32 accumulation); each
+ *                        activation enters the MMA as an FP16 pair hi + lo (two passes), so
+ *                        the outputs stay within 1e-3 relative of an FP64 evaluation
+ *   NTBC_PREC_FP16_FAST  FP16 weights and FP16 activations (one pass), the paper's half-
+ *                        precision inference (Sec. 3.3); outputs within about 4e-3 relative
+ */
+enum { NTBC_PREC_FP32 = 0, NTBC_PREC_FP16 = 1, NTBC_PREC_FP16_FAST = 2 };
 
 #define NTBC_MAX_TEXTURES 8
 #define NTBC_MAX_LEVELS 16
@@ -171,8 +180,9 @@ ntbc_status ntbc_model_get_params(const ntbc_model* model, float* dst, size_t co
  * quantised as in QAT (range [min(0,min), max(0,max)], s = range/(2^b-1),
  * z = round(-alpha/s), q = clamp(round(r/s)+z), FP32 decisions) and stored as one
  * code per byte plus (s, z) per level; grid_bits 0 keeps FP32 grids.
- * weight_prec NTBC_PREC_FP16 rounds MLP weights and biases to half precision
- * (round to nearest even); NTBC_PREC_FP32 keeps them.
+ * weight_prec NTBC_PREC_FP16 / NTBC_PREC_FP16_FAST rounds MLP weights and biases to
+ * half precision (round to nearest even) and prepares the tensor-core weight image;
+ * NTBC_PREC_FP32 keeps them.
  */
 ntbc_status ntbc_model_export(ntbc_model* model, int grid_bits, int weight_prec, void* stream);
 

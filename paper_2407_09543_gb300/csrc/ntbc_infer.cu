@@ -286,6 +286,12 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, vo
         outs.p[t] = blocks_out[t];
     }
     int n = (m->desc.width / 4) * (m->desc.height / 4);
+    if (m->weight_prec != NTBC_PREC_FP32) {
+        GridSrc csrc, esrc;
+        ntbc_status st = grid_sources(m, csrc, esrc);
+        if (st != NTBC_OK) return st;
+        return tc_launch(m, blocks_out, nullptr, n, nullptr, nullptr, csrc, esrc, (cudaStream_t)stream);
+    }
     return launch_simt<MODE_PACK>(m, outs, nullptr, n, nullptr, nullptr, (cudaStream_t)stream);
 }
 
@@ -294,6 +300,12 @@ ntbc_status ntbc_forward(const ntbc_model* m, const int32_t* block_ids, int n, f
     if (!m || !block_ids || !e_hat || !c_hat) return fail(NTBC_EINVAL, "null argument");
     if (n < 0) return fail(NTBC_EINVAL, "negative count");
     if (n == 0) return NTBC_OK;
+    if (m->weight_prec != NTBC_PREC_FP32) {
+        GridSrc csrc, esrc;
+        ntbc_status st = grid_sources(m, csrc, esrc);
+        if (st != NTBC_OK) return st;
+        return tc_launch(m, nullptr, block_ids, n, e_hat, c_hat, csrc, esrc, (cudaStream_t)stream);
+    }
     OutPtrs outs;
     memset(&outs, 0, sizeof(outs));
     return launch_simt<MODE_RAW>(m, outs, block_ids, n, e_hat, c_hat, (cudaStream_t)stream);

@@ -1,0 +1,618 @@
+// Tensor-core (tcgen05) form of the fused NTBC inference kernel (Sec. 3.2,
+// Fig. NTBC (a); Sec. 5.4) for FP16 weights, FP32 accumulation in TMEM.
+//
+// One persistent CTA per SM holds up to three independent warpgroups. A
+// warpgroup owns one work unit at a time: 128 consecutive blocks. It runs the
+// endpoint MLP on the 128 blocks as one M = 128 MMA chain, turns the sigmoid
+// outputs into quantised endpoints and FP32 palettes (kept in shared memory),
+// then runs the colour MLP on the unit's 2048 texels as 16 tiles of 128 texels
+// (8 blocks each), picks each texel's code and packs the 16 codes of a block
+// with shuffles inside the half-warp that holds the block.
+//
+// Per layer: the warpgroup writes its A tile (activations, FP16, canonical
+// K-major core-matrix layout, no swizzle) to shared memory, one elected thread
+// issues the K/16 MMAs (the bias rides in one extra K column: a constant 1 in A,
+// the bias in B) and commits to the group's mbarrier; after the bounded wait the
+// 128 threads read their row of the accumulator (tcgen05.ld 32x32b) and apply
+// SELU (or the sigmoid on the output layer). The other warpgroups of the CTA
+// keep the SM busy while one waits on its MMA.
+#include "ntbc_internal.cuh"
+#include "ntbc_kernels.cuh"
+
+namespace ntbc {
+
+constexpr int kTcRows = 128;               // M of every MMA: blocks (endpoint) or texels (colour)
+constexpr int kTcUnitBlocks = 128;
+constexpr int kTcTiles = kTcUnitBlocks * 16 / kTcRows;   // 16 colour tiles per unit
+constexpr int kTcMaxGroups = 4;
+constexpr int kTcColsPerGroup = 64;
+constexpr int kTcPalBytes = 12;            // integer palette bytes per block per texture
+constexpr long long kTcWaitLimit = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// UMMA shared-memory descriptor: K-major, no swizzle. k_stride: bytes between
+// core matrices adjacent along K; mn_stride: bytes between core matrices adjacent
+// along M (or N).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t k_stride, uint32_t mn_stride) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((k_stride >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((mn_stride >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor, kind::f16: A = B = F16, D = F32, both K-major
+__host__ __device__ constexpr uint32_t umma_idesc(int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t done = 0;
+    for (long long it = 0; it < kTcWaitLimit; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(phase));
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kTcRows) : "memory"); }
+
+// byte offset of element (r, k) in a tile of K columns (16-bit elements)
+__host__ __device__ __forceinline__ int core_byte(int r, int k, int K) {
+    return (((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)) * 2;
+}
+
+// store 8 FP16 values (k-group kg) of row r
+__device__ __forceinline__ void st_row8(unsigned char* tile, int r, int kg, int K, const float* v) {
+    __half2 h0 = __floats2half2_rn(v[0], v[1]), h1 = __floats2half2_rn(v[2], v[3]);
+    __half2 h2 = __floats2half2_rn(v[4], v[5]), h3 = __floats2half2_rn(v[6], v[7]);
+    uint4 u;
+    u.x = *reinterpret_cast<uint32_t*>(&h0);
+    u.y = *reinterpret_cast<uint32_t*>(&h1);
+    u.z = *reinterpret_cast<uint32_t*>(&h2);
+    u.w = *reinterpret_cast<uint32_t*>(&h3);
+    *reinterpret_cast<uint4*>(tile + (((r >> 3) * (K >> 3) + kg) * 128 + (r & 7) * 16)) = u;
+}
+
+// store 8 values as FP16 hi (and, when split, the FP16 rounding of the residual in lo)
+template <bool SPLIT>
+__device__ __forceinline__ void st_row8_split(unsigned char* hi_tile, unsigned char* lo_tile, int r, int kg, int K,
+                                              const float* v) {
+    if (!SPLIT) {
+        st_row8(hi_tile, r, kg, K, v);
+        return;
+    }
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        __half2 h = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+        float2 f = __half22float2(h);
+        __half2 lo = __floats2half2_rn(v[2 * j] - f.x, v[2 * j + 1] - f.y);
+        hw[j] = *reinterpret_cast<uint32_t*>(&h);
+        lw[j] = *reinterpret_cast<uint32_t*>(&lo);
+    }
+    int off = ((r >> 3) * (K >> 3) + kg) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+__device__ __forceinline__ float selu_fast(float z) {
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fminf(z, 0.f) * 1.4426950408889634f));
+    return fmaf(kSeluLA, e, fmaf(kSeluLambda, fmaxf(z, 0.f), -kSeluLA));
+}
+
+__device__ __forceinline__ float sigmoid_fast(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+
+struct TcLayer {
+    int K;           // total K of the MMA (multiple of 16, bias column included)
+    int N;           // padded output width (multiple of 16)
+    int out;         // real output width
+    int img;         // byte offset of the B tile in the weight image
+};
+
+struct TcNet {
+    int n_layers;
+    TcLayer layer[NTBC_MAX_MLP_LAYERS];
+};
+
+struct TcArgs {
+    ModelView mv;
+    TcNet net[2];             // 0 colour, 1 endpoint
+    int img_bytes;            // weight image size (multiple of 16)
+    int groups;
+    int n;                    // blocks to process
+    const int32_t* ids;       // optional block ids (else 0..n-1)
+    int mode;                 // 0 pack, 1 raw outputs
+    int* err;
+};
+
+struct TcOut {
+    uint8_t* p[NTBC_MAX_TEXTURES];
+};
+
+struct TcSmem {
+    int ones_off, table_off, lvl_off, group_off, group_bytes, a_off, lo_off, pal_off, ep_off, bar_off;
+};
+
+// Shared: weight image, ones tile (bias K block), k/255 table, per-level dequantisation
+// constants. Per group: A tile (FP16 activations), the low-half tile when split, the
+// unit's integer palettes (12 bytes per block and texture) and quantised endpoints,
+// and the group's mbarrier.
+__host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int split) {
+    TcSmem s;
+    s.ones_off = (img_bytes + 127) & ~127;
+    s.table_off = s.ones_off + kTcRows * 16 * 2;
+    s.lvl_off = s.table_off + 256 * 4;
+    s.group_off = (s.lvl_off + 2 * 2 * NTBC_MAX_LEVELS * 4 + 1023) & ~1023;
+    s.a_off = 0;
+    s.lo_off = kTcRows * 64 * 2;
+    s.pal_off = s.lo_off + (split ? kTcRows * 64 * 2 : 0);
+    s.ep_off = s.pal_off + ((n_tex * kTcUnitBlocks * kTcPalBytes + 15) & ~15);
+    s.bar_off = s.ep_off + n_tex * kTcUnitBlocks * 4;
+    s.group_bytes = (s.bar_off + 16 + 1023) & ~1023;
+    return s;
+}
+
+// One layer: MMAs from the group's A tile (K0 columns for layer 0, 64 afterwards;
+// when split, each K block twice: high and low halves of the activations) plus the
+// bias K block from the ones tile. The abort decision is uniform across the group:
+// a thread whose bounded wait gave up raises the group's flag, and every thread reads
+// the flag right after the next group barrier.
+template <bool SPLIT>
+__device__ __forceinline__ bool run_layer(const TcLayer& L, int l, unsigned char* smem, unsigned char* A, const TcSmem& sl,
+                                          uint32_t tmem, uint64_t* bar, uint32_t& phase, int g, int r,
+                                          volatile int* abort_flag) {
+    proxy_fence();
+    tc_fence_before();
+    group_sync(g);
+    if (abort_flag[g]) return false;
+    if (r == 0) {
+        tc_fence_after();
+        uint32_t idesc = umma_idesc(L.N);
+        uint32_t a_base = smem_u32(A), b_base = smem_u32(smem + L.img);
+        int Ka = l == 0 ? L.K : 64;                 // columns of the A tile
+        int nk_a = Ka / 16;
+        for (int kc = 0; kc < nk_a; ++kc) {
+            uint64_t ad = umma_desc(a_base + kc * 256, 128, (Ka / 8) * 128);
+            uint64_t bd = umma_desc(b_base + kc * 256, 128, (L.K / 8) * 128);
+            umma_f16(tmem, ad, bd, idesc, kc > 0);
+            if (SPLIT) {
+                uint64_t lo = umma_desc(a_base + (sl.lo_off - sl.a_off) + kc * 256, 128, (Ka / 8) * 128);
+                umma_f16(tmem, lo, bd, idesc, 1);
+            }
+        }
+        if (l > 0) {
+            uint64_t ad = umma_desc(smem_u32(smem + sl.ones_off), 128, 256);
+            uint64_t bd = umma_desc(b_base + nk_a * 256, 128, (L.K / 8) * 128);
+            umma_f16(tmem, ad, bd, idesc, 1);
+        }
+        umma_commit(bar);
+    }
+    if (!mbar_wait(bar, phase)) abort_flag[g] = 1;
+    phase ^= 1;
+    tc_fence_after();
+    return true;
+}
+
+// hidden-layer epilogue: accumulator row -> SELU / ReLU -> FP16 A tile (64 columns)
+template <bool SPLIT>
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, unsigned char* A, unsigned char* Alo, int r, int act) {
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem_row + c0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = act == NTBC_ACT_SELU ? selu_fast(v[j]) : fmaxf(v[j], 0.f);
+        st_row8_split<SPLIT>(A, Alo, r, c0 / 8, 64, v);
+        st_row8_split<SPLIT>(A, Alo, r, c0 / 8 + 1, 64, v + 8);
+    }
+}
+
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t v;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+    return __uint_as_float(v);
+}
+
+// a byte b as the float 1 + b * 2^-15 (byte placed in mantissa bits 8..15): exact,
+// and no integer-to-float conversion
+__device__ __forceinline__ float byte_as_unit(uint32_t word, uint32_t sel) {
+    return __uint_as_float(__byte_perm(word, 0x3F800000u, sel));
+}
+
+__device__ __forceinline__ uint32_t ld_u16(const uint8_t* p) {
+    return (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p));
+}
+
+// Grid features of one row (texel or block), level-major, 2 per level, followed by the
+// constant 1 of the layer-0 bias column; stored as FP16 chunks (high, and low halves when
+// split). Exported grids: bilinear interpolation of the codes (as 1 + q 2^-15) then the
+// dequantisation s (q - z) folded into one FMA with the per-level constants in lvl.
+template <bool SPLIT>
+__device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src, const float2* lvl, float u, float v,
+                                           int K0, unsigned char* A, unsigned char* Alo, int r, bool valid) {
+    float f[2 * NTBC_MAX_LEVELS];
+#pragma unroll
+    for (int l = 0; l < NTBC_MAX_LEVELS; ++l) {
+        float f0 = 0.f, f1 = 0.f;
+        if (l < nv.levels && valid) {
+            Bilinear b = bilinear_at(nv.res[l], u, v);
+            long long o = nv.grid_off[l] + b.base;
+            if (src.codes) {
+                const uint8_t* gp = src.codes + o;
+                uint32_t a = ld_u16(gp), c = ld_u16(gp + 2), d = ld_u16(gp + b.row), e = ld_u16(gp + b.row + 2);
+                float y0 = b.w00 * byte_as_unit(a, 0x7604) + b.w01 * byte_as_unit(c, 0x7604) +
+                           b.w10 * byte_as_unit(d, 0x7604) + b.w11 * byte_as_unit(e, 0x7604);
+                float y1 = b.w00 * byte_as_unit(a, 0x7614) + b.w01 * byte_as_unit(c, 0x7614) +
+                           b.w10 * byte_as_unit(d, 0x7614) + b.w11 * byte_as_unit(e, 0x7614);
+                float2 k = lvl[l];
+                f0 = fmaf(k.x, y0, k.y);
+                f1 = fmaf(k.x, y1, k.y);
+            } else {
+                const float* gp = src.f32 + o;
+                float2 a = __ldg(reinterpret_cast<const float2*>(gp));
+                float2 c = __ldg(reinterpret_cast<const float2*>(gp + 2));
+                float2 d = __ldg(reinterpret_cast<const float2*>(gp + b.row));
+                float2 e = __ldg(reinterpret_cast<const float2*>(gp + b.row + 2));
+                f0 = b.w00 * a.x + b.w01 * c.x + b.w10 * d.x + b.w11 * e.x;
+                f1 = b.w00 * a.y + b.w01 * c.y + b.w10 * d.y + b.w11 * e.y;
+            }
+        }
+        f[2 * l] = f0;
+        f[2 * l + 1] = f1;
+    }
+#pragma unroll
+    for (int kg = 0; kg < 6; ++kg) {
+        if (kg * 8 >= K0) break;
+        float v8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            int i = kg * 8 + j;
+            float x = i < 2 * NTBC_MAX_LEVELS ? f[i] : 0.f;
+            v8[j] = i == nv.in_dim ? 1.f : x;
+        }
+        st_row8_split<SPLIT>(A, Alo, r, kg, K0, v8);
+    }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
+infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSrc esrc, TcOut outs,
+                float* __restrict__ e_out, float* __restrict__ c_out) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag[kTcMaxGroups];
+    const ModelView& mv = args.mv;
+    const int tid = threadIdx.x;
+    const int g = tid / kTcRows, r = tid % kTcRows;
+    const TcSmem sl = tc_smem_layout(args.img_bytes, mv.n_textures, SPLIT);
+    unsigned char* gbase = smem + sl.group_off + g * sl.group_bytes;
+    unsigned char* A = gbase + sl.a_off;
+    unsigned char* Alo = gbase + sl.lo_off;
+    uint8_t* palb = gbase + sl.pal_off;
+    uint32_t* eps = reinterpret_cast<uint32_t*>(gbase + sl.ep_off);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(gbase + sl.bar_off);
+    const float* tab = reinterpret_cast<const float*>(smem + sl.table_off);
+    float2* lvl = reinterpret_cast<float2*>(smem + sl.lvl_off);           // [net][level]: (32768 s, -s (32768 + z))
+
+    // ---- set-up: weight image, ones tile, k/255 table, level constants, TMEM, barriers
+    for (int i = tid; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
+    for (int i = tid; i < kTcRows * 16; i += blockDim.x) {
+        int rr = i / 16, k = i % 16;
+        *reinterpret_cast<__half*>(smem + sl.ones_off + core_byte(rr, k, 16)) = __float2half(k == 0 ? 1.f : 0.f);
+    }
+    for (int i = tid; i < 256; i += blockDim.x) reinterpret_cast<float*>(smem + sl.table_off)[i] = __fdiv_rn((float)i, 255.f);
+    for (int i = tid; i < 2 * NTBC_MAX_LEVELS; i += blockDim.x) {
+        int net = i / NTBC_MAX_LEVELS, l = i % NTBC_MAX_LEVELS;
+        const GridSrc& src = net ? esrc : csrc;
+        int L = net ? mv.endpoint.levels : mv.color.levels;
+        float2 k = make_float2(0.f, 0.f);
+        if (src.codes && l < L) {
+            float sc = src.scale[l], z = src.zero[l];
+            k = make_float2(sc * 32768.f, -sc * (32768.f + z));
+        }
+        lvl[i] = k;
+    }
+    if (r == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        abort_flag[g] = 0;
+    }
+    const int ncols = args.groups == 1 ? 64 : (args.groups == 2 ? 128 : 256);
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot + (uint32_t)(g * kTcColsPerGroup);
+    const uint32_t tmem_row = tmem + ((uint32_t)((r / 32) * 32) << 16);   // this warp's 32 lanes
+    uint32_t phase = 0;
+    const int n_units = (args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
+    const int T = mv.n_textures;
+    bool ok = true;
+
+    for (int unit = blockIdx.x * args.groups + g; unit < n_units && ok; unit += gridDim.x * args.groups) {
+        // ================= endpoint network: row r = block r of the unit
+        {
+            const TcNet& net = args.net[1];
+            int k = unit * kTcUnitBlocks + r;
+            bool valid = k < args.n;
+            int b = valid ? (args.ids ? args.ids[k] : k) : 0;
+            int bx = b % mv.bw, by = b / mv.bw;
+            gather_row<SPLIT>(mv.endpoint, esrc, lvl + NTBC_MAX_LEVELS, ((float)bx + 0.5f) / (float)mv.bw,
+                              ((float)by + 0.5f) / (float)mv.bh, net.layer[0].K, A, Alo, r, valid);
+            for (int l = 0; l < net.n_layers && ok; ++l) {
+                ok = run_layer<SPLIT>(net.layer[l], l, smem, A, sl, tmem, bar, phase, g, r, abort_flag);
+                if (!ok) break;
+                if (l + 1 < net.n_layers) {
+                    hidden_epilogue<SPLIT>(tmem_row, A, Alo, r, mv.activation);
+                    continue;
+                }
+                if (args.mode == 1) {
+                    int out = net.layer[l].out;
+                    for (int o = 0; o < out; ++o) {
+                        float e = sigmoid_fast(tmem_ld1(tmem_row + o));
+                        tmem_wait_ld();
+                        if (valid) e_out[(long long)k * out + o] = e;
+                    }
+                    continue;
+                }
+                for (int t = 0; t < T; ++t) {
+                    int eo = mv.eoff[t];
+                    uint8_t* pb = palb + (t * kTcUnitBlocks + r) * kTcPalBytes;
+                    float e[6];
+                    if (mv.formats[t] == NTBC_BC1) {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) e[q] = tmem_ld1(tmem_row + eo + q);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) e[q] = sigmoid_fast(e[q]);
+                        uint32_t c0 = (quant_channel(e[0], 31.f, 31) << 11) | (quant_channel(e[1], 63.f, 63) << 5) |
+                                      quant_channel(e[2], 31.f, 31);
+                        uint32_t c1 = (quant_channel(e[3], 31.f, 31) << 11) | (quant_channel(e[4], 63.f, 63) << 5) |
+                                      quant_channel(e[5], 31.f, 31);
+                        if (c0 < c1) {
+                            uint32_t tt = c0;
+                            c0 = c1;
+                            c1 = tt;
+                        }
+                        int p[4][3];
+                        bc1_palette(c0, c1, p);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int ch = 0; ch < 3; ++ch) pb[q * 3 + ch] = (uint8_t)p[q][ch];
+                        eps[t * kTcUnitBlocks + r] = c0 | (c1 << 16);
+                    } else {
+                        e[0] = tmem_ld1(tmem_row + eo);
+                        e[1] = tmem_ld1(tmem_row + eo + 1);
+                        tmem_wait_ld();
+                        int r0 = quant_channel(sigmoid_fast(e[0]), 255.f, 255);
+                        int r1 = quant_channel(sigmoid_fast(e[1]), 255.f, 255);
+                        int p[8];
+                        bc4_palette(r0, r1, p);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) pb[q] = (uint8_t)p[q];
+                        eps[t * kTcUnitBlocks + r] = (uint32_t)r0 | ((uint32_t)r1 << 8);
+                    }
+                }
+            }
+        }
+        // ================= colour network: 16 tiles of 8 blocks x 16 texels
+        for (int tile = 0; tile < kTcTiles && ok; ++tile) {
+            const TcNet& net = args.net[0];
+            int blk = tile * 8 + r / 16, i = r & 15;
+            int k = unit * kTcUnitBlocks + blk;
+            bool valid = k < args.n;
+            int b = valid ? (args.ids ? args.ids[k] : k) : 0;
+            int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
+            gather_row<SPLIT>(mv.color, csrc, lvl, ((float)x + 0.5f) / (float)mv.width,
+                              ((float)y + 0.5f) / (float)mv.height, net.layer[0].K, A, Alo, r, valid);
+            for (int l = 0; l < net.n_layers && ok; ++l) {
+                ok = run_layer<SPLIT>(net.layer[l], l, smem, A, sl, tmem, bar, phase, g, r, abort_flag);
+                if (!ok) break;
+                if (l + 1 < net.n_layers) {
+                    hidden_epilogue<SPLIT>(tmem_row, A, Alo, r, mv.activation);
+                    continue;
+                }
+                if (args.mode == 1) {
+                    int out = net.layer[l].out;
+                    for (int o = 0; o < out; ++o) {
+                        float c = sigmoid_fast(tmem_ld1(tmem_row + o));
+                        tmem_wait_ld();
+                        if (valid) c_out[((long long)k * 16 + i) * out + o] = c;
+                    }
+                    continue;
+                }
+                for (int t = 0; t < T; ++t) {
+                    const uint8_t* pb = palb + (t * kTcUnitBlocks + blk) * kTcPalBytes;
+                    uint32_t ep = eps[t * kTcUnitBlocks + blk];
+                    int co = mv.coff[t];
+                    BlockPalette bp;
+                    uint64_t bits;
+                    if (mv.formats[t] == NTBC_BC1) {
+                        float cr = tmem_ld1(tmem_row + co), cg = tmem_ld1(tmem_row + co + 1), cb = tmem_ld1(tmem_row + co + 2);
+                        tmem_wait_ld();
+                        bp.solid = (ep & 0xFFFFu) == (ep >> 16);
+                        uint32_t w0 = *reinterpret_cast<const uint32_t*>(pb);
+                        uint32_t w1 = *reinterpret_cast<const uint32_t*>(pb + 4);
+                        uint32_t w2 = *reinterpret_cast<const uint32_t*>(pb + 8);
+                        uint32_t wv[3] = {w0, w1, w2};
+#pragma unroll
+                        for (int q = 0; q < 12; ++q) bp.pal[q / 3][q % 3] = tab[(wv[q / 4] >> (8 * (q % 4))) & 255];
+                        bits = (uint64_t)choose_code_bc1(bp, sigmoid_fast(cr), sigmoid_fast(cg), sigmoid_fast(cb)) << (2 * i);
+                    } else {
+                        float cv = tmem_ld1(tmem_row + co);
+                        tmem_wait_ld();
+                        uint32_t w0 = *reinterpret_cast<const uint32_t*>(pb);
+                        uint32_t w1 = *reinterpret_cast<const uint32_t*>(pb + 4);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) bp.pal[q][0] = tab[((q < 4 ? w0 : w1) >> (8 * (q % 4))) & 255];
+                        bits = (uint64_t)choose_code_bc4(bp, sigmoid_fast(cv)) << (3 * i);
+                    }
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+                    if (i == 0 && valid) {
+                        uint8_t* dst = outs.p[t] + (long long)b * 8;
+                        if (mv.formats[t] == NTBC_BC1)
+                            store_block(dst, ep, (uint32_t)bits);
+                        else
+                            store_block(dst, ep | (uint32_t)((bits & 0xFFFF) << 16), (uint32_t)(bits >> 16));
+                    }
+                }
+            }
+        }
+    }
+    // a group whose wait gave up records it and lets the MMA still in flight land
+    // (bounded wait on the phase that gave up) before TMEM is freed
+    if (!ok) {
+        if (r == 0) atomicExch(args.err, 1);
+        mbar_wait(bar, phase ^ 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(ncols));
+}
+
+// ---------------------------------------------------------------------------
+// weight image: every layer's B tile [N][K] (FP16, core-matrix layout) with the
+// bias in column `in` (layer 0) or column 64 (the extra K block of later layers)
+// ---------------------------------------------------------------------------
+
+__global__ void build_image_kernel(const float* __restrict__ params, TcArgs args, ModelView mv, __half* __restrict__ img) {
+    int total = args.img_bytes / 2;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) img[e] = __float2half(0.f);
+    __syncthreads();
+    // one pass per (net, layer): element (n, k)
+    for (int net = 0; net < 2; ++net) {
+        const NetView& nv = net ? mv.endpoint : mv.color;
+        const TcNet& tn = args.net[net];
+        for (int l = 0; l < tn.n_layers; ++l) {
+            const TcLayer& L = tn.layer[l];
+            int in = nv.layer_in[l], out = nv.layer_out[l];
+            int bias_col = l == 0 ? in : 64;
+            for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L.N * L.K; e += gridDim.x * blockDim.x) {
+                int n = e / L.K, k = e % L.K;
+                float v = 0.f;
+                if (n < out && k < in) v = params[nv.w_off[l] + (long long)n * in + k];
+                else if (n < out && k == bias_col) v = params[nv.b_off[l] + n];
+                img[(L.img + core_byte(n, k, L.K)) / 2] = __float2half(v);
+            }
+        }
+    }
+}
+
+static TcArgs tc_args(const ntbc_model* m) {
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mv = make_view(m->desc, m->layout);
+    int off = 0;
+    for (int net = 0; net < 2; ++net) {
+        const NetView& nv = net ? a.mv.endpoint : a.mv.color;
+        TcNet& tn = a.net[net];
+        tn.n_layers = nv.n_layers;
+        for (int l = 0; l < nv.n_layers; ++l) {
+            TcLayer& L = tn.layer[l];
+            L.K = l == 0 ? ((nv.in_dim + 1 + 15) / 16) * 16 : 64 + 16;
+            L.out = nv.layer_out[l];
+            L.N = ((L.out + 15) / 16) * 16;
+            L.img = off;
+            off += L.N * L.K * 2;
+        }
+    }
+    a.img_bytes = (off + 15) & ~15;
+    return a;
+}
+
+static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes) {
+    for (int groups = kTcMaxGroups; groups >= 1; --groups) {
+        TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split);
+        size_t bytes = (size_t)sl.group_off + (size_t)groups * sl.group_bytes;
+        if (bytes <= 227 * 1024) {
+            *smem_bytes = bytes;
+            return groups;
+        }
+    }
+    return 0;
+}
+
+ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s) {
+    TcArgs a = tc_args(m);
+    if (!m->umma_img) {
+        ntbc_status st = device_alloc((void**)&m->umma_img, (size_t)a.img_bytes + sizeof(int) * 4, "tensor-core weight image");
+        if (st != NTBC_OK) return st;
+    }
+    m->tc_err = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(m->umma_img) + a.img_bytes);
+    NTBC_CHECK_CUDA(cudaMemsetAsync(m->tc_err, 0, sizeof(int), s));
+    build_image_kernel<<<1, 1024, 0, s>>>(m->infer_params, a, a.mv, m->umma_img);
+    NTBC_CHECK_LAUNCH("tensor-core weight image");
+    return NTBC_OK;
+}
+
+ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int32_t* ids, int n, float* e_out,
+                      float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
+    TcArgs a = tc_args(m);
+    size_t smem = 0;
+    const bool split = m->weight_prec == NTBC_PREC_FP16;
+    a.groups = tc_groups(a, m->desc.n_textures, split, &smem);
+    if (a.groups == 0) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: shared memory too small for this model");
+    a.n = n;
+    a.ids = ids;
+    a.mode = blocks_out ? 0 : 1;
+    a.err = m->tc_err;
+    TcOut outs;
+    memset(&outs, 0, sizeof(outs));
+    if (blocks_out)
+        for (int t = 0; t < m->desc.n_textures; ++t) outs.p[t] = blocks_out[t];
+    int dev = 0, sms = 0;
+    NTBC_CHECK_CUDA(cudaGetDevice(&dev));
+    NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int units = (n + kTcUnitBlocks - 1) / kTcUnitBlocks;
+    int grid = std::min(sms, (units + a.groups - 1) / a.groups);
+    if (grid < 1) return NTBC_OK;
+    const uint4* img = reinterpret_cast<const uint4*>(m->umma_img);
+    if (split) {
+        NTBC_CHECK_CUDA(cudaFuncSetAttribute(infer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        infer_tc_kernel<true><<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
+    } else {
+        NTBC_CHECK_CUDA(cudaFuncSetAttribute(infer_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        infer_tc_kernel<false><<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
+    }
+    NTBC_CHECK_LAUNCH("ntbc inference (tcgen05)");
+    return NTBC_OK;
+}
+
+}  // namespace ntbc

@@ -68,6 +68,8 @@ struct ntbc_model {
     float* infer_params = nullptr;      // FP32 copy used by inference: FP32 grids (grid_bits 0)
                                         // and the MLP weights rounded to the export precision
     __half* w16 = nullptr;              // MLP part in FP16 (weight_prec FP16)
+    __half* umma_img = nullptr;         // FP16 weights in the tensor-core shared-memory layout
+    int* tc_err = nullptr;              // set by the tensor-core kernel when a bounded wait gives up
     struct ntbc_train_state* train = nullptr;   // training scratch (allocated on first use)
 };
 

@@ -104,4 +104,9 @@ __device__ __forceinline__ void grid_features(const NetView& nv, const GridSrc& 
 
 void ntbc_train_release(ntbc_model* m);
 
+// tensor-core inference (FP16 weights): weight image preparation and launch
+ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s);
+ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int32_t* ids, int n, float* e_out,
+                      float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s);
+
 }  // namespace ntbc

@@ -284,6 +284,7 @@ void ntbc_model_free(ntbc_model* m) {
     cudaFree(m->qscale);   // also holds the zero points and the min / max scratch
     cudaFree(m->infer_params);
     cudaFree(m->w16);
+    cudaFree(m->umma_img);               // also holds tc_err
     ntbc_train_release(m);
     delete m;
 }
@@ -328,7 +329,8 @@ ntbc_status ntbc_model_export(ntbc_model* m, int grid_bits, int weight_prec, voi
     clear_error();
     if (!m) return fail(NTBC_EINVAL, "null model");
     if (grid_bits != 0 && grid_bits != 8 && grid_bits != 4) return fail(NTBC_EINVAL, "grid_bits must be 0, 4 or 8");
-    if (weight_prec != NTBC_PREC_FP32 && weight_prec != NTBC_PREC_FP16) return fail(NTBC_EINVAL, "weight precision must be FP32 or FP16");
+    if (weight_prec != NTBC_PREC_FP32 && weight_prec != NTBC_PREC_FP16 && weight_prec != NTBC_PREC_FP16_FAST)
+        return fail(NTBC_EINVAL, "weight precision must be NTBC_PREC_FP32, NTBC_PREC_FP16 or NTBC_PREC_FP16_FAST");
     ntbc_status st = ensure_export_buffers(m);
     if (st != NTBC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -347,9 +349,12 @@ ntbc_status ntbc_model_export(ntbc_model* m, int grid_bits, int weight_prec, voi
     }
     // MLP weights
     long long nw = (long long)(L.total - L.grid_floats);
-    if (weight_prec == NTBC_PREC_FP16) {
+    m->weight_prec = weight_prec;
+    if (weight_prec != NTBC_PREC_FP32) {
         round_half_kernel<<<grid_blocks(nw), 256, 0, s>>>(m->params + L.grid_floats, m->infer_params + L.grid_floats, m->w16, nw);
         NTBC_CHECK_LAUNCH("round weights to half");
+        st = tc_prepare(m, s);
+        if (st != NTBC_OK) return st;
     } else {
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->infer_params + L.grid_floats, m->params + L.grid_floats, nw * sizeof(float),
                                         cudaMemcpyDeviceToDevice, s));
@@ -384,7 +389,7 @@ static size_t blob_parts(const ntbc_model* m, size_t* grid_b, size_t* sz_b, size
     int levels = m->desc.color_levels + m->desc.endpoint_levels;
     *sz_b = 2 * levels * sizeof(float);
     *grid_b = m->grid_bits > 0 ? L.grid_floats : L.grid_floats * sizeof(float);
-    *w_b = (L.total - L.grid_floats) * (m->weight_prec == NTBC_PREC_FP16 ? sizeof(__half) : sizeof(float));
+    *w_b = (L.total - L.grid_floats) * (m->weight_prec != NTBC_PREC_FP32 ? sizeof(__half) : sizeof(float));
     return sizeof(BlobHeader) + *sz_b + *grid_b + *w_b;
 }
 
@@ -422,7 +427,7 @@ ntbc_status ntbc_model_save(const ntbc_model* m, uint8_t* blob, size_t size, voi
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb, m->infer_params, gb, cudaMemcpyDeviceToHost, s));
     }
     const ntbc_layout& L = m->layout;
-    if (m->weight_prec == NTBC_PREC_FP16)
+    if (m->weight_prec != NTBC_PREC_FP32)
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb, m->w16, wb, cudaMemcpyDeviceToHost, s));
     else
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb, m->infer_params + L.grid_floats, wb, cudaMemcpyDeviceToHost, s));
@@ -455,10 +460,12 @@ ntbc_status ntbc_model_load(ntbc_model* m, const uint8_t* blob, size_t size, voi
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->infer_params, p + zb, gb, cudaMemcpyHostToDevice, s));
     }
     long long nw = (long long)(L.total - L.grid_floats);
-    if (m->weight_prec == NTBC_PREC_FP16) {
+    if (m->weight_prec != NTBC_PREC_FP32) {
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->w16, p + zb + gb, wb, cudaMemcpyHostToDevice, s));
         half_to_float_kernel<<<grid_blocks(nw), 256, 0, s>>>(m->w16, m->infer_params + L.grid_floats, nw);
         NTBC_CHECK_LAUNCH("expand half weights");
+        st = tc_prepare(m, s);
+        if (st != NTBC_OK) return st;
     } else {
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->infer_params + L.grid_floats, p + zb + gb, wb, cudaMemcpyHostToDevice, s));
     }

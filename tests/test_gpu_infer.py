@@ -16,6 +16,10 @@ nt = pytest.importorskip("paper_2407_09543_gb300")
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
 RTOL = 1e-3
+# pure FP16 activations (NTBC_PREC_FP16_FAST): four FP16 roundings of the activations
+# (features + three hidden layers), unit roundoff u = 2^-11, each amplified at most ~2x by
+# the rest of the network: 8u ~ 4e-3
+RTOL_FAST = 4e-3
 
 
 def make_case(side=64, kinds=("sine_rgb", "sine_r"), levels=3, lo=4, hi=16, hidden=2, act="selu", seed=0,
@@ -86,7 +90,13 @@ def test_forward_fp32_matches_oracle(act, hidden):
     np.testing.assert_allclose(c, cr, rtol=RTOL, atol=1e-6)
 
 
-def check_blocks(mat, desc, odesc, got, ref):
+# pure FP16: outputs off by up to ~RTOL_FAST flip the decisions of texels whose colour
+# lies within that distance of a boundary between palette entries (spacing ~|e1 - e0| / 3
+# for BC1, / 7 for BC4): measured 0.16%, bound 0.5%
+MISMATCH_FAST = 0.005
+
+
+def check_blocks(mat, desc, odesc, got, ref, max_mismatch=0.001):
     total_m, total_f = 0, 0
     for t, fmt in enumerate(mat.formats):
         m, f = field_mismatch(fmt, got[t], ref[t])
@@ -96,7 +106,7 @@ def check_blocks(mat, desc, odesc, got, ref):
         dec_r = obc.decode(fmt, ref[t], desc.width, desc.height)
         src = mat.textures[t][:desc.height]
         assert abs(obc.psnr(dec_g, src) - obc.psnr(dec_r, src)) <= 0.05
-    assert total_m <= 0.001 * total_f, (total_m, total_f)
+    assert total_m <= max_mismatch * total_f, (total_m, total_f)
 
 
 @pytest.mark.parametrize("side,height", [(64, 64), (264, 132)])
@@ -173,3 +183,35 @@ def test_full_size_4k_sampled():
         total_m += m
         total_f += f
     assert total_m <= 0.001 * total_f
+
+
+def test_fp16_fast_mode_stated_tolerance():
+    mat, desc, odesc, params = make_case(side=128, levels=4, lo=8, hi=64, hidden=3)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16_FAST)
+    oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 8)
+    deq = ont.dequantize_grid(oc, os_, oz)
+    nc = desc.color_levels
+    p16 = oracle_params_fp16(params)
+    ids = np.arange(odesc.n_blocks)
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p16, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    np.testing.assert_allclose(e, er, rtol=RTOL_FAST, atol=1e-5)
+    np.testing.assert_allclose(c, cr, rtol=RTOL_FAST, atol=1e-5)
+    ref = ont.infer_blocks(odesc, p16, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ref, MISMATCH_FAST)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tensor_core_ragged_and_fp32_grids(prec):
+    # block count not a multiple of the 128-block work unit, FP32 (unquantised) grids
+    mat, desc, odesc, params = make_case(side=264, height=132, levels=4, lo=4, hi=32, hidden=2)
+    model = gpu_model(desc, params, grid_bits=0, weight_prec=prec)
+    p16 = oracle_params_fp16(params)
+    ids = np.arange(odesc.n_blocks)
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p16, ids)
+    tol = RTOL if prec == 1 else RTOL_FAST
+    np.testing.assert_allclose(e, er, rtol=tol, atol=1e-5)
+    np.testing.assert_allclose(c, cr, rtol=tol, atol=1e-5)
+    check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ont.infer_blocks(odesc, p16),
+                 0.001 if prec == 1 else MISMATCH_FAST)
