@@ -222,6 +222,40 @@ def run_reference(args):
     return 0
 
 
+MUFU_PER_SM_PER_CLK = 16        # exp2 results per clock per SM (CUDA arithmetic-instruction throughput table)
+SM_COUNT = 152
+SM_MAX_GHZ = 2.07
+
+
+def inference_roofline(nt, desc, ms):
+    """Governing roofline of one inference pass: max of tensor (FP16 dense), MUFU (one exp2 per
+    SELU unit and per sigmoid output) and HBM (grid codes read once + blocks written) times."""
+    import json as _json
+    lay = nt.ntbc_model_layout(desc)
+    n_pos = (desc.width // 4) * (desc.height // 4)
+    hl = desc.hidden_layers
+    mac_c = lay.in_color * 64 + (hl - 1) * 64 * 64 + 64 * lay.out_color
+    mac_e = lay.in_endpoint * 64 + (hl - 1) * 64 * 64 + 64 * lay.out_endpoint
+    flops = 2.0 * (16 * mac_c + mac_e) * n_pos
+    exps = (16 * (hl * 64 + lay.out_color) + hl * 64 + lay.out_endpoint) * float(n_pos)
+    bytes_ = lay.grid_floats * 1 + 8.0 * n_pos * desc.n_textures
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}
+    mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * SM_MAX_GHZ * 1e9
+    t_tc = flops / (peaks["bf16_tflops"] * 1e12)
+    t_xu = exps / mufu_peak
+    t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
+    sec = ms * 1e-3
+    roofline = {"bound": "alu", "achieved": round(exps / sec / 1e12, 4), "peak": round(mufu_peak / 1e12, 4),
+                "unit": "Texp/s", "frac": round(t_xu / sec, 4), "traffic": None,
+                "kernel": "infer_tc_kernel<SPLIT=true>",
+                "peak_kind": "MUFU exp2: 152 SM x 16/clk x 2.07 GHz (derived); tensor/HBM peaks of measured"}
+    terms = {"t_tensor_ms": round(t_tc * 1e3, 4), "t_mufu_ms": round(t_xu * 1e3, 4), "t_hbm_ms": round(t_hbm * 1e3, 4),
+             "tensor_frac_of_measured": round(t_tc / sec, 4), "hbm_frac_of_measured": round(t_hbm / sec, 4),
+             "flop_per_pass": flops, "exp_per_pass": exps, "hbm_bytes_per_pass": bytes_}
+    return roofline, terms
+
+
 def run_quick(args):
     """Inference-only timing on random-init 4k weights (for profiling captures)."""
     import torch
@@ -358,14 +392,19 @@ def main():
     e2e_value = world * tex_blocks / (e2e_ms * 1e-3) / 1e6
     e2e_psnr = psnr_list(nt, obc, torch, mat, host_out, side)
 
-    # ---- roofline of the inference kernel (FP32 SIMT form: FMA-pipe bound)
-    flops_per_pos = 2 * (desc.color_levels * 2 * 64 + 64 * 64 * 2 + 64 * nt.ntbc_model_layout(desc).out_color) * 16 \
-        + 2 * (desc.endpoint_levels * 2 * 64 + 64 * 64 * 2 + 64 * nt.ntbc_model_layout(desc).out_endpoint)
-    achieved_tflops = flops_per_pos * nblk / (ms * 1e-3) / 1e12
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12        # FP32 FMA lanes x 2 FLOP x max SM clock
-    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 3), "peak": round(fp32_peak, 1),
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / fp32_peak, 4), "traffic": None,
-                "kernel": "infer_simt_kernel<MODE_PACK>", "peak_kind": "FP32 FMA pipe: 152 SM x 128 lanes x 2 x 2.07 GHz"}
+    # ---- roofline of the inference kernel (algorithmic counts per block position)
+    roofline, terms = inference_roofline(nt, desc, ms)
+
+    # ---- the same inference in the other modes (pure FP16 activations; FP32 SIMT kernel)
+    modes = {}
+    for name, prec in (("fp16_fast", nt.PREC_FP16_FAST), ("fp32_simt", nt.PREC_FP32)):
+        model.export(grid_bits=8, weight_prec=prec)
+        model.infer_to_bc(outs)
+        torch.cuda.synchronize()
+        t_m = float(np.mean(time_events(torch, infer, max(3, args.steps // 4), flush=flush)))
+        modes[name] = {"ms": round(t_m, 4), "value": round(tex_blocks / (t_m * 1e-3) / 1e6, 3),
+                       "psnr_db": psnr_list(nt, obc, torch, mat, outs, side)}
+    model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
 
     # ---- plain FP32 PyTorch path on the same GPU and weights
     plain = None
@@ -417,7 +456,7 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mblocks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (SIMT; FP16-rounded weights, u8 grids)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "fp16 tensor-core MMA (split hi+lo activations), fp32 accumulate; u8 grids", "data": "synthetic",
         "config": {"workload": f"mat4k {side}x{side}, 4 textures (2 BC1 + 2 BC4), 12 levels 16..2048 u8 QAT, "
                                f"3x64 SELU, FP16 weights", "texture_blocks": tex_blocks, "block_positions": nblk,
                    "l2": "flushed (256 MiB write) between timed iterations", "parallelism": f"replicas x{world}"},
@@ -432,6 +471,8 @@ def main():
                    "reference_bc_encode_ms": round(float(np.mean(ref_ms)), 3)},
         "plain_fp32_gpu": plain,
         "roofline": roofline,
+        "roofline_terms": terms,
+        "other_modes": modes,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "Mblocks/s", "ms_per_step": round(e2e_ms, 4),
                 "h2d_bytes_per_step": int(blob.numel()), "d2h_bytes_per_step": int(nblk * 8 * len(FORMATS))},

@@ -123,13 +123,23 @@ __device__ __forceinline__ void st_row8_split(unsigned char* hi_tile, unsigned c
     *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
-__device__ __forceinline__ float selu_fast(float z) {
+// Activations travel scaled by L = log2(e): every accumulator holds z L (the layer-0
+// features and both bias inputs carry the factor), so the exponentials are plain ex2.
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
     float e;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fminf(z, 0.f) * 1.4426950408889634f));
-    return fmaf(kSeluLA, e, fmaf(kSeluLambda, fmaxf(z, 0.f), -kSeluLA));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x));
+    return e;
 }
 
-__device__ __forceinline__ float sigmoid_fast(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+// SELU(z) L from a = z L:  lambda max(a, 0) + lambda alpha L (2^min(a, 0) - 1)
+__device__ __forceinline__ float selu_l2(float a) {
+    return fmaf(kSeluLambda, fmaxf(a, 0.f), fmaf(kSeluLA * kLog2e, ex2_approx(fminf(a, 0.f)), -kSeluLA * kLog2e));
+}
+
+// sigmoid(z) from a = z L
+__device__ __forceinline__ float sigmoid_l2(float a) { return __fdividef(1.f, 1.f + ex2_approx(-a)); }
 
 struct TcLayer {
     int K;           // total K of the MMA (multiple of 16, bias column included)
@@ -169,15 +179,15 @@ struct TcSmem {
 __host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int split) {
     TcSmem s;
     s.ones_off = (img_bytes + 127) & ~127;
-    s.table_off = s.ones_off + kTcRows * 16 * 2;
+    s.table_off = s.ones_off + 2 * kTcRows * 16 * 2;             // two constant tiles: L high, L low
     s.lvl_off = s.table_off + 256 * 4;
-    s.group_off = (s.lvl_off + 2 * 2 * NTBC_MAX_LEVELS * 4 + 1023) & ~1023;
+    s.group_off = (s.lvl_off + 2 * 2 * NTBC_MAX_LEVELS * 4 + 127) & ~127;
     s.a_off = 0;
     s.lo_off = kTcRows * 64 * 2;
     s.pal_off = s.lo_off + (split ? kTcRows * 64 * 2 : 0);
     s.ep_off = s.pal_off + ((n_tex * kTcUnitBlocks * kTcPalBytes + 15) & ~15);
     s.bar_off = s.ep_off + n_tex * kTcUnitBlocks * 4;
-    s.group_bytes = (s.bar_off + 16 + 1023) & ~1023;
+    s.group_bytes = (s.bar_off + 16 + 127) & ~127;
     return s;
 }
 
@@ -209,10 +219,10 @@ __device__ __forceinline__ bool run_layer(const TcLayer& L, int l, unsigned char
                 umma_f16(tmem, lo, bd, idesc, 1);
             }
         }
-        if (l > 0) {
-            uint64_t ad = umma_desc(smem_u32(smem + sl.ones_off), 128, 256);
+        if (l > 0) {                                // bias: A = constant L (high, and low half when split)
             uint64_t bd = umma_desc(b_base + nk_a * 256, 128, (L.K / 8) * 128);
-            umma_f16(tmem, ad, bd, idesc, 1);
+            umma_f16(tmem, umma_desc(smem_u32(smem + sl.ones_off), 128, 256), bd, idesc, 1);
+            if (SPLIT) umma_f16(tmem, umma_desc(smem_u32(smem + sl.ones_off + kTcRows * 32), 128, 256), bd, idesc, 1);
         }
         umma_commit(bar);
     }
@@ -226,14 +236,15 @@ __device__ __forceinline__ bool run_layer(const TcLayer& L, int l, unsigned char
 template <bool SPLIT>
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, unsigned char* A, unsigned char* Alo, int r, int act) {
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-        float v[16];
+    for (int c0 = 0; c0 < 64; c0 += 32) {            // two TMEM loads in flight per wait
+        float v[32];
         tmem_ld16(tmem_row + c0, v);
+        tmem_ld16(tmem_row + c0 + 16, v + 16);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = act == NTBC_ACT_SELU ? selu_fast(v[j]) : fmaxf(v[j], 0.f);
-        st_row8_split<SPLIT>(A, Alo, r, c0 / 8, 64, v);
-        st_row8_split<SPLIT>(A, Alo, r, c0 / 8 + 1, 64, v + 8);
+        for (int j = 0; j < 32; ++j) v[j] = act == NTBC_ACT_SELU ? selu_l2(v[j]) : fmaxf(v[j], 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st_row8_split<SPLIT>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
     }
 }
 
@@ -247,6 +258,26 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
 // and no integer-to-float conversion
 __device__ __forceinline__ float byte_as_unit(uint32_t word, uint32_t sel) {
     return __uint_as_float(__byte_perm(word, 0x3F800000u, sel));
+}
+
+// integer i (0 <= i < 2^22) as float via the 2^23 magic number
+__device__ __forceinline__ float small_int_float(int i) { return __int_as_float(i + 0x4B000000) - 8388608.f; }
+
+// corner-aligned bilinear set-up of level l (same arithmetic as bilinear_at, with the
+// per-level constants precomputed as floats)
+__device__ __forceinline__ Bilinear bilinear_tc(const NetView& nv, int l, float u, float v) {
+    float px = u * nv.resm1[l], py = v * nv.resm1[l];
+    int res = nv.res[l];
+    int ix = min((int)px, res - 2), iy = min((int)py, res - 2);    // px, py >= 0: truncation is floor
+    float fx = px - small_int_float(ix), fy = py - small_int_float(iy);
+    Bilinear b;
+    b.base = ((long long)iy * res + ix) * 2;
+    b.row = res * 2;
+    b.w00 = (1.f - fx) * (1.f - fy);
+    b.w01 = fx * (1.f - fy);
+    b.w10 = (1.f - fx) * fy;
+    b.w11 = fx * fy;
+    return b;
 }
 
 __device__ __forceinline__ uint32_t ld_u16(const uint8_t* p) {
@@ -265,7 +296,7 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
     for (int l = 0; l < NTBC_MAX_LEVELS; ++l) {
         float f0 = 0.f, f1 = 0.f;
         if (l < nv.levels && valid) {
-            Bilinear b = bilinear_at(nv.res[l], u, v);
+            Bilinear b = bilinear_tc(nv, l, u, v);
             long long o = nv.grid_off[l] + b.base;
             if (src.codes) {
                 const uint8_t* gp = src.codes + o;
@@ -283,8 +314,8 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
                 float2 c = __ldg(reinterpret_cast<const float2*>(gp + 2));
                 float2 d = __ldg(reinterpret_cast<const float2*>(gp + b.row));
                 float2 e = __ldg(reinterpret_cast<const float2*>(gp + b.row + 2));
-                f0 = b.w00 * a.x + b.w01 * c.x + b.w10 * d.x + b.w11 * e.x;
-                f1 = b.w00 * a.y + b.w01 * c.y + b.w10 * d.y + b.w11 * e.y;
+                f0 = (b.w00 * a.x + b.w01 * c.x + b.w10 * d.x + b.w11 * e.x) * kLog2e;
+                f1 = (b.w00 * a.y + b.w01 * c.y + b.w10 * d.y + b.w11 * e.y) * kLog2e;
             }
         }
         f[2 * l] = f0;
@@ -298,7 +329,7 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
         for (int j = 0; j < 8; ++j) {
             int i = kg * 8 + j;
             float x = i < 2 * NTBC_MAX_LEVELS ? f[i] : 0.f;
-            v8[j] = i == nv.in_dim ? 1.f : x;
+            v8[j] = i == nv.in_dim ? kLog2e : x;
         }
         st_row8_split<SPLIT>(A, Alo, r, kg, K0, v8);
     }
@@ -328,7 +359,10 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
     for (int i = tid; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
     for (int i = tid; i < kTcRows * 16; i += blockDim.x) {
         int rr = i / 16, k = i % 16;
-        *reinterpret_cast<__half*>(smem + sl.ones_off + core_byte(rr, k, 16)) = __float2half(k == 0 ? 1.f : 0.f);
+        __half hi = __float2half_rn(kLog2e);
+        __half lo = __float2half_rn(kLog2e - __half2float(hi));
+        *reinterpret_cast<__half*>(smem + sl.ones_off + core_byte(rr, k, 16)) = k == 0 ? hi : __float2half(0.f);
+        *reinterpret_cast<__half*>(smem + sl.ones_off + kTcRows * 32 + core_byte(rr, k, 16)) = k == 0 ? lo : __float2half(0.f);
     }
     for (int i = tid; i < 256; i += blockDim.x) reinterpret_cast<float*>(smem + sl.table_off)[i] = __fdiv_rn((float)i, 255.f);
     for (int i = tid; i < 2 * NTBC_MAX_LEVELS; i += blockDim.x) {
@@ -338,7 +372,7 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
         float2 k = make_float2(0.f, 0.f);
         if (src.codes && l < L) {
             float sc = src.scale[l], z = src.zero[l];
-            k = make_float2(sc * 32768.f, -sc * (32768.f + z));
+            k = make_float2(sc * 32768.f * kLog2e, -sc * (32768.f + z) * kLog2e);
         }
         lvl[i] = k;
     }
@@ -384,7 +418,7 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
                 if (args.mode == 1) {
                     int out = net.layer[l].out;
                     for (int o = 0; o < out; ++o) {
-                        float e = sigmoid_fast(tmem_ld1(tmem_row + o));
+                        float e = sigmoid_l2(tmem_ld1(tmem_row + o));
                         tmem_wait_ld();
                         if (valid) e_out[(long long)k * out + o] = e;
                     }
@@ -399,7 +433,7 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
                         for (int q = 0; q < 6; ++q) e[q] = tmem_ld1(tmem_row + eo + q);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) e[q] = sigmoid_fast(e[q]);
+                        for (int q = 0; q < 6; ++q) e[q] = sigmoid_l2(e[q]);
                         uint32_t c0 = (quant_channel(e[0], 31.f, 31) << 11) | (quant_channel(e[1], 63.f, 63) << 5) |
                                       quant_channel(e[2], 31.f, 31);
                         uint32_t c1 = (quant_channel(e[3], 31.f, 31) << 11) | (quant_channel(e[4], 63.f, 63) << 5) |
@@ -420,8 +454,8 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
                         e[0] = tmem_ld1(tmem_row + eo);
                         e[1] = tmem_ld1(tmem_row + eo + 1);
                         tmem_wait_ld();
-                        int r0 = quant_channel(sigmoid_fast(e[0]), 255.f, 255);
-                        int r1 = quant_channel(sigmoid_fast(e[1]), 255.f, 255);
+                        int r0 = quant_channel(sigmoid_l2(e[0]), 255.f, 255);
+                        int r1 = quant_channel(sigmoid_l2(e[1]), 255.f, 255);
                         int p[8];
                         bc4_palette(r0, r1, p);
 #pragma unroll
@@ -451,37 +485,45 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
                 if (args.mode == 1) {
                     int out = net.layer[l].out;
                     for (int o = 0; o < out; ++o) {
-                        float c = sigmoid_fast(tmem_ld1(tmem_row + o));
+                        float c = sigmoid_l2(tmem_ld1(tmem_row + o));
                         tmem_wait_ld();
                         if (valid) c_out[((long long)k * 16 + i) * out + o] = c;
                     }
                     continue;
                 }
-                for (int t = 0; t < T; ++t) {
+                float cv[NTBC_MAX_TEXTURES][3];
+#pragma unroll
+                for (int t = 0; t < NTBC_MAX_TEXTURES; ++t) {
+                    if (t >= T) break;
+                    int co = mv.coff[t];
+                    cv[t][0] = tmem_ld1(tmem_row + co);
+                    if (mv.formats[t] == NTBC_BC1) {
+                        cv[t][1] = tmem_ld1(tmem_row + co + 1);
+                        cv[t][2] = tmem_ld1(tmem_row + co + 2);
+                    }
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < NTBC_MAX_TEXTURES; ++t) {
+                    if (t >= T) break;
                     const uint8_t* pb = palb + (t * kTcUnitBlocks + blk) * kTcPalBytes;
                     uint32_t ep = eps[t * kTcUnitBlocks + blk];
-                    int co = mv.coff[t];
                     BlockPalette bp;
                     uint64_t bits;
                     if (mv.formats[t] == NTBC_BC1) {
-                        float cr = tmem_ld1(tmem_row + co), cg = tmem_ld1(tmem_row + co + 1), cb = tmem_ld1(tmem_row + co + 2);
-                        tmem_wait_ld();
                         bp.solid = (ep & 0xFFFFu) == (ep >> 16);
-                        uint32_t w0 = *reinterpret_cast<const uint32_t*>(pb);
-                        uint32_t w1 = *reinterpret_cast<const uint32_t*>(pb + 4);
-                        uint32_t w2 = *reinterpret_cast<const uint32_t*>(pb + 8);
-                        uint32_t wv[3] = {w0, w1, w2};
+                        uint32_t wv[3] = {*reinterpret_cast<const uint32_t*>(pb), *reinterpret_cast<const uint32_t*>(pb + 4),
+                                          *reinterpret_cast<const uint32_t*>(pb + 8)};
 #pragma unroll
                         for (int q = 0; q < 12; ++q) bp.pal[q / 3][q % 3] = tab[(wv[q / 4] >> (8 * (q % 4))) & 255];
-                        bits = (uint64_t)choose_code_bc1(bp, sigmoid_fast(cr), sigmoid_fast(cg), sigmoid_fast(cb)) << (2 * i);
+                        bits = (uint64_t)choose_code_bc1(bp, sigmoid_l2(cv[t][0]), sigmoid_l2(cv[t][1]),
+                                                         sigmoid_l2(cv[t][2])) << (2 * i);
                     } else {
-                        float cv = tmem_ld1(tmem_row + co);
-                        tmem_wait_ld();
                         uint32_t w0 = *reinterpret_cast<const uint32_t*>(pb);
                         uint32_t w1 = *reinterpret_cast<const uint32_t*>(pb + 4);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) bp.pal[q][0] = tab[((q < 4 ? w0 : w1) >> (8 * (q % 4))) & 255];
-                        bits = (uint64_t)choose_code_bc4(bp, sigmoid_fast(cv)) << (3 * i);
+                        bits = (uint64_t)choose_code_bc4(bp, sigmoid_l2(cv[t][0])) << (3 * i);
                     }
 #pragma unroll
                     for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
@@ -561,7 +603,7 @@ static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes) 
     for (int groups = kTcMaxGroups; groups >= 1; --groups) {
         TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split);
         size_t bytes = (size_t)sl.group_off + (size_t)groups * sl.group_bytes;
-        if (bytes <= 227 * 1024) {
+        if (bytes + 256 <= 227 * 1024) {             // room for the kernel's static shared variables
             *smem_bytes = bytes;
             return groups;
         }

@@ -79,6 +79,8 @@ namespace ntbc {
 struct NetView {
     int levels;
     int res[NTBC_MAX_LEVELS];
+    float resm1[NTBC_MAX_LEVELS];            // res - 1 and res - 2 as floats
+    float resm2[NTBC_MAX_LEVELS];
     long long grid_off[NTBC_MAX_LEVELS];     // element offset of each level in its grid buffer
     int features;
     int in_dim, out_dim, hidden_layers;

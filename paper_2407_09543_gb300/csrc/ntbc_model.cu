@@ -63,6 +63,8 @@ ModelView make_view(const ntbc_model_desc& d, const ntbc_layout& L) {
         const ntbc_span* gs = net ? L.endpoint_grid : L.color_grid;
         for (int l = 0; l < nv.levels; ++l) {
             nv.res[l] = net ? d.endpoint_res[l] : d.color_res[l];
+            nv.resm1[l] = (float)(nv.res[l] - 1);
+            nv.resm2[l] = (float)(nv.res[l] - 2);
             nv.grid_off[l] = (long long)gs[l].offset;
         }
         nv.in_dim = net ? L.in_endpoint : L.in_color;
