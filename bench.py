@@ -64,6 +64,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_material_seed(rank):
+    """Each rank encodes and decodes its own material (weak scaling, no data exchange)."""
+    return int(rank)
+
+
+def max_over_ranks(value, world, device=None):
+    """Time of the slowest rank (the whole job ends when it ends)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Units processed by all ranks per second, in millions."""
+    return world * units_per_rank / (ms * 1e-3) / 1e6
+
+
 # ----------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ----------------------------------------------------------------------------
@@ -310,7 +331,7 @@ def main():
     nblk = (side // 4) ** 2
     tex_blocks = nblk * len(FORMATS)
 
-    mat, desc, p0, tex_d, refs = build_workload(nt, torch, side, seed=rank, dev=dev)
+    mat, desc, p0, tex_d, refs = build_workload(nt, torch, side, seed=rank_material_seed(rank), dev=dev)
 
     # ---- reference BC targets (timed separately)
     for t, fmt in enumerate(mat.formats):
@@ -364,13 +385,9 @@ def main():
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), world, dev)
     ours_psnr = psnr_list(nt, obc, torch, mat, outs, side)
-    value = world * tex_blocks / (ms * 1e-3) / 1e6
+    value = job_throughput(tex_blocks, world, ms)
 
     # ---- end to end through the C ABI with host buffers: blob H2D, infer, blocks D2H
     blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
@@ -388,8 +405,8 @@ def main():
         e2e()
     torch.cuda.synchronize()
     e2e_times = time_events(torch, e2e, args.steps, flush=flush)
-    e2e_ms = float(np.mean(e2e_times))
-    e2e_value = world * tex_blocks / (e2e_ms * 1e-3) / 1e6
+    e2e_ms = max_over_ranks(float(np.mean(e2e_times)), world, dev)
+    e2e_value = job_throughput(tex_blocks, world, e2e_ms)
     e2e_psnr = psnr_list(nt, obc, torch, mat, host_out, side)
 
     # ---- roofline of the inference kernel (algorithmic counts per block position)

@@ -70,7 +70,7 @@ int ntbc_abi_version(void);
 
 /*
  * Reference BC encoder (stands in for the Compressonator encoder that produces
- * the training targets and the "Ref. BC" quality bar, Sec. 3.2 and Sec. 5.1).
+ * the training targets and the "Ref. BC" quality bar, Sec. 3.2 and Sec. 4.1).
  * BC1: principal-axis range fit (integer covariance, 8 FP64 power iterations,
  * extreme-projection texels as endpoints), RGB565 quantisation, exhaustive
  * per-texel code choice, colour0 > colour1. BC4: best of the 8-value mode over
@@ -84,7 +84,7 @@ ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h,
                                 uint8_t* blocks, void* stream);
 
 /*
- * Decoder (the "existing BC decompression" of Sec. 5.4): blocks -> texels with
+ * Decoder (the "existing BC decompression" of Sec. 4.4): blocks -> texels with
  * the integer palette (interpolants rounded to nearest; BC1 colour0 <= colour1
  * selects the 3-colour mode, BC4 r0 <= r1 the 6-value mode with 0 and 255).
  *   blocks  device, (w/4)*(h/4)*8 bytes
@@ -111,7 +111,7 @@ ntbc_status ntbc_outputs_to_bc(int fmt, const float* e_hat, const float* c_hat, 
 /* ------------------------------------------------------------------------- */
 
 /*
- * Architecture of one NTBC model (Sec. 3.2, Sec. 4.4, Sec. 5.1): an endpoint
+ * Architecture of one NTBC model (Sec. 3.2, Sec. 3.4, Sec. 4.1): an endpoint
  * network over block coordinates and a colour network over texel coordinates,
  * each a multi-resolution 2D feature grid (dense res x res x features per level,
  * bilinear, corner aligned) followed by an MLP with `hidden_layers` hidden layers
@@ -156,7 +156,7 @@ ntbc_status ntbc_model_layout(const ntbc_model_desc* desc, ntbc_layout* out);
 
 /*
  * Grid level resolutions res_l = floor(n_min * (n_max/n_min)^(l/(levels-1)) + 0.5)
- * (geometric ladder from the coarsest to the finest resolution, Sec. 4.4).
+ * (geometric ladder from the coarsest to the finest resolution, Sec. 3.4).
  * Host-only. out: host int[levels].
  */
 ntbc_status ntbc_level_resolutions(int levels, int n_min, int n_max, int* out);
@@ -208,7 +208,7 @@ ntbc_status ntbc_model_save(const ntbc_model* model, uint8_t* blob, size_t size,
 ntbc_status ntbc_model_load(ntbc_model* model, const uint8_t* blob, size_t size, void* stream);
 
 /* ------------------------------------------------------------------------- */
-/* Inference (Sec. 3.2, Fig. NTBC (a); Sec. 5.4)                              */
+/* Inference (Sec. 3.2, Fig. NTBC (a); Sec. 4.4)                              */
 /* ------------------------------------------------------------------------- */
 
 /*
@@ -231,7 +231,7 @@ ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int 
 
 /* ------------------------------------------------------------------------- */
 /* Training (Sec. 3.2 losses and straight-through argmax; Sec. 3.3 QAT;        */
-/* Sec. 4.4 Adam + schedule)                                                 */
+/* Sec. 3.4 Adam + schedule)                                                 */
 /* ------------------------------------------------------------------------- */
 
 typedef struct {

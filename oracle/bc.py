@@ -25,7 +25,7 @@ Direct3D one, and the interpolants round to nearest:
 The paper's palette index n runs in linear order of the weight w_n; the
 hardware code differs. LINEAR_TO_CODE_* give the map.
 
-Reference encoder (stands in for the Compressonator encoder of Sec. 5.1; this
+Reference encoder (stands in for the Compressonator encoder of Sec. 4.1; this
 is our own range fit with exhaustive index assignment, no refinement):
   BC1: integer mean/covariance -> principal axis by 8 power iterations in FP64
        (explicit operation order, no fused multiply-add) -> the texels with the
@@ -319,7 +319,7 @@ def reference_endpoints(fmt, blocks):
 
 
 # ----------------------------------------------------------------------------
-# metric (Sec. 5.3)
+# metric (Sec. 4.3)
 # ----------------------------------------------------------------------------
 
 def psnr(a, b):

@@ -13,19 +13,19 @@ Sections of the paper followed:
   * Sec. 3.2, Eq. softmax and App. A: straight-through argmax, backward of the
     softmax expectation with temperature T.
   * Sec. 2.3, Eq. quantize / dequantize / quantizer / scaling_factor, Sec. 3.3: per-level QAT.
-  * Sec. 4.4: 3 x 64 SELU hidden layers, sigmoid outputs, multi-resolution 2D
+  * Sec. 3.4: 3 x 64 SELU hidden layers, sigmoid outputs, multi-resolution 2D
     grids with 2 features per level from resolution 16, Adam (0.9, 0.999, 1e-15),
     learning rates 0.01 (grids) / 0.005 (MLPs), 10 warm-up steps then cosine to 0.
-  * Sec. 5.1: conservative / aggressive packaging (outputs per texture).
+  * Sec. 4.1: conservative / aggressive packaging (outputs per texture).
 
 Readings where the paper is silent or garbled (each one is listed in the design notes):
   * grid level resolution res_l = floor(N_min (N_max/N_min)^(l/(L-1)) + 0.5);
     each level is a dense res x res x F array (this reproduces the 13.37 MB and
-    26.74 MB model sizes of Sec. 5.3 exactly);
+    26.74 MB model sizes of Sec. 4.3 exactly);
   * corner-aligned bilinear lookup: p = u (res-1), i0 = min(floor p, res-2);
     texel centres u = (x+0.5)/W, block centres s = (bx+0.5)/(W/4);
   * the endpoint grid keeps the colour-grid levels whose resolution does not
-    exceed the number of blocks per side (7 of 8 levels in Sec. 4.4);
+    exceed the number of blocks per side (7 of 8 levels in Sec. 3.4);
   * Linear layers carry biases;
   * endpoints quantise as floor(e*31+0.5) (G: *63) or floor(e*255+0.5) in FP32;
     indices are chosen against the palette of the quantised endpoints, by
@@ -64,7 +64,7 @@ NORM_GUARD = 1e-6
 # ----------------------------------------------------------------------------
 
 def level_resolutions(levels: int, n_min: int, n_max: int):
-    """Per-level grid resolutions, geometric from n_min to n_max (Sec. 4.4)."""
+    """Per-level grid resolutions, geometric from n_min to n_max (Sec. 3.4)."""
     if levels == 1:
         return [int(n_min)]
     out = []
@@ -107,7 +107,7 @@ class ModelDesc:
 
     @property
     def out_color(self):
-        """3 N_RGB + N_SC colour outputs (Sec. 5.1, aggressive packaging)."""
+        """3 N_RGB + N_SC colour outputs (Sec. 4.1, aggressive packaging)."""
         return sum(self.channels)
 
     @property
@@ -142,7 +142,7 @@ class ModelDesc:
 
 def storage_bytes(desc: ModelDesc, grid_bits=8, weight_bytes=2):
     """Bytes of a stored model: all grid levels at grid_bits per feature plus both MLPs
-    (weights and biases) at weight_bytes per value (Sec. 5.3 model sizes)."""
+    (weights and biases) at weight_bytes per value (Sec. 4.3 model sizes)."""
     grid = sum(r * r for r in desc.color_res) + sum(r * r for r in desc.endpoint_res)
     grid_b = grid * desc.features * grid_bits // 8
     mlp = 0
@@ -208,7 +208,7 @@ def grid_lookup_backward(levels, cache, g_feats, masks=None):
 
 
 # ----------------------------------------------------------------------------
-# MLP (Sec. 4.4)
+# MLP (Sec. 3.4)
 # ----------------------------------------------------------------------------
 
 def selu(z):
@@ -581,7 +581,7 @@ def loss_value(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_bits=0
 
 
 # ----------------------------------------------------------------------------
-# Adam and the learning-rate schedule (Sec. 4.4)
+# Adam and the learning-rate schedule (Sec. 3.4)
 # ----------------------------------------------------------------------------
 
 ADAM_BETA1, ADAM_BETA2, ADAM_EPS = 0.9, 0.999, 1e-15

@@ -10,7 +10,7 @@ Five workloads:
   sweep    mat4k weights with u8 / u4 grids and FP32 / FP16 MLPs
   batch16  16 materials of uneven size (sides 512..4096, 2..5 textures)
 The endpoint grid keeps the colour-grid levels whose resolution does not exceed
-the number of blocks per side (Sec. 4.4: 7 of the 8 levels for a 4096^2 texture).
+the number of blocks per side (Sec. 3.4: 7 of the 8 levels for a 4096^2 texture).
 """
 from __future__ import annotations
 

@@ -3,7 +3,7 @@
 //
 // Format: Sec. 2.1 (8-byte blocks, RGB565 + 2-bit codes, 8-bit + 3-bit codes,
 // palettes of Eq. palette / Eq. weightBC4). The reference encoder stands in for
-// the Compressonator encoder of Sec. 5.1 and is bit-exact with the CPU oracle:
+// the Compressonator encoder of Sec. 4.1 and is bit-exact with the CPU oracle:
 // its FP64 arithmetic uses explicit round-to-nearest intrinsics (no fused
 // multiply-add) in the same order as the oracle's.
 #include <cstdlib>

@@ -1,4 +1,4 @@
-// NTBC inference to BC blocks (Sec. 3.2, Fig. NTBC (a); Sec. 5.4): one fused
+// NTBC inference to BC blocks (Sec. 3.2, Fig. NTBC (a); Sec. 4.4): one fused
 // launch performs the grid lookup and dequantisation, the endpoint MLP per
 // block, the colour MLP per texel, endpoint quantisation, the per-texel argmax
 // of -||c_hat - p_n|| and the packing into 8-byte blocks.

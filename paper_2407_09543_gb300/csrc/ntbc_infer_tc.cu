@@ -1,5 +1,5 @@
 // Tensor-core (tcgen05) form of the fused NTBC inference kernel (Sec. 3.2,
-// Fig. NTBC (a); Sec. 5.4) for FP16 weights, FP32 accumulation in TMEM.
+// Fig. NTBC (a); Sec. 4.4) for FP16 weights, FP32 accumulation in TMEM.
 //
 // One persistent CTA per SM holds up to three independent warpgroups. A
 // warpgroup owns one work unit at a time: 128 consecutive blocks. It runs the

@@ -1,7 +1,7 @@
 // NTBC model state: parameter layout, allocation, the QAT export to the stored
 // form (Sec. 2.3 Eq. quantize / scaling_factor, Sec. 3.3 per-level asymmetric
 // quantisation) and the stored blob (Sec. 3.3: grids stored as 8-bit integers,
-// half-precision MLP weights, Sec. 4.4).
+// half-precision MLP weights, Sec. 3.4).
 #include <cmath>
 #include <cstring>
 #include <vector>

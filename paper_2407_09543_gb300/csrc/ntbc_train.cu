@@ -3,7 +3,7 @@
 // lossNTBC_c) with the straight-through argmax (Eq. softmax, App. A), the hand-
 // written backward (MLP weight / input gradients, grid scatter-add), QAT fake
 // quantisation of the grids (Sec. 3.3) and dense Adam with warm-up + cosine
-// schedule (Sec. 4.4).
+// schedule (Sec. 3.4).
 //
 // Layout: every activation buffer is feature-major, [unit][sample], so that
 // consecutive threads (samples) touch consecutive addresses. The colour network

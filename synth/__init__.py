@@ -2,9 +2,9 @@
 
 This module holds no arithmetic of the compression method itself. It only draws
 data: procedural texture content standing in for the paper's 4096^2 ambientCG /
-Poly Haven materials (Sec. 5.2; the dataset is not available here), and the
+Poly Haven materials (Sec. 4.2; the dataset is not available here), and the
 random initial parameters of a model (He-normal MLP weights, zero biases, and
-U[-1e-4, 1e-4] grid features, Sec. 4.4), which both sides receive as inputs.
+U[-1e-4, 1e-4] grid features, Sec. 3.4), which both sides receive as inputs.
 
 Every array is a deterministic function of a string key and an integer seed
 (SHA-256 of the key feeds numpy's SeedSequence), so the same call gives the same
@@ -283,7 +283,7 @@ def material_batch(seed=0, count=16):
 
 
 # ----------------------------------------------------------------------------
-# initial parameters (Sec. 4.4): He-normal weights, zero biases, U[-1e-4, 1e-4] grids
+# initial parameters (Sec. 3.4): He-normal weights, zero biases, U[-1e-4, 1e-4] grids
 # ----------------------------------------------------------------------------
 
 def init_params(grid_res_color, grid_res_endpoint, features, mlp_color_dims, mlp_endpoint_dims, seed=0):

@@ -26,7 +26,7 @@ def paper_desc(n_bc1, n_bc4, side=4096):
 
 
 # ----------------------------------------------------------------------------
-# configuration and storage (Sec. 4.4, Sec. 5.3)
+# configuration and storage (Sec. 3.4, Sec. 4.3)
 # ----------------------------------------------------------------------------
 
 def test_level_resolutions_paper_grids():
@@ -44,14 +44,14 @@ def test_level_resolutions_paper_grids():
 
 
 def test_storage_matches_paper_model_sizes():
-    # Sec. 5.3: one aggressive model is 13.37 MB and the conservative pair 26.74 MB
+    # Sec. 4.3: one aggressive model is 13.37 MB and the conservative pair 26.74 MB
     # (u8 grids, half-precision MLPs, MetalPlates013 with 2 BC1 + 4 BC4 textures).
     mib = 2 ** 20
     agg = ntbc.storage_bytes(paper_desc(2, 4), grid_bits=8, weight_bytes=2)
     cons = ntbc.storage_bytes(paper_desc(2, 0), 8, 2) + ntbc.storage_bytes(paper_desc(0, 4), 8, 2)
     assert round(agg / mib, 2) == float(G["storage_aggressive_mb"][0])
     assert round(cons / mib, 2) == float(G["storage_conservative_mb"][0])
-    # the size barely depends on the texture count (Sec. 6)
+    # the size barely depends on the texture count (Sec. 5)
     assert abs(ntbc.storage_bytes(paper_desc(1, 1), 8, 2) - agg) < 0.01 * agg
 
 
@@ -254,7 +254,7 @@ def test_quantizer_rounding_is_half_away_from_zero():
 
 
 # ----------------------------------------------------------------------------
-# Adam and LR schedule (Sec. 4.4)
+# Adam and LR schedule (Sec. 3.4)
 # ----------------------------------------------------------------------------
 
 def test_adam_closed_form_steps():
@@ -348,7 +348,7 @@ def test_sampler_range_and_uniformity():
 
 
 # ----------------------------------------------------------------------------
-# the learned part: training improves on the untrained network (Sec. 5.3 ordering)
+# the learned part: training improves on the untrained network (Sec. 4.3 ordering)
 # ----------------------------------------------------------------------------
 
 def test_training_beats_untrained_and_stays_below_reference():
