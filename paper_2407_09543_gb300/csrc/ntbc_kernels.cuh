@@ -15,8 +15,10 @@ struct LevelTable {
 };
 
 LevelTable level_table(const ntbc_model_desc& d, const ntbc_layout& L);
+// per-level QAT scale / zero point; with `active` (device flag) the kernels do nothing
+// while the flag is zero (outside the QAT phase of a captured training step)
 ntbc_status launch_level_scale_zero(const float* grid, const LevelTable& lt, int bits, unsigned* mm, float* scale,
-                                    float* zero, cudaStream_t s);
+                                    float* zero, cudaStream_t s, const int* active = nullptr);
 
 // Where a network's grid comes from.
 //   f32:  FP32 features (parameter buffer), optional QAT fake quantisation (qat_bits > 0 with

@@ -224,7 +224,7 @@ __global__ void dense_bwd_data_kernel(const float* __restrict__ D, int out, int 
 }
 
 // dW[o][i] += sum_k D[o][k] A[i][k], db[o] += sum_k D[o][k] over this CTA's chunk of samples
-constexpr int kWgChunk = 2048;
+constexpr int kWgChunk = 512;
 constexpr int kWgTile = 32;
 
 __global__ void __launch_bounds__(256) dense_bwd_weight_kernel(const float* __restrict__ D, int out,
@@ -422,82 +422,94 @@ __global__ void color_loss_kernel(ModelView mv, TexPtrs tp, const int32_t* __res
     block_reduce_add(&acc[3], lcd / n_el);
 }
 
-// endpoint network: per block sample, L_e + L_cd with distances from the block's
-// texel colours to the palette of the predicted (unquantised) endpoints, decoded
-// with the reference endpoints
+// endpoint network: one thread per (sampled block, texel) -- thread k is texel k & 15 of
+// sample k >> 4, so a block's 16 texels sit in one half-warp. L_cd uses distances from the
+// texel colours to the palette of the predicted (unquantised) endpoints and decodes with
+// the reference endpoints; the half-warp sums the 16 texels' contributions to the
+// endpoint gradient, and its first lane adds L_e and writes D (through the sigmoid).
 __global__ void endpoint_loss_kernel(ModelView mv, TexPtrs tp, const int32_t* __restrict__ ids, int Bn,
                                      const float* __restrict__ Y, float T, float* __restrict__ D,
                                      double* __restrict__ acc) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    bool ok = k < Bn;
+    int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    int bi = kk >> 4, i = kk & 15;
+    bool ok = bi < Bn;
+    if (!ok) bi = 0;
+    float okf = ok ? 1.f : 0.f;
     float le = 0.f, lcd = 0.f;
-    if (ok) {
-        int b = ids[k];
-        int bx = b % mv.bw, by = b / mv.bw;
-        float n_e = (float)Bn * (float)mv.endpoint.out_dim;
-        float n_cd = (float)Bn * 16.f * (float)mv.color.out_dim;
-        for (int t = 0; t < mv.n_textures; ++t) {
-            int fmt = mv.formats[t], C = fmt == NTBC_BC1 ? 3 : 1, eo = mv.eoff[t];
-            float eh0[3], eh1[3], e0[3], e1[3], g0[3], g1[3];
-            ref_endpoints(fmt, tp.blocks[t], b, e0, e1);
-            for (int q = 0; q < C; ++q) {
-                eh0[q] = Y[(long long)(eo + q) * Bn + k];
-                eh1[q] = Y[(long long)(eo + C + q) * Bn + k];
-                float r0 = eh0[q] - e0[q], r1 = eh1[q] - e1[q];
-                le += r0 * r0 + r1 * r1;
-                g0[q] = 2.f * r0 / n_e;
-                g1[q] = 2.f * r1 / n_e;
-            }
-            float Ah[8], Bh[8], Ch[8], Ar[8], Br[8], Cr[8];
-            int K = palette_coeffs(fmt, eh0[0] > eh1[0], Ah, Bh, Ch);
-            palette_coeffs(fmt, e0[0] > e1[0], Ar, Br, Cr);
-            float Ph[8][3], Pr[8][3];
-            for (int n = 0; n < K; ++n)
-                for (int q = 0; q < C; ++q) {
-                    Ph[n][q] = Ah[n] * eh0[q] + Bh[n] * eh1[q] + Ch[n];
-                    Pr[n][q] = Ar[n] * e0[q] + Br[n] * e1[q] + Cr[n];
-                }
-            for (int i = 0; i < 16; ++i) {
-                int x = 4 * bx + (i & 3), y = 4 * by + (i >> 2);
-                float c[3];
-                for (int q = 0; q < C; ++q) c[q] = texel_value(tp.texels[t], fmt, mv.width, x, y, q);
-                float d[8], nrm[8];
-                int best = 0;
-                for (int n = 0; n < K; ++n) {
-                    float s = 0.f;
-                    for (int q = 0; q < C; ++q) {
-                        float df = c[q] - Ph[n][q];
-                        s += df * df;
-                    }
-                    nrm[n] = sqrtf(s);
-                    d[n] = -nrm[n];
-                    if (d[n] > d[best]) best = n;
-                }
-                float g_dec[3];
-                for (int q = 0; q < C; ++q) {
-                    float r = c[q] - Pr[best][q];
-                    lcd += r * r;
-                    g_dec[q] = -2.f * r / n_cd;
-                }
-                float g_d[8];
-                ste_grad(K, C, d, Pr, g_dec, T, g_d);
-                for (int n = 0; n < K; ++n) {
-                    float inv = 1.f / fmaxf(nrm[n], kNormGuard);
-                    for (int q = 0; q < C; ++q) {
-                        float gp = g_d[n] * (c[q] - Ph[n][q]) * inv;    // d d_n / d p_n = (c - p_n)/||.||
-                        g0[q] += Ah[n] * gp;
-                        g1[q] += Bh[n] * gp;
-                    }
-                }
-            }
-            for (int q = 0; q < C; ++q) {
-                D[(long long)(eo + q) * Bn + k] = g0[q] * eh0[q] * (1.f - eh0[q]);
-                D[(long long)(eo + C + q) * Bn + k] = g1[q] * eh1[q] * (1.f - eh1[q]);
-            }
-        }
-    }
+    int b = ids[bi];
+    int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
     float n_e = (float)Bn * (float)mv.endpoint.out_dim;
     float n_cd = (float)Bn * 16.f * (float)mv.color.out_dim;
+    for (int t = 0; t < mv.n_textures; ++t) {
+        int fmt = mv.formats[t], C = fmt == NTBC_BC1 ? 3 : 1, eo = mv.eoff[t];
+        float eh0[3] = {0.f, 0.f, 0.f}, eh1[3] = {0.f, 0.f, 0.f}, e0[3] = {0.f, 0.f, 0.f}, e1[3] = {0.f, 0.f, 0.f};
+        float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+        ref_endpoints(fmt, tp.blocks[t], b, e0, e1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q < C) {
+                eh0[q] = Y[(long long)(eo + q) * Bn + bi];
+                eh1[q] = Y[(long long)(eo + C + q) * Bn + bi];
+                c[q] = texel_value(tp.texels[t], fmt, mv.width, x, y, q);
+            }
+        float Ah[8], Bh[8], Ch[8], Ar[8], Br[8], Cr[8];
+        int K = palette_coeffs(fmt, eh0[0] > eh1[0], Ah, Bh, Ch);
+        palette_coeffs(fmt, e0[0] > e1[0], Ar, Br, Cr);
+        float Ph[8][3], Pr[8][3], d[8], nrm[8];
+        int best = 0;
+        for (int n = 0; n < K; ++n) {
+            float sq = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                Ph[n][q] = Ah[n] * eh0[q] + Bh[n] * eh1[q] + Ch[n];
+                Pr[n][q] = Ar[n] * e0[q] + Br[n] * e1[q] + Cr[n];
+                float df = q < C ? c[q] - Ph[n][q] : 0.f;
+                sq += df * df;
+            }
+            nrm[n] = sqrtf(sq);
+            d[n] = -nrm[n];
+            if (d[n] > d[best]) best = n;
+        }
+        float g_dec[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q < C) {
+                float rr = c[q] - Pr[best][q];
+                lcd += okf * rr * rr;
+                g_dec[q] = -2.f * okf * rr / n_cd;
+            }
+        float g_d[8];
+        ste_grad(K, C, d, Pr, g_dec, T, g_d);
+        for (int n = 0; n < K; ++n) {
+            float inv = 1.f / fmaxf(nrm[n], kNormGuard);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q < C) {
+                    float gp = g_d[n] * (c[q] - Ph[n][q]) * inv;      // d d_n / d p_n = (c - p_n)/||.||
+                    g0[q] += Ah[n] * gp;
+                    g1[q] += Bh[n] * gp;
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                g0[q] += __shfl_xor_sync(0xffffffffu, g0[q], o);
+                g1[q] += __shfl_xor_sync(0xffffffffu, g1[q], o);
+            }
+        if (i == 0 && ok) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q < C) {
+                    float r0 = eh0[q] - e0[q], r1 = eh1[q] - e1[q];
+                    le += r0 * r0 + r1 * r1;
+                    g0[q] += 2.f * r0 / n_e;
+                    g1[q] += 2.f * r1 / n_e;
+                    D[(long long)(eo + q) * Bn + bi] = g0[q] * eh0[q] * (1.f - eh0[q]);
+                    D[(long long)(eo + C + q) * Bn + bi] = g1[q] * eh1[q] * (1.f - eh1[q]);
+                }
+        }
+    }
     block_reduce_add(&acc[0], le / n_e);
     block_reduce_add(&acc[1], lcd / n_cd);
 }
@@ -516,32 +528,73 @@ __global__ void loss_finalize_kernel(const double* __restrict__ acc, float* __re
 // grid scatter-add (bilinear adjoint), with the QAT straight-through mask
 // ---------------------------------------------------------------------------
 
+// One straight-through factor per corner value: 1 where the QAT code was not clamped.
+__device__ __forceinline__ float2 ste_mask(float2 add, const float* f32, long long corner, float s, float z, float qm) {
+    float2 r = *reinterpret_cast<const float2*>(f32 + corner);
+    float q0 = roundf(__fdiv_rn(r.x, s)) + z, q1 = roundf(__fdiv_rn(r.y, s)) + z;
+    if (q0 < 0.f || q0 > qm) add.x = 0.f;
+    if (q1 < 0.f || q1 > qm) add.y = 0.f;
+    return add;
+}
+
+// Bilinear adjoint: d loss / d features back to the 4 corners of every level.
+// Colour network: the 16 texels of a block sit in one half-warp and their corner
+// indices are non-decreasing in x (lane & 3) and in y (lane >> 2), so equal corners form
+// contiguous runs; a segmented scan along x, then along y, leaves each distinct corner's
+// total in the last lane of its run, which issues the only atomic for that corner.
 __global__ void grid_scatter_kernel(ModelView mv, bool color, const int32_t* __restrict__ ids, int B,
                                     const float* __restrict__ G, GridSrc src, float* __restrict__ ggrad) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= B) return;
+    bool valid = k < B;
+    int kc = valid ? k : 0;
     const NetView& nv = color ? mv.color : mv.endpoint;
     float u, v;
     int x, y;
-    sample_coords(mv, color, ids, k, u, v, x, y);
+    sample_coords(mv, color, ids, kc, u, v, x, y);
     int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+    const int lx = k & 3, ly = (k >> 2) & 3;
     for (int l = 0; l < nv.levels; ++l) {
-        Bilinear bl = bilinear_at(nv.res[l], u, v);
-        float g0 = G[(long long)(2 * l) * B + k], g1 = G[(long long)(2 * l + 1) * B + k];
-        long long o = nv.grid_off[l] + bl.base;
-        long long corner[4] = {o, o + 2, o + bl.row, o + bl.row + 2};
-        float w[4] = {bl.w00, bl.w01, bl.w10, bl.w11};
+        int res = nv.res[l];
+        float px = u * (float)(res - 1), py = v * (float)(res - 1);
+        int ix = min((int)floorf(px), res - 2), iy = min((int)floorf(py), res - 2);
+        float fx = px - (float)ix, fy = py - (float)iy;
+        float g0 = valid ? G[(long long)(2 * l) * B + kc] : 0.f, g1 = valid ? G[(long long)(2 * l + 1) * B + kc] : 0.f;
+        float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+            int cx = ix + (j & 1), cy = iy + (j >> 1);
+            long long corner = nv.grid_off[l] + ((long long)cy * res + cx) * 2;
             float2 add = make_float2(w[j] * g0, w[j] * g1);
-            if (qat_bits > 0) {
-                float s = src.scale[l], z = src.zero[l], qm = (float)((1 << qat_bits) - 1);
-                float2 r = *reinterpret_cast<const float2*>(src.f32 + corner[j]);
-                float q0 = roundf(__fdiv_rn(r.x, s)) + z, q1 = roundf(__fdiv_rn(r.y, s)) + z;
-                if (q0 < 0.f || q0 > qm) add.x = 0.f;
-                if (q1 < 0.f || q1 > qm) add.y = 0.f;
+            if (qat_bits > 0 && valid)
+                add = ste_mask(add, src.f32, corner, src.scale[l], src.zero[l], (float)((1 << qat_bits) - 1));
+            bool issue = valid;
+            if (color) {
+#pragma unroll
+                for (int dd = 1; dd <= 2; dd <<= 1) {          // runs along x
+                    float px0 = __shfl_up_sync(0xffffffffu, add.x, dd), px1 = __shfl_up_sync(0xffffffffu, add.y, dd);
+                    int pk = __shfl_up_sync(0xffffffffu, cx, dd);
+                    if (lx >= dd && pk == cx) {
+                        add.x += px0;
+                        add.y += px1;
+                    }
+                }
+                int nx = __shfl_down_sync(0xffffffffu, cx, 1);
+                bool last_x = lx == 3 || nx != cx;
+                if (!last_x) add = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int dd = 4; dd <= 8; dd <<= 1) {          // runs along y
+                    float py0 = __shfl_up_sync(0xffffffffu, add.x, dd), py1 = __shfl_up_sync(0xffffffffu, add.y, dd);
+                    int pk = __shfl_up_sync(0xffffffffu, cy, dd);
+                    if (ly >= dd / 4 && pk == cy) {
+                        add.x += py0;
+                        add.y += py1;
+                    }
+                }
+                int ny = __shfl_down_sync(0xffffffffu, cy, 4);
+                bool last_y = ly == 3 || ny != cy;
+                issue = valid && last_x && last_y;
             }
-            atomicAdd(reinterpret_cast<float2*>(ggrad + corner[j]), add);
+            if (issue) atomicAdd(reinterpret_cast<float2*>(ggrad + corner), add);
         }
     }
 }
@@ -550,17 +603,31 @@ __global__ void grid_scatter_kernel(ModelView mv, bool color, const int32_t* __r
 // Adam (dense)
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, float bc1, float bc2) {
+    m = 0.9f * m + 0.1f * g;
+    v = 0.999f * v + 0.001f * g * g;
+    p -= lr * (m / bc1) / (sqrtf(v / bc2) + kAdamEps);
+}
+
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, long long n, long long grid_floats, const StepState* __restrict__ st) {
     float lr_g = st->lr_grid, lr_m = st->lr_mlp, bc1 = st->bc1, bc2 = st->bc2;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float gi = g[i];
-        float mi = 0.9f * m[i] + 0.1f * gi;
-        float vi = 0.999f * v[i] + 0.001f * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        float lr = i < grid_floats ? lr_g : lr_m;
-        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + kAdamEps);
+    long long n4 = n / 4;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        float4 P = reinterpret_cast<float4*>(p)[i], Gv = reinterpret_cast<const float4*>(g)[i];
+        float4 M = reinterpret_cast<float4*>(m)[i], V = reinterpret_cast<float4*>(v)[i];
+        long long e = 4 * i;
+        adam_one(P.x, Gv.x, M.x, V.x, e < grid_floats ? lr_g : lr_m, bc1, bc2);
+        adam_one(P.y, Gv.y, M.y, V.y, e + 1 < grid_floats ? lr_g : lr_m, bc1, bc2);
+        adam_one(P.z, Gv.z, M.z, V.z, e + 2 < grid_floats ? lr_g : lr_m, bc1, bc2);
+        adam_one(P.w, Gv.w, M.w, V.w, e + 3 < grid_floats ? lr_g : lr_m, bc1, bc2);
+        reinterpret_cast<float4*>(p)[i] = P;
+        reinterpret_cast<float4*>(m)[i] = M;
+        reinterpret_cast<float4*>(v)[i] = V;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) {
+        long long e = 4 * n4 + threadIdx.x;
+        adam_one(p[e], g[e], m[e], v[e], e < grid_floats ? lr_g : lr_m, bc1, bc2);
     }
 }
 
@@ -688,7 +755,7 @@ static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const
     if (color)
         color_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
     else
-        endpoint_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
+        endpoint_loss_kernel<<<blocks_for((long long)B * 16, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
     unsigned gw = blocks_for(B, kWgChunk);
     for (int l = nl - 1; l >= 0; --l) {
         const float* Ain = l == 0 ? nb.X : nb.A[l - 1];
@@ -722,7 +789,8 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
     esrc = csrc;
     if (qat_bits > 0) {
         LevelTable lt = level_table(m->desc, m->layout);
-        ntbc_status st = launch_level_scale_zero(m->params, lt, qat_bits, ts->qmm, ts->qscale, ts->qzero, s);
+        ntbc_status st = launch_level_scale_zero(m->params, lt, qat_bits, ts->qmm, ts->qscale, ts->qzero, s,
+                                                 dynamic_qat ? ts->qat_flag : nullptr);
         if (st != NTBC_OK) return st;
         csrc.scale = ts->qscale;
         csrc.zero = ts->qzero;
@@ -950,7 +1018,7 @@ static void noalloc_net(const ModelView& mv, const float* params, bool color, co
     if (color)
         color_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
     else
-        endpoint_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
+        endpoint_loss_kernel<<<blocks_for((long long)B * 16, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
     unsigned gw = blocks_for(B, kWgChunk);
     for (int l = nl - 1; l >= 0; --l) {
         const float* Ain = l == 0 ? nb.X : nb.A[l - 1];
