@@ -47,11 +47,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--train-steps", type=int, default=1000, help="main-phase encode steps actually run")
+    ap.add_argument("--train-steps", type=int, default=FULL_MAIN_STEPS,
+                    help="main-phase encode steps actually run (the QAT phase adds 10 %%)")
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16")
+    ap.add_argument("--batch", action="store_true",
+                    help="batched load-time inference: 16 uneven materials in one persistent launch (CUDA graph)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="precision sweep: u8 / u4 QAT grids x FP32 / FP16 split / FP16 fast MLP inference")
     ap.add_argument("--quick", action="store_true",
                     help="inference only on random-init weights (no material, training, plain path or oracle)")
     return ap.parse_args()
@@ -277,6 +282,120 @@ def inference_roofline(nt, desc, ms):
     return roofline, terms
 
 
+def run_sweep(args):
+    """Inference precision sweep on trained 4k weights (one encode per grid width)."""
+    import torch
+    import paper_2407_09543_gb300 as nt
+    from oracle import bc as obc, ntbc as ont
+    dev = torch.device("cuda", 0)
+    side = args.side
+    nblk = (side // 4) ** 2
+    mat, desc, p0, tex_d, refs = build_workload(nt, torch, side, seed=0, dev=dev)
+    for t, fmt in enumerate(mat.formats):
+        nt.bc_reference_encode(fmt, tex_d[t], side, side, refs[t])
+    torch.cuda.synchronize()
+    ref_psnr = psnr_list(nt, obc, torch, mat, refs, side)
+    material = nt.Material.make(side, side, mat.formats, tex_d, refs)
+    cres, eres = nt.configs.res_lists(desc)
+    od = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=desc.hidden_layers, activation="selu")
+    ids = np.sort(np.random.default_rng(0).choice(nblk, 2000, replace=False))
+    rows = []
+    for bits in (8, 4):
+        model = nt.Model(desc)
+        model.set_params(torch.from_numpy(nt.configs.flatten(desc, p0)).to(dev))
+        model.train(material, nt.TrainConfig.make(steps=args.train_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1,
+                                                  grid_bits=bits, seed=0))
+        flat = torch.empty(model.n_params, device=dev)
+        model.get_params(flat)
+        params = nt.configs.unflatten(desc, flat.cpu().numpy())
+        codes, sc, zr = ont.export_grid(params["color_grid"] + params["endpoint_grid"], bits)
+        deq = ont.dequantize_grid(codes, sc, zr)
+        nc = desc.color_levels
+        for name, prec in (("fp32", nt.PREC_FP32), ("fp16", nt.PREC_FP16), ("fp16_fast", nt.PREC_FP16_FAST)):
+            model.export(grid_bits=bits, weight_prec=prec)
+            pw = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
+            for k in ("color_mlp", "endpoint_mlp"):
+                pw[k] = [((W.astype(np.float16) if prec else W).astype(np.float64),
+                          (b.astype(np.float16) if prec else b).astype(np.float64)) for W, b in params[k]]
+            er, cr = ont.forward_blocks(od, pw, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+            idt = torch.from_numpy(ids.astype(np.int32)).to(dev)
+            lay = model.layout
+            e = torch.empty(len(ids), lay.out_endpoint, device=dev)
+            c = torch.empty(len(ids), 16, lay.out_color, device=dev)
+            model.forward(idt, e, c)
+            outs = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in mat.formats]
+            model.infer_to_bc(outs)
+            torch.cuda.synchronize()
+            rel = max(float(np.max(np.abs(e.cpu().numpy() - er) / np.abs(er))),
+                      float(np.max(np.abs(c.cpu().numpy() - cr) / np.abs(cr))))
+            ref_blocks = ont.infer_blocks(od, pw, block_ids=ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+            mism = fields = 0
+            for t, fmt in enumerate(mat.formats):
+                got = outs[t].cpu().numpy().reshape(-1, 8)[ids]
+                unpack = obc.bc1_unpack if fmt == 1 else obc.bc4_unpack
+                a0, a1, ac = unpack(got)
+                b0, b1, bc_ = unpack(ref_blocks[t])
+                mism += int((a0 != b0).sum() + (a1 != b1).sum() + (ac != bc_).sum())
+                fields += len(ids) * 18
+            rows.append({"grid_bits": bits, "mlp": name, "max_rel_err_vs_fp64": rel,
+                         "field_mismatch": mism / fields, "psnr_db": psnr_list(nt, obc, torch, mat, outs, side)})
+        model.close()
+    print(json.dumps({"mode": "sweep", "workload": f"mat4k {side}x{side}", "train_steps": args.train_steps,
+                      "reference_bc_psnr_db": ref_psnr, "rows": rows}), flush=True)
+    return 0
+
+
+KIND_FORMAT = {"diffuse": 1, "normal": 1, "roughness": 4, "ao": 4}
+
+
+def run_batch(args):
+    """16 materials of uneven size (sides 512..4096, 2..5 textures), each with its own
+    12-level grid (16 .. side/2) and 3 x 64 SELU MLPs, random-init weights, decoded to BC
+    blocks in one persistent launch captured in a CUDA graph."""
+    import torch
+    import paper_2407_09543_gb300 as nt
+    dev = torch.device("cuda", 0)
+    spec = synth.material_batch_spec(seed=0, count=16)
+    models, outs, blocks = [], [], 0
+    for i, (side, kinds) in enumerate(spec):
+        formats = [KIND_FORMAT[k] for k in kinds]
+        desc = nt.configs.model_desc(formats, side, 12, 16, side // 2, 3, nt.ACT_SELU)
+        cres, eres = nt.configs.res_lists(desc)
+        p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), i)
+        m = nt.Model(desc)
+        m.set_params(torch.from_numpy(nt.configs.flatten(desc, synth.random_params_like(p0, seed=100 + i))).to(dev))
+        m.export(grid_bits=8, weight_prec=args.prec)
+        nb = (side // 4) ** 2
+        blocks += nb * len(formats)
+        models.append(m)
+        outs.append([torch.empty(nb * 8, dtype=torch.uint8, device=dev) for _ in formats])
+    batch = nt.Batch(models, outs)
+    stream = torch.cuda.Stream()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        batch.infer()
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batch.infer()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    times = time_events(torch, g.replay, args.steps, flush=lambda: flush_buf.fill_(1))
+    per_mat = batch.times_ms(torch.cuda.current_stream())
+    seq = time_events(torch, lambda: [m.infer_to_bc(o) for m, o in zip(models, outs)], max(3, args.steps // 4),
+                      flush=lambda: flush_buf.fill_(1))
+    ms = float(np.mean(times))
+    print(json.dumps({"mode": "batch", "materials": [{"side": side, "textures": len(kinds),
+                                                      "done_ms": round(t, 4)} for (side, kinds), t in zip(spec, per_mat)],
+                      "texture_blocks": blocks, "ms_per_step": round(ms, 4),
+                      "value": round(blocks / (ms * 1e-3) / 1e6, 3), "unit": "Mblocks/s",
+                      "sequential_single_launch_ms": round(float(np.mean(seq)), 4), "gpu_launches": 1,
+                      "graph": True}), flush=True)
+    batch.close()
+    return 0
+
+
 def run_quick(args):
     """Inference-only timing on random-init 4k weights (for profiling captures)."""
     import torch
@@ -315,6 +434,10 @@ def main():
         return run_reference(args)
     if args.quick:
         return run_quick(args)
+    if args.sweep:
+        return run_sweep(args)
+    if args.batch:
+        return run_batch(args)
     import torch
     import paper_2407_09543_gb300 as nt
     from oracle import bc as obc

@@ -229,6 +229,27 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out
 ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int n,
                          float* e_hat, float* c_hat, void* stream);
 
+/*
+ * Batched load-time inference (Sec. 4.4: inference runs once per material when it is
+ * loaded): many materials, each with its own model, decoded to BC blocks in one
+ * persistent launch. Every model must be exported with the same tensor-core precision
+ * (NTBC_PREC_FP16 or NTBC_PREC_FP16_FAST).
+ *   ntbc_batch_create  models: host array of n models; blocks_out: host array of n host
+ *                      arrays, each holding that material's per-texture DEVICE outputs.
+ *                      Uploads the launch description (allocates; not capturable).
+ *   ntbc_batch_infer   one counter reset and one kernel launch on `stream`; may be
+ *                      captured in a CUDA graph and replayed.
+ *   ntbc_batch_times   synchronises `stream`; ms (host double[n]) = each material's
+ *                      completion time after the start of the last launch
+ *                      (device global timer); NTBC_ETIMEOUT if a bounded wait gave up.
+ */
+typedef struct ntbc_batch ntbc_batch;
+ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out,
+                              ntbc_batch** out);
+ntbc_status ntbc_batch_infer(ntbc_batch* batch, void* stream);
+ntbc_status ntbc_batch_times(const ntbc_batch* batch, double* ms, void* stream);
+void ntbc_batch_free(ntbc_batch* batch);
+
 /* ------------------------------------------------------------------------- */
 /* Training (Sec. 3.2 losses and straight-through argmax; Sec. 3.3 QAT;        */
 /* Sec. 3.4 Adam + schedule)                                                 */

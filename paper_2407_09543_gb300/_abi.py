@@ -116,6 +116,10 @@ _SIGS = {
                                          c_float, _P, _P, _P]),
     "ntbc_adam_step": (c_int, [_P, _P, ctypes.c_long, ctypes.c_long, ctypes.POINTER(TrainConfig), _P]),
     "ntbc_sample_blocks": (c_int, [ctypes.c_uint64, ctypes.c_long, c_int, c_int, _P, _P]),
+    "ntbc_batch_create": (c_int, [ctypes.POINTER(_P), c_int, ctypes.POINTER(ctypes.POINTER(_P)), ctypes.POINTER(_P)]),
+    "ntbc_batch_infer": (c_int, [_P, _P]),
+    "ntbc_batch_times": (c_int, [_P, ctypes.POINTER(ctypes.c_double), _P]),
+    "ntbc_batch_free": (None, [_P]),
     "ntbc_train": (c_int, [_P, ctypes.POINTER(Material), ctypes.POINTER(TrainConfig), ctypes.POINTER(c_float), _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -252,3 +256,36 @@ class Model:
         out = (c_float * 6)()
         _check(lib.ntbc_train(self.handle, ctypes.byref(material), ctypes.byref(cfg), out, _stream(stream)))
         return list(out)
+
+
+class Batch:
+    """Many materials (each its own exported Model) decoded to BC blocks in one launch."""
+
+    def __init__(self, models, blocks_out):
+        self.models = list(models)
+        self.n = len(self.models)
+        self._outs = [(_P * len(o))(*[_ptr(b) for b in o]) for o in blocks_out]
+        outer = (ctypes.POINTER(_P) * self.n)(*[ctypes.cast(o, ctypes.POINTER(_P)) for o in self._outs])
+        handles = (_P * self.n)(*[m.handle for m in self.models])
+        h = _P()
+        _check(lib.ntbc_batch_create(handles, self.n, outer, ctypes.byref(h)))
+        self.handle = h
+
+    def infer(self, stream=None):
+        _check(lib.ntbc_batch_infer(self.handle, _stream(stream)))
+
+    def times_ms(self, stream=None):
+        out = (ctypes.c_double * self.n)()
+        _check(lib.ntbc_batch_times(self.handle, out, _stream(stream)))
+        return list(out)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.ntbc_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -234,7 +234,7 @@ static size_t simt_smem_bytes(const ModelView& mv, const WeightImage& wic, const
            (size_t)mv.n_textures * threads * sizeof(uint32_t);
 }
 
-static ntbc_status grid_sources(const ntbc_model* m, GridSrc& csrc, GridSrc& esrc) {
+ntbc_status grid_sources(const ntbc_model* m, GridSrc& csrc, GridSrc& esrc) {
     if (m->grid_bits < 0) return fail(NTBC_EINVAL, "model has not been exported (call ntbc_model_export or ntbc_model_load)");
     memset(&csrc, 0, sizeof(csrc));
     memset(&esrc, 0, sizeof(esrc));

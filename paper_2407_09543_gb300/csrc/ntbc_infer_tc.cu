@@ -16,6 +16,8 @@
 // 128 threads read their row of the accumulator (tcgen05.ld 32x32b) and apply
 // SELU (or the sigmoid on the output layer). The other warpgroups of the CTA
 // keep the SM busy while one waits on its MMA.
+#include <vector>
+
 #include "ntbc_internal.cuh"
 #include "ntbc_kernels.cuh"
 
@@ -254,10 +256,10 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     return __uint_as_float(v);
 }
 
-// a byte b as the float 1 + b * 2^-15 (byte placed in mantissa bits 8..15): exact,
-// and no integer-to-float conversion
-__device__ __forceinline__ float byte_as_unit(uint32_t word, uint32_t sel) {
-    return __uint_as_float(__byte_perm(word, 0x3F800000u, sel));
+// a byte b as the exact float b: placed in the low mantissa byte of 2^23, minus 2^23
+// (a byte permute and an add instead of an integer-to-float conversion)
+__device__ __forceinline__ float byte_as_float(uint32_t word, uint32_t sel) {
+    return __uint_as_float(__byte_perm(word, 0x4B000000u, sel)) - 8388608.f;
 }
 
 // integer i (0 <= i < 2^22) as float via the 2^23 magic number
@@ -286,8 +288,8 @@ __device__ __forceinline__ uint32_t ld_u16(const uint8_t* p) {
 
 // Grid features of one row (texel or block), level-major, 2 per level, followed by the
 // constant 1 of the layer-0 bias column; stored as FP16 chunks (high, and low halves when
-// split). Exported grids: bilinear interpolation of the codes (as 1 + q 2^-15) then the
-// dequantisation s (q - z) folded into one FMA with the per-level constants in lvl.
+// split). Exported grids: bilinear interpolation of the exact codes, then the
+// dequantisation s (q - z) L as one FMA with the per-level constants in lvl.
 template <bool SPLIT>
 __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src, const float2* lvl, float u, float v,
                                            int K0, unsigned char* A, unsigned char* Alo, int r, bool valid) {
@@ -301,10 +303,10 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
             if (src.codes) {
                 const uint8_t* gp = src.codes + o;
                 uint32_t a = ld_u16(gp), c = ld_u16(gp + 2), d = ld_u16(gp + b.row), e = ld_u16(gp + b.row + 2);
-                float y0 = b.w00 * byte_as_unit(a, 0x7604) + b.w01 * byte_as_unit(c, 0x7604) +
-                           b.w10 * byte_as_unit(d, 0x7604) + b.w11 * byte_as_unit(e, 0x7604);
-                float y1 = b.w00 * byte_as_unit(a, 0x7614) + b.w01 * byte_as_unit(c, 0x7614) +
-                           b.w10 * byte_as_unit(d, 0x7614) + b.w11 * byte_as_unit(e, 0x7614);
+                float y0 = b.w00 * byte_as_float(a, 0x7540) + b.w01 * byte_as_float(c, 0x7540) +
+                           b.w10 * byte_as_float(d, 0x7540) + b.w11 * byte_as_float(e, 0x7540);
+                float y1 = b.w00 * byte_as_float(a, 0x7541) + b.w01 * byte_as_float(c, 0x7541) +
+                           b.w10 * byte_as_float(d, 0x7541) + b.w11 * byte_as_float(e, 0x7541);
                 float2 k = lvl[l];
                 f0 = fmaf(k.x, y0, k.y);
                 f1 = fmaf(k.x, y1, k.y);
@@ -335,55 +337,65 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
     }
 }
 
-template <bool SPLIT>
-__global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
-infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSrc esrc, TcOut outs,
-                float* __restrict__ e_out, float* __restrict__ c_out) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint32_t tmem_slot;
-    __shared__ volatile int abort_flag[kTcMaxGroups];
-    const ModelView& mv = args.mv;
-    const int tid = threadIdx.x;
-    const int g = tid / kTcRows, r = tid % kTcRows;
-    const TcSmem sl = tc_smem_layout(args.img_bytes, mv.n_textures, SPLIT);
-    unsigned char* gbase = smem + sl.group_off + g * sl.group_bytes;
-    unsigned char* A = gbase + sl.a_off;
-    unsigned char* Alo = gbase + sl.lo_off;
-    uint8_t* palb = gbase + sl.pal_off;
-    uint32_t* eps = reinterpret_cast<uint32_t*>(gbase + sl.ep_off);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(gbase + sl.bar_off);
-    const float* tab = reinterpret_cast<const float*>(smem + sl.table_off);
-    float2* lvl = reinterpret_cast<float2*>(smem + sl.lvl_off);           // [net][level]: (32768 s, -s (32768 + z))
+// Shared-memory pointers of one warpgroup.
+struct TcGroup {
+    unsigned char* A;
+    unsigned char* Alo;
+    uint8_t* palb;
+    uint32_t* eps;
+    uint64_t* bar;
+    uint32_t tmem, tmem_row;
+    int g, r;
+};
 
-    // ---- set-up: weight image, ones tile, k/255 table, level constants, TMEM, barriers
-    for (int i = tid; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
-    for (int i = tid; i < kTcRows * 16; i += blockDim.x) {
-        int rr = i / 16, k = i % 16;
-        __half hi = __float2half_rn(kLog2e);
-        __half lo = __float2half_rn(kLog2e - __half2float(hi));
-        *reinterpret_cast<__half*>(smem + sl.ones_off + core_byte(rr, k, 16)) = k == 0 ? hi : __float2half(0.f);
-        *reinterpret_cast<__half*>(smem + sl.ones_off + kTcRows * 32 + core_byte(rr, k, 16)) = k == 0 ? lo : __float2half(0.f);
-    }
-    for (int i = tid; i < 256; i += blockDim.x) reinterpret_cast<float*>(smem + sl.table_off)[i] = __fdiv_rn((float)i, 255.f);
-    for (int i = tid; i < 2 * NTBC_MAX_LEVELS; i += blockDim.x) {
+// Per-level dequantisation constants of both grids: (s L, -s z L).
+__device__ __forceinline__ void load_level_constants(const ModelView& mv, const GridSrc& csrc, const GridSrc& esrc,
+                                                     float2* lvl) {
+    for (int i = threadIdx.x; i < 2 * NTBC_MAX_LEVELS; i += blockDim.x) {
         int net = i / NTBC_MAX_LEVELS, l = i % NTBC_MAX_LEVELS;
         const GridSrc& src = net ? esrc : csrc;
         int L = net ? mv.endpoint.levels : mv.color.levels;
         float2 k = make_float2(0.f, 0.f);
         if (src.codes && l < L) {
             float sc = src.scale[l], z = src.zero[l];
-            k = make_float2(sc * 32768.f * kLog2e, -sc * (32768.f + z) * kLog2e);
+            k = make_float2(sc * kLog2e, -sc * z * kLog2e);
         }
         lvl[i] = k;
     }
-    if (r == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        abort_flag[g] = 0;
+}
+
+// Constant tiles (L high / low for the bias K block) and the k/255 table.
+__device__ __forceinline__ void load_constants(unsigned char* smem, const TcSmem& sl) {
+    for (int i = threadIdx.x; i < kTcRows * 16; i += blockDim.x) {
+        int rr = i / 16, k = i % 16;
+        __half hi = __float2half_rn(kLog2e);
+        __half lo = __float2half_rn(kLog2e - __half2float(hi));
+        *reinterpret_cast<__half*>(smem + sl.ones_off + core_byte(rr, k, 16)) = k == 0 ? hi : __float2half(0.f);
+        *reinterpret_cast<__half*>(smem + sl.ones_off + kTcRows * 32 + core_byte(rr, k, 16)) = k == 0 ? lo : __float2half(0.f);
     }
-    const int ncols = args.groups == 1 ? 64 : (args.groups == 2 ? 128 : 256);
-    if (tid < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) reinterpret_cast<float*>(smem + sl.table_off)[i] = __fdiv_rn((float)i, 255.f);
+}
+
+// TMEM columns, group barriers; every thread returns its group's view.
+__device__ __forceinline__ TcGroup setup_groups(unsigned char* smem, const TcSmem& sl, int groups, uint32_t* tmem_slot,
+                                                volatile int* abort_flag) {
+    TcGroup G;
+    G.g = threadIdx.x / kTcRows;
+    G.r = threadIdx.x % kTcRows;
+    unsigned char* gbase = smem + sl.group_off + G.g * sl.group_bytes;
+    G.A = gbase + sl.a_off;
+    G.Alo = gbase + sl.lo_off;
+    G.palb = gbase + sl.pal_off;
+    G.eps = reinterpret_cast<uint32_t*>(gbase + sl.ep_off);
+    G.bar = reinterpret_cast<uint64_t*>(gbase + sl.bar_off);
+    if (G.r == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(G.bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        abort_flag[G.g] = 0;
+    }
+    const int ncols = groups == 1 ? 64 : (groups == 2 ? 128 : 256);
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
@@ -391,14 +403,43 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_slot + (uint32_t)(g * kTcColsPerGroup);
-    const uint32_t tmem_row = tmem + ((uint32_t)((r / 32) * 32) << 16);   // this warp's 32 lanes
-    uint32_t phase = 0;
-    const int n_units = (args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
+    G.tmem = *tmem_slot + (uint32_t)(G.g * kTcColsPerGroup);
+    G.tmem_row = G.tmem + ((uint32_t)((G.r / 32) * 32) << 16);   // this warp's 32 lanes
+    return G;
+}
+
+__device__ __forceinline__ void teardown_groups(const TcGroup& G, int groups, bool ok, uint32_t phase, int* err,
+                                                uint32_t tmem_slot) {
+    // a group whose wait gave up records it and lets the MMA still in flight land
+    // (bounded wait on the phase that gave up) before TMEM is freed
+    if (!ok) {
+        if (G.r == 0) atomicExch(err, 1);
+        mbar_wait(G.bar, phase ^ 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    const int ncols = groups == 1 ? 64 : (groups == 2 ? 128 : 256);
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(ncols));
+}
+
+// One work unit (128 blocks): endpoint network, palettes, then 16 colour tiles.
+template <bool SPLIT>
+__device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& csrc, const GridSrc& esrc, const TcOut& outs,
+                                          float* __restrict__ e_out, float* __restrict__ c_out, int unit,
+                                          unsigned char* smem, const TcSmem& sl, const TcGroup& G, uint32_t& phase,
+                                          volatile int* abort_flag) {
+    const ModelView& mv = args.mv;
+    const int g = G.g, r = G.r;
+    unsigned char* A = G.A;
+    unsigned char* Alo = G.Alo;
+    uint8_t* palb = G.palb;
+    uint32_t* eps = G.eps;
+    uint64_t* bar = G.bar;
+    const uint32_t tmem = G.tmem, tmem_row = G.tmem_row;
+    const float* tab = reinterpret_cast<const float*>(smem + sl.table_off);
+    const float2* lvl = reinterpret_cast<const float2*>(smem + sl.lvl_off);
     const int T = mv.n_textures;
     bool ok = true;
-
-    for (int unit = blockIdx.x * args.groups + g; unit < n_units && ok; unit += gridDim.x * args.groups) {
         // ================= endpoint network: row r = block r of the unit
         {
             const TcNet& net = args.net[1];
@@ -537,16 +578,101 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
                 }
             }
         }
+    
+    return ok;
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
+infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSrc esrc, TcOut outs,
+                float* __restrict__ e_out, float* __restrict__ c_out) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag[kTcMaxGroups];
+    const TcSmem sl = tc_smem_layout(args.img_bytes, args.mv.n_textures, SPLIT);
+    for (int i = threadIdx.x; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
+    load_constants(smem, sl);
+    load_level_constants(args.mv, csrc, esrc, reinterpret_cast<float2*>(smem + sl.lvl_off));
+    TcGroup G = setup_groups(smem, sl, args.groups, &tmem_slot, abort_flag);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int n_units = (args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
+    for (int unit = blockIdx.x * args.groups + G.g; unit < n_units && ok; unit += gridDim.x * args.groups)
+        ok = process_unit<SPLIT>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, abort_flag);
+    teardown_groups(G, args.groups, ok, phase, args.err, tmem_slot);
+}
+
+// ---------------------------------------------------------------------------
+// batched load-time inference: many materials in one persistent launch
+// ---------------------------------------------------------------------------
+
+struct TcMat {
+    TcArgs args;
+    const uint4* img;
+    GridSrc csrc, esrc;
+    TcOut outs;
+    int first_cta_unit;          // index of this material's first CTA-unit (one unit per group)
+    int units;
+};
+
+struct TcBatchHeader {
+    int n_mats, total_cta_units, groups, img_bytes, max_textures;
+    int* done;                   // [n_mats] units completed
+    unsigned long long* stamps;  // [n_mats + 1]: kernel start, then each material's completion (globaltimer, ns)
+    int* err;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The grid strides over CTA-units; all groups of a CTA work on the same material, so the
+// weight image is reloaded (after a CTA barrier) only when the CTA crosses into the next
+// material. A group that gave up keeps walking the CTA-units (skipping the work) so that
+// the CTA barriers stay uniform.
+template <bool SPLIT>
+__global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
+infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag[kTcMaxGroups];
+    __shared__ TcMat cur;
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr.stamps[0] = global_ns();
+    const TcSmem sl = tc_smem_layout(hdr.img_bytes, hdr.max_textures, SPLIT);
+    load_constants(smem, sl);
+    TcGroup G = setup_groups(smem, sl, hdr.groups, &tmem_slot, abort_flag);
+    uint32_t phase = 0;
+    bool ok = true;
+    int m = -1;
+    for (int j = blockIdx.x; j < hdr.total_cta_units; j += gridDim.x) {
+        int mj = m < 0 ? 0 : m;
+        while (mj + 1 < hdr.n_mats && mats[mj + 1].first_cta_unit <= j) ++mj;
+        if (mj != m) {                                   // uniform across the CTA
+            tc_fence_before();
+            __syncthreads();
+            if (threadIdx.x == 0) cur = mats[mj];
+            __syncthreads();
+            for (int i = threadIdx.x; i < cur.args.img_bytes / 16; i += blockDim.x)
+                reinterpret_cast<uint4*>(smem)[i] = cur.img[i];
+            load_level_constants(cur.args.mv, cur.csrc, cur.esrc, reinterpret_cast<float2*>(smem + sl.lvl_off));
+            proxy_fence();
+            __syncthreads();
+            tc_fence_after();
+            m = mj;
+        }
+        int unit = (j - cur.first_cta_unit) * hdr.groups + G.g;
+        if (ok && unit < cur.units) {
+            ok = process_unit<SPLIT>(cur.args, cur.csrc, cur.esrc, cur.outs, nullptr, nullptr, unit, smem, sl, G, phase,
+                                     abort_flag);
+            if (ok && G.r == 0) {
+                __threadfence();
+                if (atomicAdd(&hdr.done[m], 1) + 1 == cur.units) hdr.stamps[m + 1] = global_ns();
+            }
+        }
     }
-    // a group whose wait gave up records it and lets the MMA still in flight land
-    // (bounded wait on the phase that gave up) before TMEM is freed
-    if (!ok) {
-        if (r == 0) atomicExch(args.err, 1);
-        mbar_wait(bar, phase ^ 1);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(ncols));
+    teardown_groups(G, hdr.groups, ok, phase, hdr.err, tmem_slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -599,11 +725,13 @@ static TcArgs tc_args(const ntbc_model* m) {
     return a;
 }
 
-static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes) {
+// static_bytes: the kernel's static shared variables (the batch kernel keeps a copy of
+// the current material's launch description)
+static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, size_t static_bytes = 256) {
     for (int groups = kTcMaxGroups; groups >= 1; --groups) {
         TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split);
         size_t bytes = (size_t)sl.group_off + (size_t)groups * sl.group_bytes;
-        if (bytes + 256 <= 227 * 1024) {             // room for the kernel's static shared variables
+        if (bytes + static_bytes <= 227 * 1024) {
             *smem_bytes = bytes;
             return groups;
         }
@@ -658,3 +786,130 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
 }
 
 }  // namespace ntbc
+
+struct ntbc_batch {
+    int n = 0, groups = 0, grid = 0;
+    bool split = true;
+    size_t smem = 0;
+    ntbc::TcBatchHeader hdr{};
+    ntbc::TcMat* d_mats = nullptr;
+    unsigned char* d_mem = nullptr;     // done counters, stamps, error flag
+};
+
+namespace ntbc {
+
+static ntbc_status batch_fail_free(ntbc_batch* b, ntbc_status st) {
+    if (b) {
+        cudaFree(b->d_mats);
+        cudaFree(b->d_mem);
+        delete b;
+    }
+    return st;
+}
+
+}  // namespace ntbc
+
+extern "C" {
+
+ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out, ntbc_batch** out) {
+    using namespace ntbc;
+    clear_error();
+    if (!models || !blocks_out || !out || n <= 0) return fail(NTBC_EINVAL, "need models, outputs and n > 0");
+    *out = nullptr;
+    int prec = -1, max_tex = 0, max_img = 0, total = 0;
+    std::vector<TcMat> mats(n);
+    for (int i = 0; i < n; ++i) {
+        const ntbc_model* m = models[i];
+        if (!m || !blocks_out[i]) return fail(NTBC_EINVAL, "material %d: null model or output list", i);
+        if (m->weight_prec == NTBC_PREC_FP32 || m->grid_bits < 0 || !m->umma_img)
+            return fail(NTBC_EINVAL, "material %d: export the model with NTBC_PREC_FP16 or NTBC_PREC_FP16_FAST first", i);
+        if (prec >= 0 && m->weight_prec != prec) return fail(NTBC_EINVAL, "all materials of a batch need the same precision");
+        prec = m->weight_prec;
+        TcMat& t = mats[i];
+        memset(&t, 0, sizeof(t));
+        t.args = tc_args(m);
+        t.args.n = (m->desc.width / 4) * (m->desc.height / 4);
+        t.args.mode = 0;
+        t.img = reinterpret_cast<const uint4*>(m->umma_img);
+        ntbc_status st = grid_sources(m, t.csrc, t.esrc);
+        if (st != NTBC_OK) return st;
+        for (int k = 0; k < m->desc.n_textures; ++k) {
+            uint8_t* o = blocks_out[i][k];
+            if (!o || (reinterpret_cast<uintptr_t>(o) & 7)) return fail(NTBC_EINVAL, "material %d texture %d: output null or not 8-byte aligned", i, k);
+            t.outs.p[k] = o;
+        }
+        t.units = (t.args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
+        max_tex = std::max(max_tex, m->desc.n_textures);
+        max_img = std::max(max_img, t.args.img_bytes);
+    }
+    ntbc_batch* b = new ntbc_batch();
+    b->n = n;
+    b->split = prec == NTBC_PREC_FP16;
+    TcArgs probe;
+    memset(&probe, 0, sizeof(probe));
+    probe.img_bytes = max_img;
+    b->groups = tc_groups(probe, max_tex, b->split, &b->smem, sizeof(TcMat) + 256);
+    if (b->groups == 0) return batch_fail_free(b, fail(NTBC_EUNSUPPORTED, "batch: shared memory too small"));
+    for (int i = 0; i < n; ++i) {
+        mats[i].first_cta_unit = total;
+        mats[i].args.groups = b->groups;
+        total += (mats[i].units + b->groups - 1) / b->groups;
+    }
+    size_t mem = (size_t)n * sizeof(int) + (size_t)(n + 1) * sizeof(unsigned long long) + 16;
+    ntbc_status st = device_alloc((void**)&b->d_mats, (size_t)n * sizeof(TcMat), "batch descriptors");
+    if (st == NTBC_OK) st = device_alloc((void**)&b->d_mem, mem, "batch counters");
+    if (st != NTBC_OK) return batch_fail_free(b, st);
+    b->hdr.n_mats = n;
+    b->hdr.total_cta_units = total;
+    b->hdr.groups = b->groups;
+    b->hdr.img_bytes = max_img;
+    b->hdr.max_textures = max_tex;
+    b->hdr.stamps = reinterpret_cast<unsigned long long*>(b->d_mem);
+    b->hdr.done = reinterpret_cast<int*>(b->d_mem + (size_t)(n + 1) * sizeof(unsigned long long));
+    b->hdr.err = b->hdr.done + n;
+    for (int i = 0; i < n; ++i) mats[i].args.err = b->hdr.err;
+    cudaError_t e = cudaMemcpy(b->d_mats, mats.data(), (size_t)n * sizeof(TcMat), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_mem, 0, mem);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = b->split ? cudaFuncSetAttribute(infer_tc_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem)
+                     : cudaFuncSetAttribute(infer_tc_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) return batch_fail_free(b, cuda_fail(e, "batch set-up"));
+    b->grid = std::min(sms, total);
+    *out = b;
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_batch_infer(ntbc_batch* b, void* stream) {
+    using namespace ntbc;
+    clear_error();
+    if (!b) return fail(NTBC_EINVAL, "null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.done, 0, (size_t)b->n * sizeof(int), s));
+    if (b->split)
+        infer_tc_batch_kernel<true><<<b->grid, kTcRows * b->groups, b->smem, s>>>(b->hdr, b->d_mats);
+    else
+        infer_tc_batch_kernel<false><<<b->grid, kTcRows * b->groups, b->smem, s>>>(b->hdr, b->d_mats);
+    NTBC_CHECK_LAUNCH("batched ntbc inference (tcgen05)");
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_batch_times(const ntbc_batch* b, double* ms, void* stream) {
+    using namespace ntbc;
+    clear_error();
+    if (!b || !ms) return fail(NTBC_EINVAL, "null argument");
+    NTBC_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<unsigned long long> st(b->n + 1);
+    int err = 0;
+    NTBC_CHECK_CUDA(cudaMemcpy(st.data(), b->hdr.stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    NTBC_CHECK_CUDA(cudaMemcpy(&err, b->hdr.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return fail(NTBC_ETIMEOUT, "a bounded wait in the batched inference gave up");
+    for (int i = 0; i < b->n; ++i) ms[i] = st[i + 1] >= st[0] ? (double)(st[i + 1] - st[0]) * 1e-6 : -1.0;
+    return NTBC_OK;
+}
+
+void ntbc_batch_free(ntbc_batch* b) { ntbc::batch_fail_free(b, NTBC_OK); }
+
+}  // extern "C"

@@ -106,6 +106,9 @@ __device__ __forceinline__ void grid_features(const NetView& nv, const GridSrc& 
 
 void ntbc_train_release(ntbc_model* m);
 
+// grid sources of an exported model (codes + scale / zero, or FP32 grids)
+ntbc_status grid_sources(const ntbc_model* m, GridSrc& csrc, GridSrc& esrc);
+
 // tensor-core inference (FP16 weights): weight image preparation and launch
 ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s);
 ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int32_t* ids, int n, float* e_out,

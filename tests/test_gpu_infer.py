@@ -215,3 +215,38 @@ def test_tensor_core_ragged_and_fp32_grids(prec):
     np.testing.assert_allclose(c, cr, rtol=tol, atol=1e-5)
     check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ont.infer_blocks(odesc, p16),
                  0.001 if prec == 1 else MISMATCH_FAST)
+
+
+def _oracle_trained(bits, seed=5):
+    """Weights trained by the oracle (FP64 Adam, QAT at `bits`) on a 64^2 three-texture material:
+    realistic, sharper weights than random ones, and none of it comes from the CUDA path."""
+    from oracle import philox
+    mat = synth.make_material("trained", 64, ["sine_rgb", "sine_r", "sine_rgb"], seed)
+    desc = nt.configs.model_desc(mat.formats, 64, 4, 8, 32, 3, nt.ACT_SELU)
+    cres, eres = nt.configs.res_lists(desc)
+    odesc = ont.ModelDesc(64, 64, mat.formats, cres, eres, hidden_layers=3, activation="selu")
+    p0 = synth.init_params(cres, eres, 2, odesc.mlp_dims("color"), odesc.mlp_dims("endpoint"), seed)
+    refs = [obc.encode(f, t, 64, 64) for f, t in zip(mat.formats, mat.textures)]
+    cfg = ont.TrainConfig(steps=200, batch_texels=1024, qat_fraction=0.1, grid_bits=bits)
+    p1, _ = ont.train(odesc, p0, mat.textures, refs, cfg, lambda s: philox.sample_blocks(1, s, 64, odesc.n_blocks))
+    p32 = nt.configs.unflatten(desc, nt.configs.flatten(desc, p1))          # the float32 weights both sides use
+    return mat, desc, odesc, p32
+
+
+@pytest.mark.parametrize("bits", [8, 4])
+def test_trained_weights_parity_all_modes(bits):
+    mat, desc, odesc, params = _oracle_trained(bits)
+    oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], bits)
+    deq = ont.dequantize_grid(oc, os_, oz)
+    nc = desc.color_levels
+    ids = np.arange(odesc.n_blocks)
+    for prec, rtol, mism in ((nt.PREC_FP32, RTOL, 0.001), (nt.PREC_FP16, RTOL, 0.001),
+                             (nt.PREC_FP16_FAST, RTOL_FAST, MISMATCH_FAST)):
+        model = gpu_model(desc, params, grid_bits=bits, weight_prec=prec)
+        pw = params if prec == nt.PREC_FP32 else oracle_params_fp16(params)
+        e, c = gpu_forward(model, ids)
+        er, cr = ont.forward_blocks(odesc, pw, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+        np.testing.assert_allclose(e, er, rtol=rtol, atol=1e-6)
+        np.testing.assert_allclose(c, cr, rtol=rtol, atol=1e-6)
+        ref = ont.infer_blocks(odesc, pw, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+        check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ref, mism)
