@@ -27,7 +27,7 @@ constexpr int kTcRows = 128;               // M of every MMA: blocks (endpoint) 
 constexpr int kTcUnitBlocks = 128;
 constexpr int kTcTiles = kTcUnitBlocks * 16 / kTcRows;   // 16 colour tiles per unit
 constexpr int kTcMaxGroups = 4;
-constexpr int kTcColsPerGroup = 64;
+constexpr int kTcColsPerGroup = 128;           // two 64-column accumulator regions per group
 constexpr int kTcPalBytes = 12;            // integer palette bytes per block per texture
 constexpr long long kTcWaitLimit = 1LL << 26;
 
@@ -115,8 +115,8 @@ __device__ __forceinline__ void st_row8_split(unsigned char* hi_tile, unsigned c
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         __half2 h = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-        float2 f = __half22float2(h);
-        __half2 lo = __floats2half2_rn(v[2 * j] - f.x, v[2 * j + 1] - f.y);
+        float2 r = __ffma2_rn(__half22float2(h), make_float2(-1.f, -1.f), make_float2(v[2 * j], v[2 * j + 1]));
+        __half2 lo = __floats2half2_rn(r.x, r.y);
         hw[j] = *reinterpret_cast<uint32_t*>(&h);
         lw[j] = *reinterpret_cast<uint32_t*>(&lo);
     }
@@ -138,6 +138,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // SELU(z) L from a = z L:  lambda max(a, 0) + lambda alpha L (2^min(a, 0) - 1)
 __device__ __forceinline__ float selu_l2(float a) {
     return fmaf(kSeluLambda, fmaxf(a, 0.f), fmaf(kSeluLA * kLog2e, ex2_approx(fminf(a, 0.f)), -kSeluLA * kLog2e));
+}
+
+// SELU on a pair of units with packed FP32 (two lanes per instruction)
+__device__ __forceinline__ float2 selu2_l2(float2 a) {
+    float2 e = make_float2(ex2_approx(fminf(a.x, 0.f)), ex2_approx(fminf(a.y, 0.f)));
+    float2 t = __ffma2_rn(make_float2(kSeluLA * kLog2e, kSeluLA * kLog2e), e,
+                          make_float2(-kSeluLA * kLog2e, -kSeluLA * kLog2e));
+    return __ffma2_rn(make_float2(kSeluLambda, kSeluLambda), make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)), t);
 }
 
 // sigmoid(z) from a = z L
@@ -244,7 +252,12 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, unsigned char
         tmem_ld16(tmem_row + c0 + 16, v + 16);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = act == NTBC_ACT_SELU ? selu_l2(v[j]) : fmaxf(v[j], 0.f);
+        for (int j = 0; j < 32; j += 2) {
+            float2 y = act == NTBC_ACT_SELU ? selu2_l2(make_float2(v[j], v[j + 1]))
+                                            : make_float2(fmaxf(v[j], 0.f), fmaxf(v[j + 1], 0.f));
+            v[j] = y.x;
+            v[j + 1] = y.y;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) st_row8_split<SPLIT>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
     }
@@ -256,10 +269,12 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     return __uint_as_float(v);
 }
 
-// a byte b as the exact float b: placed in the low mantissa byte of 2^23, minus 2^23
-// (a byte permute and an add instead of an integer-to-float conversion)
-__device__ __forceinline__ float byte_as_float(uint32_t word, uint32_t sel) {
-    return __uint_as_float(__byte_perm(word, 0x4B000000u, sel)) - 8388608.f;
+// the two codes (bytes 0 and 1) of a corner as exact floats: each byte lands in the low
+// mantissa byte of 2^23, then one packed subtract of 2^23 (no integer-to-float conversion)
+__device__ __forceinline__ float2 corner_codes(uint32_t word) {
+    return __fadd2_rn(make_float2(__uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540)),
+                                  __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7541))),
+                      make_float2(-8388608.f, -8388608.f));
 }
 
 // integer i (0 <= i < 2^22) as float via the 2^23 magic number
@@ -268,17 +283,22 @@ __device__ __forceinline__ float small_int_float(int i) { return __int_as_float(
 // corner-aligned bilinear set-up of level l (same arithmetic as bilinear_at, with the
 // per-level constants precomputed as floats)
 __device__ __forceinline__ Bilinear bilinear_tc(const NetView& nv, int l, float u, float v) {
-    float px = u * nv.resm1[l], py = v * nv.resm1[l];
+    float2 p = __fmul2_rn(make_float2(u, v), make_float2(nv.resm1[l], nv.resm1[l]));
     int res = nv.res[l];
-    int ix = min((int)px, res - 2), iy = min((int)py, res - 2);    // px, py >= 0: truncation is floor
-    float fx = px - small_int_float(ix), fy = py - small_int_float(iy);
+    int ix = min((int)p.x, res - 2), iy = min((int)p.y, res - 2);    // p >= 0: truncation is floor
+    float2 fl = __fadd2_rn(make_float2(__int_as_float(ix + 0x4B000000), __int_as_float(iy + 0x4B000000)),
+                           make_float2(-8388608.f, -8388608.f));
+    float2 f = __fadd2_rn(p, make_float2(-fl.x, -fl.y));                 // (fx, fy)
+    float2 g = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-f.x, -f.y)); // (1 - fx, 1 - fy)
+    float2 w0 = __fmul2_rn(make_float2(g.y, g.y), make_float2(g.x, f.x));  // (w00, w01)
+    float2 w1 = __fmul2_rn(make_float2(f.y, f.y), make_float2(g.x, f.x));  // (w10, w11)
     Bilinear b;
     b.base = ((long long)iy * res + ix) * 2;
     b.row = res * 2;
-    b.w00 = (1.f - fx) * (1.f - fy);
-    b.w01 = fx * (1.f - fy);
-    b.w10 = (1.f - fx) * fy;
-    b.w11 = fx * fy;
+    b.w00 = w0.x;
+    b.w01 = w0.y;
+    b.w10 = w1.x;
+    b.w11 = w1.y;
     return b;
 }
 
@@ -303,13 +323,14 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
             if (src.codes) {
                 const uint8_t* gp = src.codes + o;
                 uint32_t a = ld_u16(gp), c = ld_u16(gp + 2), d = ld_u16(gp + b.row), e = ld_u16(gp + b.row + 2);
-                float y0 = b.w00 * byte_as_float(a, 0x7540) + b.w01 * byte_as_float(c, 0x7540) +
-                           b.w10 * byte_as_float(d, 0x7540) + b.w11 * byte_as_float(e, 0x7540);
-                float y1 = b.w00 * byte_as_float(a, 0x7541) + b.w01 * byte_as_float(c, 0x7541) +
-                           b.w10 * byte_as_float(d, 0x7541) + b.w11 * byte_as_float(e, 0x7541);
+                float2 y = __fmul2_rn(make_float2(b.w00, b.w00), corner_codes(a));
+                y = __ffma2_rn(make_float2(b.w01, b.w01), corner_codes(c), y);
+                y = __ffma2_rn(make_float2(b.w10, b.w10), corner_codes(d), y);
+                y = __ffma2_rn(make_float2(b.w11, b.w11), corner_codes(e), y);
                 float2 k = lvl[l];
-                f0 = fmaf(k.x, y0, k.y);
-                f1 = fmaf(k.x, y1, k.y);
+                float2 f = __ffma2_rn(make_float2(k.x, k.x), y, make_float2(k.y, k.y));
+                f0 = f.x;
+                f1 = f.y;
             } else {
                 const float* gp = src.f32 + o;
                 float2 a = __ldg(reinterpret_cast<const float2*>(gp));
@@ -393,7 +414,7 @@ __device__ __forceinline__ TcGroup setup_groups(unsigned char* smem, const TcSme
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag[G.g] = 0;
     }
-    const int ncols = groups == 1 ? 64 : (groups == 2 ? 128 : 256);
+    const int ncols = groups == 1 ? 128 : (groups == 2 ? 256 : 512);
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(ncols));
@@ -418,8 +439,108 @@ __device__ __forceinline__ void teardown_groups(const TcGroup& G, int groups, bo
     }
     tc_fence_before();
     __syncthreads();
-    const int ncols = groups == 1 ? 64 : (groups == 2 ? 128 : 256);
+    const int ncols = groups == 1 ? 128 : (groups == 2 ? 256 : 512);
     if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(ncols));
+}
+
+// MMAs of K blocks kc0 .. kc1-1 of layer l (A tile of K0 columns for layer 0, 64
+// afterwards; when split each block twice, high and low halves) and, with `bias`, the
+// bias K block from the constant tiles, into the accumulator at tmem_d.
+template <bool SPLIT>
+__device__ __forceinline__ void issue_steps(const TcLayer& L, int l, unsigned char* smem, unsigned char* A,
+                                            const TcSmem& sl, uint32_t tmem_d, int kc0, int kc1, bool bias) {
+    uint32_t idesc = umma_idesc(L.N);
+    uint32_t a_base = smem_u32(A), b_base = smem_u32(smem + L.img);
+    int Ka = l == 0 ? L.K : 64;
+    for (int kc = kc0; kc < kc1; ++kc) {
+        uint64_t ad = umma_desc(a_base + kc * 256, 128, (Ka / 8) * 128);
+        uint64_t bd = umma_desc(b_base + kc * 256, 128, (L.K / 8) * 128);
+        umma_f16(tmem_d, ad, bd, idesc, kc > 0);
+        if (SPLIT) {
+            uint64_t lo = umma_desc(a_base + (sl.lo_off - sl.a_off) + kc * 256, 128, (Ka / 8) * 128);
+            umma_f16(tmem_d, lo, bd, idesc, 1);
+        }
+    }
+    if (bias) {
+        uint64_t bd = umma_desc(b_base + (Ka / 16) * 256, 128, (L.K / 8) * 128);
+        umma_f16(tmem_d, umma_desc(smem_u32(smem + sl.ones_off), 128, 256), bd, idesc, 1);
+        if (SPLIT) umma_f16(tmem_d, umma_desc(smem_u32(smem + sl.ones_off + kTcRows * 32), 128, 256), bd, idesc, 1);
+    }
+}
+
+// Group barrier after this thread's shared-memory writes and TMEM loads; false (for the
+// whole group) once a bounded wait of the group has given up.
+__device__ __forceinline__ bool group_barrier(int g, volatile int* abort_flag) {
+    proxy_fence();
+    tc_fence_before();
+    group_sync(g);
+    return abort_flag[g] == 0;
+}
+
+__device__ __forceinline__ void wait_mma(uint64_t* bar, uint32_t& phase, int g, volatile int* abort_flag) {
+    if (!mbar_wait(bar, phase)) abort_flag[g] = 1;
+    phase ^= 1;
+    tc_fence_after();
+}
+
+// 32 accumulator columns (c0 .. c0 + 31) -> activation -> A columns c0 .. c0 + 31
+template <bool SPLIT>
+__device__ __forceinline__ void epilogue_half(uint32_t src_row, int c0, unsigned char* A, unsigned char* Alo, int r,
+                                              int act) {
+    float v[32];
+    tmem_ld16(src_row + c0, v);
+    tmem_ld16(src_row + c0 + 16, v + 16);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+        float2 y = act == NTBC_ACT_SELU ? selu2_l2(make_float2(v[j], v[j + 1]))
+                                        : make_float2(fmaxf(v[j], 0.f), fmaxf(v[j + 1], 0.f));
+        v[j] = y.x;
+        v[j + 1] = y.y;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st_row8_split<SPLIT>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
+}
+
+// All layers of one MLP on the A tile the gather wrote. Accumulators alternate between the
+// group's two TMEM regions, and each hidden epilogue runs in two halves: once the first 32
+// activations of every row are in shared memory, the next layer's first two K blocks are
+// issued, so they run on the tensor core while the second half is computed. Leaves the
+// output layer's accumulator row at *out_row.
+template <bool SPLIT>
+__device__ __forceinline__ bool run_mlp(const TcNet& net, int act, unsigned char* smem, const TcSmem& sl,
+                                        const TcGroup& G, uint32_t& phase, uint32_t& region, volatile int* abort_flag,
+                                        uint32_t* out_row) {
+    if (!group_barrier(G.g, abort_flag)) return false;
+    uint32_t cur = region;
+    if (G.r == 0) {
+        tc_fence_after();
+        issue_steps<SPLIT>(net.layer[0], 0, smem, G.A, sl, G.tmem + 64 * cur, 0, net.layer[0].K / 16, false);
+        umma_commit(G.bar);
+    }
+    wait_mma(G.bar, phase, G.g, abort_flag);
+    for (int l = 1; l < net.n_layers; ++l) {
+        uint32_t nxt = cur ^ 1;
+        uint32_t src_row = G.tmem_row + 64 * cur;
+        epilogue_half<SPLIT>(src_row, 0, G.A, G.Alo, G.r, act);
+        if (!group_barrier(G.g, abort_flag)) return false;
+        if (G.r == 0) {
+            tc_fence_after();
+            issue_steps<SPLIT>(net.layer[l], l, smem, G.A, sl, G.tmem + 64 * nxt, 0, 2, false);
+        }
+        epilogue_half<SPLIT>(src_row, 32, G.A, G.Alo, G.r, act);
+        if (!group_barrier(G.g, abort_flag)) return false;
+        if (G.r == 0) {
+            tc_fence_after();
+            issue_steps<SPLIT>(net.layer[l], l, smem, G.A, sl, G.tmem + 64 * nxt, 2, 4, true);
+            umma_commit(G.bar);
+        }
+        wait_mma(G.bar, phase, G.g, abort_flag);
+        cur = nxt;
+    }
+    region = cur ^ 1;
+    *out_row = G.tmem_row + 64 * cur;
+    return abort_flag[G.g] == 0;
 }
 
 // One work unit (128 blocks): endpoint network, palettes, then 16 colour tiles.
@@ -427,7 +548,7 @@ template <bool SPLIT>
 __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& csrc, const GridSrc& esrc, const TcOut& outs,
                                           float* __restrict__ e_out, float* __restrict__ c_out, int unit,
                                           unsigned char* smem, const TcSmem& sl, const TcGroup& G, uint32_t& phase,
-                                          volatile int* abort_flag) {
+                                          uint32_t& region, volatile int* abort_flag) {
     const ModelView& mv = args.mv;
     const int g = G.g, r = G.r;
     unsigned char* A = G.A;
@@ -449,13 +570,10 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             int bx = b % mv.bw, by = b / mv.bw;
             gather_row<SPLIT>(mv.endpoint, esrc, lvl + NTBC_MAX_LEVELS, ((float)bx + 0.5f) / (float)mv.bw,
                               ((float)by + 0.5f) / (float)mv.bh, net.layer[0].K, A, Alo, r, valid);
-            for (int l = 0; l < net.n_layers && ok; ++l) {
-                ok = run_layer<SPLIT>(net.layer[l], l, smem, A, sl, tmem, bar, phase, g, r, abort_flag);
-                if (!ok) break;
-                if (l + 1 < net.n_layers) {
-                    hidden_epilogue<SPLIT>(tmem_row, A, Alo, r, mv.activation);
-                    continue;
-                }
+            uint32_t orow = 0;
+            ok = run_mlp<SPLIT>(net, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
+            for (int l = net.n_layers - 1; l < net.n_layers && ok; ++l) {
+                const uint32_t tmem_row = orow;
                 if (args.mode == 1) {
                     int out = net.layer[l].out;
                     for (int o = 0; o < out; ++o) {
@@ -516,13 +634,10 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
             gather_row<SPLIT>(mv.color, csrc, lvl, ((float)x + 0.5f) / (float)mv.width,
                               ((float)y + 0.5f) / (float)mv.height, net.layer[0].K, A, Alo, r, valid);
-            for (int l = 0; l < net.n_layers && ok; ++l) {
-                ok = run_layer<SPLIT>(net.layer[l], l, smem, A, sl, tmem, bar, phase, g, r, abort_flag);
-                if (!ok) break;
-                if (l + 1 < net.n_layers) {
-                    hidden_epilogue<SPLIT>(tmem_row, A, Alo, r, mv.activation);
-                    continue;
-                }
+            uint32_t orow = 0;
+            ok = run_mlp<SPLIT>(net, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
+            for (int l = net.n_layers - 1; l < net.n_layers && ok; ++l) {
+                const uint32_t tmem_row = orow;
                 if (args.mode == 1) {
                     int out = net.layer[l].out;
                     for (int o = 0; o < out; ++o) {
@@ -594,11 +709,11 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
     load_constants(smem, sl);
     load_level_constants(args.mv, csrc, esrc, reinterpret_cast<float2*>(smem + sl.lvl_off));
     TcGroup G = setup_groups(smem, sl, args.groups, &tmem_slot, abort_flag);
-    uint32_t phase = 0;
+    uint32_t phase = 0, region = 0;
     bool ok = true;
     const int n_units = (args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
     for (int unit = blockIdx.x * args.groups + G.g; unit < n_units && ok; unit += gridDim.x * args.groups)
-        ok = process_unit<SPLIT>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, abort_flag);
+        ok = process_unit<SPLIT>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, region, abort_flag);
     teardown_groups(G, args.groups, ok, phase, args.err, tmem_slot);
 }
 
@@ -643,7 +758,7 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
     const TcSmem sl = tc_smem_layout(hdr.img_bytes, hdr.max_textures, SPLIT);
     load_constants(smem, sl);
     TcGroup G = setup_groups(smem, sl, hdr.groups, &tmem_slot, abort_flag);
-    uint32_t phase = 0;
+    uint32_t phase = 0, region = 0;
     bool ok = true;
     int m = -1;
     for (int j = blockIdx.x; j < hdr.total_cta_units; j += gridDim.x) {
@@ -665,7 +780,7 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
         int unit = (j - cur.first_cta_unit) * hdr.groups + G.g;
         if (ok && unit < cur.units) {
             ok = process_unit<SPLIT>(cur.args, cur.csrc, cur.esrc, cur.outs, nullptr, nullptr, unit, smem, sl, G, phase,
-                                     abort_flag);
+                                     region, abort_flag);
             if (ok && G.r == 0) {
                 __threadfence();
                 if (atomicAdd(&hdr.done[m], 1) + 1 == cur.units) hdr.stamps[m + 1] = global_ns();
@@ -732,6 +847,9 @@ static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, 
         TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split);
         size_t bytes = (size_t)sl.group_off + (size_t)groups * sl.group_bytes;
         if (bytes + static_bytes <= 227 * 1024) {
+            // more than two groups allocate all 512 TMEM columns: ask for enough shared
+            // memory that a second CTA never lands on the SM and stalls in tcgen05.alloc
+            if (groups > 2) bytes = std::max(bytes, (size_t)116 * 1024);
             *smem_bytes = bytes;
             return groups;
         }
