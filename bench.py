@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16")
+    ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16; 3: FP8 E4M3 weights, split activations")
     ap.add_argument("--batch", action="store_true",
                     help="batched load-time inference: 16 uneven materials in one persistent launch (CUDA graph)")
     ap.add_argument("--sweep", action="store_true",
@@ -311,12 +311,18 @@ def run_sweep(args):
         codes, sc, zr = ont.export_grid(params["color_grid"] + params["endpoint_grid"], bits)
         deq = ont.dequantize_grid(codes, sc, zr)
         nc = desc.color_levels
-        for name, prec in (("fp32", nt.PREC_FP32), ("fp16", nt.PREC_FP16), ("fp16_fast", nt.PREC_FP16_FAST)):
+        # the FP64 network on the FP32 master weights: what each stored precision gives up
+        er32, cr32 = ont.forward_blocks(od, params, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+        for name, prec in (("fp32", nt.PREC_FP32), ("fp16", nt.PREC_FP16), ("fp16_fast", nt.PREC_FP16_FAST),
+                           ("fp8_e4m3", nt.PREC_FP8)):
             model.export(grid_bits=bits, weight_prec=prec)
-            pw = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
-            for k in ("color_mlp", "endpoint_mlp"):
-                pw[k] = [((W.astype(np.float16) if prec else W).astype(np.float64),
-                          (b.astype(np.float16) if prec else b).astype(np.float64)) for W, b in params[k]]
+            if prec == nt.PREC_FP8:
+                pw = ont.fp8_params(params)[0]
+            else:
+                pw = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
+                for k in ("color_mlp", "endpoint_mlp"):
+                    pw[k] = [((W.astype(np.float16) if prec else W).astype(np.float64),
+                              (b.astype(np.float16) if prec else b).astype(np.float64)) for W, b in params[k]]
             er, cr = ont.forward_blocks(od, pw, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
             idt = torch.from_numpy(ids.astype(np.int32)).to(dev)
             lay = model.layout
@@ -326,8 +332,9 @@ def run_sweep(args):
             outs = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in mat.formats]
             model.infer_to_bc(outs)
             torch.cuda.synchronize()
-            rel = max(float(np.max(np.abs(e.cpu().numpy() - er) / np.abs(er))),
-                      float(np.max(np.abs(c.cpu().numpy() - cr) / np.abs(cr))))
+            eg, cg = e.cpu().numpy(), c.cpu().numpy()
+            rel = max(float(np.max(np.abs(eg - er) / np.abs(er))), float(np.max(np.abs(cg - cr) / np.abs(cr))))
+            rel32 = max(float(np.max(np.abs(eg - er32) / np.abs(er32))), float(np.max(np.abs(cg - cr32) / np.abs(cr32))))
             ref_blocks = ont.infer_blocks(od, pw, block_ids=ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
             mism = fields = 0
             for t, fmt in enumerate(mat.formats):
@@ -338,6 +345,7 @@ def run_sweep(args):
                 mism += int((a0 != b0).sum() + (a1 != b1).sum() + (ac != bc_).sum())
                 fields += len(ids) * 18
             rows.append({"grid_bits": bits, "mlp": name, "max_rel_err_vs_fp64": rel,
+                         "max_rel_err_vs_fp64_fp32_weights": rel32,
                          "field_mismatch": mism / fields, "psnr_db": psnr_list(nt, obc, torch, mat, outs, side)})
         model.close()
     print(json.dumps({"mode": "sweep", "workload": f"mat4k {side}x{side}", "train_steps": args.train_steps,

@@ -50,8 +50,15 @@ enum { NTBC_ACT_SELU = 0, NTBC_ACT_RELU = 1 };
  *                        the outputs stay within 1e-3 relative of an FP64 evaluation
  *   NTBC_PREC_FP16_FAST  FP16 weights and FP16 activations (one pass), the paper's half-
  *                        precision inference (Sec. 3.3); outputs within about 4e-3 relative
+ *   NTBC_PREC_FP8        MLP weights and biases stored as FP8 E4M3 codes (round to nearest
+ *                        even, saturating at +-448) with one power-of-two scale 2^e per
+ *                        layer, e the smallest integer with max|w| <= 448 * 2^e; the values
+ *                        q * 2^e are exact in FP16 and run on the NTBC_PREC_FP16 path (split
+ *                        activations), so the outputs stay within 1e-3 relative of an FP64
+ *                        evaluation with the same FP8 weights. The paper stores FP16 weights;
+ *                        this mode is an extension for the weight-precision study.
  */
-enum { NTBC_PREC_FP32 = 0, NTBC_PREC_FP16 = 1, NTBC_PREC_FP16_FAST = 2 };
+enum { NTBC_PREC_FP32 = 0, NTBC_PREC_FP16 = 1, NTBC_PREC_FP16_FAST = 2, NTBC_PREC_FP8 = 3 };
 
 #define NTBC_MAX_TEXTURES 8
 #define NTBC_MAX_LEVELS 16
@@ -182,6 +189,8 @@ ntbc_status ntbc_model_get_params(const ntbc_model* model, float* dst, size_t co
  * code per byte plus (s, z) per level; grid_bits 0 keeps FP32 grids.
  * weight_prec NTBC_PREC_FP16 / NTBC_PREC_FP16_FAST rounds MLP weights and biases to
  * half precision (round to nearest even) and prepares the tensor-core weight image;
+ * NTBC_PREC_FP8 quantises them to E4M3 with per-layer power-of-two scales (layers in
+ * the order colour 0.., endpoint 0..; a layer's weights and bias share its scale);
  * NTBC_PREC_FP32 keeps them.
  */
 ntbc_status ntbc_model_export(ntbc_model* model, int grid_bits, int weight_prec, void* stream);
@@ -232,8 +241,8 @@ ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int 
 /*
  * Batched load-time inference (Sec. 4.4: inference runs once per material when it is
  * loaded): many materials, each with its own model, decoded to BC blocks in one
- * persistent launch. Every model must be exported with the same tensor-core precision
- * (NTBC_PREC_FP16 or NTBC_PREC_FP16_FAST).
+ * persistent launch. Every model must be exported for the same tensor-core kernel:
+ * all NTBC_PREC_FP16 / NTBC_PREC_FP8 (split activations), or all NTBC_PREC_FP16_FAST.
  *   ntbc_batch_create  models: host array of n models; blocks_out: host array of n host
  *                      arrays, each holding that material's per-texture DEVICE outputs.
  *                      Uploads the launch description (allocates; not capturable).
@@ -286,6 +295,26 @@ typedef struct {
 ntbc_status ntbc_train_grads(ntbc_model* model, const ntbc_material* mat, const int32_t* block_ids,
                              int n_blocks, int qat_bits, float temperature, float* grads,
                              float* losses, void* stream);
+
+/*
+ * Forward and vector-Jacobian product of the raw network outputs on the FP32 master
+ * parameters: the training forward (grid lookup, fake quantisation of the grids when
+ * qat_bits > 0, MLPs, sigmoid) and the hand-written backward (weight and bias
+ * gradients, input gradients, grid scatter-add, straight-through quantiser) that the
+ * losses of Sec. 3.2 drive, here driven by an arbitrary upstream gradient. This is the
+ * differentiable-function form of the network for gradient checks and for use inside
+ * other losses; every call recomputes the activations from the parameters (nothing is
+ * kept between a forward and a later backward).
+ *   block_ids  device int32 [n_blocks] (repeats allowed)
+ *   g_e, g_c   device float, upstream d f / d e_hat [n_blocks][out_endpoint] and
+ *              d f / d c_hat [n_blocks][16][out_color], or both NULL (forward only)
+ *   grads      device float [layout.total], overwritten with sum g . d outputs / d params
+ *              (may be NULL when g_e, g_c are NULL)
+ *   e_hat, c_hat  device float outputs in the layout of ntbc_forward, or NULL
+ */
+ntbc_status ntbc_vjp(ntbc_model* model, const int32_t* block_ids, int n_blocks, int qat_bits,
+                     const float* g_e, const float* g_c, float* grads, float* e_hat, float* c_hat,
+                     void* stream);
 
 /*
  * Allocation-free variant of ntbc_train_grads. The paper has no counterpart.

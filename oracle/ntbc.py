@@ -42,7 +42,10 @@ Readings where the paper is silent or garbled (each one is listed in the design 
     [min(0, min level), max(0, max level)] and z = round(-alpha / s), so zero is
     exactly representable (the property the paper asks of z); round half away
     from zero; all-zero level: s = 1, z = 0; STE gradient 1 where unclamped;
-  * one LR schedule spans the main and the QAT phase.
+  * one LR schedule spans the main and the QAT phase;
+  * FP8 weights (an extension for the precision study; the paper stores FP16): E4M3
+    round to nearest even, saturating; one power-of-two scale per layer shared by its
+    weights and bias.
 """
 from __future__ import annotations
 
@@ -315,6 +318,77 @@ def dequantize_grid(codes, scales, zeros):
 
 
 # ----------------------------------------------------------------------------
+# FP8 E4M3 weights with per-layer power-of-two scales (weight-precision study;
+# the paper stores FP16 MLP weights, Sec. 3.4)
+# ----------------------------------------------------------------------------
+
+E4M3_MAX = 448.0          # 1.75 * 2^8: largest finite E4M3 value (exponent bias 7, 3 mantissa bits)
+E4M3_MIN_NORMAL = 2.0 ** -6
+
+
+def e4m3_round(x):
+    """Nearest FP8 E4M3 value, ties to even mantissa, saturating at +-448.
+
+    E4M3 has 1 sign bit, 4 exponent bits (bias 7) and 3 mantissa bits, subnormals
+    below 2^-6 with spacing 2^-9, and no infinities. In the binade [2^k, 2^(k+1))
+    the spacing is 2^(k-3); np.round is half-to-even, so a tie lands on the
+    neighbour with the even mantissa."""
+    x = np.asarray(x, np.float64)
+    a = np.minimum(np.abs(x), E4M3_MAX)
+    _, ex = np.frexp(np.maximum(a, E4M3_MIN_NORMAL))      # a = m 2^ex, m in [0.5, 1)
+    step = np.ldexp(1.0, ex - 1 - 3)                      # 2^(floor(log2 a) - 3)
+    q = np.minimum(np.round(a / step) * step, E4M3_MAX)
+    return np.where(x < 0, -q, q)
+
+
+def e4m3_code(v):
+    """Bit pattern (uint8) of an exactly representable E4M3 value v."""
+    v = np.asarray(v, np.float64)
+    a = np.abs(v)
+    sign = np.signbit(v).astype(np.int64) << 7          # a negative value that rounds to zero keeps its sign
+    _, ex = np.frexp(np.maximum(a, E4M3_MIN_NORMAL))
+    normal = a >= E4M3_MIN_NORMAL
+    efield = np.where(normal, ex - 1 + 7, 0)
+    mant = np.where(normal, a / np.ldexp(1.0, ex - 1) - 1.0, a / 2.0 ** -6) * 8.0
+    assert np.all(mant == np.round(mant)), "value not representable in E4M3"
+    return (sign | (efield << 3) | mant.astype(np.int64)).astype(np.uint8)
+
+
+def fp8_layer_exponent(values):
+    """Per-layer scale 2^e: the smallest integer e with max|w| <= 448 * 2^e (e = 0 for an
+    all-zero layer). Compared exactly (powers of two scale exactly)."""
+    m = float(np.max(np.abs(np.asarray(values, np.float64)))) if np.size(values) else 0.0
+    if m == 0.0:
+        return 0
+    e = math.frexp(m)[1] - 1 - 8
+    while m > math.ldexp(E4M3_MAX, e):
+        e += 1
+    while m <= math.ldexp(E4M3_MAX, e - 1):
+        e -= 1
+    return e
+
+
+def fp8_params(params):
+    """MLP weights as the FP8 export holds them: per layer (W, b share one scale 2^e),
+    w -> e4m3_round(w / 2^e) 2^e. Returns (params with the quantised MLPs, exponents in
+    the order colour layers then endpoint layers, codes per layer as (W codes, b codes))."""
+    out = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
+    exps, codes = [], []
+    for k in ("color_mlp", "endpoint_mlp"):
+        layers = []
+        for W, b in params[k]:
+            W = np.asarray(W, np.float64)
+            b = np.asarray(b, np.float64)
+            e = fp8_layer_exponent(np.concatenate([W.ravel(), b.ravel()]))
+            qW, qb = e4m3_round(np.ldexp(W, -e)), e4m3_round(np.ldexp(b, -e))
+            layers.append((np.ldexp(qW, e), np.ldexp(qb, e)))
+            exps.append(e)
+            codes.append((e4m3_code(qW), e4m3_code(qb)))
+        out[k] = layers
+    return out, exps, codes
+
+
+# ----------------------------------------------------------------------------
 # forward over a material
 # ----------------------------------------------------------------------------
 
@@ -571,6 +645,41 @@ def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_
                   L_endpoint=L_e + L_cd_e, L_color=L_c + L_cd_c)
     grads = dict(color_grid=g_cgrid, endpoint_grid=g_egrid, color_mlp=g_cmlp, endpoint_mlp=g_emlp)
     return losses, grads
+
+
+def outputs_vjp(desc, params, block_ids, g_e, g_c, qat_bits=0):
+    """Vector-Jacobian product of the raw outputs: with f = sum g_e . e_hat + sum g_c . c_hat
+    (e_hat [nb, out_e], c_hat [nb, 16, out_c] as forward_blocks returns them), the gradient
+    of f w.r.t. every parameter, through the same backward the losses use (sigmoid, MLP,
+    bilinear scatter, and with qat_bits the fake-quantised grids and straight-through mask).
+    Returns (e_hat, c_hat, grads shaped like params)."""
+    block_ids = np.asarray(block_ids, np.int64)
+    nb = len(block_ids)
+
+    def grids(key):
+        lv = _as64(params[key])
+        if qat_bits:
+            fq = [qat_fake_quant(g, qat_bits) for g in lv]
+            return [f[0] for f in fq], [f[1] for f in fq]
+        return lv, None
+
+    eg, emask = grids("endpoint_grid")
+    s, t = block_coords(desc.blocks_x, desc.blocks_y, block_ids % desc.blocks_x, block_ids // desc.blocks_x)
+    xe, ecache_g = grid_lookup(eg, s, t)
+    e_hat, ecache = mlp_forward(params["endpoint_mlp"], xe, desc.activation)
+    g_xe, g_emlp = mlp_backward(params["endpoint_mlp"], ecache, e_hat, np.asarray(g_e, np.float64), desc.activation)
+    g_egrid = grid_lookup_backward(eg, ecache_g, g_xe, emask)
+
+    cg, cmask = grids("color_grid")
+    xs, ys = block_texel_xy(desc, block_ids)
+    u, v = texel_coords(desc.width, desc.height, xs.ravel(), ys.ravel())
+    xc, ccache_g = grid_lookup(cg, u, v)
+    c_flat, ccache = mlp_forward(params["color_mlp"], xc, desc.activation)
+    g_xc, g_cmlp = mlp_backward(params["color_mlp"], ccache, c_flat,
+                                np.asarray(g_c, np.float64).reshape(nb * 16, desc.out_color), desc.activation)
+    g_cgrid = grid_lookup_backward(cg, ccache_g, g_xc, cmask)
+    grads = dict(color_grid=g_cgrid, endpoint_grid=g_egrid, color_mlp=g_cmlp, endpoint_mlp=g_emlp)
+    return e_hat, c_flat.reshape(nb, 16, desc.out_color), grads
 
 
 def loss_value(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_bits=0, soft=False):

@@ -9,7 +9,7 @@ library_path = os.path.join(HERE, "libntbc.so")
 
 BC1, BC4 = 1, 4
 ACT_SELU, ACT_RELU = 0, 1
-PREC_FP32, PREC_FP16, PREC_FP16_FAST = 0, 1, 2
+PREC_FP32, PREC_FP16, PREC_FP16_FAST, PREC_FP8 = 0, 1, 2, 3
 MAX_TEXTURES, MAX_LEVELS, MAX_MLP_LAYERS = 8, 16, 4
 STATUS_NAMES = {0: "NTBC_OK", 1: "NTBC_EINVAL", 2: "NTBC_ENOMEM", 3: "NTBC_ECUDA", 4: "NTBC_ETIMEOUT",
                 5: "NTBC_ENONFINITE", 6: "NTBC_EUNSUPPORTED"}
@@ -114,6 +114,7 @@ _SIGS = {
     "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, _P, _P, _P]),
     "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
                                          c_float, _P, _P, _P]),
+    "ntbc_vjp": (c_int, [_P, _P, c_int, c_int, _P, _P, _P, _P, _P, _P]),
     "ntbc_adam_step": (c_int, [_P, _P, ctypes.c_long, ctypes.c_long, ctypes.POINTER(TrainConfig), _P]),
     "ntbc_sample_blocks": (c_int, [ctypes.c_uint64, ctypes.c_long, c_int, c_int, _P, _P]),
     "ntbc_batch_create": (c_int, [ctypes.POINTER(_P), c_int, ctypes.POINTER(ctypes.POINTER(_P)), ctypes.POINTER(_P)]),
@@ -248,6 +249,10 @@ class Model:
                     stream=None):
         _check(lib.ntbc_train_grads(self.handle, ctypes.byref(material), _ptr(block_ids), block_ids.numel(),
                                     qat_bits, temperature, _ptr(grads), _ptr(losses), _stream(stream)))
+
+    def vjp(self, block_ids, qat_bits=0, g_e=None, g_c=None, grads=None, e_hat=None, c_hat=None, stream=None):
+        _check(lib.ntbc_vjp(self.handle, _ptr(block_ids), block_ids.numel(), qat_bits, _ptr(g_e), _ptr(g_c),
+                            _ptr(grads), _ptr(e_hat), _ptr(c_hat), _stream(stream)))
 
     def adam_step(self, grads, step, total_steps, cfg: TrainConfig, stream=None):
         _check(lib.ntbc_adam_step(self.handle, _ptr(grads), step, total_steps, ctypes.byref(cfg), _stream(stream)))

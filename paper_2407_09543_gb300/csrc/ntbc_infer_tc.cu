@@ -874,7 +874,7 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
                       float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
     TcArgs a = tc_args(m);
     size_t smem = 0;
-    const bool split = m->weight_prec == NTBC_PREC_FP16;
+    const bool split = m->weight_prec != NTBC_PREC_FP16_FAST;     // FP16 and FP8 weights
     a.groups = tc_groups(a, m->desc.n_textures, split, &smem);
     if (a.groups == 0) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: shared memory too small for this model");
     a.n = n;
@@ -940,9 +940,10 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         const ntbc_model* m = models[i];
         if (!m || !blocks_out[i]) return fail(NTBC_EINVAL, "material %d: null model or output list", i);
         if (m->weight_prec == NTBC_PREC_FP32 || m->grid_bits < 0 || !m->umma_img)
-            return fail(NTBC_EINVAL, "material %d: export the model with NTBC_PREC_FP16 or NTBC_PREC_FP16_FAST first", i);
-        if (prec >= 0 && m->weight_prec != prec) return fail(NTBC_EINVAL, "all materials of a batch need the same precision");
-        prec = m->weight_prec;
+            return fail(NTBC_EINVAL, "material %d: export the model with a tensor-core precision first", i);
+        int kind = m->weight_prec == NTBC_PREC_FP16_FAST ? NTBC_PREC_FP16_FAST : NTBC_PREC_FP16;
+        if (prec >= 0 && kind != prec) return fail(NTBC_EINVAL, "all materials of a batch need the same tensor-core kernel");
+        prec = kind;
         TcMat& t = mats[i];
         memset(&t, 0, sizeof(t));
         t.args = tc_args(m);

@@ -67,7 +67,9 @@ struct ntbc_model {
     float* qzero = nullptr;
     float* infer_params = nullptr;      // FP32 copy used by inference: FP32 grids (grid_bits 0)
                                         // and the MLP weights rounded to the export precision
-    __half* w16 = nullptr;              // MLP part in FP16 (weight_prec FP16)
+    __half* w16 = nullptr;              // MLP part in FP16 (weight_prec FP16, and FP8 expanded)
+    uint8_t* w8 = nullptr;              // MLP part as E4M3 codes (weight_prec FP8), then
+    int* w8_exp = nullptr;              // the per-layer scale exponents (inside the w8 allocation)
     __half* umma_img = nullptr;         // FP16 weights in the tensor-core shared-memory layout
     int* tc_err = nullptr;              // set by the tensor-core kernel when a bounded wait gives up
     struct ntbc_train_state* train = nullptr;   // training scratch (allocated on first use)

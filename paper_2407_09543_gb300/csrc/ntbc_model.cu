@@ -2,6 +2,8 @@
 // form (Sec. 2.3 Eq. quantize / scaling_factor, Sec. 3.3 per-level asymmetric
 // quantisation) and the stored blob (Sec. 3.3: grids stored as 8-bit integers,
 // half-precision MLP weights, Sec. 3.4).
+#include <cuda_fp8.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -193,6 +195,87 @@ ntbc_status launch_level_scale_zero(const float* grid, const LevelTable& lt, int
     return NTBC_OK;
 }
 
+// FP8 E4M3 weights with one power-of-two scale per layer. A layer is its weight matrix and
+// bias (two spans of the parameter buffer); one CTA per layer.
+struct Fp8Layers {
+    int n;
+    long long w_off[2 * NTBC_MAX_MLP_LAYERS], w_cnt[2 * NTBC_MAX_MLP_LAYERS];
+    long long b_off[2 * NTBC_MAX_MLP_LAYERS], b_cnt[2 * NTBC_MAX_MLP_LAYERS];
+};
+
+static Fp8Layers fp8_layers(const ntbc_model_desc& d, const ntbc_layout& L) {
+    Fp8Layers f;
+    memset(&f, 0, sizeof(f));
+    int per_net = d.hidden_layers + 1;
+    for (int net = 0; net < 2; ++net)
+        for (int l = 0; l < per_net; ++l) {
+            const ntbc_span& w = net ? L.endpoint_w[l] : L.color_w[l];
+            const ntbc_span& b = net ? L.endpoint_b[l] : L.color_b[l];
+            f.w_off[f.n] = (long long)w.offset;
+            f.w_cnt[f.n] = (long long)w.count;
+            f.b_off[f.n] = (long long)b.offset;
+            f.b_cnt[f.n] = (long long)b.count;
+            ++f.n;
+        }
+    return f;
+}
+
+__device__ __forceinline__ long long fp8_index(const Fp8Layers& f, int l, long long j) {
+    return j < f.w_cnt[l] ? f.w_off[l] + j : f.b_off[l] + (j - f.w_cnt[l]);
+}
+
+__device__ __forceinline__ float e4m3_value(uint8_t q) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+// quantise (codes == written) or expand stored codes; writes the exact values q 2^e as
+// FP32 (dst, same indexing as the parameter buffer) and FP16 (h, MLP part only)
+__global__ void __launch_bounds__(256) fp8_layers_kernel(const float* __restrict__ params, Fp8Layers f,
+                                                         long long grid_floats, int quantise, uint8_t* __restrict__ codes,
+                                                         int* __restrict__ exps, float* __restrict__ dst,
+                                                         __half* __restrict__ h) {
+    __shared__ float wmax[8];
+    __shared__ int e_sh;
+    const int l = blockIdx.x;
+    const long long n = f.w_cnt[l] + f.b_cnt[l];
+    if (quantise) {
+        float m = 0.f;
+        for (long long j = threadIdx.x; j < n; j += blockDim.x) m = fmaxf(m, fabsf(params[fp8_index(f, l, j)]));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+            int e = 0;
+            if (m > 0.f) {                 // smallest e with m <= 448 * 2^e (exact comparisons)
+                e = ilogbf(m) - 8;
+                while (m > ldexpf(448.f, e)) ++e;
+                while (m <= ldexpf(448.f, e - 1)) --e;
+            }
+            e_sh = e;
+            exps[l] = e;
+        }
+    } else if (threadIdx.x == 0) {
+        e_sh = exps[l];
+    }
+    __syncthreads();
+    const int e = e_sh;
+    for (long long j = threadIdx.x; j < n; j += blockDim.x) {
+        long long i = fp8_index(f, l, j);
+        uint8_t q;
+        if (quantise) {
+            q = (uint8_t)__nv_cvt_float_to_fp8(ldexpf(params[i], -e), __NV_SATFINITE, __NV_E4M3);
+            codes[i - grid_floats] = q;
+        } else {
+            q = codes[i - grid_floats];
+        }
+        float v = ldexpf(e4m3_value(q), e);
+        dst[i] = v;
+        h[i - grid_floats] = __float2half_rn(v);
+    }
+}
+
 static int grid_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 8); }
 
 }  // namespace ntbc
@@ -290,6 +373,7 @@ void ntbc_model_free(ntbc_model* m) {
     cudaFree(m->qscale);   // also holds the zero points and the min / max scratch
     cudaFree(m->infer_params);
     cudaFree(m->w16);
+    cudaFree(m->w8);                     // also holds w8_exp
     cudaFree(m->umma_img);               // also holds tc_err
     ntbc_train_release(m);
     delete m;
@@ -328,6 +412,11 @@ static ntbc_status ensure_export_buffers(ntbc_model* m) {
     if (st == NTBC_OK && !m->qzero) m->qzero = m->qscale + levels;
     if (st == NTBC_OK && !m->infer_params) st = device_alloc((void**)&m->infer_params, L.total * sizeof(float), "inference parameters");
     if (st == NTBC_OK && !m->w16) st = device_alloc((void**)&m->w16, (L.total - L.grid_floats) * sizeof(__half), "half weights");
+    if (st == NTBC_OK && !m->w8) {
+        size_t codes = ((L.total - L.grid_floats) + 15) & ~(size_t)15;
+        st = device_alloc((void**)&m->w8, codes + 2 * NTBC_MAX_MLP_LAYERS * sizeof(int), "FP8 weights");
+        if (st == NTBC_OK) m->w8_exp = reinterpret_cast<int*>(m->w8 + codes);
+    }
     return st;
 }
 
@@ -335,8 +424,9 @@ ntbc_status ntbc_model_export(ntbc_model* m, int grid_bits, int weight_prec, voi
     clear_error();
     if (!m) return fail(NTBC_EINVAL, "null model");
     if (grid_bits != 0 && grid_bits != 8 && grid_bits != 4) return fail(NTBC_EINVAL, "grid_bits must be 0, 4 or 8");
-    if (weight_prec != NTBC_PREC_FP32 && weight_prec != NTBC_PREC_FP16 && weight_prec != NTBC_PREC_FP16_FAST)
-        return fail(NTBC_EINVAL, "weight precision must be NTBC_PREC_FP32, NTBC_PREC_FP16 or NTBC_PREC_FP16_FAST");
+    if (weight_prec != NTBC_PREC_FP32 && weight_prec != NTBC_PREC_FP16 && weight_prec != NTBC_PREC_FP16_FAST &&
+        weight_prec != NTBC_PREC_FP8)
+        return fail(NTBC_EINVAL, "weight precision must be NTBC_PREC_FP32, NTBC_PREC_FP16, NTBC_PREC_FP16_FAST or NTBC_PREC_FP8");
     ntbc_status st = ensure_export_buffers(m);
     if (st != NTBC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -356,7 +446,14 @@ ntbc_status ntbc_model_export(ntbc_model* m, int grid_bits, int weight_prec, voi
     // MLP weights
     long long nw = (long long)(L.total - L.grid_floats);
     m->weight_prec = weight_prec;
-    if (weight_prec != NTBC_PREC_FP32) {
+    if (weight_prec == NTBC_PREC_FP8) {
+        Fp8Layers f = fp8_layers(m->desc, L);
+        fp8_layers_kernel<<<f.n, 256, 0, s>>>(m->params, f, (long long)L.grid_floats, 1, m->w8, m->w8_exp,
+                                              m->infer_params, m->w16);
+        NTBC_CHECK_LAUNCH("quantise weights to FP8");
+        st = tc_prepare(m, s);
+        if (st != NTBC_OK) return st;
+    } else if (weight_prec != NTBC_PREC_FP32) {
         round_half_kernel<<<grid_blocks(nw), 256, 0, s>>>(m->params + L.grid_floats, m->infer_params + L.grid_floats, m->w16, nw);
         NTBC_CHECK_LAUNCH("round weights to half");
         st = tc_prepare(m, s);
@@ -395,7 +492,11 @@ static size_t blob_parts(const ntbc_model* m, size_t* grid_b, size_t* sz_b, size
     int levels = m->desc.color_levels + m->desc.endpoint_levels;
     *sz_b = 2 * levels * sizeof(float);
     *grid_b = m->grid_bits > 0 ? L.grid_floats : L.grid_floats * sizeof(float);
-    *w_b = (L.total - L.grid_floats) * (m->weight_prec != NTBC_PREC_FP32 ? sizeof(__half) : sizeof(float));
+    size_t nw = L.total - L.grid_floats;
+    if (m->weight_prec == NTBC_PREC_FP8)
+        *w_b = 2 * NTBC_MAX_MLP_LAYERS * sizeof(int) + nw;        // exponents, then codes
+    else
+        *w_b = nw * (m->weight_prec != NTBC_PREC_FP32 ? sizeof(__half) : sizeof(float));
     return sizeof(BlobHeader) + *sz_b + *grid_b + *w_b;
 }
 
@@ -433,7 +534,11 @@ ntbc_status ntbc_model_save(const ntbc_model* m, uint8_t* blob, size_t size, voi
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb, m->infer_params, gb, cudaMemcpyDeviceToHost, s));
     }
     const ntbc_layout& L = m->layout;
-    if (m->weight_prec != NTBC_PREC_FP32)
+    if (m->weight_prec == NTBC_PREC_FP8) {
+        const size_t eb = 2 * NTBC_MAX_MLP_LAYERS * sizeof(int);
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb, m->w8_exp, eb, cudaMemcpyDeviceToHost, s));
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb + eb, m->w8, wb - eb, cudaMemcpyDeviceToHost, s));
+    } else if (m->weight_prec != NTBC_PREC_FP32)
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb, m->w16, wb, cudaMemcpyDeviceToHost, s));
     else
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb, m->infer_params + L.grid_floats, wb, cudaMemcpyDeviceToHost, s));
@@ -466,7 +571,17 @@ ntbc_status ntbc_model_load(ntbc_model* m, const uint8_t* blob, size_t size, voi
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->infer_params, p + zb, gb, cudaMemcpyHostToDevice, s));
     }
     long long nw = (long long)(L.total - L.grid_floats);
-    if (m->weight_prec != NTBC_PREC_FP32) {
+    if (m->weight_prec == NTBC_PREC_FP8) {
+        const size_t eb = 2 * NTBC_MAX_MLP_LAYERS * sizeof(int);
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(m->w8_exp, p + zb + gb, eb, cudaMemcpyHostToDevice, s));
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(m->w8, p + zb + gb + eb, wb - eb, cudaMemcpyHostToDevice, s));
+        Fp8Layers f = fp8_layers(m->desc, L);
+        fp8_layers_kernel<<<f.n, 256, 0, s>>>(m->params, f, (long long)L.grid_floats, 0, m->w8, m->w8_exp,
+                                              m->infer_params, m->w16);
+        NTBC_CHECK_LAUNCH("expand FP8 weights");
+        st = tc_prepare(m, s);
+        if (st != NTBC_OK) return st;
+    } else if (m->weight_prec != NTBC_PREC_FP32) {
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->w16, p + zb + gb, wb, cudaMemcpyHostToDevice, s));
         half_to_float_kernel<<<grid_blocks(nw), 256, 0, s>>>(m->w16, m->infer_params + L.grid_floats, nw);
         NTBC_CHECK_LAUNCH("expand half weights");

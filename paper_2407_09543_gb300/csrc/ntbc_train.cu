@@ -729,11 +729,10 @@ static ntbc_status check_material(const ntbc_model* m, const ntbc_material* mat)
     return NTBC_OK;
 }
 
-// one network's forward + loss + backward on the gathered batch
-static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const TexPtrs& tp, const int32_t* ids, int B,
-                           GridSrc src, float T, float* grads, double* acc, cudaStream_t s) {
-    ntbc_train_state* ts = m->train;
-    NetBuffers& nb = color ? ts->color : ts->endpoint;
+// gather + dense layers of one network on the batch: features in nb.X, hidden
+// activations in nb.A, sigmoid outputs in nb.Y (feature-major)
+static void net_forward(const ntbc_model* m, const ModelView& mv, bool color, NetBuffers& nb, const int32_t* ids,
+                        int B, GridSrc src, cudaStream_t s) {
     const NetView& nv = color ? mv.color : mv.endpoint;
     const int thr = 128;
     unsigned g = blocks_for(B, thr);
@@ -750,14 +749,19 @@ static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const
             dense_fwd_kernel<kHidden><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, m->params + nv.w_off[l], m->params + nv.b_off[l], nv.layer_out[l], act, outbuf);
         prev = outbuf;
     }
+}
+
+// backward from the output-layer deltas in nb.D0 (d loss / d pre-sigmoid): weight and
+// bias gradients, input gradients, and the grid scatter-add (through the QAT mask)
+static void net_backward(const ntbc_model* m, const ModelView& mv, bool color, NetBuffers& nb, const int32_t* ids,
+                         int B, GridSrc src, float* grads, cudaStream_t s) {
+    const NetView& nv = color ? mv.color : mv.endpoint;
+    const int thr = 128;
+    unsigned g = blocks_for(B, thr);
     float* D = nb.D0;
     float* Dn = nb.D1;
-    if (color)
-        color_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
-    else
-        endpoint_loss_kernel<<<blocks_for((long long)B * 16, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
     unsigned gw = blocks_for(B, kWgChunk);
-    for (int l = nl - 1; l >= 0; --l) {
+    for (int l = nv.n_layers - 1; l >= 0; --l) {
         const float* Ain = l == 0 ? nb.X : nb.A[l - 1];
         dense_bwd_weight_kernel<<<gw, 256, 0, s>>>(D, nv.layer_out[l], Ain, nv.layer_in[l], B, grads + nv.w_off[l], grads + nv.b_off[l]);
         dense_bwd_data_kernel<<<g, thr, 0, s>>>(D, nv.layer_out[l], B, m->params + nv.w_off[l], nv.layer_in[l],
@@ -767,21 +771,40 @@ static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const
         Dn = t;
     }
     grid_scatter_kernel<<<g, thr, 0, s>>>(mv, color, ids, B, D, src, grads);
+}
+
+// one network's forward + loss + backward on the gathered batch
+static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const TexPtrs& tp, const int32_t* ids, int B,
+                           GridSrc src, float T, float* grads, double* acc, cudaStream_t s) {
+    NetBuffers& nb = color ? m->train->color : m->train->endpoint;
+    net_forward(m, mv, color, nb, ids, B, src, s);
+    const int thr = 128;
+    if (color)
+        color_loss_kernel<<<blocks_for(B, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, nb.D0, acc);
+    else
+        endpoint_loss_kernel<<<blocks_for((long long)B * 16, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, nb.D0, acc);
+    net_backward(m, mv, color, nb, ids, B, src, grads, s);
     NTBC_CHECK_LAUNCH(color ? "colour network step" : "endpoint network step");
     return NTBC_OK;
 }
 
-static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const int32_t* ids, int nb, int qat_bits,
-                                bool dynamic_qat, float T, float* grads, cudaStream_t s) {
+// outputs to the row-major [k][o] layout of ntbc_forward and, with an upstream gradient g
+// (same layout), the output-layer deltas D[o][k] = g[k][o] y (1 - y)
+__global__ void vjp_seed_kernel(const float* __restrict__ Y, int out, int B, const float* __restrict__ g,
+                                float* __restrict__ D, float* __restrict__ y_out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * out) return;
+    long long k = i / out;
+    int o = (int)(i % out);
+    float y = Y[(long long)o * B + k];
+    if (y_out) y_out[i] = y;
+    if (g) D[(long long)o * B + k] = g[i] * y * (1.f - y);
+}
+
+// grid sources of the FP32 master parameters, with static QAT fake quantisation
+static ntbc_status train_sources(ntbc_model* m, int qat_bits, bool dynamic_qat, GridSrc& csrc, GridSrc& esrc,
+                                 cudaStream_t s) {
     ntbc_train_state* ts = m->train;
-    ModelView mv = make_view(m->desc, m->layout);
-    TexPtrs tp;
-    memset(&tp, 0, sizeof(tp));
-    for (int t = 0; t < mat->n_textures; ++t) {
-        tp.texels[t] = mat->texels[t];
-        tp.blocks[t] = mat->ref_blocks[t];
-    }
-    GridSrc csrc, esrc;
     memset(&csrc, 0, sizeof(csrc));
     csrc.f32 = m->params;
     csrc.qat_bits = qat_bits;
@@ -797,6 +820,22 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
         esrc.scale = ts->qscale + m->desc.color_levels;
         esrc.zero = ts->qzero + m->desc.color_levels;
     }
+    return NTBC_OK;
+}
+
+static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const int32_t* ids, int nb, int qat_bits,
+                                bool dynamic_qat, float T, float* grads, cudaStream_t s) {
+    ntbc_train_state* ts = m->train;
+    ModelView mv = make_view(m->desc, m->layout);
+    TexPtrs tp;
+    memset(&tp, 0, sizeof(tp));
+    for (int t = 0; t < mat->n_textures; ++t) {
+        tp.texels[t] = mat->texels[t];
+        tp.blocks[t] = mat->ref_blocks[t];
+    }
+    GridSrc csrc, esrc;
+    ntbc_status st0 = train_sources(m, qat_bits, dynamic_qat, csrc, esrc, s);
+    if (st0 != NTBC_OK) return st0;
     NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
     NTBC_CHECK_CUDA(cudaMemsetAsync(ts->loss_acc, 0, 6 * sizeof(double), s));
     ntbc_status st = run_net(m, mv, true, tp, ids, nb * 16, csrc, T, grads, ts->loss_acc, s);
@@ -845,6 +884,36 @@ ntbc_status ntbc_train_grads(ntbc_model* m, const ntbc_material* mat, const int3
     st = grads_on_ids(m, mat, block_ids, n_blocks, qat_bits, false, temperature, grads, s);
     if (st != NTBC_OK) return st;
     if (losses) NTBC_CHECK_CUDA(cudaMemcpyAsync(losses, m->train->losses, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_vjp(ntbc_model* m, const int32_t* block_ids, int n_blocks, int qat_bits, const float* g_e,
+                     const float* g_c, float* grads, float* e_hat, float* c_hat, void* stream) {
+    clear_error();
+    if (!m || !block_ids) return fail(NTBC_EINVAL, "null argument");
+    if (n_blocks <= 0) return fail(NTBC_EINVAL, "need at least one block");
+    if (qat_bits != 0 && qat_bits != 8 && qat_bits != 4) return fail(NTBC_EINVAL, "qat_bits must be 0, 4 or 8");
+    if ((g_e == nullptr) != (g_c == nullptr)) return fail(NTBC_EINVAL, "give both upstream gradients or neither");
+    if (g_e && !grads) return fail(NTBC_EINVAL, "upstream gradients need a gradient buffer");
+    ntbc_status st = ensure_train_state(m, n_blocks);
+    if (st != NTBC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    GridSrc csrc, esrc;
+    st = train_sources(m, qat_bits, false, csrc, esrc, s);
+    if (st != NTBC_OK) return st;
+    ModelView mv = make_view(m->desc, m->layout);
+    if (g_e) NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
+    for (int net = 0; net < 2; ++net) {
+        const bool color = net == 0;
+        NetBuffers& nb = color ? m->train->color : m->train->endpoint;
+        const int B = color ? n_blocks * 16 : n_blocks;
+        const int out = color ? m->layout.out_color : m->layout.out_endpoint;
+        net_forward(m, mv, color, nb, block_ids, B, color ? csrc : esrc, s);
+        vjp_seed_kernel<<<blocks_for((long long)B * out, 256), 256, 0, s>>>(nb.Y, out, B, color ? g_c : g_e, nb.D0,
+                                                                            color ? c_hat : e_hat);
+        if (g_e) net_backward(m, mv, color, nb, block_ids, B, color ? csrc : esrc, grads, s);
+        NTBC_CHECK_LAUNCH(color ? "colour network vjp" : "endpoint network vjp");
+    }
     return NTBC_OK;
 }
 

@@ -155,6 +155,55 @@ def test_blob_roundtrip_reproduces_blocks():
         np.testing.assert_array_equal(a, b)
 
 
+def _blob_fp8_part(model, desc, n_layers):
+    """(per-layer exponents, codes in parameter-layout order) from a saved FP8 blob: header
+    (magic, version, desc, grid_bits, weight_prec), (s, z) per level, grid codes, then the
+    MLP part as 2 * NTBC_MAX_MLP_LAYERS int32 exponents followed by one code per parameter."""
+    import ctypes
+    blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
+    model.save(blob)
+    b = blob.numpy()
+    lay = model.layout
+    levels = desc.color_levels + desc.endpoint_levels
+    head = 8 + ctypes.sizeof(nt.ModelDesc) + 8
+    wpart = b[head + 8 * levels + lay.grid_floats:]
+    nw = lay.total - lay.grid_floats
+    exps = wpart[:4 * 2 * 4].view(np.int32)[:n_layers]
+    return exps, wpart[32:32 + nw]
+
+
+def test_fp8_weights_codes_and_parity():
+    mat, desc, odesc, params = make_case(side=128, levels=4, lo=8, hi=64, hidden=3)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP8)
+    p8, exps, codes = ont.fp8_params(params)
+    # codes and exponents bit-exact with the oracle's E4M3 rounding
+    gexps, gcodes = _blob_fp8_part(model, desc, len(exps))
+    np.testing.assert_array_equal(gexps, np.array(exps))
+    code_params = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"],
+                       color_mlp=codes[:len(params["color_mlp"])], endpoint_mlp=codes[len(params["color_mlp"]):])
+    want = nt.configs.flatten(desc, code_params)[model.layout.grid_floats:].astype(np.uint8)
+    np.testing.assert_array_equal(gcodes, want)
+    # outputs within 1e-3 of the FP64 network with the same FP8 weights
+    oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 8)
+    deq = ont.dequantize_grid(oc, os_, oz)
+    nc = desc.color_levels
+    ids = np.arange(odesc.n_blocks)
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p8, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    np.testing.assert_allclose(e, er, rtol=RTOL, atol=1e-6)
+    np.testing.assert_allclose(c, cr, rtol=RTOL, atol=1e-6)
+    ref = ont.infer_blocks(odesc, p8, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ref)
+    # the stored blob reproduces the blocks
+    before = gpu_blocks(model, desc)
+    blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
+    model.save(blob)
+    other = nt.Model(desc)
+    other.load(blob)
+    for a, b in zip(before, gpu_blocks(other, desc)):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_full_size_4k_sampled():
     # the 4096^2 four-texture workload in the launch configuration the benchmark times;
     # the oracle evaluates a seeded sample of blocks one by one
@@ -241,9 +290,14 @@ def test_trained_weights_parity_all_modes(bits):
     nc = desc.color_levels
     ids = np.arange(odesc.n_blocks)
     for prec, rtol, mism in ((nt.PREC_FP32, RTOL, 0.001), (nt.PREC_FP16, RTOL, 0.001),
-                             (nt.PREC_FP16_FAST, RTOL_FAST, MISMATCH_FAST)):
+                             (nt.PREC_FP16_FAST, RTOL_FAST, MISMATCH_FAST), (nt.PREC_FP8, RTOL, 0.001)):
         model = gpu_model(desc, params, grid_bits=bits, weight_prec=prec)
-        pw = params if prec == nt.PREC_FP32 else oracle_params_fp16(params)
+        if prec == nt.PREC_FP32:
+            pw = params
+        elif prec == nt.PREC_FP8:
+            pw = ont.fp8_params(params)[0]
+        else:
+            pw = oracle_params_fp16(params)
         e, c = gpu_forward(model, ids)
         er, cr = ont.forward_blocks(odesc, pw, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
         np.testing.assert_allclose(e, er, rtol=rtol, atol=1e-6)

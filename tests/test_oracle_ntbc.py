@@ -369,3 +369,144 @@ def test_training_beats_untrained_and_stays_below_reference():
         after = bc.psnr(bc.decode(fmt, ntbc.infer_blocks(desc, p1)[t], 64, 64), mat.textures[t])
         assert after > before + 3.0
         assert after < ref_psnr
+
+
+# ----------------------------------------------------------------------------
+# FP8 E4M3 weights (precision study)
+# ----------------------------------------------------------------------------
+
+def _e4m3_table():
+    """All finite non-negative E4M3 values from the format definition: exponent field
+    e (bias 7), mantissa m; e = 0 is subnormal m 2^-9; code 0x7F is NaN."""
+    vals = []
+    for code in range(0x7F):
+        e, m = code >> 3, code & 7
+        vals.append(m * 2.0 ** -9 if e == 0 else (1 + m / 8) * 2.0 ** (e - 7))
+    return np.array(vals)
+
+
+def test_e4m3_round_brute_force_nearest_ties_even():
+    table = _e4m3_table()
+    assert table.max() == 448.0 and len(np.unique(table)) == 127
+    rng = np.random.default_rng(0)
+    mags = np.concatenate([np.exp(rng.uniform(np.log(1e-4), np.log(600.0), 4000)),
+                           (table[:-1] + table[1:]) / 2,             # every tie
+                           table, [0.0, 448.0, 449.0, 464.0, 1e6]])
+    x = mags * np.where(rng.random(mags.size) < 0.5, -1.0, 1.0)
+    got = ntbc.e4m3_round(x)
+    a = np.minimum(np.abs(x), 448.0)
+    d = np.abs(a[:, None] - table[None, :])
+    best = d.min(axis=1, keepdims=True)
+    cand = np.where(d == best, np.arange(127)[None, :], 10 ** 6)
+    # among equidistant neighbours take the even mantissa (code & 1 == 0)
+    even = np.where((cand % 2 == 0) & (cand < 10 ** 6), cand, 10 ** 6).min(axis=1)
+    pick = np.where(even < 10 ** 6, even, cand.min(axis=1))
+    want = np.sign(x) * table[pick]
+    np.testing.assert_array_equal(np.abs(got), np.abs(want))
+    assert np.all(np.sign(got[got != 0]) == np.sign(x[got != 0]))
+
+
+def test_e4m3_round_matches_torch_cast_in_range():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(20000) * np.exp(rng.uniform(-8, 5, 20000))
+    # FP32 inputs (the weights are FP32): torch converts through FP32, which would round
+    # an FP64 input twice
+    x = x[np.abs(x) <= 448.0].astype(np.float32).astype(np.float64)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(ntbc.e4m3_round(x), want)
+
+
+def test_e4m3_codes_round_trip():
+    table = _e4m3_table()
+    codes = ntbc.e4m3_code(table)
+    np.testing.assert_array_equal(codes, np.arange(127, dtype=np.uint8))
+    np.testing.assert_array_equal(ntbc.e4m3_code(-table), np.arange(127, dtype=np.uint8) | 0x80)
+    assert ntbc.e4m3_code(ntbc.e4m3_round(-1e-5)) == 0x80                       # rounds to -0
+
+
+@pytest.mark.parametrize("m", [1.0, 448.0, 448.0 * 2 ** -5, 448.0 * 2 ** 3 + 1e-9, 0.0731, 3.5e-3, 1234.5, 2.0 ** -20])
+def test_fp8_layer_exponent_is_smallest(m):
+    e = ntbc.fp8_layer_exponent(np.array([0.5 * m, -m, 0.0]))
+    assert m <= 448.0 * 2.0 ** e and m > 448.0 * 2.0 ** (e - 1)
+    assert ntbc.fp8_layer_exponent(np.zeros(4)) == 0
+
+
+def test_fp8_params_error_bound():
+    """Relative error of a normal E4M3 rounding is at most 2^-4; every layer's maximum
+    lands in the top binade (no saturation)."""
+    rng = np.random.default_rng(2)
+    params = dict(color_grid=[], endpoint_grid=[],
+                  color_mlp=[(rng.standard_normal((64, 24)) * 0.3, rng.standard_normal(64) * 0.01)],
+                  endpoint_mlp=[(rng.standard_normal((16, 64)) * 3.0, np.zeros(16))])
+    q, exps, codes = ntbc.fp8_params(params)
+    for (W, b), (qW, qb), e in zip(params["color_mlp"] + params["endpoint_mlp"], q["color_mlp"] + q["endpoint_mlp"], exps):
+        for v, qv in ((W, qW), (b, qb)):
+            big = np.abs(v) >= 2.0 ** (e - 6)
+            assert np.all(np.abs(qv - v)[big] <= 2.0 ** -4 * np.abs(v)[big])
+            assert np.all(np.abs(qv - v)[~big] <= 2.0 ** (e - 10))
+        assert np.max(np.abs(np.concatenate([qW.ravel(), qb.ravel()]))) <= 448.0 * 2.0 ** e
+
+
+# ----------------------------------------------------------------------------
+# vector-Jacobian product of the raw outputs (the differentiable-function form)
+# ----------------------------------------------------------------------------
+
+def _vjp_case(seed=0, act="selu"):
+    cres = [4, 7]
+    desc = ntbc.ModelDesc(16, 16, [1, 4], cres, ntbc.endpoint_resolutions(cres, 4), hidden_layers=2, activation=act)
+    p0 = synth.init_params(cres, desc.endpoint_res, 2, desc.mlp_dims("color"), desc.mlp_dims("endpoint"), seed)
+    params = synth.random_params_like(p0, seed=seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    ids = np.array([0, 3, 5, 15, 3])
+    g_e = rng.standard_normal((len(ids), desc.out_endpoint))
+    g_c = rng.standard_normal((len(ids), 16, desc.out_color))
+    return desc, params, ids, g_e, g_c
+
+
+@pytest.mark.parametrize("act", ["selu", "relu"])
+def test_outputs_vjp_directional_finite_difference(act):
+    desc, params, ids, g_e, g_c = _vjp_case(act=act)
+    e, c, grads = ntbc.outputs_vjp(desc, params, ids, g_e, g_c)
+    e2, c2 = ntbc.forward_blocks(desc, params, ids)
+    np.testing.assert_allclose(e, e2, rtol=1e-12)
+    np.testing.assert_allclose(c, c2, rtol=1e-12)
+    parts = [np.asarray(a, np.float64) for a in ntbc.flatten_params(params)]
+    flat = np.concatenate([a.ravel() for a in parts])
+    gflat = np.concatenate([np.asarray(a, np.float64).ravel() for a in ntbc.flatten_params(grads)])
+    cuts = np.cumsum([a.size for a in parts])[:-1]
+
+    def unflat(x):
+        return ntbc.unflatten_like(params, [c.reshape(a.shape) for c, a in zip(np.split(x, cuts), parts)])
+
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    for _ in range(4):
+        d = rng.standard_normal(flat.size)
+
+        def f(x):
+            p = unflat(x)
+            ee, cc = ntbc.forward_blocks(desc, p, ids)
+            return float(np.sum(g_e * ee) + np.sum(g_c * cc))
+        fd = (f(flat + h * d) - f(flat - h * d)) / (2 * h)
+        assert abs(fd - float(gflat @ d)) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_outputs_vjp_qat_is_straight_through():
+    # with QAT the gradient is the float-grid gradient taken at the fake-quantised grids,
+    # times the unclamped mask (Sec. 2.3: the STE passes the gradient through round())
+    desc, params, ids, g_e, g_c = _vjp_case(seed=3)
+    _, _, gq = ntbc.outputs_vjp(desc, params, ids, g_e, g_c, qat_bits=4)
+    fq = dict(params)
+    masks = {}
+    for key in ("color_grid", "endpoint_grid"):
+        pairs = [ntbc.qat_fake_quant(g, 4) for g in params[key]]
+        fq[key] = [p[0] for p in pairs]
+        masks[key] = [p[1] for p in pairs]
+    _, _, gf = ntbc.outputs_vjp(desc, fq, ids, g_e, g_c)
+    for key in ("color_grid", "endpoint_grid"):
+        for a, b, m in zip(gq[key], gf[key], masks[key]):
+            np.testing.assert_allclose(a, b * m, rtol=1e-12, atol=1e-15)
+    for key in ("color_mlp", "endpoint_mlp"):
+        for (aW, ab), (bW, bb) in zip(gq[key], gf[key]):
+            np.testing.assert_allclose(aW, bW, rtol=1e-12)
+            np.testing.assert_allclose(ab, bb, rtol=1e-12)
