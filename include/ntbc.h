@@ -280,21 +280,34 @@ typedef struct {
     float temperature;          /* softmax temperature T (0.01) */
     int warmup;                 /* linear warm-up steps (10) */
     uint64_t seed;              /* Philox key of the batch sampler */
+    int precision;              /* NTBC_TRAIN_FP32 or NTBC_TRAIN_BF16 (see below) */
 } ntbc_train_config;
+
+/*
+ * Training arithmetic:
+ *   NTBC_TRAIN_FP32  layer-by-layer FP32 kernels (activations in HBM, feature-major)
+ *   NTBC_TRAIN_BF16  one fused tensor-core pass per network: BF16 MMA operands (features,
+ *                    activations, weights, deltas) with FP32 accumulation in TMEM; losses,
+ *                    sigmoid, straight-through argmax, grid gather / scatter and Adam in FP32.
+ *                    Activations live on chip for one 128-sample tile, so device memory does
+ *                    not grow with the batch. Gradients within about 2e-2 of FP64.
+ */
+enum { NTBC_TRAIN_FP32 = 0, NTBC_TRAIN_BF16 = 1 };
 
 /*
  * Losses and gradients of one training step on the given blocks (all 16
  * texels of each), for the current FP32 master parameters.
  *   block_ids  device int32 [n_blocks]
  *   qat_bits   0 (float grids) or the QAT width (fake-quantised grids, STE)
+ *   precision  NTBC_TRAIN_FP32 or NTBC_TRAIN_BF16
  *   grads      device float [layout.total], overwritten with d loss / d params
  *              (endpoint parameters: of L_e + L_cd; colour: of L_c + L_cd)
  *   losses     device float [6]: L_e, L_cd(endpoint), L_c, L_cd(colour),
  *              L_endpoint, L_color
  */
 ntbc_status ntbc_train_grads(ntbc_model* model, const ntbc_material* mat, const int32_t* block_ids,
-                             int n_blocks, int qat_bits, float temperature, float* grads,
-                             float* losses, void* stream);
+                             int n_blocks, int qat_bits, float temperature, int precision,
+                             float* grads, float* losses, void* stream);
 
 /*
  * Forward and vector-Jacobian product of the raw network outputs on the FP32 master

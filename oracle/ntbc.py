@@ -234,28 +234,57 @@ def _act_grad(z, kind):
     return selu_grad(z) if kind == "selu" else (z > 0).astype(np.float64)
 
 
-def mlp_forward(layers, x, kind):
-    """layers: [(W [out, in], b [out]), ...]; hidden layers use `kind`, the last sigmoid."""
-    h = x
+def bf16_round(x):
+    """Nearest BFloat16 value (1 sign, 8 exponent, 7 mantissa bits: the FP32 exponent range
+    with a 2^-7 relative spacing, subnormal spacing 2^-133), ties to even mantissa."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(np.maximum(a, 2.0 ** -126))          # a = m 2^ex, m in [0.5, 1)
+    step = np.ldexp(1.0, ex - 1 - 7)
+    q = np.round(a / step) * step
+    return np.copysign(q, x)
+
+
+def _act_grad_from_out(a, kind):
+    """The activation's derivative written through its output a: SELU' = lambda (a > 0),
+    a + lambda alpha (a <= 0, since SELU(z) = lambda alpha (e^z - 1) there); ReLU' = [a > 0]."""
+    if kind == "selu":
+        return np.where(a > 0, SELU_LAMBDA, a + SELU_LAMBDA * SELU_ALPHA)
+    return (a > 0).astype(np.float64)
+
+
+def mlp_forward(layers, x, kind, rnd=None):
+    """layers: [(W [out, in], b [out]), ...]; hidden layers use `kind`, the last sigmoid.
+    rnd (optional): rounding applied to every matrix-product operand (inputs, hidden
+    activations, weights and biases), the products themselves exact: the reduced-precision
+    training arithmetic (BF16 operands, wide accumulation)."""
+    r = rnd or (lambda v: v)
+    h = r(x)
     cache = []
     for i, (W, b) in enumerate(layers):
-        z = h @ np.asarray(W, np.float64).T + np.asarray(b, np.float64)
+        z = h @ r(np.asarray(W, np.float64)).T + r(np.asarray(b, np.float64))
         cache.append((h, z))
-        h = _act(z, kind) if i + 1 < len(layers) else sigmoid(z)
+        h = r(_act(z, kind)) if i + 1 < len(layers) else sigmoid(z)
     return h, cache
 
 
-def mlp_backward(layers, cache, y, g_y, kind):
-    """Returns (g_x, [(gW, gb), ...])."""
+def mlp_backward(layers, cache, y, g_y, kind, rnd=None):
+    """Returns (g_x, [(gW, gb), ...]). With rnd, every matrix-product operand of the backward
+    (the deltas and the weights; the activations were rounded by the forward) is rounded,
+    and the activation derivative is taken from the rounded activation."""
     grads = [None] * len(layers)
-    g = g_y * y * (1.0 - y)                                   # through the sigmoid
+    r = rnd or (lambda v: v)
+    g = r(g_y * y * (1.0 - y))                                # through the sigmoid
     for i in range(len(layers) - 1, -1, -1):
-        W = np.asarray(layers[i][0], np.float64)
+        W = r(np.asarray(layers[i][0], np.float64))
         h, _ = cache[i]
         grads[i] = (g.T @ h, g.sum(axis=0))
         g_h = g @ W
         if i > 0:
-            g = g_h * _act_grad(cache[i - 1][1], kind)
+            if rnd is None:
+                g = g_h * _act_grad(cache[i - 1][1], kind)
+            else:
+                g = r(g_h * _act_grad_from_out(cache[i][0], kind))
         else:
             g = g_h
     return g, grads
@@ -557,12 +586,13 @@ def _dist(a, P):
     return -nrm, diff, np.maximum(nrm, NORM_GUARD)
 
 
-def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_bits=0, soft=False):
+def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_bits=0, soft=False, bf16=False):
     """One training step's losses and gradients (FP64) for a batch of whole blocks.
 
     textures: list of uint8 arrays (H x W x 3 or H x W); ref_blocks: list of [nblocks, 8].
     soft=True evaluates the surrogate in which the forward decode is the softmax
     expectation itself (the backward is then that surrogate's exact gradient).
+    bf16=True rounds every MLP matrix-product operand to BF16 (forward and backward).
     Returns (losses dict, grads dict shaped like params).
     """
     block_ids = np.asarray(block_ids, np.int64)
@@ -594,7 +624,8 @@ def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_
     eg, emask = grids("endpoint_grid")
     s, tt = block_coords(desc.blocks_x, desc.blocks_y, block_ids % desc.blocks_x, block_ids // desc.blocks_x)
     xe, ecache_g = grid_lookup(eg, s, tt)
-    e_hat, ecache = mlp_forward(params["endpoint_mlp"], xe, desc.activation)
+    rnd = bf16_round if bf16 else None
+    e_hat, ecache = mlp_forward(params["endpoint_mlp"], xe, desc.activation, rnd)
     L_e = np.mean((e_hat - e_ref) ** 2)
     g_e = 2.0 * (e_hat - e_ref) / e_hat.size
     n_cd = nb * 16 * C_out
@@ -614,14 +645,14 @@ def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_
         g_p = g_d[..., None] * diff / nrm[..., None]                     # d d_n / d p_n = (c - p_n)/||.||
         g_e[:, eo:eo + ch] += np.einsum("bikc,bk->bc", g_p, a_n)
         g_e[:, eo + ch:eo + 2 * ch] += np.einsum("bikc,bk->bc", g_p, b_n)
-    g_xe, g_emlp = mlp_backward(params["endpoint_mlp"], ecache, e_hat, g_e, desc.activation)
+    g_xe, g_emlp = mlp_backward(params["endpoint_mlp"], ecache, e_hat, g_e, desc.activation, rnd)
     g_egrid = grid_lookup_backward(eg, ecache_g, g_xe, emask)
 
     # ---- colour network
     cg, cmask = grids("color_grid")
     u, v = texel_coords(desc.width, desc.height, xs.ravel(), ys.ravel())
     xc, ccache_g = grid_lookup(cg, u, v)
-    c_flat, ccache = mlp_forward(params["color_mlp"], xc, desc.activation)
+    c_flat, ccache = mlp_forward(params["color_mlp"], xc, desc.activation, rnd)
     c_hat = c_flat.reshape(nb, 16, C_out)
     L_c = np.mean((c_hat - c_ref) ** 2)
     g_c = 2.0 * (c_hat - c_ref) / c_hat.size
@@ -638,7 +669,8 @@ def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_
         g_dec = -2.0 * (c - dec) / n_cd
         g_d = _ste_grad_d(g_dec, sig, pr[:, None], T)
         g_c[:, :, co:co + ch] += np.einsum("bik,bikc->bic", g_d, -diff / nrm[..., None])
-    g_xc, g_cmlp = mlp_backward(params["color_mlp"], ccache, c_flat, g_c.reshape(nb * 16, C_out), desc.activation)
+    g_xc, g_cmlp = mlp_backward(params["color_mlp"], ccache, c_flat, g_c.reshape(nb * 16, C_out), desc.activation,
+                                rnd)
     g_cgrid = grid_lookup_backward(cg, ccache_g, g_xc, cmask)
 
     losses = dict(L_e=L_e, L_cd_endpoint=L_cd_e, L_c=L_c, L_cd_color=L_cd_c,

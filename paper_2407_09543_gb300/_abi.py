@@ -10,6 +10,7 @@ library_path = os.path.join(HERE, "libntbc.so")
 BC1, BC4 = 1, 4
 ACT_SELU, ACT_RELU = 0, 1
 PREC_FP32, PREC_FP16, PREC_FP16_FAST, PREC_FP8 = 0, 1, 2, 3
+TRAIN_FP32, TRAIN_BF16 = 0, 1
 MAX_TEXTURES, MAX_LEVELS, MAX_MLP_LAYERS = 8, 16, 4
 STATUS_NAMES = {0: "NTBC_OK", 1: "NTBC_EINVAL", 2: "NTBC_ENOMEM", 3: "NTBC_ECUDA", 4: "NTBC_ETIMEOUT",
                 5: "NTBC_ENONFINITE", 6: "NTBC_EUNSUPPORTED"}
@@ -82,12 +83,12 @@ class Material(ctypes.Structure):
 class TrainConfig(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_long), ("batch_texels", c_int), ("qat_fraction", c_float), ("grid_bits", c_int),
                 ("lr_grid", c_float), ("lr_mlp", c_float), ("temperature", c_float), ("warmup", c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("precision", c_int)]
 
     @classmethod
     def make(cls, steps, batch_texels, qat_fraction=0.0, grid_bits=8, lr_grid=0.01, lr_mlp=0.005,
-             temperature=0.01, warmup=10, seed=0):
-        return cls(steps, batch_texels, qat_fraction, grid_bits, lr_grid, lr_mlp, temperature, warmup, seed)
+             temperature=0.01, warmup=10, seed=0, precision=0):
+        return cls(steps, batch_texels, qat_fraction, grid_bits, lr_grid, lr_mlp, temperature, warmup, seed, precision)
 
 
 _P = c_void_p
@@ -111,7 +112,7 @@ _SIGS = {
     "ntbc_model_load": (c_int, [_P, _P, c_size_t, _P]),
     "ntbc_infer_to_bc": (c_int, [_P, ctypes.POINTER(_P), _P]),
     "ntbc_forward": (c_int, [_P, _P, c_int, _P, _P, _P]),
-    "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, _P, _P, _P]),
+    "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, c_int, _P, _P, _P]),
     "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
                                          c_float, _P, _P, _P]),
     "ntbc_vjp": (c_int, [_P, _P, c_int, c_int, _P, _P, _P, _P, _P, _P]),
@@ -246,9 +247,9 @@ class Model:
                                 _stream(stream)))
 
     def train_grads(self, material: Material, block_ids, grads, losses=None, qat_bits=0, temperature=0.01,
-                    stream=None):
+                    precision=0, stream=None):
         _check(lib.ntbc_train_grads(self.handle, ctypes.byref(material), _ptr(block_ids), block_ids.numel(),
-                                    qat_bits, temperature, _ptr(grads), _ptr(losses), _stream(stream)))
+                                    qat_bits, temperature, precision, _ptr(grads), _ptr(losses), _stream(stream)))
 
     def vjp(self, block_ids, qat_bits=0, g_e=None, g_c=None, grads=None, e_hat=None, c_hat=None, stream=None):
         _check(lib.ntbc_vjp(self.handle, _ptr(block_ids), block_ids.numel(), qat_bits, _ptr(g_e), _ptr(g_c),

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libntbc.so")
-SOURCES = ["bc_codec.cu", "ntbc_model.cu", "ntbc_infer.cu", "ntbc_infer_tc.cu", "ntbc_train.cu"]
+SOURCES = ["bc_codec.cu", "ntbc_model.cu", "ntbc_infer.cu", "ntbc_infer_tc.cu", "ntbc_train.cu", "ntbc_train_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-v"]
 

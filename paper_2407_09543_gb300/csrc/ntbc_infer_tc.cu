@@ -20,6 +20,7 @@
 
 #include "ntbc_internal.cuh"
 #include "ntbc_kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace ntbc {
 
@@ -29,68 +30,6 @@ constexpr int kTcTiles = kTcUnitBlocks * 16 / kTcRows;   // 16 colour tiles per 
 constexpr int kTcMaxGroups = 4;
 constexpr int kTcColsPerGroup = 128;           // two 64-column accumulator regions per group
 constexpr int kTcPalBytes = 12;            // integer palette bytes per block per texture
-constexpr long long kTcWaitLimit = 1LL << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// UMMA shared-memory descriptor: K-major, no swizzle. k_stride: bytes between
-// core matrices adjacent along K; mn_stride: bytes between core matrices adjacent
-// along M (or N).
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t k_stride, uint32_t mn_stride) {
-    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((k_stride >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((mn_stride >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// instruction descriptor, kind::f16: A = B = F16, D = F32, both K-major
-__host__ __device__ constexpr uint32_t umma_idesc(int n) {
-    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-    uint32_t done = 0;
-    for (long long it = 0; it < kTcWaitLimit; ++it) {
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(smem_u32(bar)), "r"(phase));
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kTcRows) : "memory"); }
-
-// byte offset of element (r, k) in a tile of K columns (16-bit elements)
-__host__ __device__ __forceinline__ int core_byte(int r, int k, int K) {
-    return (((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)) * 2;
-}
-
 // store 8 FP16 values (k-group kg) of row r
 __device__ __forceinline__ void st_row8(unsigned char* tile, int r, int kg, int K, const float* v) {
     __half2 h0 = __floats2half2_rn(v[0], v[1]), h1 = __floats2half2_rn(v[2], v[3]);

@@ -15,12 +15,13 @@
 
 #include "ntbc_internal.cuh"
 #include "ntbc_kernels.cuh"
+#include "ntbc_train_common.cuh"
+#include "ntbc_train_tc.cuh"
 
 namespace ntbc {
 
 constexpr double kAdamB1 = 0.9, kAdamB2 = 0.999;
 constexpr float kAdamEps = 1e-15f;
-constexpr float kNormGuard = 1e-6f;
 
 struct StepState {
     long long step;          // current step index (0-based)
@@ -52,6 +53,8 @@ struct ntbc_train_state {
     float* qzero = nullptr;
     unsigned* qmm = nullptr;
     int* qat_flag = nullptr;          // points at st->qat
+    unsigned char* tc_img = nullptr;  // BF16 weight images of both networks (tensor-core training)
+    int* tc_err = nullptr;            // set when a bounded wait of the tensor-core training gives up
 };
 
 namespace ntbc {
@@ -120,25 +123,6 @@ __global__ void set_qat_kernel(StepState* st, int on) {
 // ---------------------------------------------------------------------------
 // batch gather of grid features
 // ---------------------------------------------------------------------------
-
-// sample k of the colour network is texel (k & 15) of block ids[k >> 4];
-// sample k of the endpoint network is block ids[k]
-__device__ __forceinline__ void sample_coords(const ModelView& mv, bool color, const int32_t* ids, int k, float& u,
-                                              float& v, int& x, int& y) {
-    if (color) {
-        int b = ids[k >> 4], i = k & 15;
-        x = 4 * (b % mv.bw) + (i & 3);
-        y = 4 * (b / mv.bw) + (i >> 2);
-        u = ((float)x + 0.5f) / (float)mv.width;
-        v = ((float)y + 0.5f) / (float)mv.height;
-    } else {
-        int b = ids[k];
-        x = b % mv.bw;
-        y = b / mv.bw;
-        u = ((float)x + 0.5f) / (float)mv.bw;
-        v = ((float)y + 0.5f) / (float)mv.bh;
-    }
-}
 
 __global__ void gather_kernel(ModelView mv, bool color, GridSrc src, const int32_t* __restrict__ ids, int B,
                               float* __restrict__ X) {
@@ -279,92 +263,6 @@ __global__ void __launch_bounds__(256) dense_bwd_weight_kernel(const float* __re
 // ---------------------------------------------------------------------------
 // losses with the straight-through argmax
 // ---------------------------------------------------------------------------
-
-// linear-order float palette P_n = a_n e0 + b_n e1 + const_n (Eq. palette / Eq. weightBC4)
-__device__ __forceinline__ int palette_coeffs(int fmt, bool eight, float a[8], float b[8], float c[8]) {
-    if (fmt == NTBC_BC1) {
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            float w = (float)n / 3.f;
-            a[n] = 1.f - w;
-            b[n] = w;
-            c[n] = 0.f;
-        }
-        return 4;
-    }
-    if (eight) {
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            float w = (float)n / 7.f;
-            a[n] = 1.f - w;
-            b[n] = w;
-            c[n] = 0.f;
-        }
-    } else {
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            bool interp = n >= 1 && n <= 6;
-            float w = interp ? (float)(n - 1) / 5.f : 0.f;
-            a[n] = interp ? 1.f - w : 0.f;
-            b[n] = interp ? w : 0.f;
-            c[n] = n == 7 ? 1.f : 0.f;
-        }
-    }
-    return 8;
-}
-
-// decoded reference endpoints in [0, 1] (stored order) of block b of texture t
-__device__ __forceinline__ void ref_endpoints(int fmt, const uint8_t* blocks, int b, float e0[3], float e1[3]) {
-    uint32_t lo = *reinterpret_cast<const uint32_t*>(blocks + (long long)b * 8);
-    if (fmt == NTBC_BC1) {
-        int r, g, bb;
-        expand565(lo & 0xFFFF, r, g, bb);
-        e0[0] = r / 255.f; e0[1] = g / 255.f; e0[2] = bb / 255.f;
-        expand565(lo >> 16, r, g, bb);
-        e1[0] = r / 255.f; e1[1] = g / 255.f; e1[2] = bb / 255.f;
-    } else {
-        e0[0] = (float)(lo & 0xFF) / 255.f;
-        e1[0] = (float)((lo >> 8) & 0xFF) / 255.f;
-    }
-}
-
-__device__ __forceinline__ float texel_value(const uint8_t* tex, int fmt, int w, int x, int y, int ch) {
-    int C = fmt == NTBC_BC1 ? 3 : 1;
-    return (float)tex[((long long)y * w + x) * C + ch] / 255.f;
-}
-
-struct TexPtrs {
-    const uint8_t* texels[NTBC_MAX_TEXTURES];
-    const uint8_t* blocks[NTBC_MAX_TEXTURES];
-};
-
-__device__ __forceinline__ void block_reduce_add(double* acc, float v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc, (double)v);
-}
-
-// Softmax-expectation backward of the hard decode dec = P_{argmax d}:
-// g_d[n] = (1/T) sigma_n sum_c g_dec[c] (P[n][c] - sum_i sigma_i P[i][c])
-__device__ __forceinline__ void ste_grad(int K, int C, const float d[8], const float P[8][3], const float g_dec[3],
-                                         float T, float g_d[8]) {
-    float m = d[0];
-    for (int n = 1; n < K; ++n) m = fmaxf(m, d[n]);
-    float sig[8], sum = 0.f;
-    for (int n = 0; n < K; ++n) {
-        sig[n] = expf((d[n] - m) / T);
-        sum += sig[n];
-    }
-    float pbar[3] = {0.f, 0.f, 0.f};
-    for (int n = 0; n < K; ++n) {
-        sig[n] /= sum;
-        for (int c = 0; c < C; ++c) pbar[c] += sig[n] * P[n][c];
-    }
-    for (int n = 0; n < K; ++n) {
-        float s = 0.f;
-        for (int c = 0; c < C; ++c) s += g_dec[c] * (P[n][c] - pbar[c]);
-        g_d[n] = sig[n] * s / T;
-    }
-}
 
 // colour network: per texel sample, L_c + L_cd with distances from c_hat to the
 // reference palette; writes D[o][k] = dL/dz_out (through the sigmoid)
@@ -528,75 +426,17 @@ __global__ void loss_finalize_kernel(const double* __restrict__ acc, float* __re
 // grid scatter-add (bilinear adjoint), with the QAT straight-through mask
 // ---------------------------------------------------------------------------
 
-// One straight-through factor per corner value: 1 where the QAT code was not clamped.
-__device__ __forceinline__ float2 ste_mask(float2 add, const float* f32, long long corner, float s, float z, float qm) {
-    float2 r = *reinterpret_cast<const float2*>(f32 + corner);
-    float q0 = roundf(__fdiv_rn(r.x, s)) + z, q1 = roundf(__fdiv_rn(r.y, s)) + z;
-    if (q0 < 0.f || q0 > qm) add.x = 0.f;
-    if (q1 < 0.f || q1 > qm) add.y = 0.f;
-    return add;
-}
-
-// Bilinear adjoint: d loss / d features back to the 4 corners of every level.
-// Colour network: the 16 texels of a block sit in one half-warp and their corner
-// indices are non-decreasing in x (lane & 3) and in y (lane >> 2), so equal corners form
-// contiguous runs; a segmented scan along x, then along y, leaves each distinct corner's
-// total in the last lane of its run, which issues the only atomic for that corner.
+// grid scatter-add of the batch's feature gradients G (feature-major [2L][B])
 __global__ void grid_scatter_kernel(ModelView mv, bool color, const int32_t* __restrict__ ids, int B,
                                     const float* __restrict__ G, GridSrc src, float* __restrict__ ggrad) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = k < B;
     int kc = valid ? k : 0;
     const NetView& nv = color ? mv.color : mv.endpoint;
-    float u, v;
-    int x, y;
-    sample_coords(mv, color, ids, kc, u, v, x, y);
-    int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
-    const int lx = k & 3, ly = (k >> 2) & 3;
-    for (int l = 0; l < nv.levels; ++l) {
-        int res = nv.res[l];
-        float px = u * (float)(res - 1), py = v * (float)(res - 1);
-        int ix = min((int)floorf(px), res - 2), iy = min((int)floorf(py), res - 2);
-        float fx = px - (float)ix, fy = py - (float)iy;
-        float g0 = valid ? G[(long long)(2 * l) * B + kc] : 0.f, g1 = valid ? G[(long long)(2 * l + 1) * B + kc] : 0.f;
-        float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+    float g[2 * NTBC_MAX_LEVELS];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int cx = ix + (j & 1), cy = iy + (j >> 1);
-            long long corner = nv.grid_off[l] + ((long long)cy * res + cx) * 2;
-            float2 add = make_float2(w[j] * g0, w[j] * g1);
-            if (qat_bits > 0 && valid)
-                add = ste_mask(add, src.f32, corner, src.scale[l], src.zero[l], (float)((1 << qat_bits) - 1));
-            bool issue = valid;
-            if (color) {
-#pragma unroll
-                for (int dd = 1; dd <= 2; dd <<= 1) {          // runs along x
-                    float px0 = __shfl_up_sync(0xffffffffu, add.x, dd), px1 = __shfl_up_sync(0xffffffffu, add.y, dd);
-                    int pk = __shfl_up_sync(0xffffffffu, cx, dd);
-                    if (lx >= dd && pk == cx) {
-                        add.x += px0;
-                        add.y += px1;
-                    }
-                }
-                int nx = __shfl_down_sync(0xffffffffu, cx, 1);
-                bool last_x = lx == 3 || nx != cx;
-                if (!last_x) add = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int dd = 4; dd <= 8; dd <<= 1) {          // runs along y
-                    float py0 = __shfl_up_sync(0xffffffffu, add.x, dd), py1 = __shfl_up_sync(0xffffffffu, add.y, dd);
-                    int pk = __shfl_up_sync(0xffffffffu, cy, dd);
-                    if (ly >= dd / 4 && pk == cy) {
-                        add.x += py0;
-                        add.y += py1;
-                    }
-                }
-                int ny = __shfl_down_sync(0xffffffffu, cy, 4);
-                bool last_y = ly == 3 || ny != cy;
-                issue = valid && last_x && last_y;
-            }
-            if (issue) atomicAdd(reinterpret_cast<float2*>(ggrad + corner), add);
-        }
-    }
+    for (int i = 0; i < 2 * NTBC_MAX_LEVELS; ++i) g[i] = (valid && i < 2 * nv.levels) ? G[(long long)i * B + kc] : 0.f;
+    scatter_sample(mv, color, ids, kc, k, valid, g, src, ggrad);
 }
 
 // ---------------------------------------------------------------------------
@@ -654,6 +494,7 @@ void ntbc_train_release(ntbc_model* m) {
     cudaFree(ts->loss_acc);
     cudaFree(ts->st);
     cudaFree(ts->qscale);
+    cudaFree(ts->tc_img);
     delete ts;
     m->train = nullptr;
 }
@@ -694,6 +535,15 @@ static ntbc_status ensure_train_state(ntbc_model* m, int n_blocks) {
         ts->qmm = reinterpret_cast<unsigned*>(ts->qscale + 2 * levels);
         ts->qat_flag = &ts->st->qat;
         NTBC_CHECK_CUDA(cudaMemset(ts->st, 0, sizeof(StepState)));
+        ModelView mv = make_view(m->desc, m->layout);
+        size_t img = (size_t)train_tc_net_desc(mv, true).img_bytes + train_tc_net_desc(mv, false).img_bytes;
+        st = device_alloc((void**)&ts->tc_img, img + 16, "training weight images");
+        if (st != NTBC_OK) {
+            ntbc_train_release(m);
+            return st;
+        }
+        ts->tc_err = reinterpret_cast<int*>(ts->tc_img + img);
+        NTBC_CHECK_CUDA(cudaMemset(ts->tc_err, 0, sizeof(int)));
     }
     (void)grads_keep;
     ts->cap_blocks = n_blocks;
@@ -824,7 +674,7 @@ static ntbc_status train_sources(ntbc_model* m, int qat_bits, bool dynamic_qat, 
 }
 
 static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const int32_t* ids, int nb, int qat_bits,
-                                bool dynamic_qat, float T, float* grads, cudaStream_t s) {
+                                bool dynamic_qat, float T, int precision, float* grads, cudaStream_t s) {
     ntbc_train_state* ts = m->train;
     ModelView mv = make_view(m->desc, m->layout);
     TexPtrs tp;
@@ -838,8 +688,21 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
     if (st0 != NTBC_OK) return st0;
     NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
     NTBC_CHECK_CUDA(cudaMemsetAsync(ts->loss_acc, 0, 6 * sizeof(double), s));
-    ntbc_status st = run_net(m, mv, true, tp, ids, nb * 16, csrc, T, grads, ts->loss_acc, s);
-    if (st == NTBC_OK) st = run_net(m, mv, false, tp, ids, nb, esrc, T, grads, ts->loss_acc, s);
+    ntbc_status st;
+    if (precision == NTBC_TRAIN_BF16) {
+        TrNet cn = train_tc_net_desc(mv, true), en = train_tc_net_desc(mv, false);
+        unsigned char* cimg = ts->tc_img;
+        unsigned char* eimg = ts->tc_img + cn.img_bytes;
+        st = train_tc_image(m->params, cn, cimg, s);
+        if (st == NTBC_OK) st = train_tc_image(m->params, en, eimg, s);
+        if (st == NTBC_OK)
+            st = train_tc_launch(mv, true, cn, cimg, csrc, tp, ids, nb * 16, T, grads, ts->loss_acc, ts->tc_err, s);
+        if (st == NTBC_OK)
+            st = train_tc_launch(mv, false, en, eimg, esrc, tp, ids, nb, T, grads, ts->loss_acc, ts->tc_err, s);
+    } else {
+        st = run_net(m, mv, true, tp, ids, nb * 16, csrc, T, grads, ts->loss_acc, s);
+        if (st == NTBC_OK) st = run_net(m, mv, false, tp, ids, nb, esrc, T, grads, ts->loss_acc, s);
+    }
     if (st != NTBC_OK) return st;
     loss_finalize_kernel<<<1, 32, 0, s>>>(ts->loss_acc, ts->losses);
     NTBC_CHECK_LAUNCH("loss finalize");
@@ -870,7 +733,7 @@ ntbc_status ntbc_sample_blocks(uint64_t seed, long step, int n, int n_blocks, in
 }
 
 ntbc_status ntbc_train_grads(ntbc_model* m, const ntbc_material* mat, const int32_t* block_ids, int n_blocks,
-                             int qat_bits, float temperature, float* grads, float* losses, void* stream) {
+                             int qat_bits, float temperature, int precision, float* grads, float* losses, void* stream) {
     clear_error();
     if (!m || !block_ids || !grads) return fail(NTBC_EINVAL, "null argument");
     ntbc_status st = check_material(m, mat);
@@ -878,10 +741,11 @@ ntbc_status ntbc_train_grads(ntbc_model* m, const ntbc_material* mat, const int3
     if (n_blocks <= 0) return fail(NTBC_EINVAL, "need at least one block");
     if (qat_bits != 0 && qat_bits != 8 && qat_bits != 4) return fail(NTBC_EINVAL, "qat_bits must be 0, 4 or 8");
     if (!(temperature > 0.f)) return fail(NTBC_EINVAL, "temperature must be positive");
+    if (precision != NTBC_TRAIN_FP32 && precision != NTBC_TRAIN_BF16) return fail(NTBC_EINVAL, "unknown training precision");
     st = ensure_train_state(m, n_blocks);
     if (st != NTBC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    st = grads_on_ids(m, mat, block_ids, n_blocks, qat_bits, false, temperature, grads, s);
+    st = grads_on_ids(m, mat, block_ids, n_blocks, qat_bits, false, temperature, precision, grads, s);
     if (st != NTBC_OK) return st;
     if (losses) NTBC_CHECK_CUDA(cudaMemcpyAsync(losses, m->train->losses, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return NTBC_OK;
@@ -946,6 +810,8 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     if (cfg->qat_fraction < 0.f || (cfg->qat_fraction > 0.f && cfg->grid_bits != 8 && cfg->grid_bits != 4))
         return fail(NTBC_EINVAL, "QAT needs grid_bits 8 or 4");
     if (!(cfg->temperature > 0.f) || cfg->warmup < 0) return fail(NTBC_EINVAL, "bad temperature or warm-up");
+    if (cfg->precision != NTBC_TRAIN_FP32 && cfg->precision != NTBC_TRAIN_BF16)
+        return fail(NTBC_EINVAL, "unknown training precision");
     int nb = cfg->batch_texels / 16;
     int n_blocks = (m->desc.width / 4) * (m->desc.height / 4);
     long long qat_steps = cfg->qat_fraction > 0.f ? (long long)std::ceil((double)cfg->qat_fraction * (double)cfg->steps) : 0;
@@ -968,7 +834,7 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     NTBC_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     step_begin_kernel<<<1, 32, 0, cap>>>(ts->st, -1, cfg->steps, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup, qbits);
     sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, 0, nb, n_blocks, ts->ids);
-    st = grads_on_ids(m, mat, ts->ids, nb, qbits, true, cfg->temperature, ts->grads, cap);
+    st = grads_on_ids(m, mat, ts->ids, nb, qbits, true, cfg->temperature, cfg->precision, ts->grads, cap);
     if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap);
     step_end_kernel<<<1, 32, 0, cap>>>(ts->st);
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
@@ -989,6 +855,9 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     cudaStreamDestroy(cap);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphLaunch");
     if (se != cudaSuccess) return cuda_fail(se, "training steps");
+    int tc_err = 0;
+    NTBC_CHECK_CUDA(cudaMemcpy(&tc_err, ts->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tc_err) return fail(NTBC_ETIMEOUT, "tensor-core training: a bounded wait gave up");
     float host_losses[6];
     NTBC_CHECK_CUDA(cudaMemcpy(host_losses, ts->losses, sizeof(host_losses), cudaMemcpyDeviceToHost));
     if (losses_out) memcpy(losses_out, host_losses, sizeof(host_losses));

@@ -1,0 +1,848 @@
+// Fused tensor-core training pass of one network (BF16 operands, FP32 accumulation in
+// TMEM): the grid gather with QAT fake quantisation (Sec. 3.3), the MLP forward, the loss
+// with the straight-through argmax (Sec. 3.2, App. A), the backward through every layer
+// and the grid scatter-add, for tiles of 128 samples, with every intermediate kept on chip.
+//
+// A persistent CTA per SM runs one or two independent warpgroups. A warpgroup takes a tile
+// of 128 samples (texels of 8 sampled blocks, or 128 sampled blocks for the endpoint
+// network); row r of every tile is thread r's sample. Shared memory holds, per group, the
+// input features X [128][K0], the hidden activations A_l [128][80] (64 units + the bias
+// column, constant 1) and one delta tile D, all BF16 in the canonical no-swizzle core-matrix
+// layout, plus the CTA's copy of the BF16 weight image (each layer's [N][K] tile).
+//
+// MMAs (M = 128; one elected thread issues, the group waits on its mbarrier):
+//   forward      Z_l = A_{l-1} W_l^T      A K-major (rows = samples), B = the W_l tile
+//   data grad    dA_{l-1} = D_l W_l       A = D (K-major), B = the same W_l tile read
+//                                         MN-major (N = inputs along the tile's columns)
+//   weight grad  dW_l^T += A_{l-1}^T D_l  both operands MN-major: K = the 128 samples;
+//                                         M = the 80 input columns (rows 80..127 of the
+//                                         accumulator are never read), N = the outputs
+//   layer 0      dW_0 += D_0^T X          M = the 64 units (rows 64..127 unused), N = K0
+// The weight-gradient accumulators stay in TMEM across all tiles of the group and are
+// added to the global gradient once, at the end.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "ntbc_internal.cuh"
+#include "ntbc_kernels.cuh"
+#include "ntbc_train_common.cuh"
+#include "ntbc_train_tc.cuh"
+#include "tcgen05.cuh"
+
+namespace ntbc {
+
+constexpr int kTrRows = 128;
+constexpr int kTrHidCols = 80;            // 64 hidden units + the bias K block (column 64 = 1)
+constexpr int kTrMaxGroups = 2;
+constexpr int kTrPad = 1024;              // bytes after a group's tiles: MN-major reads of the
+                                          // unused accumulator rows run past the last tile
+
+// byte offset of the core-matrix chunk (8 columns starting at 8 * kg) of row r, tile of C columns
+__host__ __device__ __forceinline__ int chunk_byte(int r, int kg, int C) {
+    return (((r >> 3) * (C >> 3) + kg) * 64 + (r & 7) * 8) * 2;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void st_chunk_bf16(unsigned char* tile, int r, int kg, int C, const float* v) {
+    uint4 u = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                         pack_bf16x2(v[6], v[7]));
+    *reinterpret_cast<uint4*>(tile + chunk_byte(r, kg, C)) = u;
+}
+
+__device__ __forceinline__ void ld_chunk_bf16(const unsigned char* tile, int r, int kg, int C, float* v) {
+    uint4 u = *reinterpret_cast<const uint4*>(tile + chunk_byte(r, kg, C));
+    uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w[j]);
+        float2 f = __bfloat1622float2(h);
+        v[2 * j] = f.x;
+        v[2 * j + 1] = f.y;
+    }
+}
+
+__device__ __forceinline__ float tmem_ld1f(uint32_t taddr) {
+    uint32_t v;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+    return __uint_as_float(v);
+}
+
+struct TrGroup {
+    unsigned char* X;
+    unsigned char* A[3];
+    unsigned char* D;
+    uint64_t* bar;
+    uint32_t tmem, row;       // group's TMEM base column; this thread's lane address
+    int g, r;
+};
+
+__device__ __forceinline__ bool tr_barrier(int g, volatile int* abort_flag) {
+    proxy_fence();
+    tc_fence_before();
+    group_sync(g);
+    return abort_flag[g] == 0;
+}
+
+__device__ __forceinline__ void tr_wait(const TrGroup& G, uint32_t& phase, volatile int* abort_flag) {
+    if (!mbar_wait(G.bar, phase)) abort_flag[G.g] = 1;
+    phase ^= 1;
+    tc_fence_after();
+}
+
+// ---------------------------------------------------------------------------
+// fast arithmetic (MUFU); every result feeds a BF16 operand or a loss gradient whose
+// comparison bar is far above these errors (relative ~2^-22)
+// ---------------------------------------------------------------------------
+
+constexpr float kL2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_fast(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float act_fast(float z, int act) {
+    if (act != NTBC_ACT_SELU) return fmaxf(z, 0.f);
+    float e = fmaf(kSeluLA, ex2_fast(fminf(z, 0.f) * kL2e), -kSeluLA);
+    return z > 0.f ? kSeluLambda * z : e;
+}
+__device__ __forceinline__ float sigmoid_fast(float z) { return rcp_fast(1.f + ex2_fast(-z * kL2e)); }
+
+// ---------------------------------------------------------------------------
+// losses: every palette / softmax loop runs over all 8 entries (entries n >= K carry no
+// weight) and over a compile-time channel count, so nothing leaves the registers
+// ---------------------------------------------------------------------------
+
+// Softmax-expectation backward of the hard decode (App. A, corrected form):
+// g_d[n] = (1/T) sigma_n sum_c g_dec[c] (P[n][c] - sum_i sigma_i P[i][c]), sigma = softmax(d / T)
+template <int C>
+__device__ __forceinline__ void ste_fast(int K, const float d[8], const float P[8][C], const float g_dec[C], float invT,
+                                         float g_d[8]) {
+    float m = d[0];
+#pragma unroll
+    for (int n = 1; n < 8; ++n)
+        if (n < K) m = fmaxf(m, d[n]);
+    float sig[8], sum = 0.f;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        sig[n] = n < K ? ex2_fast((d[n] - m) * (invT * kL2e)) : 0.f;
+        sum += sig[n];
+    }
+    const float inv = rcp_fast(sum);
+    float pbar[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) pbar[q] = 0.f;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        sig[n] *= inv;
+#pragma unroll
+        for (int q = 0; q < C; ++q) pbar[q] = fmaf(sig[n], P[n][q], pbar[q]);
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < C; ++q) t = fmaf(g_dec[q], P[n][q] - pbar[q], t);
+        g_d[n] = sig[n] * t * invT;
+    }
+}
+
+// linear palette P_n = a_n e0 + b_n e1 + c_n (Eq. palette / Eq. weightBC4), distances
+// d_n = -||x - P_n|| (n < K) and their inverse norms, and the argmax (ties: lowest n)
+template <int C>
+__device__ __forceinline__ int palette_distances(int fmt, const float* e0, const float* e1, const float* x, float P[8][C],
+                                                 float a8[8], float b8[8], float d[8], float inv[8], int& best) {
+    float c8[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) a8[n] = b8[n] = c8[n] = 0.f;       // BC1 fills only n < 4
+    int K = palette_coeffs(fmt, e0[0] > e1[0], a8, b8, c8);
+    float bestv = -3.0e38f;
+    best = 0;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        float sq = 0.f;
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            P[n][q] = fmaf(a8[n], e0[q], fmaf(b8[n], e1[q], c8[n]));
+            float df = x[q] - P[n][q];
+            sq = fmaf(df, df, sq);
+        }
+        float nrm = sqrt_fast(sq);
+        d[n] = n < K ? -nrm : -3.0e38f;
+        inv[n] = rcp_fast(fmaxf(nrm, kNormGuard));
+        if (d[n] > bestv) {
+            bestv = d[n];
+            best = n;
+        }
+    }
+    return K;
+}
+
+template <int C>
+__device__ __forceinline__ void pick(const float P[8][C], int best, float* out) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) out[q] = P[0][q];
+#pragma unroll
+    for (int n = 1; n < 8; ++n)
+        if (n == best)
+#pragma unroll
+            for (int q = 0; q < C; ++q) out[q] = P[n][q];
+}
+
+// colour network, one texture of a texel sample: L_c + L_cd with distances from c_hat to
+// the reference palette; dz = d loss / d z_out (through the sigmoid)
+template <int C>
+__device__ __forceinline__ void color_texture(int fmt, const float* ch, const float* c, const float* e0, const float* e1,
+                                              float invT, float inv_n, bool valid, float* dz, float& lc, float& lcd) {
+    float P[8][C], a8[8], b8[8], d[8], inv[8];
+    int best;
+    int K = palette_distances<C>(fmt, e0, e1, ch, P, a8, b8, d, inv, best);
+    float pb[C], g_dec[C], g[C];
+    pick<C>(P, best, pb);
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        float rr = c[q] - pb[q], e = ch[q] - c[q];
+        if (valid) {
+            lcd = fmaf(rr, rr, lcd);
+            lc = fmaf(e, e, lc);
+        }
+        g_dec[q] = -2.f * rr * inv_n;
+        g[q] = 2.f * e * inv_n;
+    }
+    float g_d[8];
+    ste_fast<C>(K, d, P, g_dec, invT, g_d);
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+        for (int q = 0; q < C; ++q) g[q] -= g_d[n] * (ch[q] - P[n][q]) * inv[n];
+#pragma unroll
+    for (int q = 0; q < C; ++q) dz[q] = valid ? g[q] * ch[q] * (1.f - ch[q]) : 0.f;
+}
+
+// endpoint network, one (block, texel) pair of one texture: the texel's L_cd term with
+// distances to the palette of the predicted endpoints (eh0, eh1) and the decode from the
+// reference palette; adds the pair's contribution to d loss / d (eh0, eh1)
+template <int C>
+__device__ __forceinline__ void endpoint_texel(int fmt, const float* eh0, const float* eh1, const float* e0,
+                                               const float* e1, const float* c, float invT, float inv_ncd, bool valid,
+                                               float* g0, float* g1, float& lcd) {
+    float Ph[8][C], ah[8], bh[8], d[8], inv[8];
+    int best;
+    int K = palette_distances<C>(fmt, eh0, eh1, c, Ph, ah, bh, d, inv, best);
+    float ar[8], br[8], cr[8], Pr[8][C];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) ar[n] = br[n] = cr[n] = 0.f;
+    palette_coeffs(fmt, e0[0] > e1[0], ar, br, cr);
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+        for (int q = 0; q < C; ++q) Pr[n][q] = fmaf(ar[n], e0[q], fmaf(br[n], e1[q], cr[n]));
+    float pb[C], g_dec[C];
+    pick<C>(Pr, best, pb);
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        float rr = c[q] - pb[q];
+        if (valid) lcd = fmaf(rr, rr, lcd);
+        g_dec[q] = valid ? -2.f * rr * inv_ncd : 0.f;
+    }
+    float g_d[8];
+    ste_fast<C>(K, d, Pr, g_dec, invT, g_d);
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            float gp = g_d[n] * (c[q] - Ph[n][q]) * inv[n];       // d d_n / d P_n = (c - P_n) / ||.||
+            g0[q] = fmaf(ah[n], gp, g0[q]);
+            g1[q] = fmaf(bh[n], gp, g1[q]);
+        }
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char* tile, int r, int col, int C, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(tile + chunk_byte(r, col >> 3, C) + (col & 7) * 2) = __float2bfloat16_rn(v);
+}
+
+// colour loss of texel sample s (row r): writes the output deltas of every texture
+__device__ __forceinline__ void color_loss_row(const TrArgs& a, int s, bool valid, uint32_t zrow, unsigned char* D,
+                                               int r, float& lc, float& lcd) {
+    const ModelView& mv = a.mv;
+    int b = a.ids[s >> 4], i = s & 15;
+    int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
+    const float inv_n = 1.f / ((float)a.B * (float)a.net.out_dim), invT = 1.f / a.T;
+    for (int t = 0; t < mv.n_textures; ++t) {
+        const int fmt = mv.formats[t], co = mv.coff[t];
+        float e0[3], e1[3];
+        ref_endpoints(fmt, a.tp.blocks[t], b, e0, e1);
+        if (fmt == NTBC_BC1) {
+            float ch[3], c[3], dz[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ch[q] = tmem_ld1f(zrow + co + q);
+            tmem_wait_ld_regs<3>(ch);
+            const uint8_t* tp = a.tp.texels[t] + ((long long)y * mv.width + x) * 3;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                ch[q] = sigmoid_fast(ch[q]);
+                c[q] = (float)tp[q] * (1.f / 255.f);
+            }
+            color_texture<3>(fmt, ch, c, e0, e1, invT, inv_n, valid, dz, lc, lcd);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) st_bf16(D, r, co + q, a.net.out_pad, dz[q]);
+        } else {
+            float ch[1], c[1], dz[1];
+            ch[0] = tmem_ld1f(zrow + co);
+            tmem_wait_ld_regs<1>(ch);
+            ch[0] = sigmoid_fast(ch[0]);
+            c[0] = (float)a.tp.texels[t][(long long)y * mv.width + x] * (1.f / 255.f);
+            color_texture<1>(fmt, ch, c, e0, e1, invT, inv_n, valid, dz, lc, lcd);
+            st_bf16(D, r, co, a.net.out_pad, dz[0]);
+        }
+    }
+}
+
+// endpoint L_cd of one (block, texel) pair over every texture: per-texture gradient
+// contributions summed over the block's 16 texels (one half-warp) into Gs[bb]
+__device__ __forceinline__ void endpoint_pair(const TrArgs& a, int s, int bb, int i, bool valid, const float* Ys,
+                                              float* Gs, float& lcd) {
+    const ModelView& mv = a.mv;
+    const int od = mv.endpoint.out_dim;
+    int b = a.ids[s];
+    int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
+    const float inv_ncd = 1.f / ((float)a.B * 16.f * (float)mv.color.out_dim), invT = 1.f / a.T;
+    const float* yrow = Ys + bb * od;
+    for (int t = 0; t < mv.n_textures; ++t) {
+        const int fmt = mv.formats[t], eo = mv.eoff[t];
+        float e0[3], e1[3];
+        ref_endpoints(fmt, a.tp.blocks[t], b, e0, e1);
+        if (fmt == NTBC_BC1) {
+            float eh0[3], eh1[3], c[3], g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
+            const uint8_t* tp = a.tp.texels[t] + ((long long)y * mv.width + x) * 3;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                eh0[q] = yrow[eo + q];
+                eh1[q] = yrow[eo + 3 + q];
+                c[q] = (float)tp[q] * (1.f / 255.f);
+            }
+            endpoint_texel<3>(fmt, eh0, eh1, e0, e1, c, invT, inv_ncd, valid, g0, g1, lcd);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    g0[q] += __shfl_xor_sync(0xffffffffu, g0[q], o);
+                    g1[q] += __shfl_xor_sync(0xffffffffu, g1[q], o);
+                }
+            if (i == 0)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    Gs[bb * od + eo + q] = g0[q];
+                    Gs[bb * od + eo + 3 + q] = g1[q];
+                }
+        } else {
+            float eh0[1] = {yrow[eo]}, eh1[1] = {yrow[eo + 1]}, g0[1] = {0.f}, g1[1] = {0.f};
+            float c[1] = {(float)a.tp.texels[t][(long long)y * mv.width + x] * (1.f / 255.f)};
+            endpoint_texel<1>(fmt, eh0, eh1, e0, e1, c, invT, inv_ncd, valid, g0, g1, lcd);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                g0[0] += __shfl_xor_sync(0xffffffffu, g0[0], o);
+                g1[0] += __shfl_xor_sync(0xffffffffu, g1[0], o);
+            }
+            if (i == 0) {
+                Gs[bb * od + eo] = g0[0];
+                Gs[bb * od + eo + 1] = g1[0];
+            }
+        }
+    }
+}
+
+// endpoint block row r: L_e and the output deltas from the summed L_cd gradients
+__device__ __forceinline__ void endpoint_block_row(const TrArgs& a, int s, bool valid, int r, const float* Ys,
+                                                   const float* Gs, unsigned char* D, float& le) {
+    const ModelView& mv = a.mv;
+    const int od = mv.endpoint.out_dim;
+    int b = a.ids[s];
+    const float inv_ne = 1.f / ((float)a.B * (float)od);
+    for (int t = 0; t < mv.n_textures; ++t) {
+        const int fmt = mv.formats[t], C = fmt == NTBC_BC1 ? 3 : 1, eo = mv.eoff[t];
+        float e0[3], e1[3];
+        ref_endpoints(fmt, a.tp.blocks[t], b, e0, e1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q < C)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    int col = eo + k * C + q;
+                    float yh = Ys[r * od + col], ref = k ? e1[q] : e0[q];
+                    float rr = yh - ref;
+                    if (valid) le = fmaf(rr, rr, le);
+                    float g = Gs[r * od + col] + 2.f * rr * inv_ne;
+                    st_bf16(D, r, col, a.net.out_pad, valid ? g * yh * (1.f - yh) : 0.f);
+                }
+    }
+}
+
+// grid features of one sample (FP32 master grid, QAT fake quantisation while active)
+// straight into the BF16 X row: level l -> columns 2l, 2l + 1
+__device__ __forceinline__ void gather_row_train(const NetView& nv, const GridSrc& src, float u, float v,
+                                                 unsigned char* X, int r, int K0) {
+    const int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+#pragma unroll 4
+    for (int l = 0; l < nv.levels; ++l) {
+        Bilinear bl = bilinear_at(nv.res[l], u, v);
+        const float* gp = src.f32 + nv.grid_off[l] + bl.base;
+        float2 p00 = __ldg(reinterpret_cast<const float2*>(gp));
+        float2 p01 = __ldg(reinterpret_cast<const float2*>(gp + 2));
+        float2 p10 = __ldg(reinterpret_cast<const float2*>(gp + bl.row));
+        float2 p11 = __ldg(reinterpret_cast<const float2*>(gp + bl.row + 2));
+        if (qat_bits > 0) {
+            float sc = src.scale[l], z = src.zero[l], qm = (float)((1 << qat_bits) - 1);
+            p00 = make_float2(fake_quant(p00.x, sc, z, qm), fake_quant(p00.y, sc, z, qm));
+            p01 = make_float2(fake_quant(p01.x, sc, z, qm), fake_quant(p01.y, sc, z, qm));
+            p10 = make_float2(fake_quant(p10.x, sc, z, qm), fake_quant(p10.y, sc, z, qm));
+            p11 = make_float2(fake_quant(p11.x, sc, z, qm), fake_quant(p11.y, sc, z, qm));
+        }
+        float f0 = bl.w00 * p00.x + bl.w01 * p01.x + bl.w10 * p10.x + bl.w11 * p11.x;
+        float f1 = bl.w00 * p00.y + bl.w01 * p01.y + bl.w10 * p10.y + bl.w11 * p11.y;
+        *reinterpret_cast<uint32_t*>(X + chunk_byte(r, (2 * l) >> 3, K0) + ((2 * l) & 7) * 2) = pack_bf16x2(f0, f1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+
+constexpr int kTrEndpointThreads = 512;   // endpoint CTA: warpgroup 0 runs the tile, all 16 warps the loss
+
+template <bool COLOR>
+__global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointThreads, 1)
+    train_tc_kernel(const __grid_constant__ TrArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag[kTrMaxGroups];
+    const TrNet& net = a.net;
+    const TrSmem& sl = a.sl;
+    const NetView& nv = COLOR ? a.mv.color : a.mv.endpoint;
+    const int act = a.mv.activation;
+    const bool tile_thread = threadIdx.x < a.groups * kTrRows;
+
+    // weight image -> shared memory; tiles zeroed (no stale NaN bit patterns ever reach an MMA)
+    for (int i = threadIdx.x; i < net.img_bytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(smem)[i] = reinterpret_cast<const uint4*>(a.img)[i];
+    for (int i = threadIdx.x; i < a.groups * sl.group_bytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(smem + sl.group_off)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+
+    TrGroup G;
+    G.g = tile_thread ? threadIdx.x / kTrRows : 0;
+    G.r = threadIdx.x % kTrRows;
+    unsigned char* gb = smem + sl.group_off + G.g * sl.group_bytes;
+    G.X = gb + sl.x_off;
+    for (int l = 0; l < 3; ++l) G.A[l] = gb + sl.a_off[l];
+    G.D = gb + sl.d_off;
+    G.bar = reinterpret_cast<uint64_t*>(gb + sl.bar_off);
+    const int r = G.r;
+    if (tile_thread) {
+        // constant columns: the bias column of every hidden tile (64 = 1) and of X (in_dim = 1)
+        for (int l = 0; l < net.n_layers - 1; ++l) {
+            float v8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            st_chunk_bf16(G.A[l], r, 8, kTrHidCols, v8);
+        }
+        for (int kg = net.in_dim / 8; kg < net.K0 / 8; ++kg) {
+            float v8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v8[j] = kg * 8 + j == net.in_dim ? 1.f : 0.f;
+            st_chunk_bf16(G.X, r, kg, net.K0, v8);
+        }
+        if (r == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(G.bar)), "r"(1));
+            asm volatile("fence.mbarrier_init.release.cluster;");
+            abort_flag[G.g] = 0;
+        }
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    G.tmem = tmem_slot + (uint32_t)(G.g * 256);
+    G.row = G.tmem + ((uint32_t)((r / 32) * 32) << 16);
+    volatile int* abort = abort_flag;
+
+    const int L = net.n_layers;
+    const uint32_t R = G.tmem;                 // forward / data-gradient accumulator (64 columns)
+    const int od = net.out_dim;
+    float* Ys = reinterpret_cast<float*>(smem + sl.stage_off);   // endpoint only
+    float* Gs = Ys + kTrRows * od;
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    float loss0 = 0.f, loss1 = 0.f;
+    const int tile0 = COLOR ? blockIdx.x * a.groups + G.g : blockIdx.x;
+    const int tstep = COLOR ? gridDim.x * a.groups : gridDim.x;
+
+    for (int tile = tile0; tile < a.tiles; tile += tstep) {
+        const int s_raw = tile * kTrRows + r;
+        const bool valid = s_raw < a.B;
+        const int s = valid ? s_raw : a.B - 1;
+
+        if (tile_thread && ok) {
+            // ---- gather
+            {
+                float u, v;
+                int x, y;
+                sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
+                gather_row_train(nv, a.src, u, v, G.X, r, net.K0);
+            }
+            // ---- forward
+            for (int l = 0; l < L; ++l) {
+                const TrLayer& Ly = net.layer[l];
+                if (!tr_barrier(G.g, abort)) {
+                    ok = false;
+                    break;
+                }
+                if (r == 0) {
+                    tc_fence_after();
+                    const unsigned char* src = l == 0 ? G.X : G.A[l - 1];
+                    const int C = l == 0 ? net.K0 : kTrHidCols;
+                    const uint32_t idesc = umma_idesc_kind(Ly.N, 1, 0, 0);
+                    for (int kc = 0; kc < Ly.K / 16; ++kc) {
+                        uint64_t ad = umma_desc(smem_u32(src) + kc * 256, 128, (C / 8) * 128);
+                        uint64_t bd = umma_desc(smem_u32(smem + Ly.img) + kc * 256, 128, (Ly.K / 8) * 128);
+                        umma_f16(R, ad, bd, idesc, kc > 0);
+                    }
+                    umma_commit(G.bar);
+                }
+                tr_wait(G, phase, abort);
+                if (l + 1 < L) {
+#pragma unroll
+                    for (int c0 = 0; c0 < 64; c0 += 32) {
+                        float z[32];
+                        tmem_ld16(G.row + c0, z);
+                        tmem_ld16(G.row + c0 + 16, z + 16);
+                        tmem_wait_ld_regs<32>(z);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) z[j] = act_fast(z[j], act);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) st_chunk_bf16(G.A[l], r, c0 / 8 + q, kTrHidCols, z + 8 * q);
+                    }
+                }
+            }
+            // ---- outputs -> loss (colour) or staging (endpoint)
+            if (ok) {
+                if (COLOR) {
+#pragma unroll
+                    for (int kg = 0; kg < 6; ++kg) {
+                        if (kg * 8 >= net.out_pad) break;
+                        float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                        st_chunk_bf16(G.D, r, kg, net.out_pad, zero8);
+                    }
+                    color_loss_row(a, s, valid, G.row, G.D, r, loss0, loss1);
+                } else {
+                    for (int c0 = 0; c0 < net.out_pad; c0 += 16) {
+                        float z[16];
+                        tmem_ld16(G.row + c0, z);
+                        tmem_wait_ld_regs<16>(z);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < od) Ys[r * od + c0 + j] = sigmoid_fast(z[j]);
+                    }
+                }
+            }
+        }
+
+        if (!COLOR) {
+            // ---- endpoint L_cd over the tile's 128 blocks x 16 texels, shared by all 16 warps
+            __syncthreads();
+            if (abort[0]) break;
+            for (int p = threadIdx.x; p < kTrRows * 16; p += blockDim.x) {
+                const int bb = p >> 4, i = p & 15, sb = tile * kTrRows + bb;
+                const bool pv = sb < a.B;
+                endpoint_pair(a, pv ? sb : a.B - 1, bb, i, pv, Ys, Gs, loss1);
+            }
+            __syncthreads();
+            if (tile_thread) {
+#pragma unroll
+                for (int kg = 0; kg < 6; ++kg) {
+                    if (kg * 8 >= net.out_pad) break;
+                    float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    st_chunk_bf16(G.D, r, kg, net.out_pad, zero8);
+                }
+                endpoint_block_row(a, s, valid, r, Ys, Gs, G.D, loss0);
+            }
+        }
+
+        if (tile_thread && ok) {
+            // ---- backward
+            for (int l = L - 1; l >= 0; --l) {
+                const TrLayer& Ly = net.layer[l];
+                const int CD = l == L - 1 ? net.out_pad : 64;       // columns of the delta tile
+                if (!tr_barrier(G.g, abort)) {
+                    ok = false;
+                    break;
+                }
+                if (r == 0) {
+                    tc_fence_after();
+                    const uint32_t dw = G.tmem + (uint32_t)Ly.dw_col;
+                    const uint32_t d_base = smem_u32(G.D);
+                    const uint32_t dstride = (uint32_t)(CD / 8) * 128;
+                    if (l > 0) {          // dW_l^T[i][o] += sum_s A_{l-1}[s][i] D_l[s][o]
+                        const uint32_t a_base = smem_u32(G.A[l - 1]);
+                        const uint32_t idw = umma_idesc_kind(Ly.N, 1, 1, 1);
+                        for (int ks = 0; ks < kTrRows / 16; ++ks) {
+                            uint64_t ad = umma_desc(a_base + ks * 2 * (kTrHidCols / 8) * 128, (kTrHidCols / 8) * 128, 128);
+                            uint64_t bd = umma_desc(d_base + ks * 2 * dstride, dstride, 128);
+                            umma_f16(dw, ad, bd, idw, !(first && ks == 0));
+                        }
+                    } else {              // dW_0[o][i] += sum_s D_0[s][o] X[s][i]
+                        const uint32_t x_base = smem_u32(G.X);
+                        const uint32_t xstride = (uint32_t)(net.K0 / 8) * 128;
+                        const uint32_t idw = umma_idesc_kind(net.K0, 1, 1, 1);
+                        for (int ks = 0; ks < kTrRows / 16; ++ks) {
+                            uint64_t ad = umma_desc(d_base + ks * 2 * dstride, dstride, 128);
+                            uint64_t bd = umma_desc(x_base + ks * 2 * xstride, xstride, 128);
+                            umma_f16(dw, ad, bd, idw, !(first && ks == 0));
+                        }
+                    }
+                    // dA_{l-1} = D_l W_l (N = the layer's inputs, incl. the bias column for l = 0)
+                    const int n_in = l > 0 ? 64 : net.K0;
+                    const uint32_t idd = umma_idesc_kind(n_in, 1, 0, 1);
+                    const uint32_t wstride = (uint32_t)(Ly.K / 8) * 128;
+                    for (int kc = 0; kc < CD / 16; ++kc) {
+                        uint64_t ad = umma_desc(d_base + kc * 256, 128, dstride);
+                        uint64_t bd = umma_desc(smem_u32(smem + Ly.img) + kc * 2 * wstride, wstride, 128);
+                        umma_f16(R, ad, bd, idd, kc > 0);
+                    }
+                    umma_commit(G.bar);
+                }
+                tr_wait(G, phase, abort);
+                if (l > 0) {              // D_{l-1} = dA_{l-1} * act'(A_{l-1})
+#pragma unroll
+                    for (int c0 = 0; c0 < 64; c0 += 32) {
+                        float dA[32];
+                        tmem_ld16(G.row + c0, dA);
+                        tmem_ld16(G.row + c0 + 16, dA + 16);
+                        tmem_wait_ld_regs<32>(dA);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float av[8];
+                            ld_chunk_bf16(G.A[l - 1], r, c0 / 8 + q, kTrHidCols, av);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                dA[8 * q + j] = valid ? dA[8 * q + j] * act_grad_from_out(av[j], act) : 0.f;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) st_chunk_bf16(G.D, r, c0 / 8 + q, 64, dA + 8 * q);
+                    }
+                } else {                  // d loss / d features -> grid scatter-add
+                    float gx[32];
+                    tmem_ld16(G.row, gx);
+                    tmem_ld16(G.row + 16, gx + 16);
+                    tmem_wait_ld_regs<32>(gx);
+                    float* gs = reinterpret_cast<float*>(G.D) + r * 33;    // the delta tile is free now
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) gs[j] = gx[j];
+                    float u, v;
+                    int x, y;
+                    sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
+                    const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+#pragma unroll 1
+                    for (int lv = 0; lv < nv.levels; ++lv)
+                        scatter_level(nv, COLOR, lv, u, v, r, valid, gs[2 * lv], gs[2 * lv + 1], a.src, qat_bits, a.grads);
+                }
+            }
+            if (ok) first = false;
+        }
+        if (!COLOR) {
+            __syncthreads();                // staging reused by the next tile
+            if (abort[0]) break;
+        } else if (!ok) {
+            break;
+        }
+    }
+
+    // ---- losses (one double atomic per warp and term)
+    {
+        float n0 = COLOR ? (float)a.B * (float)od : (float)a.B * (float)od;
+        float n1 = COLOR ? n0 : (float)a.B * 16.f * (float)a.mv.color.out_dim;
+        block_reduce_add(&a.acc[COLOR ? 2 : 0], loss0 / n0);
+        block_reduce_add(&a.acc[COLOR ? 3 : 1], loss1 / n1);
+    }
+
+    // ---- weight gradients: TMEM accumulators -> global (one atomic per element and group)
+    if (tile_thread && ok && !first) {
+        for (int l = 0; l < L; ++l) {
+            const TrLayer& Ly = net.layer[l];
+            const int ncol = l == 0 ? net.K0 : Ly.N;
+            for (int c0 = 0; c0 < ncol; c0 += 16) {
+                float v[16];
+                tmem_ld16(G.row + (uint32_t)Ly.dw_col + c0, v);
+                tmem_wait_ld_regs<16>(v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    int c = c0 + j;
+                    if (l == 0) {             // lane = unit o, column = input i
+                        if (r < Ly.out && c < Ly.in) atomicAdd(a.grads + Ly.w_off + (long long)r * Ly.in + c, v[j]);
+                        else if (r < Ly.out && c == Ly.in) atomicAdd(a.grads + Ly.b_off + r, v[j]);
+                    } else {                  // lane = input i (64 = bias), column = unit o
+                        if (c < Ly.out && r < Ly.in) atomicAdd(a.grads + Ly.w_off + (long long)c * Ly.in + r, v[j]);
+                        else if (c < Ly.out && r == Ly.in) atomicAdd(a.grads + Ly.b_off + c, v[j]);
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- teardown: a group whose wait gave up lets its in-flight MMAs land before TMEM is freed
+    if (tile_thread && !ok) {
+        if (r == 0) atomicExch(a.err, 1);
+        mbar_wait(G.bar, phase ^ 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(512));
+}
+
+// BF16 weight image of one network: per layer the [N][K] tile (W in columns 0..in-1, the
+// bias in column `in`, zeros elsewhere), canonical K-major core-matrix layout
+__global__ void train_image_kernel(const float* __restrict__ params, TrNet net, __nv_bfloat16* __restrict__ img) {
+    for (int l = 0; l < net.n_layers; ++l) {
+        const TrLayer& Ly = net.layer[l];
+        __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(img) + Ly.img);
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ly.N * Ly.K; e += gridDim.x * blockDim.x) {
+            int n = e / Ly.K, k = e % Ly.K;
+            float w = 0.f;
+            if (n < Ly.out) {
+                if (k < Ly.in) w = params[Ly.w_off + (long long)n * Ly.in + k];
+                else if (k == Ly.in) w = params[Ly.b_off + n];
+            }
+            t[core_byte(n, k, Ly.K) / 2] = __float2bfloat16_rn(w);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+TrNet train_tc_net_desc(const ModelView& mv, bool color) {
+    const NetView& nv = color ? mv.color : mv.endpoint;
+    TrNet n;
+    memset(&n, 0, sizeof(n));
+    n.n_layers = nv.n_layers;
+    n.in_dim = nv.in_dim;
+    n.out_dim = nv.out_dim;
+    n.out_pad = (nv.out_dim + 15) / 16 * 16;
+    n.K0 = (nv.in_dim + 1 + 15) / 16 * 16;
+    int img = 0, col = 64;
+    for (int l = 0; l < nv.n_layers; ++l) {
+        TrLayer& L = n.layer[l];
+        L.in = nv.layer_in[l];
+        L.out = nv.layer_out[l];
+        L.K = l == 0 ? n.K0 : kTrHidCols;
+        L.N = l + 1 == nv.n_layers ? n.out_pad : 64;
+        L.img = img;
+        img += L.N * L.K * 2;
+        L.w_off = nv.w_off[l];
+        L.b_off = nv.b_off[l];
+        L.dw_col = col;
+        col += l == 0 ? n.K0 : L.N;
+    }
+    n.img_bytes = (img + 127) & ~127;
+    return n;
+}
+
+int train_tc_tmem_cols(const TrNet& n) { return n.layer[n.n_layers - 1].dw_col + n.layer[n.n_layers - 1].N; }
+
+static TrSmem train_tc_smem(const TrNet& n) {
+    TrSmem s;
+    memset(&s, 0, sizeof(s));
+    s.group_off = n.img_bytes;
+    int o = 0;
+    s.x_off = o;
+    o += kTrRows * n.K0 * 2;
+    for (int l = 0; l < 3; ++l) {
+        s.a_off[l] = o;
+        if (l < n.n_layers - 1) o += kTrRows * kTrHidCols * 2;
+    }
+    s.d_off = o;
+    o += kTrRows * 64 * 2 + kTrPad;
+    s.bar_off = o;
+    o += 16;
+    s.group_bytes = (o + 127) & ~127;
+    s.stage_off = 0;
+    return s;
+}
+
+ntbc_status train_tc_image(const float* params, const TrNet& net, unsigned char* img, cudaStream_t s) {
+    train_image_kernel<<<64, 256, 0, s>>>(params, net, reinterpret_cast<__nv_bfloat16*>(img));
+    NTBC_CHECK_LAUNCH("training weight image");
+    return NTBC_OK;
+}
+
+ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, const unsigned char* img,
+                            const GridSrc& src, const TexPtrs& tp, const int32_t* ids, int B, float T, float* grads,
+                            double* acc, int* err, cudaStream_t s) {
+    if (net.in_dim > 2 * NTBC_MAX_LEVELS || net.out_pad > 48)
+        return fail(NTBC_EUNSUPPORTED, "tensor-core training: network shape outside the kernel's tiles");
+    const int cols = train_tc_tmem_cols(net);
+    if (cols > 512) return fail(NTBC_EUNSUPPORTED, "tensor-core training: accumulators exceed TMEM");
+    TrArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mv = mv;
+    a.net = net;
+    a.sl = train_tc_smem(net);
+    a.src = src;
+    a.tp = tp;
+    a.ids = ids;
+    a.B = B;
+    a.tiles = (B + kTrRows - 1) / kTrRows;
+    a.color = color;
+    a.T = T;
+    a.grads = grads;
+    a.acc = acc;
+    a.err = err;
+    a.img = img;
+    size_t smem = (size_t)a.sl.group_off + 2 * (size_t)a.sl.group_bytes;
+    // colour: two warpgroups when their accumulators fit; endpoint: one tile per CTA
+    // (the loss then runs on all 16 warps) with the FP32 staging of outputs and gradients
+    a.groups = (color && cols <= 256 && smem + 1024 <= 227 * 1024) ? 2 : 1;
+    smem = (size_t)a.sl.group_off + (size_t)a.groups * a.sl.group_bytes;
+    if (!color) {
+        a.sl.stage_off = (int)smem;
+        smem += 2 * (size_t)kTrRows * net.out_dim * sizeof(float);
+    }
+    if (smem + 1024 > 227 * 1024) return fail(NTBC_EUNSUPPORTED, "tensor-core training: shared memory too small");
+    smem = std::max(smem, (size_t)116 * 1024);     // one CTA per SM: each CTA allocates all 512 TMEM columns
+    int dev = 0, sms = 0;
+    NTBC_CHECK_CUDA(cudaGetDevice(&dev));
+    NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int grid = std::min(sms, (a.tiles + a.groups - 1) / a.groups);
+    if (grid < 1) return NTBC_OK;
+    if (color) {
+        NTBC_CHECK_CUDA(cudaFuncSetAttribute(train_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        train_tc_kernel<true><<<grid, kTrRows * a.groups, smem, s>>>(a);
+    } else {
+        NTBC_CHECK_CUDA(cudaFuncSetAttribute(train_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        train_tc_kernel<false><<<grid, kTrEndpointThreads, smem, s>>>(a);
+    }
+    NTBC_CHECK_LAUNCH(color ? "tensor-core training (colour)" : "tensor-core training (endpoint)");
+    return NTBC_OK;
+}
+
+}  // namespace ntbc

@@ -1,0 +1,58 @@
+// Fused tensor-core (BF16) training pass of one network: kernel arguments and host entry
+// points (the kernel is in ntbc_train_tc.cu).
+#pragma once
+
+#include "ntbc_internal.cuh"
+#include "ntbc_kernels.cuh"
+#include "ntbc_train_common.cuh"
+
+namespace ntbc {
+
+struct TrLayer {
+    int K;                    // forward MMA K: input columns incl. the bias column, multiple of 16
+    int N;                    // forward MMA N: 64 (hidden) or the padded output width
+    int in, out;              // real sizes
+    int img;                  // byte offset of the layer's [N][K] BF16 tile in the weight image
+    long long w_off, b_off;   // parameter offsets of W [out][in] and b [out]
+    int dw_col;               // TMEM column (within the group) of the weight-gradient accumulator
+};
+
+struct TrNet {
+    int n_layers, K0, in_dim, out_dim, out_pad;
+    TrLayer layer[NTBC_MAX_MLP_LAYERS];
+    int img_bytes;
+};
+
+struct TrSmem {               // byte offsets: weight image at 0, then the groups
+    int group_off, group_bytes;
+    int x_off, a_off[3], d_off, bar_off;   // inside a group
+    int stage_off;            // endpoint network: FP32 outputs and summed L_cd gradients, [128][out]
+};
+
+struct TrArgs {
+    ModelView mv;
+    TrNet net;
+    TrSmem sl;
+    GridSrc src;
+    TexPtrs tp;
+    const int32_t* ids;
+    int B, tiles, groups, color;
+    float T;
+    float* grads;
+    double* acc;
+    int* err;
+    const unsigned char* img;  // global BF16 weight image of this network
+};
+
+// layer table of one network (weight image offsets from 0)
+TrNet train_tc_net_desc(const ModelView& mv, bool color);
+// TMEM columns one warpgroup needs (data accumulator + every weight-gradient accumulator)
+int train_tc_tmem_cols(const TrNet& n);
+// BF16 weight image of the network from the FP32 master parameters (device img, img_bytes)
+ntbc_status train_tc_image(const float* params, const TrNet& net, unsigned char* img, cudaStream_t s);
+// forward + loss + backward of B samples; adds into grads and the loss accumulators
+ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, const unsigned char* img,
+                            const GridSrc& src, const TexPtrs& tp, const int32_t* ids, int B, float T, float* grads,
+                            double* acc, int* err, cudaStream_t s);
+
+}  // namespace ntbc

@@ -510,3 +510,40 @@ def test_outputs_vjp_qat_is_straight_through():
         for (aW, ab), (bW, bb) in zip(gq[key], gf[key]):
             np.testing.assert_allclose(aW, bW, rtol=1e-12)
             np.testing.assert_allclose(ab, bb, rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# BF16 operand rounding (the reduced-precision training arithmetic)
+# ----------------------------------------------------------------------------
+
+def test_bf16_round_brute_force_and_torch():
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(50000) * np.exp(rng.uniform(-40, 40, 50000))).astype(np.float32).astype(np.float64)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(ntbc.bf16_round(x), want)
+    # every BF16 value in [1, 2) and the midpoints between neighbours: ties go to the even mantissa
+    vals = 1.0 + np.arange(129) / 128.0
+    np.testing.assert_array_equal(ntbc.bf16_round(vals), vals)
+    mids = (vals[:-1] + vals[1:]) / 2
+    even = np.where(np.arange(128) % 2 == 0, vals[:-1], vals[1:])
+    np.testing.assert_array_equal(ntbc.bf16_round(mids), even)
+    np.testing.assert_array_equal(ntbc.bf16_round(-mids), -even)
+
+
+@pytest.mark.parametrize("act", ["selu", "relu"])
+def test_backward_through_activation_output_equals_through_preactivation(act):
+    # the BF16 mode takes act' from the activation's output; with an identity rounding it
+    # must give exactly the gradients of the default (pre-activation) form
+    rng = np.random.default_rng(4)
+    layers = [(rng.standard_normal((16, 6)), rng.standard_normal(16)), (rng.standard_normal((16, 16)), rng.standard_normal(16)),
+              (rng.standard_normal((3, 16)), rng.standard_normal(3))]
+    x = rng.standard_normal((40, 6))
+    y, cache = ntbc.mlp_forward(layers, x, act)
+    g_y = rng.standard_normal(y.shape)
+    gx0, g0 = ntbc.mlp_backward(layers, cache, y, g_y, act)
+    y1, cache1 = ntbc.mlp_forward(layers, x, act, rnd=lambda v: v)
+    gx1, g1 = ntbc.mlp_backward(layers, cache1, y1, g_y, act, rnd=lambda v: v)
+    np.testing.assert_allclose(gx1, gx0, rtol=1e-12, atol=1e-13)
+    for (a, b), (c, d) in zip(g1, g0):
+        np.testing.assert_allclose(a, c, rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(b, d, rtol=1e-12, atol=1e-13)
