@@ -9,7 +9,8 @@ One timed step = one NTBC inference pass over the whole material (all 4 textures
 resident in HBM; the L2 is flushed (256 MiB write) between timed iterations, each
 iteration bracketed by its own CUDA events on the launching stream.
 Also reported: the encode (training) time per step and the full-schedule encode
-seconds extrapolated from the measured steps, the same metric end to end with host
+seconds (BF16 tensor-core training; the FP32-kernel encode beside it for decoded-PSNR
+parity), the same metric end to end with host
 buffers (model blob H2D, blocks D2H), the plain FP32 PyTorch path on the same GPU,
 and the CPU oracle on a bounded sample (cpu_baseline).
 
@@ -52,6 +53,7 @@ def parse():
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32-train", action="store_true", help="skip the FP32-kernel encode (PSNR comparison)")
     ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16; 3: FP8 E4M3 weights, split activations")
     ap.add_argument("--batch", action="store_true",
                     help="batched load-time inference: 16 uneven materials in one persistent launch (CUDA graph)")
@@ -304,7 +306,7 @@ def run_sweep(args):
         model = nt.Model(desc)
         model.set_params(torch.from_numpy(nt.configs.flatten(desc, p0)).to(dev))
         model.train(material, nt.TrainConfig.make(steps=args.train_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1,
-                                                  grid_bits=bits, seed=0))
+                                                  grid_bits=bits, seed=0, precision=nt.TRAIN_BF16))
         flat = torch.empty(model.n_params, device=dev)
         model.get_params(flat)
         params = nt.configs.unflatten(desc, flat.cpu().numpy())
@@ -482,15 +484,34 @@ def main():
     untrained_psnr = psnr_list(nt, obc, torch, mat, untrained, side)
     material = nt.Material.make(side, side, mat.formats, tex_d, refs)
     main_steps = args.train_steps
-    cfg = nt.TrainConfig.make(steps=main_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1, grid_bits=8, seed=rank)
     total_steps = main_steps + int(np.ceil(0.1 * main_steps))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    last_losses = model.train(material, cfg)
-    train_s = time.perf_counter() - t0
+
+    def encode(m, precision):
+        cfg = nt.TrainConfig.make(steps=main_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1, grid_bits=8,
+                                  seed=rank, precision=precision)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = m.train(material, cfg)
+        return time.perf_counter() - t0, losses
+
+    # headline encode: the fused BF16 tensor-core training pass
+    train_s, last_losses = encode(model, nt.TRAIN_BF16)
     ms_per_train_step = 1e3 * train_s / total_steps
     encode_full_s = ms_per_train_step * (FULL_MAIN_STEPS + FULL_QAT_STEPS) / 1e3
     model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+    # the same encode with the FP32 layer-by-layer kernels (decoded-PSNR parity of the BF16 encode)
+    fp32_encode = None
+    if not args.no_fp32_train:
+        m32 = nt.Model(desc)
+        m32.set_params(flat0)
+        t32, _ = encode(m32, nt.TRAIN_FP32)
+        m32.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+        o32 = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in FORMATS]
+        m32.infer_to_bc(o32)
+        fp32_encode = {"measured_s": round(t32, 2), "ms_per_step": round(1e3 * t32 / total_steps, 3),
+                       "psnr_db": psnr_list(nt, obc, torch, mat, o32, side)}
+        m32.close()
+        del o32
 
     # ---- inference timing (device-resident inputs)
     outs = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in FORMATS]
@@ -611,12 +632,14 @@ def main():
         "block_positions_per_s_M": round(nblk * world / (ms * 1e-3) / 1e6, 3),
         "psnr_db": {"ntbc": ours_psnr, "untrained": untrained_psnr, "reference_bc": ref_psnr,
                     "e2e": e2e_psnr, "plain_fp32": plain["psnr_db"] if plain else None},
-        "encode": {"ms_per_step": round(ms_per_train_step, 3), "steps_run": total_steps,
+        "encode": {"precision": "bf16 tensor-core MMA operands, fp32 accumulate / loss / Adam",
+                   "ms_per_step": round(ms_per_train_step, 3), "steps_run": total_steps,
                    "batch_texels": BATCH_TEXELS, "measured_s": round(train_s, 2),
                    "full_schedule_s_extrapolated": round(encode_full_s, 1),
                    "full_schedule_steps": FULL_MAIN_STEPS + FULL_QAT_STEPS,
                    "last_losses": [round(x, 6) for x in last_losses],
-                   "reference_bc_encode_ms": round(float(np.mean(ref_ms)), 3)},
+                   "reference_bc_encode_ms": round(float(np.mean(ref_ms)), 3),
+                   "fp32_kernels": fp32_encode},
         "plain_fp32_gpu": plain,
         "roofline": roofline,
         "roofline_terms": terms,
