@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32-train", action="store_true", help="skip the FP32-kernel encode (PSNR comparison)")
+    ap.add_argument("--no-conservative", action="store_true", help="skip the conservative-packaging encode and decode")
     ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16; 3: FP8 E4M3 weights, split activations")
     ap.add_argument("--batch", action="store_true",
                     help="batched load-time inference: 16 uneven materials in one persistent launch (CUDA graph)")
@@ -575,6 +576,50 @@ def main():
                        "psnr_db": psnr_list(nt, obc, torch, mat, outs, side)}
     model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
 
+    # ---- conservative packaging (Sec. 4.1): one model for the BC1 textures, one for the BC4
+    # textures, both encoded with the BF16 pass and decoded together in one batched launch
+    conservative = None
+    if not args.no_conservative:
+        w = nt.configs.WORKLOADS["mat4k"]
+        groups = nt.configs.packaging_groups(FORMATS, "conservative")
+        c_models, c_outs, c_train_s, c_bytes = [], [], 0.0, 0
+        for gi, g in enumerate(groups):
+            fm = [FORMATS[t] for t in g]
+            d = nt.configs.desc_for(w, fm, side=side)
+            cres, eres = nt.configs.res_lists(d)
+            pc = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(d, "color"), nt.configs.mlp_dims(d, "endpoint"),
+                                   rank_material_seed(rank) + 17 * (gi + 1))
+            mc = nt.Model(d)
+            mc.set_params(torch.from_numpy(nt.configs.flatten(d, pc)).to(dev))
+            mat_c = nt.Material.make(side, side, fm, [tex_d[t] for t in g], [refs[t] for t in g])
+            cfg_c = nt.TrainConfig.make(steps=main_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1, grid_bits=8,
+                                        seed=rank, precision=nt.TRAIN_BF16)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mc.train(mat_c, cfg_c)
+            c_train_s += time.perf_counter() - t0
+            mc.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+            c_bytes += mc.blob_size()
+            c_models.append(mc)
+            c_outs.append([torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in g])
+        c_batch = nt.Batch(c_models, c_outs)
+        c_batch.infer()
+        torch.cuda.synchronize()
+        c_times = time_events(torch, c_batch.infer, max(3, args.steps // 2), flush=flush)
+        c_ms = float(np.mean(c_times))
+        by_tex = [None] * len(FORMATS)
+        for g, o in zip(groups, c_outs):
+            for t, oo in zip(g, o):
+                by_tex[t] = oo
+        conservative = {"models": len(groups), "textures_per_model": [len(g) for g in groups],
+                        "encode_s_measured": round(c_train_s, 2), "infer_ms": round(c_ms, 4),
+                        "infer_value": round(tex_blocks / (c_ms * 1e-3) / 1e6, 3), "unit": "Mblocks/s",
+                        "psnr_db": psnr_list(nt, obc, torch, mat, by_tex, side),
+                        "storage_bytes": int(c_bytes), "aggressive_storage_bytes": int(model.blob_size())}
+        c_batch.close()
+        for mc in c_models:
+            mc.close()
+
     # ---- plain FP32 PyTorch path on the same GPU and weights
     plain = None
     if not args.no_plain:
@@ -641,6 +686,7 @@ def main():
                    "reference_bc_encode_ms": round(float(np.mean(ref_ms)), 3),
                    "fp32_kernels": fp32_encode},
         "plain_fp32_gpu": plain,
+        "conservative": conservative,
         "roofline": roofline,
         "roofline_terms": terms,
         "other_modes": modes,

@@ -11,6 +11,8 @@ Five workloads:
   batch16  16 materials of uneven size (sides 512..4096, 2..5 textures)
 The endpoint grid keeps the colour-grid levels whose resolution does not exceed
 the number of blocks per side (Sec. 3.4: 7 of the 8 levels for a 4096^2 texture).
+Packaging (Sec. 4.1): aggressive = one model per material, conservative = one model for
+the BC1 textures and one for the BC4 textures (`packaging_groups`).
 """
 from __future__ import annotations
 
@@ -42,6 +44,19 @@ WORKLOADS = {
     "mat1k": Workload("mat1k", 1024, 8, 16, 512, 3, ACT_SELU, 5000, 1 << 16, 0.0, 0, 1),
     "mat4k": Workload("mat4k", 4096, 12, 16, 2048, 3, ACT_SELU, 20000, 1 << 18, 0.1, 8, 1),
 }
+
+
+def packaging_groups(formats, packaging="aggressive"):
+    """Texture indices per model (Sec. 4.1): aggressive packaging trains one model for all
+    textures of the material; conservative packaging trains one model for the RGB (BC1)
+    textures and one for the single-channel (BC4) textures."""
+    formats = list(formats)
+    if packaging == "aggressive":
+        return [list(range(len(formats)))]
+    if packaging != "conservative":
+        raise ValueError(f"unknown packaging {packaging!r}")
+    groups = [[t for t, f in enumerate(formats) if f == 1], [t for t, f in enumerate(formats) if f == 4]]
+    return [g for g in groups if g]
 
 
 def grid_levels(levels, min_res, max_res, side):
