@@ -234,6 +234,7 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out
  *   block_ids  device int32 [n]
  *   e_hat      device float [n][out_endpoint]
  *   c_hat      device float [n][16][out_color]  (texel i = 4y + x of each block)
+ * n = 0 returns NTBC_OK without touching the pointers (which may then be NULL).
  */
 ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int n,
                          float* e_hat, float* c_hat, void* stream);

@@ -297,9 +297,10 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, vo
 
 ntbc_status ntbc_forward(const ntbc_model* m, const int32_t* block_ids, int n, float* e_hat, float* c_hat, void* stream) {
     clear_error();
-    if (!m || !block_ids || !e_hat || !c_hat) return fail(NTBC_EINVAL, "null argument");
+    if (!m) return fail(NTBC_EINVAL, "null model");
     if (n < 0) return fail(NTBC_EINVAL, "negative count");
-    if (n == 0) return NTBC_OK;
+    if (n == 0) return NTBC_OK;                       // nothing to read or write
+    if (!block_ids || !e_hat || !c_hat) return fail(NTBC_EINVAL, "null argument");
     if (m->weight_prec != NTBC_PREC_FP32) {
         GridSrc csrc, esrc;
         ntbc_status st = grid_sources(m, csrc, esrc);

@@ -1,0 +1,153 @@
+"""The largest model the kernels take (8 textures, 16 colour levels: 32 input features, 18
+colour and 36 endpoint outputs) and the degenerate cases of the method: every block solid
+(equal endpoints: BC1 all codes 0, BC4 six-value mode with r0 = r1), an empty block list."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import bc as obc, ntbc as ont
+
+nt = pytest.importorskip("paper_2407_09543_gb300")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+KINDS = ["sine_rgb", "sine_r", "sine_rgb", "sine_rgb", "sine_r", "sine_rgb", "sine_r", "sine_rgb"]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).ravel()).to(DEV)
+
+
+def max_case(seed=0):
+    side = 64
+    mat = synth.make_material("limits", side, KINDS, seed)
+    assert len(mat.formats) == nt.MAX_TEXTURES
+    desc = nt.configs.model_desc(mat.formats, side, nt.MAX_LEVELS, 4, 64, 3, nt.ACT_SELU)
+    assert desc.color_levels == nt.MAX_LEVELS
+    cres, eres = nt.configs.res_lists(desc)
+    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
+    params = synth.random_params_like(p0, seed=seed + 1)
+    odesc = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=3, activation="selu")
+    return mat, desc, odesc, params
+
+
+def fp16_params(params):
+    out = dict(params)
+    for k in ("color_mlp", "endpoint_mlp"):
+        out[k] = [(W.astype(np.float16).astype(np.float64), b.astype(np.float16).astype(np.float64)) for W, b in params[k]]
+    return out
+
+
+def run_blocks(model, desc):
+    n = (desc.width // 4) * (desc.height // 4)
+    outs = [torch.empty(n * 8, dtype=torch.uint8, device=DEV) for _ in range(desc.n_textures)]
+    model.infer_to_bc(outs)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy().reshape(-1, 8) for o in outs]
+
+
+def mismatch(formats, got, ref):
+    m = f = 0
+    for fmt, a, b in zip(formats, got, ref):
+        unpack = obc.bc1_unpack if fmt == 1 else obc.bc4_unpack
+        a0, a1, ac = unpack(a)
+        b0, b1, bc_ = unpack(b)
+        m += int((a0 != b0).sum() + (a1 != b1).sum() + (ac != bc_).sum())
+        f += a0.size * 18
+    return m, f
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_largest_model_inference(prec):
+    mat, desc, odesc, params = max_case()
+    assert odesc.out_color == 18 and odesc.out_endpoint == 36 and odesc.in_color == 32
+    m = nt.Model(desc)
+    m.set_params(_dev(nt.configs.flatten(desc, params)))
+    m.export(grid_bits=8, weight_prec=prec)
+    oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 8)
+    deq = ont.dequantize_grid(oc, os_, oz)
+    nc = desc.color_levels
+    pw = params if prec == 0 else fp16_params(params)
+    ids = np.arange(odesc.n_blocks)
+    lay = m.layout
+    e = torch.empty(len(ids), lay.out_endpoint, device=DEV)
+    c = torch.empty(len(ids), 16, lay.out_color, device=DEV)
+    m.forward(_dev(ids.astype(np.int32)), e, c)
+    torch.cuda.synchronize()
+    er, cr = ont.forward_blocks(odesc, pw, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    np.testing.assert_allclose(e.cpu().numpy(), er, rtol=1e-3, atol=1e-6)
+    np.testing.assert_allclose(c.cpu().numpy(), cr, rtol=1e-3, atol=1e-6)
+    got = run_blocks(m, desc)
+    mm, ff = mismatch(mat.formats, got, ont.infer_blocks(odesc, pw, color_grid=deq[:nc], endpoint_grid=deq[nc:]))
+    assert mm <= 0.001 * ff
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_largest_model_gradients(precision):
+    # BF16: the colour pass needs 272 TMEM columns here, so it runs one warpgroup per CTA
+    mat, desc, odesc, params = max_case(seed=2)
+    refs = [obc.encode(f, t, 64, 64) for f, t in zip(mat.formats, mat.textures)]
+    tex_d = [_dev(t) for t in mat.textures]
+    ref_d = [_dev(r) for r in refs]
+    material = nt.Material.make(64, 64, mat.formats, tex_d, ref_d)
+    m = nt.Model(desc)
+    m.set_params(_dev(nt.configs.flatten(desc, params)))
+    ids = np.array([0, 3, 7, 15, 100, 255, 128, 64, 3, 200], np.int64)
+    grads = torch.empty(m.n_params, device=DEV)
+    losses = torch.empty(6, device=DEV)
+    m.train_grads(material, _dev(ids.astype(np.int32)), grads, losses, qat_bits=8, precision=precision)
+    torch.cuda.synchronize()
+    L, g = ont.losses_and_grads(odesc, params, mat.textures, refs, ids, qat_bits=8, bf16=bool(precision))
+    want_l = [L["L_e"], L["L_cd_endpoint"], L["L_c"], L["L_cd_color"], L["L_endpoint"], L["L_color"]]
+    np.testing.assert_allclose(losses.cpu().numpy(), want_l, rtol=2e-3)
+    gg = nt.configs.unflatten(desc, grads.cpu().numpy())
+    tol = 5e-3 if precision else 2e-3
+    for key in ("color_grid", "endpoint_grid"):
+        for a, b in zip(gg[key], g[key]):
+            assert np.linalg.norm(a - b) <= tol * max(np.linalg.norm(b), 1e-30), key
+    for key in ("color_mlp", "endpoint_mlp"):
+        for (aW, ab), (bW, bb) in zip(gg[key], g[key]):
+            assert np.linalg.norm(aW - bW) <= tol * np.linalg.norm(bW), key
+            assert np.linalg.norm(ab - bb) <= tol * np.linalg.norm(bb), key
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solid_blocks_everywhere(prec):
+    # endpoint MLP output layer W = 0: every block gets the same endpoints, one constant
+    # per channel; BC1 colour0 == colour1 -> all codes 0; BC4 r0 == r1 -> six-value mode
+    mat, desc, odesc, params = max_case(seed=4)
+    params = dict(params)
+    W, b = params["endpoint_mlp"][-1]
+    params["endpoint_mlp"] = params["endpoint_mlp"][:-1] + [(np.zeros_like(W), np.full_like(b, 0.3))]
+    m = nt.Model(desc)
+    m.set_params(_dev(nt.configs.flatten(desc, params)))
+    m.export(grid_bits=8, weight_prec=prec)
+    oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 8)
+    deq = ont.dequantize_grid(oc, os_, oz)
+    nc = desc.color_levels
+    pw = params if prec == 0 else fp16_params(params)
+    got = run_blocks(m, desc)
+    ref = ont.infer_blocks(odesc, pw, color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    mm, ff = mismatch(mat.formats, got, ref)
+    assert mm <= (0.001 if prec < 2 else 0.005) * ff
+    for fmt, a, r in zip(mat.formats, got, ref):
+        np.testing.assert_array_equal(a[:, :2 if fmt == 4 else 4], r[:, :2 if fmt == 4 else 4])   # endpoints
+        if fmt == 1:
+            c0, c1, codes = obc.bc1_unpack(a)
+            assert np.all(c0 == c1) and np.all(codes == 0)
+        else:
+            r0, r1, _ = obc.bc4_unpack(a)
+            assert np.all(r0 == r1)
+
+
+def test_empty_block_list():
+    mat, desc, odesc, params = max_case()
+    m = nt.Model(desc)
+    m.set_params(_dev(nt.configs.flatten(desc, params)))
+    m.export(grid_bits=8, weight_prec=1)
+    lay = m.layout
+    e = torch.zeros(1, lay.out_endpoint, device=DEV)
+    c = torch.zeros(1, 16, lay.out_color, device=DEV)
+    m.forward(torch.empty(0, dtype=torch.int32, device=DEV), e, c)
+    torch.cuda.synchronize()
+    assert float(e.abs().sum()) == 0.0 and float(c.abs().sum()) == 0.0
