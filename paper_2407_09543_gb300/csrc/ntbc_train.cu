@@ -54,6 +54,8 @@ struct ntbc_train_state {
     unsigned* qmm = nullptr;
     int* qat_flag = nullptr;          // points at st->qat
     unsigned char* tc_img = nullptr;  // BF16 weight images of both networks (tensor-core training)
+    float* tc_part = nullptr;         // weight-gradient partial sums of the tensor-core pass
+    int tc_part_rows = 0;
     int* tc_err = nullptr;            // set when a bounded wait of the tensor-core training gives up
 };
 
@@ -443,31 +445,59 @@ __global__ void grid_scatter_kernel(ModelView mv, bool color, const int32_t* __r
 // Adam (dense)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, float bc1, float bc2) {
-    m = 0.9f * m + 0.1f * g;
-    v = 0.999f * v + 0.001f * g * g;
-    p -= lr * (m / bc1) / (sqrtf(v / bc2) + kAdamEps);
+// one Adam update; step = lr / (1 - beta1^t), rsb2 = 1 / sqrt(1 - beta2^t):
+// p -= lr (m / bc1) / (sqrt(v / bc2) + eps), rearranged so that each element costs one
+// square root and one (fast) division
+__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float step, float rsb2) {
+    m = fmaf(0.9f, m, 0.1f * g);
+    v = fmaf(0.999f, v, 0.001f * g * g);
+    p -= step * __fdividef(m, fmaf(sqrtf(v), rsb2, kAdamEps));
 }
 
+__device__ __forceinline__ void adam4(float4& P, float4 G, float4& M, float4& V, long long e, long long grid_floats,
+                                      float step_g, float step_m, float rsb2) {
+    adam_one(P.x, G.x, M.x, V.x, e < grid_floats ? step_g : step_m, rsb2);
+    adam_one(P.y, G.y, M.y, V.y, e + 1 < grid_floats ? step_g : step_m, rsb2);
+    adam_one(P.z, G.z, M.z, V.z, e + 2 < grid_floats ? step_g : step_m, rsb2);
+    adam_one(P.w, G.w, M.w, V.w, e + 3 < grid_floats ? step_g : step_m, rsb2);
+}
+
+// dense Adam over all parameters, two float4 of every array in flight per thread; the
+// streams are touched once per step, so they bypass L2 retention (evict-first hints)
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, long long n, long long grid_floats, const StepState* __restrict__ st) {
-    float lr_g = st->lr_grid, lr_m = st->lr_mlp, bc1 = st->bc1, bc2 = st->bc2;
-    long long n4 = n / 4;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
-        float4 P = reinterpret_cast<float4*>(p)[i], Gv = reinterpret_cast<const float4*>(g)[i];
-        float4 M = reinterpret_cast<float4*>(m)[i], V = reinterpret_cast<float4*>(v)[i];
-        long long e = 4 * i;
-        adam_one(P.x, Gv.x, M.x, V.x, e < grid_floats ? lr_g : lr_m, bc1, bc2);
-        adam_one(P.y, Gv.y, M.y, V.y, e + 1 < grid_floats ? lr_g : lr_m, bc1, bc2);
-        adam_one(P.z, Gv.z, M.z, V.z, e + 2 < grid_floats ? lr_g : lr_m, bc1, bc2);
-        adam_one(P.w, Gv.w, M.w, V.w, e + 3 < grid_floats ? lr_g : lr_m, bc1, bc2);
-        reinterpret_cast<float4*>(p)[i] = P;
-        reinterpret_cast<float4*>(m)[i] = M;
-        reinterpret_cast<float4*>(v)[i] = V;
+    const float inv_bc1 = 1.f / st->bc1, rsb2 = rsqrtf(st->bc2);
+    const float step_g = st->lr_grid * inv_bc1, step_m = st->lr_mlp * inv_bc1;
+    const long long n4 = n / 4;
+    float4* P4 = reinterpret_cast<float4*>(p);
+    const float4* G4 = reinterpret_cast<const float4*>(g);
+    float4* M4 = reinterpret_cast<float4*>(m);
+    float4* V4 = reinterpret_cast<float4*>(v);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + stride < n4; i += 2 * stride) {
+        const long long j = i + stride;
+        float4 Pa = __ldcs(P4 + i), Ga = __ldcs(G4 + i), Ma = __ldcs(M4 + i), Va = __ldcs(V4 + i);
+        float4 Pb = __ldcs(P4 + j), Gb = __ldcs(G4 + j), Mb = __ldcs(M4 + j), Vb = __ldcs(V4 + j);
+        adam4(Pa, Ga, Ma, Va, 4 * i, grid_floats, step_g, step_m, rsb2);
+        adam4(Pb, Gb, Mb, Vb, 4 * j, grid_floats, step_g, step_m, rsb2);
+        __stcs(P4 + i, Pa);
+        __stcs(M4 + i, Ma);
+        __stcs(V4 + i, Va);
+        __stcs(P4 + j, Pb);
+        __stcs(M4 + j, Mb);
+        __stcs(V4 + j, Vb);
+    }
+    if (i < n4) {
+        float4 Pa = __ldcs(P4 + i), Ga = __ldcs(G4 + i), Ma = __ldcs(M4 + i), Va = __ldcs(V4 + i);
+        adam4(Pa, Ga, Ma, Va, 4 * i, grid_floats, step_g, step_m, rsb2);
+        __stcs(P4 + i, Pa);
+        __stcs(M4 + i, Ma);
+        __stcs(V4 + i, Va);
     }
     if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) {
         long long e = 4 * n4 + threadIdx.x;
-        adam_one(p[e], g[e], m[e], v[e], e < grid_floats ? lr_g : lr_m, bc1, bc2);
+        adam_one(p[e], g[e], m[e], v[e], e < grid_floats ? step_g : step_m, rsb2);
     }
 }
 
@@ -495,6 +525,7 @@ void ntbc_train_release(ntbc_model* m) {
     cudaFree(ts->st);
     cudaFree(ts->qscale);
     cudaFree(ts->tc_img);
+    cudaFree(ts->tc_part);
     delete ts;
     m->train = nullptr;
 }
@@ -544,6 +575,14 @@ static ntbc_status ensure_train_state(ntbc_model* m, int n_blocks) {
         }
         ts->tc_err = reinterpret_cast<int*>(ts->tc_img + img);
         NTBC_CHECK_CUDA(cudaMemset(ts->tc_err, 0, sizeof(int)));
+        TrNet cn = train_tc_net_desc(mv, true), en = train_tc_net_desc(mv, false);
+        ts->tc_part_rows = train_tc_max_partial_rows();
+        size_t part = (size_t)ts->tc_part_rows * std::max(cn.mlp_params, en.mlp_params) * sizeof(float);
+        st = device_alloc((void**)&ts->tc_part, part, "weight-gradient partials");
+        if (st != NTBC_OK) {
+            ntbc_train_release(m);
+            return st;
+        }
     }
     (void)grads_keep;
     ts->cap_blocks = n_blocks;
@@ -696,9 +735,11 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
         st = train_tc_image(m->params, cn, cimg, s);
         if (st == NTBC_OK) st = train_tc_image(m->params, en, eimg, s);
         if (st == NTBC_OK)
-            st = train_tc_launch(mv, true, cn, cimg, csrc, tp, ids, nb * 16, T, grads, ts->loss_acc, ts->tc_err, s);
+            st = train_tc_launch(mv, true, cn, cimg, csrc, tp, ids, nb * 16, T, grads, ts->loss_acc, ts->tc_err,
+                                 ts->tc_part, ts->tc_part_rows, s);
         if (st == NTBC_OK)
-            st = train_tc_launch(mv, false, en, eimg, esrc, tp, ids, nb, T, grads, ts->loss_acc, ts->tc_err, s);
+            st = train_tc_launch(mv, false, en, eimg, esrc, tp, ids, nb, T, grads, ts->loss_acc, ts->tc_err,
+                                 ts->tc_part, ts->tc_part_rows, s);
     } else {
         st = run_net(m, mv, true, tp, ids, nb * 16, csrc, T, grads, ts->loss_acc, s);
         if (st == NTBC_OK) st = run_net(m, mv, false, tp, ids, nb, esrc, T, grads, ts->loss_acc, s);

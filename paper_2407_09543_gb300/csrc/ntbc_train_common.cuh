@@ -116,6 +116,12 @@ __device__ __forceinline__ void ste_grad(int K, int C, const float d[8], const f
     }
 }
 
+// Fire-and-forget vector reduction into global memory (8-byte aligned address): no value
+// comes back, so the thread does not wait for the L2 round trip.
+__device__ __forceinline__ void red_add_f32x2(float* addr, float2 v) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // One straight-through factor per corner value: 1 where the QAT code was not clamped.
 __device__ __forceinline__ float2 ste_mask(float2 add, const float* f32, long long corner, float s, float z, float qm) {
     float2 r = *reinterpret_cast<const float2*>(f32 + corner);
@@ -176,7 +182,7 @@ __device__ __forceinline__ void scatter_level(const NetView& nv, bool color, int
             bool last_y = ly == 3 || ny != cy;
             issue = valid && last_x && last_y;
         }
-        if (issue) atomicAdd(reinterpret_cast<float2*>(ggrad + corner), add);
+        if (issue) red_add_f32x2(ggrad + corner, add);
     }
 }
 

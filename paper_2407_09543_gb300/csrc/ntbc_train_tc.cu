@@ -125,8 +125,8 @@ __device__ __forceinline__ float act_fast(float z, int act) {
 __device__ __forceinline__ float sigmoid_fast(float z) { return rcp_fast(1.f + ex2_fast(-z * kL2e)); }
 
 // ---------------------------------------------------------------------------
-// losses: every palette / softmax loop runs over all 8 entries (entries n >= K carry no
-// weight) and over a compile-time channel count, so nothing leaves the registers
+// losses: every palette / softmax loop runs over a compile-time entry count (4 for BC1,
+// C = 3; 8 for BC4, C = 1) and channel count, so nothing leaves the registers
 // ---------------------------------------------------------------------------
 
 // Softmax-expectation backward of the hard decode (App. A, corrected form):
@@ -136,11 +136,11 @@ __device__ __forceinline__ void ste_fast(int K, const float d[8], const float P[
                                          float g_d[8]) {
     float m = d[0];
 #pragma unroll
-    for (int n = 1; n < 8; ++n)
+    for (int n = 1; n < (C == 3 ? 4 : 8); ++n)
         if (n < K) m = fmaxf(m, d[n]);
     float sig[8], sum = 0.f;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
         sig[n] = n < K ? ex2_fast((d[n] - m) * (invT * kL2e)) : 0.f;
         sum += sig[n];
     }
@@ -149,13 +149,13 @@ __device__ __forceinline__ void ste_fast(int K, const float d[8], const float P[
 #pragma unroll
     for (int q = 0; q < C; ++q) pbar[q] = 0.f;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
         sig[n] *= inv;
 #pragma unroll
         for (int q = 0; q < C; ++q) pbar[q] = fmaf(sig[n], P[n][q], pbar[q]);
     }
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
         float t = 0.f;
 #pragma unroll
         for (int q = 0; q < C; ++q) t = fmaf(g_dec[q], P[n][q] - pbar[q], t);
@@ -170,12 +170,12 @@ __device__ __forceinline__ int palette_distances(int fmt, const float* e0, const
                                                  float a8[8], float b8[8], float d[8], float inv[8], int& best) {
     float c8[8];
 #pragma unroll
-    for (int n = 0; n < 8; ++n) a8[n] = b8[n] = c8[n] = 0.f;       // BC1 fills only n < 4
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) a8[n] = b8[n] = c8[n] = 0.f;       // BC1 fills only n < 4
     int K = palette_coeffs(fmt, e0[0] > e1[0], a8, b8, c8);
     float bestv = -3.0e38f;
     best = 0;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
         float sq = 0.f;
 #pragma unroll
         for (int q = 0; q < C; ++q) {
@@ -199,7 +199,7 @@ __device__ __forceinline__ void pick(const float P[8][C], int best, float* out) 
 #pragma unroll
     for (int q = 0; q < C; ++q) out[q] = P[0][q];
 #pragma unroll
-    for (int n = 1; n < 8; ++n)
+    for (int n = 1; n < (C == 3 ? 4 : 8); ++n)
         if (n == best)
 #pragma unroll
             for (int q = 0; q < C; ++q) out[q] = P[n][q];
@@ -228,7 +228,7 @@ __device__ __forceinline__ void color_texture(int fmt, const float* ch, const fl
     float g_d[8];
     ste_fast<C>(K, d, P, g_dec, invT, g_d);
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n)
 #pragma unroll
         for (int q = 0; q < C; ++q) g[q] -= g_d[n] * (ch[q] - P[n][q]) * inv[n];
 #pragma unroll
@@ -247,10 +247,10 @@ __device__ __forceinline__ void endpoint_texel(int fmt, const float* eh0, const 
     int K = palette_distances<C>(fmt, eh0, eh1, c, Ph, ah, bh, d, inv, best);
     float ar[8], br[8], cr[8], Pr[8][C];
 #pragma unroll
-    for (int n = 0; n < 8; ++n) ar[n] = br[n] = cr[n] = 0.f;
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) ar[n] = br[n] = cr[n] = 0.f;
     palette_coeffs(fmt, e0[0] > e1[0], ar, br, cr);
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n)
 #pragma unroll
         for (int q = 0; q < C; ++q) Pr[n][q] = fmaf(ar[n], e0[q], fmaf(br[n], e1[q], cr[n]));
     float pb[C], g_dec[C];
@@ -264,13 +264,25 @@ __device__ __forceinline__ void endpoint_texel(int fmt, const float* eh0, const 
     float g_d[8];
     ste_fast<C>(K, d, Pr, g_dec, invT, g_d);
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
+    for (int n = 0; n < (C == 3 ? 4 : 8); ++n)
 #pragma unroll
         for (int q = 0; q < C; ++q) {
             float gp = g_d[n] * (c[q] - Ph[n][q]) * inv[n];       // d d_n / d P_n = (c - P_n) / ||.||
             g0[q] = fmaf(ah[n], gp, g0[q]);
             g1[q] = fmaf(bh[n], gp, g1[q]);
         }
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// start the global reads of every texture a loss row needs (the reference block's endpoints
+// and the texel) before the per-texture arithmetic, so they overlap instead of chaining
+__device__ __forceinline__ void prefetch_row(const TrArgs& a, int b, int x, int y) {
+    const ModelView& mv = a.mv;
+    for (int t = 0; t < mv.n_textures; ++t) {
+        prefetch_l1(a.tp.blocks[t] + (long long)b * 8);
+        prefetch_l1(a.tp.texels[t] + ((long long)y * mv.width + x) * (mv.formats[t] == NTBC_BC1 ? 3 : 1));
+    }
 }
 
 __device__ __forceinline__ void st_bf16(unsigned char* tile, int r, int col, int C, float v) {
@@ -284,6 +296,7 @@ __device__ __forceinline__ void color_loss_row(const TrArgs& a, int s, bool vali
     int b = a.ids[s >> 4], i = s & 15;
     int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
     const float inv_n = 1.f / ((float)a.B * (float)a.net.out_dim), invT = 1.f / a.T;
+    prefetch_row(a, b, x, y);
     for (int t = 0; t < mv.n_textures; ++t) {
         const int fmt = mv.formats[t], co = mv.coff[t];
         float e0[3], e1[3];
@@ -324,6 +337,7 @@ __device__ __forceinline__ void endpoint_pair(const TrArgs& a, int s, int bb, in
     int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
     const float inv_ncd = 1.f / ((float)a.B * 16.f * (float)mv.color.out_dim), invT = 1.f / a.T;
     const float* yrow = Ys + bb * od;
+    prefetch_row(a, b, x, y);
     for (int t = 0; t < mv.n_textures; ++t) {
         const int fmt = mv.formats[t], eo = mv.eoff[t];
         float e0[3], e1[3];
@@ -399,6 +413,12 @@ __device__ __forceinline__ void endpoint_block_row(const TrArgs& a, int s, bool 
 __device__ __forceinline__ void gather_row_train(const NetView& nv, const GridSrc& src, float u, float v,
                                                  unsigned char* X, int r, int K0) {
     const int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+    for (int l = 0; l < nv.levels; ++l) {               // both corner rows of every level into L1
+        Bilinear bl = bilinear_at(nv.res[l], u, v);
+        const float* gp = src.f32 + nv.grid_off[l] + bl.base;
+        prefetch_l1(gp);
+        prefetch_l1(gp + bl.row);
+    }
 #pragma unroll 4
     for (int l = 0; l < nv.levels; ++l) {
         Bilinear bl = bilinear_at(nv.res[l], u, v);
@@ -657,51 +677,92 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
                     float* gs = reinterpret_cast<float*>(G.D) + r * 33;    // the delta tile is free now
 #pragma unroll
                     for (int j = 0; j < 32; ++j) gs[j] = gx[j];
-                    float u, v;
-                    int x, y;
-                    sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
-                    const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+                    if (COLOR) {          // texels: warp-aggregated along the block's rows and columns
+                        float u, v;
+                        int x, y;
+                        sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
+                        const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
 #pragma unroll 1
-                    for (int lv = 0; lv < nv.levels; ++lv)
-                        scatter_level(nv, COLOR, lv, u, v, r, valid, gs[2 * lv], gs[2 * lv + 1], a.src, qat_bits, a.grads);
+                        for (int lv = 0; lv < nv.levels; ++lv)
+                            scatter_level(nv, COLOR, lv, u, v, r, valid, gs[2 * lv], gs[2 * lv + 1], a.src, qat_bits,
+                                          a.grads);
+                    }
                 }
             }
             if (ok) first = false;
         }
         if (!COLOR) {
-            __syncthreads();                // staging reused by the next tile
+            // blocks: the (sample, level) scatter items spread over all 16 warps
+            __syncthreads();
             if (abort[0]) break;
+            const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+            const float* gs_all = reinterpret_cast<const float*>(G.D);
+            for (int p = threadIdx.x; p < kTrRows * nv.levels; p += blockDim.x) {
+                const int rr = p % kTrRows, lv = p / kTrRows, sb = tile * kTrRows + rr;
+                const bool pv = sb < a.B;
+                float u, v;
+                int x, y;
+                sample_coords(a.mv, false, a.ids, pv ? sb : a.B - 1, u, v, x, y);
+                scatter_level(nv, false, lv, u, v, rr, pv, gs_all[rr * 33 + 2 * lv], gs_all[rr * 33 + 2 * lv + 1], a.src,
+                              qat_bits, a.grads);
+            }
+            __syncthreads();                // staging reused by the next tile
         } else if (!ok) {
             break;
         }
     }
 
-    // ---- losses (one double atomic per warp and term)
+    // ---- losses: warp sums, then one double atomic per CTA and term
     {
-        float n0 = COLOR ? (float)a.B * (float)od : (float)a.B * (float)od;
-        float n1 = COLOR ? n0 : (float)a.B * 16.f * (float)a.mv.color.out_dim;
-        block_reduce_add(&a.acc[COLOR ? 2 : 0], loss0 / n0);
-        block_reduce_add(&a.acc[COLOR ? 3 : 1], loss1 / n1);
+        __shared__ float loss_red[2][kTrEndpointThreads / 32];
+        const float n0 = (float)a.B * (float)od;
+        const float n1 = COLOR ? n0 : (float)a.B * 16.f * (float)a.mv.color.out_dim;
+        float v0 = loss0 / n0, v1 = loss1 / n1;
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+            v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            loss_red[0][threadIdx.x >> 5] = v0;
+            loss_red[1][threadIdx.x >> 5] = v1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                s0 += loss_red[0][w];
+                s1 += loss_red[1][w];
+            }
+            atomicAdd(&a.acc[COLOR ? 2 : 0], s0);
+            atomicAdd(&a.acc[COLOR ? 3 : 1], s1);
+        }
     }
 
-    // ---- weight gradients: TMEM accumulators -> global (one atomic per element and group)
-    if (tile_thread && ok && !first) {
+    // ---- weight gradients: this group's TMEM accumulators -> its row of partial sums (plain
+    // stores; a second kernel adds the rows of all groups, so no address sees contention)
+    if (tile_thread && ok) {
+        float* part = a.partials + (long long)(blockIdx.x * a.groups + G.g) * net.mlp_params;
         for (int l = 0; l < L; ++l) {
             const TrLayer& Ly = net.layer[l];
             const int ncol = l == 0 ? net.K0 : Ly.N;
             for (int c0 = 0; c0 < ncol; c0 += 16) {
                 float v[16];
-                tmem_ld16(G.row + (uint32_t)Ly.dw_col + c0, v);
-                tmem_wait_ld_regs<16>(v);
+                if (!first) {
+                    tmem_ld16(G.row + (uint32_t)Ly.dw_col + c0, v);
+                    tmem_wait_ld_regs<16>(v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;      // a group without tiles adds nothing
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     int c = c0 + j;
                     if (l == 0) {             // lane = unit o, column = input i
-                        if (r < Ly.out && c < Ly.in) atomicAdd(a.grads + Ly.w_off + (long long)r * Ly.in + c, v[j]);
-                        else if (r < Ly.out && c == Ly.in) atomicAdd(a.grads + Ly.b_off + r, v[j]);
+                        if (r < Ly.out && c < Ly.in) part[Ly.w_off - net.mlp_base + (long long)r * Ly.in + c] = v[j];
+                        else if (r < Ly.out && c == Ly.in) part[Ly.b_off - net.mlp_base + r] = v[j];
                     } else {                  // lane = input i (64 = bias), column = unit o
-                        if (c < Ly.out && r < Ly.in) atomicAdd(a.grads + Ly.w_off + (long long)c * Ly.in + r, v[j]);
-                        else if (c < Ly.out && r == Ly.in) atomicAdd(a.grads + Ly.b_off + c, v[j]);
+                        if (c < Ly.out && r < Ly.in) part[Ly.w_off - net.mlp_base + (long long)c * Ly.in + r] = v[j];
+                        else if (c < Ly.out && r == Ly.in) part[Ly.b_off - net.mlp_base + c] = v[j];
                     }
                 }
             }
@@ -716,6 +777,15 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(512));
+}
+
+// grads[mlp_base + j] += sum over the groups' partial rows
+__global__ void reduce_partials_kernel(const float* __restrict__ part, int rows, int n, float* __restrict__ grads) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int p = 0; p < rows; ++p) acc += part[(long long)p * n + j];
+        grads[j] += acc;
+    }
 }
 
 // BF16 weight image of one network: per layer the [N][K] tile (W in columns 0..in-1, the
@@ -763,6 +833,8 @@ TrNet train_tc_net_desc(const ModelView& mv, bool color) {
         L.dw_col = col;
         col += l == 0 ? n.K0 : L.N;
     }
+    n.mlp_base = n.layer[0].w_off;
+    n.mlp_params = (int)(n.layer[nv.n_layers - 1].b_off + n.layer[nv.n_layers - 1].out - n.mlp_base);
     n.img_bytes = (img + 127) & ~127;
     return n;
 }
@@ -795,9 +867,11 @@ ntbc_status train_tc_image(const float* params, const TrNet& net, unsigned char*
     return NTBC_OK;
 }
 
+int train_tc_max_partial_rows() { return 2 * 152; }
+
 ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, const unsigned char* img,
                             const GridSrc& src, const TexPtrs& tp, const int32_t* ids, int B, float T, float* grads,
-                            double* acc, int* err, cudaStream_t s) {
+                            double* acc, int* err, float* partials, int max_rows, cudaStream_t s) {
     if (net.in_dim > 2 * NTBC_MAX_LEVELS || net.out_pad > 48)
         return fail(NTBC_EUNSUPPORTED, "tensor-core training: network shape outside the kernel's tiles");
     const int cols = train_tc_tmem_cols(net);
@@ -818,6 +892,7 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
     a.acc = acc;
     a.err = err;
     a.img = img;
+    a.partials = partials;
     size_t smem = (size_t)a.sl.group_off + 2 * (size_t)a.sl.group_bytes;
     // colour: two warpgroups when their accumulators fit; endpoint: one tile per CTA
     // (the loss then runs on all 16 warps) with the FP32 staging of outputs and gradients
@@ -834,6 +909,7 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
     NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int grid = std::min(sms, (a.tiles + a.groups - 1) / a.groups);
     if (grid < 1) return NTBC_OK;
+    grid = std::min(grid, max_rows / a.groups);
     if (color) {
         NTBC_CHECK_CUDA(cudaFuncSetAttribute(train_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         train_tc_kernel<true><<<grid, kTrRows * a.groups, smem, s>>>(a);
@@ -842,6 +918,9 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
         train_tc_kernel<false><<<grid, kTrEndpointThreads, smem, s>>>(a);
     }
     NTBC_CHECK_LAUNCH(color ? "tensor-core training (colour)" : "tensor-core training (endpoint)");
+    reduce_partials_kernel<<<(net.mlp_params + 255) / 256, 256, 0, s>>>(partials, grid * a.groups, net.mlp_params,
+                                                                      grads + net.mlp_base);
+    NTBC_CHECK_LAUNCH("weight-gradient partials");
     return NTBC_OK;
 }
 

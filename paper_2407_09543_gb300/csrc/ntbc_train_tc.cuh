@@ -21,6 +21,8 @@ struct TrNet {
     int n_layers, K0, in_dim, out_dim, out_pad;
     TrLayer layer[NTBC_MAX_MLP_LAYERS];
     int img_bytes;
+    long long mlp_base;       // parameter offset of the network's first MLP weight
+    int mlp_params;           // MLP parameters of the network (contiguous from mlp_base)
 };
 
 struct TrSmem {               // byte offsets: weight image at 0, then the groups
@@ -42,6 +44,7 @@ struct TrArgs {
     double* acc;
     int* err;
     const unsigned char* img;  // global BF16 weight image of this network
+    float* partials;           // [grid * groups][mlp_params] weight-gradient partial sums
 };
 
 // layer table of one network (weight image offsets from 0)
@@ -50,9 +53,12 @@ TrNet train_tc_net_desc(const ModelView& mv, bool color);
 int train_tc_tmem_cols(const TrNet& n);
 // BF16 weight image of the network from the FP32 master parameters (device img, img_bytes)
 ntbc_status train_tc_image(const float* params, const TrNet& net, unsigned char* img, cudaStream_t s);
-// forward + loss + backward of B samples; adds into grads and the loss accumulators
+// rows of the partial-sum scratch a launch may use (one per warpgroup)
+int train_tc_max_partial_rows();
+// forward + loss + backward of B samples; adds into grads and the loss accumulators;
+// partials: scratch of max_rows x mlp_params floats
 ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, const unsigned char* img,
                             const GridSrc& src, const TexPtrs& tp, const int32_t* ids, int B, float T, float* grads,
-                            double* acc, int* err, cudaStream_t s);
+                            double* acc, int* err, float* partials, int max_rows, cudaStream_t s);
 
 }  // namespace ntbc
