@@ -74,11 +74,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return e;
 }
 
-// SELU(z) L from a = z L:  lambda max(a, 0) + lambda alpha L (2^min(a, 0) - 1)
-__device__ __forceinline__ float selu_l2(float a) {
-    return fmaf(kSeluLambda, fmaxf(a, 0.f), fmaf(kSeluLA * kLog2e, ex2_approx(fminf(a, 0.f)), -kSeluLA * kLog2e));
-}
-
 // SELU on a pair of units with packed FP32 (two lanes per instruction)
 __device__ __forceinline__ float2 selu2_l2(float2 a) {
     float2 e = make_float2(ex2_approx(fminf(a.x, 0.f)), ex2_approx(fminf(a.y, 0.f)));
@@ -140,68 +135,6 @@ __host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int s
     return s;
 }
 
-// One layer: MMAs from the group's A tile (K0 columns for layer 0, 64 afterwards;
-// when split, each K block twice: high and low halves of the activations) plus the
-// bias K block from the ones tile. The abort decision is uniform across the group:
-// a thread whose bounded wait gave up raises the group's flag, and every thread reads
-// the flag right after the next group barrier.
-template <bool SPLIT>
-__device__ __forceinline__ bool run_layer(const TcLayer& L, int l, unsigned char* smem, unsigned char* A, const TcSmem& sl,
-                                          uint32_t tmem, uint64_t* bar, uint32_t& phase, int g, int r,
-                                          volatile int* abort_flag) {
-    proxy_fence();
-    tc_fence_before();
-    group_sync(g);
-    if (abort_flag[g]) return false;
-    if (r == 0) {
-        tc_fence_after();
-        uint32_t idesc = umma_idesc(L.N);
-        uint32_t a_base = smem_u32(A), b_base = smem_u32(smem + L.img);
-        int Ka = l == 0 ? L.K : 64;                 // columns of the A tile
-        int nk_a = Ka / 16;
-        for (int kc = 0; kc < nk_a; ++kc) {
-            uint64_t ad = umma_desc(a_base + kc * 256, 128, (Ka / 8) * 128);
-            uint64_t bd = umma_desc(b_base + kc * 256, 128, (L.K / 8) * 128);
-            umma_f16(tmem, ad, bd, idesc, kc > 0);
-            if (SPLIT) {
-                uint64_t lo = umma_desc(a_base + (sl.lo_off - sl.a_off) + kc * 256, 128, (Ka / 8) * 128);
-                umma_f16(tmem, lo, bd, idesc, 1);
-            }
-        }
-        if (l > 0) {                                // bias: A = constant L (high, and low half when split)
-            uint64_t bd = umma_desc(b_base + nk_a * 256, 128, (L.K / 8) * 128);
-            umma_f16(tmem, umma_desc(smem_u32(smem + sl.ones_off), 128, 256), bd, idesc, 1);
-            if (SPLIT) umma_f16(tmem, umma_desc(smem_u32(smem + sl.ones_off + kTcRows * 32), 128, 256), bd, idesc, 1);
-        }
-        umma_commit(bar);
-    }
-    if (!mbar_wait(bar, phase)) abort_flag[g] = 1;
-    phase ^= 1;
-    tc_fence_after();
-    return true;
-}
-
-// hidden-layer epilogue: accumulator row -> SELU / ReLU -> FP16 A tile (64 columns)
-template <bool SPLIT>
-__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, unsigned char* A, unsigned char* Alo, int r, int act) {
-#pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 32) {            // two TMEM loads in flight per wait
-        float v[32];
-        tmem_ld16(tmem_row + c0, v);
-        tmem_ld16(tmem_row + c0 + 16, v + 16);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-            float2 y = act == NTBC_ACT_SELU ? selu2_l2(make_float2(v[j], v[j + 1]))
-                                            : make_float2(fmaxf(v[j], 0.f), fmaxf(v[j + 1], 0.f));
-            v[j] = y.x;
-            v[j + 1] = y.y;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) st_row8_split<SPLIT>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
-    }
-}
-
 __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     uint32_t v;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
@@ -215,9 +148,6 @@ __device__ __forceinline__ float2 corner_codes(uint32_t word) {
                                   __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7541))),
                       make_float2(-8388608.f, -8388608.f));
 }
-
-// integer i (0 <= i < 2^22) as float via the 2^23 magic number
-__device__ __forceinline__ float small_int_float(int i) { return __int_as_float(i + 0x4B000000) - 8388608.f; }
 
 // corner-aligned bilinear set-up of level l (same arithmetic as bilinear_at, with the
 // per-level constants precomputed as floats)
