@@ -256,6 +256,25 @@ SM_COUNT = 152
 SM_MAX_GHZ = 2.07
 
 
+def encode_roofline(nt, desc, ms_step):
+    """Bounds of one encode step at BATCH_TEXELS: tensor time of the forward + backward MLP
+    FLOPs (3x the forward, BF16 dense peak) and HBM time of the dense Adam pass (read p, g,
+    m, v; write p, m, v), the gradient clear and one read of both FP32 grids."""
+    lay = nt.ntbc_model_layout(desc)
+    hl = desc.hidden_layers
+    mac_c = lay.in_color * 64 + (hl - 1) * 64 * 64 + 64 * lay.out_color
+    mac_e = lay.in_endpoint * 64 + (hl - 1) * 64 * 64 + 64 * lay.out_endpoint
+    flops = 3 * 2.0 * (BATCH_TEXELS * mac_c + BATCH_TEXELS // 16 * mac_e)
+    bytes_ = lay.total * 4.0 * (7 + 1 + 1)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}
+    t_tc = flops / (peaks["bf16_tflops"] * 1e12) * 1e3
+    t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9) * 1e3
+    return {"flop_per_step": flops, "hbm_bytes_per_step": bytes_, "t_tensor_ms": round(t_tc, 4),
+            "t_hbm_ms": round(t_hbm, 4), "bound": "hbm" if t_hbm > t_tc else "tensor",
+            "frac_of_measured": round(max(t_tc, t_hbm) / ms_step, 4)}
+
+
 def inference_roofline(nt, desc, ms):
     """Governing roofline of one inference pass: max of tensor (FP16 dense), MUFU (one exp2 per
     SELU unit and per sigmoid output) and HBM (grid codes read once + blocks written) times."""
@@ -564,6 +583,7 @@ def main():
 
     # ---- roofline of the inference kernel (algorithmic counts per block position)
     roofline, terms = inference_roofline(nt, desc, ms)
+    encode_terms = encode_roofline(nt, desc, ms_per_train_step)
 
     # ---- the same inference in the other modes (pure FP16 activations; FP32 SIMT kernel)
     modes = {}
@@ -683,10 +703,13 @@ def main():
                    "full_schedule_s_extrapolated": round(encode_full_s, 1),
                    "full_schedule_steps": FULL_MAIN_STEPS + FULL_QAT_STEPS,
                    "last_losses": [round(x, 6) for x in last_losses],
+                   "roofline_terms": encode_terms,
                    "reference_bc_encode_ms": round(float(np.mean(ref_ms)), 3),
                    "fp32_kernels": fp32_encode},
         "plain_fp32_gpu": plain,
         "conservative": conservative,
+        "storage": {"ntbc_blob_bytes": int(model.blob_size()), "bc_bytes": int(nblk * 8 * len(FORMATS)),
+                    "weights": "FP16", "grids": "u8"},
         "roofline": roofline,
         "roofline_terms": terms,
         "other_modes": modes,

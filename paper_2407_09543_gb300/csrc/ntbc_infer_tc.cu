@@ -106,7 +106,18 @@ struct TcArgs {
     const int32_t* ids;       // optional block ids (else 0..n-1)
     int mode;                 // 0 pack, 1 raw outputs
     int* err;
+    float inv_w, inv_h, inv_bw, inv_bh;   // reciprocals of the texel and block extents
 };
+
+// block index -> (bx, by) without an integer division: q = floor(b / bw) from the FP32
+// reciprocal (off by at most one for b < 2^24), then one correction step
+__device__ __forceinline__ void block_xy(int b, int bw, float inv_bw, int& bx, int& by) {
+    int q = (int)((float)b * inv_bw);
+    q -= q * bw > b;
+    q += (q + 1) * bw <= b;
+    by = q;
+    bx = b - q * bw;
+}
 
 struct TcOut {
     uint8_t* p[NTBC_MAX_TEXTURES];
@@ -436,9 +447,10 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             int k = unit * kTcUnitBlocks + r;
             bool valid = k < args.n;
             int b = valid ? (args.ids ? args.ids[k] : k) : 0;
-            int bx = b % mv.bw, by = b / mv.bw;
-            gather_row<SPLIT>(mv.endpoint, esrc, lvl + NTBC_MAX_LEVELS, ((float)bx + 0.5f) / (float)mv.bw,
-                              ((float)by + 0.5f) / (float)mv.bh, net.layer[0].K, A, Alo, r, valid);
+            int bx, by;
+            block_xy(b, mv.bw, args.inv_bw, bx, by);
+            gather_row<SPLIT>(mv.endpoint, esrc, lvl + NTBC_MAX_LEVELS, ((float)bx + 0.5f) * args.inv_bw,
+                              ((float)by + 0.5f) * args.inv_bh, net.layer[0].K, A, Alo, r, valid);
             uint32_t orow = 0;
             ok = run_mlp<SPLIT>(net, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
             for (int l = net.n_layers - 1; l < net.n_layers && ok; ++l) {
@@ -500,9 +512,11 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             int k = unit * kTcUnitBlocks + blk;
             bool valid = k < args.n;
             int b = valid ? (args.ids ? args.ids[k] : k) : 0;
-            int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
-            gather_row<SPLIT>(mv.color, csrc, lvl, ((float)x + 0.5f) / (float)mv.width,
-                              ((float)y + 0.5f) / (float)mv.height, net.layer[0].K, A, Alo, r, valid);
+            int bx, by;
+            block_xy(b, mv.bw, args.inv_bw, bx, by);
+            int x = 4 * bx + (i & 3), y = 4 * by + (i >> 2);
+            gather_row<SPLIT>(mv.color, csrc, lvl, ((float)x + 0.5f) * args.inv_w, ((float)y + 0.5f) * args.inv_h,
+                              net.layer[0].K, A, Alo, r, valid);
             uint32_t orow = 0;
             ok = run_mlp<SPLIT>(net, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
             for (int l = net.n_layers - 1; l < net.n_layers && ok; ++l) {
@@ -535,23 +549,26 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                     uint32_t ep = eps[t * kTcUnitBlocks + blk];
                     BlockPalette bp;
                     uint64_t bits;
-                    if (mv.formats[t] == NTBC_BC1) {
+                    if (mv.formats[t] == NTBC_BC1) {           // 2-bit codes: the block's 32 bits in one word
                         bp.solid = (ep & 0xFFFFu) == (ep >> 16);
                         uint32_t wv[3] = {*reinterpret_cast<const uint32_t*>(pb), *reinterpret_cast<const uint32_t*>(pb + 4),
                                           *reinterpret_cast<const uint32_t*>(pb + 8)};
 #pragma unroll
                         for (int q = 0; q < 12; ++q) bp.pal[q / 3][q % 3] = tab[(wv[q / 4] >> (8 * (q % 4))) & 255];
-                        bits = (uint64_t)choose_code_bc1(bp, sigmoid_l2(cv[t][0]), sigmoid_l2(cv[t][1]),
-                                                         sigmoid_l2(cv[t][2])) << (2 * i);
-                    } else {
+                        uint32_t w = (uint32_t)choose_code_bc1(bp, sigmoid_l2(cv[t][0]), sigmoid_l2(cv[t][1]),
+                                                               sigmoid_l2(cv[t][2])) << (2 * i);
+#pragma unroll
+                        for (int o = 8; o > 0; o >>= 1) w |= __shfl_xor_sync(0xffffffffu, w, o);
+                        bits = w;
+                    } else {                                   // 3-bit codes: 48 bits
                         uint32_t w0 = *reinterpret_cast<const uint32_t*>(pb);
                         uint32_t w1 = *reinterpret_cast<const uint32_t*>(pb + 4);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) bp.pal[q][0] = tab[((q < 4 ? w0 : w1) >> (8 * (q % 4))) & 255];
                         bits = (uint64_t)choose_code_bc4(bp, sigmoid_l2(cv[t][0])) << (3 * i);
-                    }
 #pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+                        for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+                    }
                     if (i == 0 && valid) {
                         uint8_t* dst = outs.p[t] + (long long)b * 8;
                         if (mv.formats[t] == NTBC_BC1)
@@ -706,6 +723,10 @@ static TcArgs tc_args(const ntbc_model* m) {
         }
     }
     a.img_bytes = (off + 15) & ~15;
+    a.inv_w = 1.f / (float)a.mv.width;
+    a.inv_h = 1.f / (float)a.mv.height;
+    a.inv_bw = 1.f / (float)a.mv.bw;
+    a.inv_bh = 1.f / (float)a.mv.bh;
     return a;
 }
 
