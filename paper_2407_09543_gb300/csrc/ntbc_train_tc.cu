@@ -235,44 +235,6 @@ __device__ __forceinline__ void color_texture(int fmt, const float* ch, const fl
     for (int q = 0; q < C; ++q) dz[q] = valid ? g[q] * ch[q] * (1.f - ch[q]) : 0.f;
 }
 
-// endpoint network, one (block, texel) pair of one texture: the texel's L_cd term with
-// distances to the palette of the predicted endpoints (eh0, eh1) and the decode from the
-// reference palette; adds the pair's contribution to d loss / d (eh0, eh1)
-template <int C>
-__device__ __forceinline__ void endpoint_texel(int fmt, const float* eh0, const float* eh1, const float* e0,
-                                               const float* e1, const float* c, float invT, float inv_ncd, bool valid,
-                                               float* g0, float* g1, float& lcd) {
-    float Ph[8][C], ah[8], bh[8], d[8], inv[8];
-    int best;
-    int K = palette_distances<C>(fmt, eh0, eh1, c, Ph, ah, bh, d, inv, best);
-    float ar[8], br[8], cr[8], Pr[8][C];
-#pragma unroll
-    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) ar[n] = br[n] = cr[n] = 0.f;
-    palette_coeffs(fmt, e0[0] > e1[0], ar, br, cr);
-#pragma unroll
-    for (int n = 0; n < (C == 3 ? 4 : 8); ++n)
-#pragma unroll
-        for (int q = 0; q < C; ++q) Pr[n][q] = fmaf(ar[n], e0[q], fmaf(br[n], e1[q], cr[n]));
-    float pb[C], g_dec[C];
-    pick<C>(Pr, best, pb);
-#pragma unroll
-    for (int q = 0; q < C; ++q) {
-        float rr = c[q] - pb[q];
-        if (valid) lcd = fmaf(rr, rr, lcd);
-        g_dec[q] = valid ? -2.f * rr * inv_ncd : 0.f;
-    }
-    float g_d[8];
-    ste_fast<C>(K, d, Pr, g_dec, invT, g_d);
-#pragma unroll
-    for (int n = 0; n < (C == 3 ? 4 : 8); ++n)
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            float gp = g_d[n] * (c[q] - Ph[n][q]) * inv[n];       // d d_n / d P_n = (c - P_n) / ||.||
-            g0[q] = fmaf(ah[n], gp, g0[q]);
-            g1[q] = fmaf(bh[n], gp, g1[q]);
-        }
-}
-
 __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // start the global reads of every texture a loss row needs (the reference block's endpoints
@@ -327,58 +289,95 @@ __device__ __forceinline__ void color_loss_row(const TrArgs& a, int s, bool vali
     }
 }
 
-// endpoint L_cd of one (block, texel) pair over every texture: per-texture gradient
-// contributions summed over the block's 16 texels (one half-warp) into Gs[bb]
-__device__ __forceinline__ void endpoint_pair(const TrArgs& a, int s, int bb, int i, bool valid, const float* Ys,
-                                              float* Gs, float& lcd) {
+// endpoint network, one (block, texture) item: the L_cd terms of the block's 16 texels,
+// with distances to the palette of the predicted endpoints (eh0, eh1) and the decode from
+// the reference palette (both palettes built once per item); the item's gradient
+// d loss / d (eh0, eh1), summed over the texels, goes to grow.
+template <int C>
+__device__ __forceinline__ void endpoint_item(const TrArgs& a, int fmt, int b, int eo, const float* yrow,
+                                              const uint8_t* blocks, const uint8_t* tex, bool valid, float* grow,
+                                              float& lcd) {
+    constexpr int KM = C == 3 ? 4 : 8;
     const ModelView& mv = a.mv;
-    const int od = mv.endpoint.out_dim;
-    int b = a.ids[s];
-    int x = 4 * (b % mv.bw) + (i & 3), y = 4 * (b / mv.bw) + (i >> 2);
     const float inv_ncd = 1.f / ((float)a.B * 16.f * (float)mv.color.out_dim), invT = 1.f / a.T;
-    const float* yrow = Ys + bb * od;
-    prefetch_row(a, b, x, y);
-    for (int t = 0; t < mv.n_textures; ++t) {
-        const int fmt = mv.formats[t], eo = mv.eoff[t];
-        float e0[3], e1[3];
-        ref_endpoints(fmt, a.tp.blocks[t], b, e0, e1);
-        if (fmt == NTBC_BC1) {
-            float eh0[3], eh1[3], c[3], g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
-            const uint8_t* tp = a.tp.texels[t] + ((long long)y * mv.width + x) * 3;
+    const int bx = b % mv.bw, by = b / mv.bw;
+    const uint8_t* row0 = tex + ((long long)(4 * by) * mv.width + 4 * bx) * C;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                eh0[q] = yrow[eo + q];
-                eh1[q] = yrow[eo + 3 + q];
-                c[q] = (float)tp[q] * (1.f / 255.f);
+    for (int yy = 0; yy < 4; ++yy) {
+        prefetch_l1(row0 + (long long)yy * mv.width * C);
+        prefetch_l1(row0 + (long long)yy * mv.width * C + 4 * C - 1);
+    }
+    float eh0[3] = {0.f, 0.f, 0.f}, eh1[3] = {0.f, 0.f, 0.f}, e0[3], e1[3];
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        eh0[q] = yrow[eo + q];
+        eh1[q] = yrow[eo + C + q];
+    }
+    ref_endpoints(fmt, blocks, b, e0, e1);
+    float ah[8], bh[8], chh[8], ar[8], br[8], cr[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) ah[n] = bh[n] = chh[n] = ar[n] = br[n] = cr[n] = 0.f;
+    const int K = palette_coeffs(fmt, eh0[0] > eh1[0], ah, bh, chh);
+    palette_coeffs(fmt, e0[0] > e1[0], ar, br, cr);
+    float Ph[8][C], Pr[8][C];
+#pragma unroll
+    for (int n = 0; n < KM; ++n)
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            Ph[n][q] = fmaf(ah[n], eh0[q], fmaf(bh[n], eh1[q], chh[n]));
+            Pr[n][q] = fmaf(ar[n], e0[q], fmaf(br[n], e1[q], cr[n]));
+        }
+    float g0[C], g1[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) g0[q] = g1[q] = 0.f;
+#pragma unroll 2
+    for (int i = 0; i < 16; ++i) {
+        const uint8_t* tp = row0 + ((long long)(i >> 2) * mv.width + (i & 3)) * C;
+        float c[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) c[q] = (float)tp[q] * (1.f / 255.f);
+        float d[8], inv[8];
+        float bestv = -3.0e38f;
+        int best = 0;
+#pragma unroll
+        for (int n = 0; n < KM; ++n) {
+            float sq = 0.f;
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                float df = c[q] - Ph[n][q];
+                sq = fmaf(df, df, sq);
             }
-            endpoint_texel<3>(fmt, eh0, eh1, e0, e1, c, invT, inv_ncd, valid, g0, g1, lcd);
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    g0[q] += __shfl_xor_sync(0xffffffffu, g0[q], o);
-                    g1[q] += __shfl_xor_sync(0xffffffffu, g1[q], o);
-                }
-            if (i == 0)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    Gs[bb * od + eo + q] = g0[q];
-                    Gs[bb * od + eo + 3 + q] = g1[q];
-                }
-        } else {
-            float eh0[1] = {yrow[eo]}, eh1[1] = {yrow[eo + 1]}, g0[1] = {0.f}, g1[1] = {0.f};
-            float c[1] = {(float)a.tp.texels[t][(long long)y * mv.width + x] * (1.f / 255.f)};
-            endpoint_texel<1>(fmt, eh0, eh1, e0, e1, c, invT, inv_ncd, valid, g0, g1, lcd);
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) {
-                g0[0] += __shfl_xor_sync(0xffffffffu, g0[0], o);
-                g1[0] += __shfl_xor_sync(0xffffffffu, g1[0], o);
-            }
-            if (i == 0) {
-                Gs[bb * od + eo] = g0[0];
-                Gs[bb * od + eo + 1] = g1[0];
+            float nrm = sqrt_fast(sq);
+            d[n] = -nrm;
+            inv[n] = rcp_fast(fmaxf(nrm, kNormGuard));
+            if (d[n] > bestv) {
+                bestv = d[n];
+                best = n;
             }
         }
+        float pb[C], g_dec[C];
+        pick<C>(Pr, best, pb);
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            float rr = c[q] - pb[q];
+            if (valid) lcd = fmaf(rr, rr, lcd);
+            g_dec[q] = valid ? -2.f * rr * inv_ncd : 0.f;
+        }
+        float g_d[8];
+        ste_fast<C>(K, d, Pr, g_dec, invT, g_d);
+#pragma unroll
+        for (int n = 0; n < KM; ++n)
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                float gp = g_d[n] * (c[q] - Ph[n][q]) * inv[n];   // d d_n / d P_n = (c - P_n) / ||.||
+                g0[q] = fmaf(ah[n], gp, g0[q]);
+                g1[q] = fmaf(bh[n], gp, g1[q]);
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        grow[eo + q] = g0[q];
+        grow[eo + C + q] = g1[q];
     }
 }
 
@@ -590,10 +589,17 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
             // ---- endpoint L_cd over the tile's 128 blocks x 16 texels, shared by all 16 warps
             __syncthreads();
             if (abort[0]) break;
-            for (int p = threadIdx.x; p < kTrRows * 16; p += blockDim.x) {
-                const int bb = p >> 4, i = p & 15, sb = tile * kTrRows + bb;
+            // one (block, texture) item per thread; a warp holds 32 blocks of one texture
+            for (int item = threadIdx.x; item < kTrRows * a.mv.n_textures; item += blockDim.x) {
+                const int t = item / kTrRows, bb = item % kTrRows, sb = tile * kTrRows + bb;
                 const bool pv = sb < a.B;
-                endpoint_pair(a, pv ? sb : a.B - 1, bb, i, pv, Ys, Gs, loss1);
+                const int b = a.ids[pv ? sb : a.B - 1];
+                if (a.mv.formats[t] == NTBC_BC1)
+                    endpoint_item<3>(a, NTBC_BC1, b, a.mv.eoff[t], Ys + bb * od, a.tp.blocks[t], a.tp.texels[t], pv,
+                                     Gs + bb * od, loss1);
+                else
+                    endpoint_item<1>(a, NTBC_BC4, b, a.mv.eoff[t], Ys + bb * od, a.tp.blocks[t], a.tp.texels[t], pv,
+                                     Gs + bb * od, loss1);
             }
             __syncthreads();
             if (tile_thread) {
