@@ -136,15 +136,45 @@ __device__ __forceinline__ float2 ste_mask(float2 add, const float* f32, long lo
 // indices are non-decreasing in x (lane & 3) and in y (lane >> 2), so equal corners form
 // contiguous runs; a segmented scan along x, then along y, leaves each distinct corner's
 // total in the last lane of its run, which issues the only atomic for that corner.
+// The keys of those runs (the neighbours' corner indices) are recomputed from the
+// neighbours' coordinates, shuffled once per sample (`Neighbours`), with the same arithmetic
+// the neighbour uses, so only the gradient values travel through shuffles per level.
+struct Neighbours {
+    float u_m1, u_m2, u_p1;      // u of the texels 1 and 2 to the left and 1 to the right
+    float v_m1, v_m2, v_p1;      // v of the texels 1 and 2 rows up and 1 row down
+};
+
+__device__ __forceinline__ Neighbours neighbours(float u, float v) {
+    Neighbours n;
+    n.u_m1 = __shfl_up_sync(0xffffffffu, u, 1);
+    n.u_m2 = __shfl_up_sync(0xffffffffu, u, 2);
+    n.u_p1 = __shfl_down_sync(0xffffffffu, u, 1);
+    n.v_m1 = __shfl_up_sync(0xffffffffu, v, 4);
+    n.v_m2 = __shfl_up_sync(0xffffffffu, v, 8);
+    n.v_p1 = __shfl_down_sync(0xffffffffu, v, 4);
+    return n;
+}
+
+__device__ __forceinline__ int cell_of(float t, int res) { return min((int)floorf(t * (float)(res - 1)), res - 2); }
+
 // One level l: (g0, g1) = d loss / d features of the sample at this level. All 32 lanes of
 // the warp must call it together.
 __device__ __forceinline__ void scatter_level(const NetView& nv, bool color, int l, float u, float v, int lane_k,
                                               bool valid, float g0, float g1, const GridSrc& src, int qat_bits,
-                                              float* __restrict__ ggrad) {
+                                              float* __restrict__ ggrad, const Neighbours& nb = Neighbours()) {
     const int lx = lane_k & 3, ly = (lane_k >> 2) & 3;
     int res = nv.res[l];
     float px = u * (float)(res - 1), py = v * (float)(res - 1);
     int ix = min((int)floorf(px), res - 2), iy = min((int)floorf(py), res - 2);
+    int kx_m1 = 0, kx_m2 = 0, kx_p1 = 0, ky_m1 = 0, ky_m2 = 0, ky_p1 = 0;
+    if (color) {
+        kx_m1 = cell_of(nb.u_m1, res);
+        kx_m2 = cell_of(nb.u_m2, res);
+        kx_p1 = cell_of(nb.u_p1, res);
+        ky_m1 = cell_of(nb.v_m1, res);
+        ky_m2 = cell_of(nb.v_m2, res);
+        ky_p1 = cell_of(nb.v_p1, res);
+    }
     float fx = px - (float)ix, fy = py - (float)iy;
     if (!valid) g0 = g1 = 0.f;
     float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
@@ -157,29 +187,28 @@ __device__ __forceinline__ void scatter_level(const NetView& nv, bool color, int
             add = ste_mask(add, src.f32, corner, src.scale[l], src.zero[l], (float)((1 << qat_bits) - 1));
         bool issue = valid;
         if (color) {
+            const int dx = j & 1, dy = j >> 1;
 #pragma unroll
             for (int dd = 1; dd <= 2; dd <<= 1) {          // runs along x
                 float px0 = __shfl_up_sync(0xffffffffu, add.x, dd), px1 = __shfl_up_sync(0xffffffffu, add.y, dd);
-                int pk = __shfl_up_sync(0xffffffffu, cx, dd);
+                int pk = (dd == 1 ? kx_m1 : kx_m2) + dx;
                 if (lx >= dd && pk == cx) {
                     add.x += px0;
                     add.y += px1;
                 }
             }
-            int nx = __shfl_down_sync(0xffffffffu, cx, 1);
-            bool last_x = lx == 3 || nx != cx;
+            bool last_x = lx == 3 || kx_p1 + dx != cx;
             if (!last_x) add = make_float2(0.f, 0.f);
 #pragma unroll
             for (int dd = 4; dd <= 8; dd <<= 1) {          // runs along y
                 float py0 = __shfl_up_sync(0xffffffffu, add.x, dd), py1 = __shfl_up_sync(0xffffffffu, add.y, dd);
-                int pk = __shfl_up_sync(0xffffffffu, cy, dd);
+                int pk = (dd == 4 ? ky_m1 : ky_m2) + dy;
                 if (ly >= dd / 4 && pk == cy) {
                     add.x += py0;
                     add.y += py1;
                 }
             }
-            int ny = __shfl_down_sync(0xffffffffu, cy, 4);
-            bool last_y = ly == 3 || ny != cy;
+            bool last_y = ly == 3 || ky_p1 + dy != cy;
             issue = valid && last_x && last_y;
         }
         if (issue) red_add_f32x2(ggrad + corner, add);
@@ -197,10 +226,11 @@ __device__ __forceinline__ void scatter_sample(const ModelView& mv, bool color, 
     int x, y;
     sample_coords(mv, color, ids, kc, u, v, x, y);
     int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+    const Neighbours nb = color ? neighbours(u, v) : Neighbours();
 #pragma unroll
     for (int l = 0; l < NTBC_MAX_LEVELS; ++l) {              // unrolled: g stays in registers
         if (l >= nv.levels) break;
-        scatter_level(nv, color, l, u, v, lane_k, valid, g[2 * l], g[2 * l + 1], src, qat_bits, ggrad);
+        scatter_level(nv, color, l, u, v, lane_k, valid, g[2 * l], g[2 * l + 1], src, qat_bits, ggrad, nb);
     }
 }
 

@@ -688,10 +688,11 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
                         int x, y;
                         sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
                         const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+                        const Neighbours nbr = neighbours(u, v);
 #pragma unroll 1
                         for (int lv = 0; lv < nv.levels; ++lv)
                             scatter_level(nv, COLOR, lv, u, v, r, valid, gs[2 * lv], gs[2 * lv + 1], a.src, qat_bits,
-                                          a.grads);
+                                          a.grads, nbr);
                     }
                 }
             }
