@@ -595,6 +595,16 @@ def main():
         modes[name] = {"ms": round(t_m, 4), "value": round(tex_blocks / (t_m * 1e-3) / 1e6, 3),
                        "psnr_db": psnr_list(nt, obc, torch, mat, outs, side)}
     model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+    # the roughness and AO textures written as one BC5 texture (16-byte blocks, interleaved)
+    bc5 = torch.empty(nblk * 16, dtype=torch.uint8, device=dev)
+    bc5_ptrs = [outs[0].data_ptr(), outs[1].data_ptr(), bc5.data_ptr(), bc5.data_ptr() + 8]
+    model.infer_to_bc(bc5_ptrs, strides=[8, 8, 16, 16])
+    torch.cuda.synchronize()
+    t_b5 = float(np.mean(time_events(torch, lambda: model.infer_to_bc(bc5_ptrs, strides=[8, 8, 16, 16]),
+                                     max(3, args.steps // 4), flush=flush)))
+    modes["bc5_layout"] = {"ms": round(t_b5, 4), "value": round(tex_blocks / (t_b5 * 1e-3) / 1e6, 3),
+                           "note": "roughness + AO as one BC5 texture (strided 16-byte blocks)"}
+    del bc5
 
     # ---- conservative packaging (Sec. 4.1): one model for the BC1 textures, one for the BC4
     # textures, both encoded with the BF16 pass and decoded together in one batched launch

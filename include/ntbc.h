@@ -41,6 +41,17 @@ typedef enum {
 } ntbc_status;
 
 enum { NTBC_BC1 = 1, NTBC_BC4 = 4 };
+/*
+ * Compositions of the two (Sec. 2.1: BC2, BC3 and BC5 combine BC1 and BC4), 16-byte blocks,
+ * accepted by the codec (bc_reference_encode, bc_decode):
+ *   NTBC_BC3  RGBA8 texels; bytes 0-7 the alpha channel as a BC4 block, bytes 8-15 the colour
+ *             as a BC1 block that always decodes with the four-colour palette
+ *   NTBC_BC5  two-channel texels (2 bytes each); bytes 0-7 channel 0 as a BC4 block, bytes
+ *             8-15 channel 1
+ * A model encodes them as their parts (a BC1 and a BC4 texture, or two BC4 textures) and
+ * writes the interleaved blocks with ntbc_infer_to_bc_strided.
+ */
+enum { NTBC_BC3 = 3, NTBC_BC5 = 5 };
 enum { NTBC_ACT_SELU = 0, NTBC_ACT_RELU = 1 };
 /*
  * Inference precision (the stored MLP weights are FP16 for the two FP16 modes):
@@ -83,9 +94,9 @@ int ntbc_abi_version(void);
  * per-texel code choice, colour0 > colour1. BC4: best of the 8-value mode over
  * [min, max] and the 6-value mode over the texels other than 0 and 255.
  * Deterministic; bit-exact with the CPU oracle.
- *   fmt     NTBC_BC1 or NTBC_BC4
- *   texels  device, w*h*3 (BC1) or w*h (BC4) bytes, row-major
- *   blocks  device, (w/4)*(h/4)*8 bytes, written
+ *   fmt     NTBC_BC1, NTBC_BC4, or the compositions NTBC_BC3 / NTBC_BC5
+ *   texels  device, w*h*C bytes, row-major, C = 3 (BC1), 1 (BC4), 4 (BC3), 2 (BC5)
+ *   blocks  device, (w/4)*(h/4)*8 bytes (BC1, BC4) or *16 (BC3, BC5), written
  */
 ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h,
                                 uint8_t* blocks, void* stream);
@@ -94,8 +105,8 @@ ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h,
  * Decoder (the "existing BC decompression" of Sec. 4.4): blocks -> texels with
  * the integer palette (interpolants rounded to nearest; BC1 colour0 <= colour1
  * selects the 3-colour mode, BC4 r0 <= r1 the 6-value mode with 0 and 255).
- *   blocks  device, (w/4)*(h/4)*8 bytes
- *   texels  device, w*h*3 (BC1) or w*h (BC4) bytes, written
+ *   blocks  device, (w/4)*(h/4)*8 (BC1, BC4) or *16 (BC3, BC5) bytes
+ *   texels  device, w*h*C bytes (C as for the encoder), written
  */
 ntbc_status bc_decode(int fmt, const uint8_t* blocks, int w, int h,
                       uint8_t* texels, void* stream);
@@ -228,6 +239,15 @@ ntbc_status ntbc_model_load(ntbc_model* model, const uint8_t* blob, size_t size,
  *   blocks_out  host array of n_textures DEVICE pointers, each (w/4)*(h/4)*8 bytes
  */
 ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out, void* stream);
+
+/*
+ * The same with a block stride per texture: block b of texture t is written at
+ * blocks_out[t] + b * block_stride[t] (a positive multiple of 8; NULL means 8 for all). With
+ * stride 16 two textures of the model fill one 16-byte-block texture: a BC4 alpha texture
+ * at offset 0 and a BC1 colour texture at offset 8 make BC3; two BC4 textures make BC5.
+ */
+ntbc_status ntbc_infer_to_bc_strided(const ntbc_model* model, uint8_t* const* blocks_out,
+                                     const int* block_stride, void* stream);
 
 /*
  * Raw network outputs (pre-quantisation) of the exported model at given blocks:

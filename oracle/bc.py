@@ -45,6 +45,12 @@ import numpy as np
 
 BC1 = 1
 BC4 = 4
+# Compositions (Sec. 2.1: BC2, BC3 and BC5 combine BC1 and BC4), 16-byte blocks:
+#   BC3 (RGBA8 texels): bytes 0-7 the alpha channel as a BC4 block, bytes 8-15 the colour as
+#       a BC1 block that always decodes with the four-colour palette;
+#   BC5 (two-channel texels): bytes 0-7 channel 0 as a BC4 block, bytes 8-15 channel 1.
+BC3 = 3
+BC5 = 5
 
 # paper's linear index n (increasing weight w_n) -> hardware code
 LINEAR_TO_CODE_BC1 = np.array([0, 2, 3, 1])
@@ -57,6 +63,10 @@ def channels(fmt):
         return 3
     if fmt == BC4:
         return 1
+    if fmt == BC3:
+        return 4
+    if fmt == BC5:
+        return 2
     raise ValueError(f"unsupported format {fmt}")
 
 
@@ -110,6 +120,14 @@ def bc1_palette(c0, c1):
     p2 = np.where(four, (2 * e0 + e1 + 1) // 3, (e0 + e1 + 1) // 2)
     p3 = np.where(four, (e0 + 2 * e1 + 1) // 3, 0)
     return np.stack([e0, e1, p2, p3], axis=-2)
+
+
+def bc1_palette4(c0, c1):
+    """Four-colour palette whatever the endpoint order (the colour block of BC3)."""
+    c0 = np.asarray(c0, np.int64)
+    c1 = np.asarray(c1, np.int64)
+    e0, e1 = expand565(c0), expand565(c1)
+    return np.stack([e0, e1, (2 * e0 + e1 + 1) // 3, (e0 + 2 * e1 + 1) // 3], axis=-2)
 
 
 def bc4_palette(r0, r1):
@@ -190,7 +208,16 @@ def bc4_unpack(blocks):
 # ----------------------------------------------------------------------------
 
 def decode(fmt, blocks, w, h):
-    """Compressed blocks -> H x W x 3 (BC1) or H x W (BC4) uint8."""
+    """Compressed blocks -> H x W x 3 (BC1), H x W (BC4), H x W x 4 (BC3), H x W x 2 (BC5) uint8."""
+    if fmt in (BC3, BC5):
+        b16 = np.asarray(blocks, np.uint8).reshape(-1, 16)
+        first = decode(BC4, b16[:, :8], w, h)
+        if fmt == BC5:
+            return np.stack([first, decode(BC4, b16[:, 8:], w, h)], axis=-1)
+        c0, c1, codes = bc1_unpack(b16[:, 8:])
+        pal = bc1_palette4(c0, c1)
+        rgb = from_blocks(np.take_along_axis(pal, codes[..., None].repeat(3, -1), axis=1), w, h).astype(np.uint8)
+        return np.concatenate([rgb, first[..., None]], axis=-1)
     blocks = np.asarray(blocks, np.uint8).reshape(-1, 8)
     if blocks.shape[0] != (w // 4) * (h // 4):
         raise ValueError("block count does not match the texture size")
@@ -299,7 +326,15 @@ def bc4_encode_blocks(x):
 
 
 def encode(fmt, tex, w, h):
-    """Reference BC encode of a whole texture -> [(w/4)*(h/4), 8] uint8."""
+    """Reference BC encode of a whole texture -> [(w/4)*(h/4), 8] uint8 (BC1, BC4) or
+    [(w/4)*(h/4), 16] (BC3: alpha by the BC4 encoder, colour by the BC1 encoder, whose
+    blocks already have colour0 >= colour1; BC5: one BC4 block per channel)."""
+    if fmt == BC3:
+        t = np.asarray(tex)
+        return np.concatenate([encode(BC4, t[..., 3], w, h), encode(BC1, t[..., :3], w, h)], axis=1)
+    if fmt == BC5:
+        t = np.asarray(tex)
+        return np.concatenate([encode(BC4, t[..., 0], w, h), encode(BC4, t[..., 1], w, h)], axis=1)
     blk = to_blocks(tex, w, h)
     if fmt == BC1:
         return bc1_encode_blocks(blk)

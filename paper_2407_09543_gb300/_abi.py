@@ -8,6 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "libntbc.so")
 
 BC1, BC4 = 1, 4
+BC3, BC5 = 3, 5
 ACT_SELU, ACT_RELU = 0, 1
 PREC_FP32, PREC_FP16, PREC_FP16_FAST, PREC_FP8 = 0, 1, 2, 3
 TRAIN_FP32, TRAIN_BF16 = 0, 1
@@ -112,6 +113,7 @@ _SIGS = {
     "ntbc_model_load": (c_int, [_P, _P, c_size_t, _P]),
     "ntbc_infer_to_bc": (c_int, [_P, ctypes.POINTER(_P), _P]),
     "ntbc_forward": (c_int, [_P, _P, c_int, _P, _P, _P]),
+    "ntbc_infer_to_bc_strided": (c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(c_int), _P]),
     "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, c_int, _P, _P, _P]),
     "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
                                          c_float, _P, _P, _P]),
@@ -238,9 +240,15 @@ class Model:
     def load(self, host_buf, stream=None):
         _check(lib.ntbc_model_load(self.handle, _ptr(host_buf), host_buf.numel(), _stream(stream)))
 
-    def infer_to_bc(self, blocks_out, stream=None):
+    def infer_to_bc(self, blocks_out, stream=None, strides=None):
+        """blocks_out: per texture a device tensor (or an int address) of its first block;
+        strides: optional bytes between blocks per texture (8 or 16; BC3 / BC5 layouts)."""
         arr = (_P * len(blocks_out))(*[_ptr(b) for b in blocks_out])
-        _check(lib.ntbc_infer_to_bc(self.handle, arr, _stream(stream)))
+        if strides is None:
+            _check(lib.ntbc_infer_to_bc(self.handle, arr, _stream(stream)))
+        else:
+            st = (c_int * len(strides))(*strides)
+            _check(lib.ntbc_infer_to_bc_strided(self.handle, arr, st, _stream(stream)))
 
     def forward(self, block_ids, e_hat, c_hat, stream=None):
         _check(lib.ntbc_forward(self.handle, _ptr(block_ids), block_ids.numel(), _ptr(e_hat), _ptr(c_hat),

@@ -58,7 +58,8 @@ ntbc_status device_alloc(void** ptr, size_t bytes, const char* what) {
 }
 
 ntbc_status check_texture_args(int fmt, const void* a, const void* b, int w, int h) {
-    if (fmt != NTBC_BC1 && fmt != NTBC_BC4) return fail(NTBC_EINVAL, "format must be NTBC_BC1 or NTBC_BC4, got %d", fmt);
+    if (fmt != NTBC_BC1 && fmt != NTBC_BC4 && fmt != NTBC_BC3 && fmt != NTBC_BC5)
+        return fail(NTBC_EINVAL, "format must be NTBC_BC1, NTBC_BC3, NTBC_BC4 or NTBC_BC5, got %d", fmt);
     if (w <= 0 || h <= 0 || (w & 3) || (h & 3))
         return fail(NTBC_EINVAL, "width and height must be positive multiples of 4, got %dx%d", w, h);
     if ((long long)w * h > (1LL << 30)) return fail(NTBC_EINVAL, "texture too large (%dx%d)", w, h);
@@ -75,7 +76,9 @@ constexpr int kPowerIterations = 8;
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 
-__global__ void bc1_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, uint8_t* __restrict__ out) {
+// texels: ts bytes per texel, the encoded channel(s) from byte to; blocks bs bytes apart
+__global__ void bc1_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, int ts, int to,
+                                  uint8_t* __restrict__ out, int bs) {
     int bw = w >> 2, bh = h >> 2;
     long long nb = (long long)bw * bh;
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,7 +87,7 @@ __global__ void bc1_encode_kernel(const uint8_t* __restrict__ tex, int w, int h,
     int x[16][3];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const uint8_t* p = tex + ((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * 3;
+        const uint8_t* p = tex + ((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * ts + to;
         x[i][0] = p[0];
         x[i][1] = p[1];
         x[i][2] = p[2];
@@ -177,7 +180,7 @@ __global__ void bc1_encode_kernel(const uint8_t* __restrict__ tex, int w, int h,
             idx |= (uint32_t)best << (2 * i);
         }
     }
-    store_block(out + b * 8, c0 | (c1 << 16), idx);
+    store_block(out + b * bs, c0 | (c1 << 16), idx);
 }
 
 __device__ __forceinline__ void bc4_codes(const int x[16], int r0, int r1, uint64_t& idx, int& sse) {
@@ -201,7 +204,8 @@ __device__ __forceinline__ void bc4_codes(const int x[16], int r0, int r1, uint6
     }
 }
 
-__global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, uint8_t* __restrict__ out) {
+__global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, int ts, int to,
+                                  uint8_t* __restrict__ out, int bs) {
     int bw = w >> 2, bh = h >> 2;
     long long nb = (long long)bw * bh;
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -211,7 +215,7 @@ __global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h,
     int mx = 0, mn = 255, lo = 256, hi = -1;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        x[i] = tex[(long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)];
+        x[i] = tex[((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * ts + to];
         mx = max(mx, x[i]);
         mn = min(mn, x[i]);
         if (x[i] != 0 && x[i] != 255) {
@@ -245,27 +249,44 @@ __global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h,
     }
     uint32_t wlo = (uint32_t)r0 | ((uint32_t)r1 << 8) | (uint32_t)((idx & 0xFFFF) << 16);
     uint32_t whi = (uint32_t)(idx >> 16);
-    store_block(out + b * 8, wlo, whi);
+    store_block(out + b * bs, wlo, whi);
 }
 
 // ---------------------------------------------------------------------------
 // decoder: one thread per block, 16 texels written
 // ---------------------------------------------------------------------------
 
-__global__ void bc_decode_kernel(int fmt, const uint8_t* __restrict__ blocks, int w, int h, uint8_t* __restrict__ tex) {
+// blocks bs bytes apart; texels ts bytes apart, channel(s) from byte to. four: the BC1
+// colour block always uses the four-colour palette (the colour block of BC3).
+__global__ void bc_decode_kernel(int fmt, const uint8_t* __restrict__ blocks, int bs, int w, int h,
+                                 uint8_t* __restrict__ tex, int ts, int to, int four) {
     int bw = w >> 2, bh = h >> 2;
     long long nb = (long long)bw * bh;
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     int bx = (int)(b % bw), by = (int)(b / bw);
-    uint2 blk = *reinterpret_cast<const uint2*>(blocks + b * 8);
+    uint2 blk = *reinterpret_cast<const uint2*>(blocks + b * bs);
     if (fmt == NTBC_BC1) {
         int pal[4][3];
-        bc1_palette(blk.x & 0xFFFF, blk.x >> 16, pal);
+        uint32_t c0 = blk.x & 0xFFFF, c1 = blk.x >> 16;
+        if (four && c0 <= c1) {                  // interpolants at 1/3 and 2/3 whatever the order
+            int e0[3], e1[3];
+            expand565(c0, e0[0], e0[1], e0[2]);
+            expand565(c1, e1[0], e1[1], e1[2]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                pal[0][c] = e0[c];
+                pal[1][c] = e1[c];
+                pal[2][c] = (2 * e0[c] + e1[c] + 1) / 3;
+                pal[3][c] = (e0[c] + 2 * e1[c] + 1) / 3;
+            }
+        } else {
+            bc1_palette(c0, c1, pal);
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             int code = (blk.y >> (2 * i)) & 3;
-            uint8_t* p = tex + ((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * 3;
+            uint8_t* p = tex + ((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * ts + to;
             p[0] = (uint8_t)pal[code][0];
             p[1] = (uint8_t)pal[code][1];
             p[2] = (uint8_t)pal[code][2];
@@ -277,7 +298,7 @@ __global__ void bc_decode_kernel(int fmt, const uint8_t* __restrict__ blocks, in
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             int code = (int)((idx >> (3 * i)) & 7);
-            tex[(long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)] = (uint8_t)pal[code];
+            tex[((long long)(4 * by + (i >> 2)) * w + 4 * bx + (i & 3)) * ts + to] = (uint8_t)pal[code];
         }
     }
 }
@@ -330,10 +351,17 @@ ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h, ui
     int threads = 128;
     unsigned grid = (unsigned)((nb + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
-    if (fmt == NTBC_BC1)
-        bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, blocks);
-    else
-        bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, blocks);
+    switch (fmt) {
+        case NTBC_BC1: bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 3, 0, blocks, 8); break;
+        case NTBC_BC4: bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 1, 0, blocks, 8); break;
+        case NTBC_BC3:   // alpha (byte 3 of RGBA) as BC4, then the colour as BC1
+            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 4, 3, blocks, 16);
+            bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 4, 0, blocks + 8, 16);
+            break;
+        default:         // BC5: one BC4 block per channel
+            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 2, 0, blocks, 16);
+            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 2, 1, blocks + 8, 16);
+    }
     NTBC_CHECK_LAUNCH("bc_reference_encode");
     return NTBC_OK;
 }
@@ -345,7 +373,18 @@ ntbc_status bc_decode(int fmt, const uint8_t* blocks, int w, int h, uint8_t* tex
     long long nb = (long long)(w / 4) * (h / 4);
     int threads = 128;
     unsigned grid = (unsigned)((nb + threads - 1) / threads);
-    bc_decode_kernel<<<grid, threads, 0, (cudaStream_t)stream>>>(fmt, blocks, w, h, texels);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (fmt) {
+        case NTBC_BC1: bc_decode_kernel<<<grid, threads, 0, s>>>(NTBC_BC1, blocks, 8, w, h, texels, 3, 0, 0); break;
+        case NTBC_BC4: bc_decode_kernel<<<grid, threads, 0, s>>>(NTBC_BC4, blocks, 8, w, h, texels, 1, 0, 0); break;
+        case NTBC_BC3:
+            bc_decode_kernel<<<grid, threads, 0, s>>>(NTBC_BC4, blocks, 16, w, h, texels, 4, 3, 0);
+            bc_decode_kernel<<<grid, threads, 0, s>>>(NTBC_BC1, blocks + 8, 16, w, h, texels, 4, 0, 1);
+            break;
+        default:
+            bc_decode_kernel<<<grid, threads, 0, s>>>(NTBC_BC4, blocks, 16, w, h, texels, 2, 0, 0);
+            bc_decode_kernel<<<grid, threads, 0, s>>>(NTBC_BC4, blocks + 8, 16, w, h, texels, 2, 1, 0);
+    }
     NTBC_CHECK_LAUNCH("bc_decode");
     return NTBC_OK;
 }

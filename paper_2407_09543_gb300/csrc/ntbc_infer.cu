@@ -104,6 +104,7 @@ __device__ void mlp_eval(const NetView& nv, const WeightImage& wi, const float* 
 
 struct OutPtrs {
     uint8_t* p[NTBC_MAX_TEXTURES];
+    int stride[NTBC_MAX_TEXTURES];     // bytes between consecutive blocks of a texture
 };
 
 // MODE_PACK: write BC blocks; MODE_RAW: write e_hat / c_hat of the listed blocks
@@ -218,7 +219,7 @@ infer_simt_kernel(ModelView mv, const float* __restrict__ params, GridSrc csrc, 
         for (int t = 0; t < NTBC_MAX_TEXTURES; ++t) {
             if (t >= mv.n_textures) break;
             uint32_t ep = epbase[t * stride + tid];
-            uint8_t* dst = outs.p[t] + (long long)b * 8;
+            uint8_t* dst = outs.p[t] + (long long)b * outs.stride[t];
             if (mv.formats[t] == NTBC_BC1) {
                 store_block(dst, ep, (uint32_t)idx[t]);       // equal colours carry all-zero codes
             } else {
@@ -275,7 +276,8 @@ using namespace ntbc;
 
 extern "C" {
 
-ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, void* stream) {
+ntbc_status ntbc_infer_to_bc_strided(const ntbc_model* m, uint8_t* const* blocks_out, const int* block_stride,
+                                     void* stream) {
     clear_error();
     if (!m || !blocks_out) return fail(NTBC_EINVAL, "null argument");
     OutPtrs outs;
@@ -284,15 +286,22 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, vo
         if (!blocks_out[t]) return fail(NTBC_EINVAL, "null output pointer for texture %d", t);
         if (reinterpret_cast<uintptr_t>(blocks_out[t]) & 7) return fail(NTBC_EINVAL, "output %d not 8-byte aligned", t);
         outs.p[t] = blocks_out[t];
+        outs.stride[t] = block_stride ? block_stride[t] : 8;
+        if (outs.stride[t] < 8 || (outs.stride[t] & 7))
+            return fail(NTBC_EINVAL, "block stride of texture %d must be a positive multiple of 8, got %d", t, outs.stride[t]);
     }
     int n = (m->desc.width / 4) * (m->desc.height / 4);
     if (m->weight_prec != NTBC_PREC_FP32) {
         GridSrc csrc, esrc;
         ntbc_status st = grid_sources(m, csrc, esrc);
         if (st != NTBC_OK) return st;
-        return tc_launch(m, blocks_out, nullptr, n, nullptr, nullptr, csrc, esrc, (cudaStream_t)stream);
+        return tc_launch(m, blocks_out, outs.stride, nullptr, n, nullptr, nullptr, csrc, esrc, (cudaStream_t)stream);
     }
     return launch_simt<MODE_PACK>(m, outs, nullptr, n, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, void* stream) {
+    return ntbc_infer_to_bc_strided(m, blocks_out, nullptr, stream);
 }
 
 ntbc_status ntbc_forward(const ntbc_model* m, const int32_t* block_ids, int n, float* e_hat, float* c_hat, void* stream) {
@@ -305,7 +314,7 @@ ntbc_status ntbc_forward(const ntbc_model* m, const int32_t* block_ids, int n, f
         GridSrc csrc, esrc;
         ntbc_status st = grid_sources(m, csrc, esrc);
         if (st != NTBC_OK) return st;
-        return tc_launch(m, nullptr, block_ids, n, e_hat, c_hat, csrc, esrc, (cudaStream_t)stream);
+        return tc_launch(m, nullptr, nullptr, block_ids, n, e_hat, c_hat, csrc, esrc, (cudaStream_t)stream);
     }
     OutPtrs outs;
     memset(&outs, 0, sizeof(outs));

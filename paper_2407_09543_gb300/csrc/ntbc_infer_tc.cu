@@ -121,6 +121,7 @@ __device__ __forceinline__ void block_xy(int b, int bw, float inv_bw, int& bx, i
 
 struct TcOut {
     uint8_t* p[NTBC_MAX_TEXTURES];
+    int stride[NTBC_MAX_TEXTURES];     // bytes between consecutive blocks of a texture
 };
 
 struct TcSmem {
@@ -570,7 +571,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                         for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
                     }
                     if (i == 0 && valid) {
-                        uint8_t* dst = outs.p[t] + (long long)b * 8;
+                        uint8_t* dst = outs.p[t] + (long long)b * outs.stride[t];
                         if (mv.formats[t] == NTBC_BC1)
                             store_block(dst, ep, (uint32_t)bits);
                         else
@@ -760,8 +761,8 @@ ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s) {
     return NTBC_OK;
 }
 
-ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int32_t* ids, int n, float* e_out,
-                      float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
+ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
+                      float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
     TcArgs a = tc_args(m);
     size_t smem = 0;
     const bool split = m->weight_prec != NTBC_PREC_FP16_FAST;     // FP16 and FP8 weights
@@ -774,7 +775,10 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
     TcOut outs;
     memset(&outs, 0, sizeof(outs));
     if (blocks_out)
-        for (int t = 0; t < m->desc.n_textures; ++t) outs.p[t] = blocks_out[t];
+        for (int t = 0; t < m->desc.n_textures; ++t) {
+            outs.p[t] = blocks_out[t];
+            outs.stride[t] = strides ? strides[t] : 8;
+        }
     int dev = 0, sms = 0;
     NTBC_CHECK_CUDA(cudaGetDevice(&dev));
     NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -846,6 +850,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
             uint8_t* o = blocks_out[i][k];
             if (!o || (reinterpret_cast<uintptr_t>(o) & 7)) return fail(NTBC_EINVAL, "material %d texture %d: output null or not 8-byte aligned", i, k);
             t.outs.p[k] = o;
+            t.outs.stride[k] = 8;
         }
         t.units = (t.args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
         max_tex = std::max(max_tex, m->desc.n_textures);

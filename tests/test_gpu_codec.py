@@ -101,3 +101,32 @@ def test_invalid_arguments_launch_nothing():
         nt.bc_reference_encode(1, torch.zeros(30, dtype=torch.uint8, device=DEV), 10, 1,
                                torch.zeros(8, dtype=torch.uint8, device=DEV))
     assert ei.value.status == 1
+
+
+# ----------------------------------------------------------------------------
+# BC3 / BC5: compositions of BC1 and BC4 (16-byte blocks)
+# ----------------------------------------------------------------------------
+
+def _comp_texture(fmt, w, h, seed):
+    mat = synth.make_material("comp", max(w, h), ["sine_rgb", "sine_r", "sine_r"], seed)
+    if fmt == nt.BC3:
+        return np.concatenate([mat.textures[0][:h, :w], mat.textures[1][:h, :w, None]], axis=-1)
+    return np.stack([mat.textures[1][:h, :w], mat.textures[2][:h, :w]], axis=-1)
+
+
+@pytest.mark.parametrize("fmt", [3, 5])
+def test_composed_formats_encode_and_decode_bit_exact(fmt):
+    w, h = 72, 40
+    tex = np.ascontiguousarray(_comp_texture(fmt, w, h, 5))
+    blocks = torch.empty((w // 4) * (h // 4) * 16, dtype=torch.uint8, device=DEV)
+    nt.bc_reference_encode(fmt, _dev(tex), w, h, blocks)
+    torch.cuda.synchronize()
+    got = blocks.cpu().numpy().reshape(-1, 16)
+    np.testing.assert_array_equal(got, obc.encode(fmt, tex, w, h))
+    # decode random blocks too (BC3 colour blocks with colour0 <= colour1 included)
+    rnd = np.random.default_rng(7).integers(0, 256, got.shape, dtype=np.uint8)
+    for b in (got, rnd):
+        out = torch.empty(w * h * tex.shape[-1], dtype=torch.uint8, device=DEV)
+        nt.bc_decode(fmt, _dev(b), w, h, out)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy().reshape(h, w, -1), obc.decode(fmt, b, w, h))

@@ -304,3 +304,27 @@ def test_trained_weights_parity_all_modes(bits):
         np.testing.assert_allclose(c, cr, rtol=rtol, atol=1e-6)
         ref = ont.infer_blocks(odesc, pw, color_grid=deq[:nc], endpoint_grid=deq[nc:])
         check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ref, mism)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_strided_outputs_make_bc3_and_bc5(prec):
+    # textures [BC1 colour, BC4 alpha, BC4 r, BC4 g]: (alpha, colour) -> one BC3 texture,
+    # (r, g) -> one BC5 texture, the same blocks as the unstrided outputs interleaved
+    mat, desc, odesc, params = make_case(side=64, kinds=("sine_rgb", "sine_r", "sine_r", "sine_r"), levels=3)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=prec)
+    plain = gpu_blocks(model, desc)
+    n = (desc.width // 4) * (desc.height // 4)
+    bc3 = torch.zeros(n * 16, dtype=torch.uint8, device=DEV)
+    bc5 = torch.zeros(n * 16, dtype=torch.uint8, device=DEV)
+    model.infer_to_bc([bc3.data_ptr() + 8, bc3.data_ptr(), bc5.data_ptr(), bc5.data_ptr() + 8],
+                      strides=[16, 16, 16, 16])
+    torch.cuda.synchronize()
+    b3 = bc3.cpu().numpy().reshape(-1, 16)
+    b5 = bc5.cpu().numpy().reshape(-1, 16)
+    np.testing.assert_array_equal(b3[:, :8], plain[1])
+    np.testing.assert_array_equal(b3[:, 8:], plain[0])
+    np.testing.assert_array_equal(b5[:, :8], plain[2])
+    np.testing.assert_array_equal(b5[:, 8:], plain[3])
+    # the BC3 decode of the composed blocks equals the parts' decodes
+    dec = obc.decode(obc.BC3, b3, desc.width, desc.height)
+    np.testing.assert_array_equal(dec[..., 3], obc.decode(obc.BC4, plain[1], desc.width, desc.height))

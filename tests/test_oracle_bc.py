@@ -208,3 +208,50 @@ def test_linear_to_code_maps_follow_weights():
     p = bc.bc1_palette(np.array([c0]), np.array([c1]))[0]
     lin1 = p[bc.LINEAR_TO_CODE_BC1]
     assert (np.diff(lin1[:, 0]) < 0).all() and (np.diff(lin1[:, 2]) > 0).all()
+
+
+# ----------------------------------------------------------------------------
+# BC3 / BC5 (compositions of BC1 and BC4, Sec. 2.1)
+# ----------------------------------------------------------------------------
+
+def test_bc5_is_two_bc4_blocks():
+    rng = np.random.default_rng(11)
+    tex = rng.integers(0, 256, (16, 24, 2), dtype=np.uint8)
+    blocks = bc.encode(bc.BC5, tex, 24, 16)
+    assert blocks.shape == (24, 16)
+    for k in range(2):
+        np.testing.assert_array_equal(blocks[:, 8 * k:8 * k + 8], bc.encode(bc.BC4, tex[..., k], 24, 16))
+    dec = bc.decode(bc.BC5, blocks, 24, 16)
+    for k in range(2):
+        np.testing.assert_array_equal(dec[..., k], bc.decode(bc.BC4, blocks[:, 8 * k:8 * k + 8], 24, 16))
+
+
+def test_bc3_colour_block_decodes_in_four_colour_mode():
+    # the four-colour palette is symmetric: swapping the endpoints and the codes 0<->1, 2<->3
+    # gives the same texels -- which the three-colour mode (c0 <= c1 in BC1) would break
+    rng = np.random.default_rng(12)
+    n = 64
+    c0 = rng.integers(0, 1 << 16, n)
+    c1 = rng.integers(0, 1 << 16, n)
+    codes = rng.integers(0, 4, (n, 16))
+    alpha = bc.bc4_pack(rng.integers(0, 256, n), rng.integers(0, 256, n), rng.integers(0, 8, (n, 16)))
+    swap = np.array([1, 0, 3, 2])
+    a = np.concatenate([alpha, bc.bc1_pack(c0, c1, codes)], axis=1)
+    b = np.concatenate([alpha, bc.bc1_pack(c1, c0, swap[codes])], axis=1)
+    da, db = bc.decode(bc.BC3, a, 32, 32), bc.decode(bc.BC3, b, 32, 32)
+    np.testing.assert_array_equal(da, db)
+    three = (c0 <= c1) & (c0 != c1)
+    assert three.any()
+    # the same colour blocks read as BC1 differ wherever BC1 would use its three-colour mode
+    d1 = bc.decode(bc.BC1, bc.bc1_pack(c0, c1, codes), 32, 32)
+    assert not np.array_equal(d1, da[..., :3])
+
+
+def test_bc3_round_trip_alpha_and_colour():
+    rng = np.random.default_rng(13)
+    tex = rng.integers(0, 256, (8, 8, 4), dtype=np.uint8)
+    tex[..., 3] = 200                                            # solid alpha is exact
+    blocks = bc.encode(bc.BC3, tex, 8, 8)
+    dec = bc.decode(bc.BC3, blocks, 8, 8)
+    assert np.all(dec[..., 3] == 200)
+    np.testing.assert_array_equal(dec[..., :3], bc.decode(bc.BC1, blocks[:, 8:], 8, 8))
