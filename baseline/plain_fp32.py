@@ -99,6 +99,17 @@ def _expand565(c):
     return torch.stack([(r5 << 3) | (r5 >> 2), (g6 << 2) | (g6 >> 4), (b5 << 3) | (b5 >> 2)], -1)
 
 
+def reference_endpoints(fmt, blocks):
+    """Decoded endpoints of stored blocks in [0, 1], stored order: BC1 [n, 6], BC4 [n, 2]
+    (blocks: uint8 tensor [n, 8]); the L_e targets."""
+    b = blocks.reshape(-1, 8).long()
+    if fmt == BC1:
+        c0 = b[:, 0] | (b[:, 1] << 8)
+        c1 = b[:, 2] | (b[:, 3] << 8)
+        return torch.cat([_expand565(c0), _expand565(c1)], 1).float() / 255.0
+    return torch.stack([b[:, 0], b[:, 1]], 1).float() / 255.0
+
+
 def _quant(e, levels):
     return torch.clamp(torch.floor(e * levels + 0.5), 0, levels).long()
 

@@ -58,8 +58,6 @@ def parse():
     ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16; 3: FP8 E4M3 weights, split activations")
     ap.add_argument("--batch", action="store_true",
                     help="batched load-time inference: 16 uneven materials in one persistent launch (CUDA graph)")
-    ap.add_argument("--sweep", action="store_true",
-                    help="precision sweep: u8 / u4 QAT grids x FP32 / FP16 split / FP16 fast MLP inference")
     ap.add_argument("--quick", action="store_true",
                     help="inference only on random-init weights (no material, training, plain path or oracle)")
     return ap.parse_args()
@@ -177,11 +175,18 @@ def time_events(torch, fn, iters, flush=None, stream=None):
     return times
 
 
-def psnr_list(nt, obc, torch, mat, blocks, side):
+def psnr_list(nt, torch, mat, blocks, side):
+    """Decoded PSNR per texture (Sec. 4.1: 10 log10(1 / MSE) over all channels in [0, 1]):
+    the blocks decoded by the library's GPU decoder, compared with the source texels."""
     out = []
+    dev = torch.device("cuda", torch.cuda.current_device())
     for t, fmt in enumerate(mat.formats):
-        b = blocks[t].cpu().numpy().reshape(-1, 8)
-        out.append(round(obc.psnr(obc.decode(fmt, b, side, side), mat.textures[t]), 3))
+        src = torch.from_numpy(np.ascontiguousarray(mat.textures[t]).ravel()).to(dev)
+        dec = torch.empty_like(src)
+        b = torch.as_tensor(blocks[t]).reshape(-1).to(dev)          # host results are copied over first
+        nt.bc_decode(fmt, b, side, side, dec)
+        mse = float(((dec.double() - src.double()) / 255.0).pow(2).mean())
+        out.append(round(float("inf") if mse == 0 else 10.0 * float(np.log10(1.0 / mse)), 3))
     return out
 
 
@@ -304,80 +309,6 @@ def inference_roofline(nt, desc, ms):
     return roofline, terms
 
 
-def run_sweep(args):
-    """Inference precision sweep on trained 4k weights (one encode per grid width)."""
-    import torch
-    import paper_2407_09543_gb300 as nt
-    from oracle import bc as obc, ntbc as ont
-    dev = torch.device("cuda", 0)
-    side = args.side
-    nblk = (side // 4) ** 2
-    mat, desc, p0, tex_d, refs = build_workload(nt, torch, side, seed=0, dev=dev)
-    for t, fmt in enumerate(mat.formats):
-        nt.bc_reference_encode(fmt, tex_d[t], side, side, refs[t])
-    torch.cuda.synchronize()
-    ref_psnr = psnr_list(nt, obc, torch, mat, refs, side)
-    material = nt.Material.make(side, side, mat.formats, tex_d, refs)
-    cres, eres = nt.configs.res_lists(desc)
-    od = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=desc.hidden_layers, activation="selu")
-    ids = np.sort(np.random.default_rng(0).choice(nblk, 2000, replace=False))
-    rows = []
-    for bits in (8, 4):
-        model = nt.Model(desc)
-        model.set_params(torch.from_numpy(nt.configs.flatten(desc, p0)).to(dev))
-        model.train(material, nt.TrainConfig.make(steps=args.train_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1,
-                                                  grid_bits=bits, seed=0, precision=nt.TRAIN_BF16))
-        flat = torch.empty(model.n_params, device=dev)
-        model.get_params(flat)
-        params = nt.configs.unflatten(desc, flat.cpu().numpy())
-        codes, sc, zr = ont.export_grid(params["color_grid"] + params["endpoint_grid"], bits)
-        deq = ont.dequantize_grid(codes, sc, zr)
-        nc = desc.color_levels
-        # the FP64 network on the FP32 master weights: what each stored precision gives up
-        er32, cr32 = ont.forward_blocks(od, params, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
-        for name, prec in (("fp32", nt.PREC_FP32), ("fp16", nt.PREC_FP16), ("fp16_fast", nt.PREC_FP16_FAST),
-                           ("fp8_e4m3", nt.PREC_FP8)):
-            model.export(grid_bits=bits, weight_prec=prec)
-            if prec == nt.PREC_FP8:
-                pw = ont.fp8_params(params)[0]
-            else:
-                pw = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
-                for k in ("color_mlp", "endpoint_mlp"):
-                    pw[k] = [((W.astype(np.float16) if prec else W).astype(np.float64),
-                              (b.astype(np.float16) if prec else b).astype(np.float64)) for W, b in params[k]]
-            er, cr = ont.forward_blocks(od, pw, ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
-            idt = torch.from_numpy(ids.astype(np.int32)).to(dev)
-            lay = model.layout
-            e = torch.empty(len(ids), lay.out_endpoint, device=dev)
-            c = torch.empty(len(ids), 16, lay.out_color, device=dev)
-            model.forward(idt, e, c)
-            outs = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in mat.formats]
-            model.infer_to_bc(outs)
-            torch.cuda.synchronize()
-            eg, cg = e.cpu().numpy(), c.cpu().numpy()
-            rel = max(float(np.max(np.abs(eg - er) / np.abs(er))), float(np.max(np.abs(cg - cr) / np.abs(cr))))
-            rel32 = max(float(np.max(np.abs(eg - er32) / np.abs(er32))), float(np.max(np.abs(cg - cr32) / np.abs(cr32))))
-            ref_blocks = ont.infer_blocks(od, pw, block_ids=ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
-            mism = fields = 0
-            for t, fmt in enumerate(mat.formats):
-                got = outs[t].cpu().numpy().reshape(-1, 8)[ids]
-                unpack = obc.bc1_unpack if fmt == 1 else obc.bc4_unpack
-                a0, a1, ac = unpack(got)
-                b0, b1, bc_ = unpack(ref_blocks[t])
-                mism += int((a0 != b0).sum() + (a1 != b1).sum() + (ac != bc_).sum())
-                fields += len(ids) * 18
-            rows.append({"grid_bits": bits, "mlp": name, "max_rel_err_vs_fp64": rel,
-                         "max_rel_err_vs_fp64_fp32_weights": rel32,
-                         "field_mismatch": mism / fields, "psnr_db": psnr_list(nt, obc, torch, mat, outs, side)})
-        model.close()
-    print(json.dumps({"mode": "sweep", "workload": f"mat4k {side}x{side}", "train_steps": args.train_steps,
-                      "reference_bc_psnr_db": ref_psnr, "rows": rows}), flush=True)
-    return 0
-
-
-KIND_FORMAT = {"diffuse": 1, "normal": 1, "roughness": 4, "ao": 4}
-
-
 def run_batch(args):
     """16 materials of uneven size (sides 512..4096, 2..5 textures), each with its own
     12-level grid (16 .. side/2) and 3 x 64 SELU MLPs, random-init weights, decoded to BC
@@ -464,14 +395,10 @@ def main():
         return run_reference(args)
     if args.quick:
         return run_quick(args)
-    if args.sweep:
-        return run_sweep(args)
     if args.batch:
         return run_batch(args)
     import torch
     import paper_2407_09543_gb300 as nt
-    from oracle import bc as obc
-
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -492,7 +419,7 @@ def main():
     torch.cuda.synchronize()
     ref_ms = time_events(torch, lambda: [nt.bc_reference_encode(f, tex_d[t], side, side, refs[t])
                                          for t, f in enumerate(mat.formats)], 3)
-    ref_psnr = psnr_list(nt, obc, torch, mat, refs, side)
+    ref_psnr = psnr_list(nt, torch, mat, refs, side)
 
     # ---- encode (training) on the GPU: measured steps, full schedule extrapolated
     model = nt.Model(desc)
@@ -501,7 +428,7 @@ def main():
     model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
     untrained = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in FORMATS]
     model.infer_to_bc(untrained)
-    untrained_psnr = psnr_list(nt, obc, torch, mat, untrained, side)
+    untrained_psnr = psnr_list(nt, torch, mat, untrained, side)
     material = nt.Material.make(side, side, mat.formats, tex_d, refs)
     main_steps = args.train_steps
     total_steps = main_steps + int(np.ceil(0.1 * main_steps))
@@ -529,7 +456,7 @@ def main():
         o32 = [torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in FORMATS]
         m32.infer_to_bc(o32)
         fp32_encode = {"measured_s": round(t32, 2), "ms_per_step": round(1e3 * t32 / total_steps, 3),
-                       "psnr_db": psnr_list(nt, obc, torch, mat, o32, side)}
+                       "psnr_db": psnr_list(nt, torch, mat, o32, side)}
         m32.close()
         del o32
 
@@ -558,7 +485,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     ms = max_over_ranks(float(np.mean(times)), world, dev)
-    ours_psnr = psnr_list(nt, obc, torch, mat, outs, side)
+    ours_psnr = psnr_list(nt, torch, mat, outs, side)
     value = job_throughput(tex_blocks, world, ms)
 
     # ---- end to end through the C ABI with host buffers: blob H2D, infer, blocks D2H
@@ -579,7 +506,7 @@ def main():
     e2e_times = time_events(torch, e2e, args.steps, flush=flush)
     e2e_ms = max_over_ranks(float(np.mean(e2e_times)), world, dev)
     e2e_value = job_throughput(tex_blocks, world, e2e_ms)
-    e2e_psnr = psnr_list(nt, obc, torch, mat, host_out, side)
+    e2e_psnr = psnr_list(nt, torch, mat, host_out, side)
 
     # ---- roofline of the inference kernel (algorithmic counts per block position)
     roofline, terms = inference_roofline(nt, desc, ms)
@@ -593,7 +520,7 @@ def main():
         torch.cuda.synchronize()
         t_m = float(np.mean(time_events(torch, infer, max(3, args.steps // 4), flush=flush)))
         modes[name] = {"ms": round(t_m, 4), "value": round(tex_blocks / (t_m * 1e-3) / 1e6, 3),
-                       "psnr_db": psnr_list(nt, obc, torch, mat, outs, side)}
+                       "psnr_db": psnr_list(nt, torch, mat, outs, side)}
     model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
     # the roughness and AO textures written as one BC5 texture (16-byte blocks, interleaved)
     bc5 = torch.empty(nblk * 16, dtype=torch.uint8, device=dev)
@@ -644,7 +571,7 @@ def main():
         conservative = {"models": len(groups), "textures_per_model": [len(g) for g in groups],
                         "encode_s_measured": round(c_train_s, 2), "infer_ms": round(c_ms, 4),
                         "infer_value": round(tex_blocks / (c_ms * 1e-3) / 1e6, 3), "unit": "Mblocks/s",
-                        "psnr_db": psnr_list(nt, obc, torch, mat, by_tex, side),
+                        "psnr_db": psnr_list(nt, torch, mat, by_tex, side),
                         "storage_bytes": int(c_bytes), "aggressive_storage_bytes": int(model.blob_size())}
         c_batch.close()
         for mc in c_models:
@@ -671,10 +598,9 @@ def main():
         p_times = time_events(torch, lambda: pf.infer_to_bc(pm, grids=grids), 2, flush=flush)
         p_ms = float(np.mean(p_times))
         p_outs = pf.infer_to_bc(pm, grids=grids)
-        plain_psnr = psnr_list(nt, obc, torch, mat, [o.reshape(-1) for o in p_outs], side)
+        plain_psnr = psnr_list(nt, torch, mat, [o.reshape(-1) for o in p_outs], side)
         # training step of the plain path
-        ref_e = [torch.from_numpy(obc.reference_endpoints(f, r.cpu().numpy().reshape(-1, 8))).float().to(dev)
-                 for f, r in zip(mat.formats, refs)]
+        ref_e = [pf.reference_endpoints(f, r) for f, r in zip(mat.formats, refs)]
         texs = [torch.from_numpy(t).to(dev) for t in mat.textures]
         trainer = pf.PlainTrainer(pm, FULL_MAIN_STEPS + FULL_QAT_STEPS)
         ids = torch.randint(0, nblk, (BATCH_TEXELS // 16,), device=dev)
