@@ -175,6 +175,38 @@ def time_events(torch, fn, iters, flush=None, stream=None):
     return times
 
 
+def ssim_gpu(torch, a, b):
+    """Mean SSIM (Wang et al. 2004; Sec. 4.1 reports it beside PSNR) of two H x W x C uint8
+    images on the GPU: 11 x 11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2 on values
+    in [0, 1], valid region only, averaged over the channels."""
+    import torch.nn.functional as F
+    g = torch.exp(-((torch.arange(11, device=a.device, dtype=torch.float64) - 5.0) ** 2) / (2 * 1.5 ** 2))
+    g = g / g.sum()
+    win = (g[:, None] * g[None, :])[None, None]
+    x = a.double().permute(2, 0, 1)[:, None] / 255.0
+    y = b.double().permute(2, 0, 1)[:, None] / 255.0
+    mx, my = F.conv2d(x, win), F.conv2d(y, win)
+    sxx = F.conv2d(x * x, win) - mx * mx
+    syy = F.conv2d(y * y, win) - my * my
+    sxy = F.conv2d(x * y, win) - mx * my
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    m = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+    return float(m.mean(dim=(1, 2, 3)).mean())
+
+
+def ssim_list(nt, torch, mat, blocks, side):
+    """Decoded SSIM per texture (GPU decoder, GPU SSIM)."""
+    out = []
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for t, fmt in enumerate(mat.formats):
+        src = torch.from_numpy(np.ascontiguousarray(mat.textures[t]).ravel()).to(dev)
+        dec = torch.empty_like(src)
+        nt.bc_decode(fmt, torch.as_tensor(blocks[t]).reshape(-1).to(dev), side, side, dec)
+        shape = (side, side, 3 if fmt == 1 else 1)
+        out.append(round(ssim_gpu(torch, dec.reshape(shape), src.reshape(shape)), 4))
+    return out
+
+
 def psnr_list(nt, torch, mat, blocks, side):
     """Decoded PSNR per texture (Sec. 4.1: 10 log10(1 / MSE) over all channels in [0, 1]):
     the blocks decoded by the library's GPU decoder, compared with the source texels."""
@@ -631,6 +663,7 @@ def main():
                                f"3x64 SELU, FP16 weights", "texture_blocks": tex_blocks, "block_positions": nblk,
                    "l2": "flushed (256 MiB write) between timed iterations", "parallelism": f"replicas x{world}"},
         "block_positions_per_s_M": round(nblk * world / (ms * 1e-3) / 1e6, 3),
+        "ssim": {"ntbc": ssim_list(nt, torch, mat, outs, side), "reference_bc": ssim_list(nt, torch, mat, refs, side)},
         "psnr_db": {"ntbc": ours_psnr, "untrained": untrained_psnr, "reference_bc": ref_psnr,
                     "e2e": e2e_psnr, "plain_fp32": plain["psnr_db"] if plain else None},
         "encode": {"precision": "bf16 tensor-core MMA operands, fp32 accumulate / loss / Adam",
