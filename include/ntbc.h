@@ -102,6 +102,17 @@ ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h,
                                 uint8_t* blocks, void* stream);
 
 /*
+ * The same encoder followed by up to `refine` (0..16) least-squares refinement steps, our
+ * reading of the "refine steps" Sec. 4.1 mentions for Compressonator: the endpoints that
+ * minimise the block's squared error for its current codes (closed-form 2x2 normal
+ * equations), re-quantised with round-half-up in exact integer arithmetic, the codes
+ * re-chosen (BC4 keeps its mode), kept while the squared error strictly falls. Bit-exact
+ * with the oracle. refine = 0 is bc_reference_encode.
+ */
+ntbc_status bc_reference_encode_refined(int fmt, const uint8_t* texels, int w, int h, int refine,
+                                        uint8_t* blocks, void* stream);
+
+/*
  * Decoder (the "existing BC decompression" of Sec. 4.4): blocks -> texels with
  * the integer palette (interpolants rounded to nearest; BC1 colour0 <= colour1
  * selects the 3-colour mode, BC4 r0 <= r1 the 6-value mode with 0 and 255).

@@ -325,6 +325,115 @@ def bc4_encode_blocks(x):
     return bc4_pack(r0, r1, codes)
 
 
+# ----------------------------------------------------------------------------
+# optional refinement of the reference encoder (the "refine steps" Sec. 4.1 mentions for
+# Compressonator, whose definition the paper does not give; reading: least-squares
+# endpoints for the current codes, re-quantised, codes re-chosen, kept while the block's
+# squared error strictly falls, at most `iterations` times). All integer arithmetic.
+# ----------------------------------------------------------------------------
+
+BC1_CODE_W3 = np.array([0, 3, 1, 2])                    # code -> weight of e1, in thirds
+BC4_8_CODE_W7 = np.array([0, 7, 1, 2, 3, 4, 5, 6])       # r0 > r1: code -> weight of r1, in sevenths
+BC4_6_CODE_W5 = np.array([0, 5, 1, 2, 3, 4, -1, -1])     # r0 <= r1: in fifths; codes 6, 7 are 0 and 255
+
+
+def ls_endpoints(x, wts, D, use):
+    """Least-squares endpoints for fixed codes: minimise sum_i |x_i - ((D - w_i) a + w_i b) / D|^2
+    over the texels with use_i. x [n, 16, C] int, wts [n, 16] weights in units of 1/D.
+    With A11 = sum (D-w)^2, A12 = sum (D-w) w, A22 = sum w^2, R1 = sum (D-w) x, R2 = sum w x
+    (normal equations times D^2): a = D (A22 R1 - A12 R2) / det, b = D (A11 R2 - A12 R1) / det,
+    det = A11 A22 - A12^2. Returns the integer numerators [n, C] of a and b (without the
+    factor D) and det [n]."""
+    x = np.asarray(x, np.int64)
+    w = np.where(use, np.asarray(wts, np.int64), 0)
+    u = np.where(use, D - w, 0)
+    A11, A12, A22 = (u * u).sum(1), (u * w).sum(1), (w * w).sum(1)
+    R1 = (u[..., None] * x).sum(1)
+    R2 = (w[..., None] * x).sum(1)
+    det = A11 * A22 - A12 * A12
+    return A22[:, None] * R1 - A12[:, None] * R2, A11[:, None] * R2 - A12[:, None] * R1, det
+
+
+def quantise_ls(num, det, D, L):
+    """round-half-up(D num / det * L / 255) clamped to [0, L] (exact integer arithmetic,
+    det > 0; a non-positive numerator gives 0)."""
+    num = np.asarray(num, np.int64)
+    d = np.maximum(det, 1)[..., None] if num.ndim > np.ndim(det) else np.maximum(det, 1)
+    q = (2 * D * num * L + 255 * d) // (510 * d)
+    return np.where(num <= 0, 0, np.minimum(q, L))
+
+
+def bc1_sse(x, c0, c1, codes):
+    pal = bc1_palette(c0, c1)
+    sel = np.take_along_axis(pal, np.asarray(codes, np.int64)[..., None].repeat(3, -1), axis=1)
+    return ((np.asarray(x, np.int64) - sel) ** 2).sum(axis=(1, 2))
+
+
+def bc1_refine(x, blocks, iterations):
+    """x [n, 16, 3] RGB8, blocks [n, 8] -> refined [n, 8]."""
+    x = np.asarray(x, np.int64)
+    c0, c1, codes = bc1_unpack(blocks)
+    sse = bc1_sse(x, c0, c1, codes)
+    for _ in range(iterations):
+        wts = BC1_CODE_W3[codes]
+        na, nb, det = ls_endpoints(x, wts, 3, np.ones_like(codes, bool))
+        ok = det > 0
+        lv = np.array([31, 63, 31])
+        qa = np.stack([quantise_ls(na[:, c], det, 3, lv[c]) for c in range(3)], 1)
+        qb = np.stack([quantise_ls(nb[:, c], det, 3, lv[c]) for c in range(3)], 1)
+        a0, a1 = pack565(qa[:, 0], qa[:, 1], qa[:, 2]), pack565(qb[:, 0], qb[:, 1], qb[:, 2])
+        n0, n1 = np.maximum(a0, a1), np.minimum(a0, a1)
+        pal = bc1_palette(n0, n1)
+        err = ((x[:, :, None, :] - pal[:, None, :, :]) ** 2).sum(-1)
+        ncodes = np.where((n0 == n1)[:, None], 0, np.argmin(err, -1))
+        nsse = bc1_sse(x, n0, n1, ncodes)
+        better = ok & (nsse < sse)
+        c0, c1 = np.where(better, n0, c0), np.where(better, n1, c1)
+        codes = np.where(better[:, None], ncodes, codes)
+        sse = np.where(better, nsse, sse)
+    return bc1_pack(c0, c1, codes)
+
+
+def bc4_refine(x, blocks, iterations):
+    """x [n, 16] R8, blocks [n, 8] -> refined [n, 8] (the block's mode is kept)."""
+    x = np.asarray(x, np.int64)
+    r0, r1, codes = bc4_unpack(blocks)
+    sse = ((x - np.take_along_axis(bc4_palette(r0, r1), codes, axis=1)) ** 2).sum(1)
+    for _ in range(iterations):
+        eight = r0 > r1
+        D = np.where(eight, 7, 5)
+        wts = np.where(eight[:, None], BC4_8_CODE_W7[codes], BC4_6_CODE_W5[codes])
+        use = wts >= 0
+        na8, nb8, det8 = ls_endpoints(x[..., None], wts, 7, use)
+        na6, nb6, det6 = ls_endpoints(x[..., None], wts, 5, use)
+        na, nb, det = np.where(eight[:, None], na8, na6)[:, 0], np.where(eight[:, None], nb8, nb6)[:, 0], \
+            np.where(eight, det8, det6)
+        qa = np.where(eight, quantise_ls(na, det, 7, 255), quantise_ls(na, det, 5, 255))
+        qb = np.where(eight, quantise_ls(nb, det, 7, 255), quantise_ls(nb, det, 5, 255))
+        # keep the mode: r0 > r1 for eight values, r0 <= r1 for six
+        n0 = np.where(eight, np.maximum(qa, qb), np.minimum(qa, qb))
+        n1 = np.where(eight, np.minimum(qa, qb), np.maximum(qa, qb))
+        ok = (det > 0) & np.where(eight, n0 > n1, True)
+        pal = bc4_palette(n0, n1)
+        ncodes = np.argmin(np.abs(x[:, :, None] - pal[:, None, :]), -1)
+        nsse = ((x - np.take_along_axis(pal, ncodes, axis=1)) ** 2).sum(1)
+        better = ok & (nsse < sse)
+        r0, r1 = np.where(better, n0, r0), np.where(better, n1, r1)
+        codes = np.where(better[:, None], ncodes, codes)
+        sse = np.where(better, nsse, sse)
+    return bc4_pack(r0, r1, codes)
+
+
+def encode_refined(fmt, tex, w, h, iterations=2):
+    """The reference encoder followed by `iterations` least-squares refinement steps."""
+    blk = to_blocks(tex, w, h)
+    if fmt == BC1:
+        return bc1_refine(blk, bc1_encode_blocks(blk), iterations)
+    if fmt == BC4:
+        return bc4_refine(blk[..., 0], bc4_encode_blocks(blk[..., 0]), iterations)
+    raise ValueError(f"unsupported format {fmt}")
+
+
 def encode(fmt, tex, w, h):
     """Reference BC encode of a whole texture -> [(w/4)*(h/4), 8] uint8 (BC1, BC4) or
     [(w/4)*(h/4), 16] (BC3: alpha by the BC4 encoder, colour by the BC1 encoder, whose

@@ -98,6 +98,7 @@ _SIGS = {
     "ntbc_abi_version": (c_int, []),
     "bc_reference_encode": (c_int, [c_int, _P, c_int, c_int, _P, _P]),
     "bc_decode": (c_int, [c_int, _P, c_int, c_int, _P, _P]),
+    "bc_reference_encode_refined": (c_int, [c_int, _P, c_int, c_int, c_int, _P, _P]),
     "ntbc_outputs_to_bc": (c_int, [c_int, _P, _P, c_int, _P, _P]),
     "ntbc_model_layout": (c_int, [ctypes.POINTER(ModelDesc), ctypes.POINTER(Layout)]),
     "ntbc_level_resolutions": (c_int, [c_int, c_int, c_int, ctypes.POINTER(c_int)]),
@@ -153,8 +154,12 @@ def _stream(stream):
     return stream if isinstance(stream, int) else stream.cuda_stream
 
 
-def bc_reference_encode(fmt, texels, w, h, blocks, stream=None):
-    _check(lib.bc_reference_encode(fmt, _ptr(texels), w, h, _ptr(blocks), _stream(stream)))
+def bc_reference_encode(fmt, texels, w, h, blocks, stream=None, refine=0):
+    """Reference BC encode; refine > 0 adds that many least-squares refinement steps."""
+    if refine:
+        _check(lib.bc_reference_encode_refined(fmt, _ptr(texels), w, h, refine, _ptr(blocks), _stream(stream)))
+    else:
+        _check(lib.bc_reference_encode(fmt, _ptr(texels), w, h, _ptr(blocks), _stream(stream)))
 
 
 def bc_decode(fmt, blocks, w, h, texels, stream=None):

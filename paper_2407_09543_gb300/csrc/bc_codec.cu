@@ -76,9 +76,51 @@ constexpr int kPowerIterations = 8;
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 
-// texels: ts bytes per texel, the encoded channel(s) from byte to; blocks bs bytes apart
+// BC1 codes of least integer squared RGB distance (ties: lowest code) for c0 >= c1
+// (c0 == c1: all codes 0), and the block's total squared error
+__device__ __forceinline__ void bc1_codes(const int x[16][3], uint32_t c0, uint32_t c1, uint32_t& idx, int& sse) {
+    int pal[4][3];
+    bc1_palette(c0, c1, pal);
+    idx = 0;
+    sse = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        int best = 0, bestd = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int dr = x[i][0] - pal[k][0], dg = x[i][1] - pal[k][1], db = x[i][2] - pal[k][2];
+            int d = dr * dr + dg * dg + db * db;
+            if (k == 0 || d < bestd) {
+                bestd = d;
+                best = k;
+            }
+        }
+        if (c0 == c1) {
+            best = 0;
+            int dr = x[i][0] - pal[0][0], dg = x[i][1] - pal[0][1], db = x[i][2] - pal[0][2];
+            bestd = dr * dr + dg * dg + db * db;
+        }
+        idx |= (uint32_t)best << (2 * i);
+        sse += bestd;
+    }
+}
+
+// Least-squares refinement (optional; the reading of Compressonator's "refine steps"):
+// endpoints a, b minimising sum_i |x_i - ((D - w_i) a + w_i b) / D|^2 for the current codes
+// (w_i: the code's weight of the second endpoint in units of 1/D) are, with A11 = sum
+// (D-w)^2, A12 = sum (D-w) w, A22 = sum w^2, R1 = sum (D-w) x, R2 = sum w x and det = A11 A22 -
+// A12^2: a = D (A22 R1 - A12 R2) / det, b = D (A11 R2 - A12 R1) / det. The quantised value
+// round-half-up(a L / 255), clamped to [0, L], is taken in exact integer arithmetic.
+__device__ __forceinline__ int quantise_ls(long long num, long long det, int D, int L) {
+    if (num <= 0) return 0;
+    long long q = (2LL * D * num * L + 255LL * det) / (510LL * det);
+    return (int)(q < L ? q : L);
+}
+
+// texels: ts bytes per texel, the encoded channel(s) from byte to; blocks bs bytes apart;
+// refine: least-squares refinement steps (kept while the squared error strictly falls)
 __global__ void bc1_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, int ts, int to,
-                                  uint8_t* __restrict__ out, int bs) {
+                                  uint8_t* __restrict__ out, int bs, int refine) {
     int bw = w >> 2, bh = h >> 2;
     long long nb = (long long)bw * bh;
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,24 +203,44 @@ __global__ void bc1_encode_kernel(const uint8_t* __restrict__ tex, int w, int h,
         c0 = c1;
         c1 = t;
     }
-    uint32_t idx = 0;
-    if (c0 != c1) {
-        int pal[4][3];
-        bc1_palette(c0, c1, pal);
+    uint32_t idx;
+    int sse;
+    bc1_codes(x, c0, c1, idx, sse);
+    for (int it = 0; it < refine; ++it) {
+        const int w3[4] = {0, 3, 1, 2};             // code -> weight of colour1, in thirds
+        long long A11 = 0, A12 = 0, A22 = 0, R1[3] = {0, 0, 0}, R2[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            int best = 0, bestd = 0;
+            int wi = w3[(idx >> (2 * i)) & 3], ui = 3 - wi;
+            A11 += ui * ui;
+            A12 += ui * wi;
+            A22 += wi * wi;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                int dr = x[i][0] - pal[k][0], dg = x[i][1] - pal[k][1], db = x[i][2] - pal[k][2];
-                int d = dr * dr + dg * dg + db * db;
-                if (k == 0 || d < bestd) {
-                    bestd = d;
-                    best = k;
-                }
+            for (int c = 0; c < 3; ++c) {
+                R1[c] += ui * x[i][c];
+                R2[c] += wi * x[i][c];
             }
-            idx |= (uint32_t)best << (2 * i);
         }
+        long long det = A11 * A22 - A12 * A12;
+        if (det <= 0) break;
+        const int L[3] = {31, 63, 31};
+        int qa[3], qb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            qa[c] = quantise_ls(A22 * R1[c] - A12 * R2[c], det, 3, L[c]);
+            qb[c] = quantise_ls(A11 * R2[c] - A12 * R1[c], det, 3, L[c]);
+        }
+        uint32_t a0 = ((uint32_t)qa[0] << 11) | ((uint32_t)qa[1] << 5) | (uint32_t)qa[2];
+        uint32_t a1 = ((uint32_t)qb[0] << 11) | ((uint32_t)qb[1] << 5) | (uint32_t)qb[2];
+        uint32_t n0 = a0 > a1 ? a0 : a1, n1 = a0 > a1 ? a1 : a0;
+        uint32_t nidx;
+        int nsse;
+        bc1_codes(x, n0, n1, nidx, nsse);
+        if (nsse >= sse) break;
+        c0 = n0;
+        c1 = n1;
+        idx = nidx;
+        sse = nsse;
     }
     store_block(out + b * bs, c0 | (c1 << 16), idx);
 }
@@ -205,7 +267,7 @@ __device__ __forceinline__ void bc4_codes(const int x[16], int r0, int r1, uint6
 }
 
 __global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h, int ts, int to,
-                                  uint8_t* __restrict__ out, int bs) {
+                                  uint8_t* __restrict__ out, int bs, int refine) {
     int bw = w >> 2, bh = h >> 2;
     long long nb = (long long)bw * bh;
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -223,7 +285,7 @@ __global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h,
             hi = max(hi, x[i]);
         }
     }
-    int r0, r1;
+    int r0, r1, sse = 0;
     uint64_t idx;
     if (mx == mn) {
         r0 = r1 = mx;
@@ -241,11 +303,44 @@ __global__ void bc4_encode_kernel(const uint8_t* __restrict__ tex, int w, int h,
             r0 = mx;
             r1 = mn;
             idx = ia;
+            sse = sa;
         } else {
             r0 = lo;
             r1 = hi;
             idx = ib;
+            sse = sb;
         }
+    }
+    for (int it = 0; it < refine; ++it) {          // the block keeps its mode
+        const bool eight = r0 > r1;
+        const int D = eight ? 7 : 5;
+        const int w8[8] = {0, 7, 1, 2, 3, 4, 5, 6}, w6[8] = {0, 5, 1, 2, 3, 4, -1, -1};
+        long long A11 = 0, A12 = 0, A22 = 0, R1 = 0, R2 = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            int code = (int)((idx >> (3 * i)) & 7);
+            int wi = eight ? w8[code] : w6[code];
+            if (wi < 0) continue;                      // the constants 0 and 255 of the six-value mode
+            int ui = D - wi;
+            A11 += ui * ui;
+            A12 += ui * wi;
+            A22 += wi * wi;
+            R1 += ui * x[i];
+            R2 += wi * x[i];
+        }
+        long long det = A11 * A22 - A12 * A12;
+        if (det <= 0) break;
+        int qa = quantise_ls(A22 * R1 - A12 * R2, det, D, 255), qb = quantise_ls(A11 * R2 - A12 * R1, det, D, 255);
+        int n0 = eight ? max(qa, qb) : min(qa, qb), n1 = eight ? min(qa, qb) : max(qa, qb);
+        if (eight && n0 <= n1) break;
+        uint64_t nidx;
+        int nsse;
+        bc4_codes(x, n0, n1, nidx, nsse);
+        if (nsse >= sse) break;
+        r0 = n0;
+        r1 = n1;
+        idx = nidx;
+        sse = nsse;
     }
     uint32_t wlo = (uint32_t)r0 | ((uint32_t)r1 << 8) | (uint32_t)((idx & 0xFFFF) << 16);
     uint32_t whi = (uint32_t)(idx >> 16);
@@ -344,23 +439,29 @@ const char* ntbc_last_error(void) { return g_last_error.c_str(); }
 int ntbc_abi_version(void) { return 1; }
 
 ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h, uint8_t* blocks, void* stream) {
+    return bc_reference_encode_refined(fmt, texels, w, h, 0, blocks, stream);
+}
+
+ntbc_status bc_reference_encode_refined(int fmt, const uint8_t* texels, int w, int h, int refine, uint8_t* blocks,
+                                        void* stream) {
     clear_error();
     ntbc_status st = check_texture_args(fmt, texels, blocks, w, h);
     if (st != NTBC_OK) return st;
+    if (refine < 0 || refine > 16) return fail(NTBC_EINVAL, "refinement steps must be in 0..16, got %d", refine);
     long long nb = (long long)(w / 4) * (h / 4);
     int threads = 128;
     unsigned grid = (unsigned)((nb + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
     switch (fmt) {
-        case NTBC_BC1: bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 3, 0, blocks, 8); break;
-        case NTBC_BC4: bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 1, 0, blocks, 8); break;
+        case NTBC_BC1: bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 3, 0, blocks, 8, refine); break;
+        case NTBC_BC4: bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 1, 0, blocks, 8, refine); break;
         case NTBC_BC3:   // alpha (byte 3 of RGBA) as BC4, then the colour as BC1
-            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 4, 3, blocks, 16);
-            bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 4, 0, blocks + 8, 16);
+            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 4, 3, blocks, 16, refine);
+            bc1_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 4, 0, blocks + 8, 16, refine);
             break;
         default:         // BC5: one BC4 block per channel
-            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 2, 0, blocks, 16);
-            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 2, 1, blocks + 8, 16);
+            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 2, 0, blocks, 16, refine);
+            bc4_encode_kernel<<<grid, threads, 0, s>>>(texels, w, h, 2, 1, blocks + 8, 16, refine);
     }
     NTBC_CHECK_LAUNCH("bc_reference_encode");
     return NTBC_OK;

@@ -130,3 +130,35 @@ def test_composed_formats_encode_and_decode_bit_exact(fmt):
         nt.bc_decode(fmt, _dev(b), w, h, out)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy().reshape(h, w, -1), obc.decode(fmt, b, w, h))
+
+
+@pytest.mark.parametrize("fmt,refine", [(1, 1), (1, 2), (4, 2), (4, 4)])
+def test_refined_reference_encode_bit_exact(fmt, refine):
+    mat = synth.tiny_material()
+    tex = mat.textures[0 if fmt == 1 else 1]
+    blocks = torch.empty(64 * 64 * 8, dtype=torch.uint8, device=DEV)
+    nt.bc_reference_encode(fmt, _dev(tex), 256, 256, blocks, refine=refine)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(blocks.cpu().numpy().reshape(-1, 8), obc.encode_refined(fmt, tex, 256, 256, refine))
+
+
+def test_refined_reference_encode_4k_sampled_and_better():
+    # the 4096^2 material: sampled blocks bit-exact, and a higher decoded PSNR than unrefined
+    mat = synth.material_4k(seed=0)
+    for t, fmt in enumerate(mat.formats):
+        tex = mat.textures[t]
+        base = torch.empty(1024 * 1024 * 8, dtype=torch.uint8, device=DEV)
+        ref2 = torch.empty_like(base)
+        d = _dev(tex)
+        nt.bc_reference_encode(fmt, d, 4096, 4096, base)
+        nt.bc_reference_encode(fmt, d, 4096, 4096, ref2, refine=2)
+        torch.cuda.synchronize()
+        got = ref2.cpu().numpy().reshape(-1, 8)
+        rows = np.random.default_rng(t).choice(1024, 8, replace=False)
+        for by in rows:                                   # whole block rows: 16 texel rows x 4096
+            sub = tex[4 * by:4 * by + 4]
+            want = obc.encode_refined(fmt, sub, 4096, 4, 2)
+            np.testing.assert_array_equal(got[by * 1024:(by + 1) * 1024], want)
+        p0 = obc.psnr(obc.decode(fmt, base.cpu().numpy(), 4096, 4096), tex)
+        p2 = obc.psnr(obc.decode(fmt, got, 4096, 4096), tex)
+        assert p2 > p0

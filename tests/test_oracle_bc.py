@@ -255,3 +255,57 @@ def test_bc3_round_trip_alpha_and_colour():
     dec = bc.decode(bc.BC3, blocks, 8, 8)
     assert np.all(dec[..., 3] == 200)
     np.testing.assert_array_equal(dec[..., :3], bc.decode(bc.BC1, blocks[:, 8:], 8, 8))
+
+
+# ----------------------------------------------------------------------------
+# least-squares refinement of the reference encoder
+# ----------------------------------------------------------------------------
+
+def test_least_squares_endpoints_solve_the_normal_equations():
+    # exact rationals: the residual of the fitted line is orthogonal to both basis weights
+    from fractions import Fraction
+    rng = np.random.default_rng(21)
+    x = rng.integers(0, 256, (5, 16, 3))
+    w = rng.integers(0, 4, (5, 16))
+    na, nb, det = bc.ls_endpoints(x, w, 3, np.ones((5, 16), bool))
+    for n in range(5):
+        if det[n] == 0:
+            continue
+        for c in range(3):
+            a = Fraction(3 * int(na[n, c]), int(det[n]))
+            b_ = Fraction(3 * int(nb[n, c]), int(det[n]))
+            r = [Fraction(int(x[n, i, c])) - (Fraction(3 - int(w[n, i])) * a + Fraction(int(w[n, i])) * b_) / 3
+                 for i in range(16)]
+            assert sum(ri * (3 - int(w[n, i])) for i, ri in enumerate(r)) == 0
+            assert sum(ri * int(w[n, i]) for i, ri in enumerate(r)) == 0
+            # and agrees with a library least-squares solve
+            A = np.stack([(3 - w[n]) / 3.0, w[n] / 3.0], 1)
+            sol = np.linalg.lstsq(A, x[n, :, c].astype(float), rcond=None)[0]
+            assert abs(sol[0] - float(a)) < 1e-8 and abs(sol[1] - float(b_)) < 1e-8
+
+
+def test_quantise_ls_is_round_half_up_clamped():
+    from fractions import Fraction
+    rng = np.random.default_rng(22)
+    num = rng.integers(-2000, 200000, 3000)
+    det = rng.integers(1, 5000, 3000)
+    for D, L in ((3, 31), (3, 63), (7, 255), (5, 255)):
+        q = bc.quantise_ls(num, det, D, L)
+        for k in range(0, 3000, 37):
+            v = Fraction(D * int(num[k]), int(det[k])) * L / 255
+            want = 0 if num[k] <= 0 else min(L, int((v + Fraction(1, 2)) // 1))
+            assert q[k] == want
+
+
+@pytest.mark.parametrize("fmt", [1, 4])
+def test_refinement_never_increases_error(fmt):
+    mat = synth.tiny_material()
+    tex = mat.textures[0 if fmt == 1 else 1][:64, :64]
+    base = bc.encode(fmt, tex, 64, 64)
+    np.testing.assert_array_equal(bc.encode_refined(fmt, tex, 64, 64, 0), base)
+    err = lambda b: ((bc.decode(fmt, b, 64, 64).astype(np.int64) - tex.astype(np.int64)) ** 2)  # noqa: E731
+    e0 = err(base).reshape(16, 4, 16, 4, -1).sum(axis=(1, 3, 4))
+    for k in (1, 2, 4):
+        ek = err(bc.encode_refined(fmt, tex, 64, 64, k)).reshape(16, 4, 16, 4, -1).sum(axis=(1, 3, 4))
+        assert np.all(ek <= e0)
+        assert ek.sum() < e0.sum()
