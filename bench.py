@@ -12,7 +12,10 @@ Also reported: the encode (training) time per step and the full-schedule encode
 seconds (BF16 tensor-core training; the FP32-kernel encode beside it for decoded-PSNR
 parity), the same metric end to end with host
 buffers (model blob H2D, blocks D2H), the plain FP32 PyTorch path on the same GPU,
-and the CPU oracle on a bounded sample (cpu_baseline).
+the CPU oracle on a bounded sample (cpu_baseline), and a quality / storage study
+(Fig. average: mean decoded PSNR and SSIM as ratios of the reference BC's against stored
+bytes, aggressive and conservative packaging, 8-bit and 4-bit QAT grids). The reference
+BC targets are the range-fit encoder with two least-squares endpoint refits.
 
 --impl reference times the CPU oracle (the reference arm of this build) on a
 bounded sample of the same workload.
@@ -39,6 +42,9 @@ FULL_MAIN_STEPS = 20000
 FULL_QAT_STEPS = 2000
 BATCH_TEXELS = 1 << 18
 FORMATS = [1, 1, 4, 4]
+# the reference BC targets: range fit + two least-squares endpoint refits (the paper's
+# reference encoder runs two refinement steps, Sec. 4.1)
+REF_REFINE = 2
 METRIC = "NTBC infer Mblocks/s (4k material, 4 textures) + 4k-material encode s, vs plain FP32 GPU, at decoded-PSNR parity"
 
 
@@ -55,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32-train", action="store_true", help="skip the FP32-kernel encode (PSNR comparison)")
     ap.add_argument("--no-conservative", action="store_true", help="skip the conservative-packaging encode and decode")
+    ap.add_argument("--no-study", action="store_true",
+                    help="skip the quality / storage study (4-bit-grid encodes of both packagings)")
     ap.add_argument("--prec", type=int, default=1, help="1: FP16 weights, split FP16 activations; 2: pure FP16; 3: FP8 E4M3 weights, split activations")
     ap.add_argument("--batch", action="store_true",
                     help="batched load-time inference: 16 uneven materials in one persistent launch (CUDA graph)")
@@ -445,13 +453,15 @@ def main():
 
     mat, desc, p0, tex_d, refs = build_workload(nt, torch, side, seed=rank_material_seed(rank), dev=dev)
 
-    # ---- reference BC targets (timed separately)
+    # ---- reference BC targets (timed separately); the unrefined range fit for comparison
     for t, fmt in enumerate(mat.formats):
         nt.bc_reference_encode(fmt, tex_d[t], side, side, refs[t])
     torch.cuda.synchronize()
-    ref_ms = time_events(torch, lambda: [nt.bc_reference_encode(f, tex_d[t], side, side, refs[t])
+    ref_psnr_unrefined = psnr_list(nt, torch, mat, refs, side)
+    ref_ms = time_events(torch, lambda: [nt.bc_reference_encode(f, tex_d[t], side, side, refs[t], refine=REF_REFINE)
                                          for t, f in enumerate(mat.formats)], 3)
     ref_psnr = psnr_list(nt, torch, mat, refs, side)
+    ref_ssim = ssim_list(nt, torch, mat, refs, side)
 
     # ---- encode (training) on the GPU: measured steps, full schedule extrapolated
     model = nt.Model(desc)
@@ -518,6 +528,7 @@ def main():
         torch.distributed.barrier()
     ms = max_over_ranks(float(np.mean(times)), world, dev)
     ours_psnr = psnr_list(nt, torch, mat, outs, side)
+    ours_ssim = ssim_list(nt, torch, mat, outs, side)
     value = job_throughput(tex_blocks, world, ms)
 
     # ---- end to end through the C ABI with host buffers: blob H2D, infer, blocks D2H
@@ -565,49 +576,89 @@ def main():
                            "note": "roughness + AO as one BC5 texture (strided 16-byte blocks)"}
     del bc5
 
-    # ---- conservative packaging (Sec. 4.1): one model for the BC1 textures, one for the BC4
-    # textures, both encoded with the BF16 pass and decoded together in one batched launch
-    conservative = None
-    if not args.no_conservative:
-        w = nt.configs.WORKLOADS["mat4k"]
-        groups = nt.configs.packaging_groups(FORMATS, "conservative")
-        c_models, c_outs, c_train_s, c_bytes = [], [], 0.0, 0
+    # ---- packagings (Sec. 4.1): aggressive = one model for all textures, conservative = one
+    # model for the BC1 textures and one for the BC4 textures; each encoded with the BF16 pass
+    # at the given QAT grid width and exported with grids of that width and FP16 weights
+    wl = nt.configs.WORKLOADS["mat4k"]
+
+    def encode_package(packaging, grid_bits):
+        groups = nt.configs.packaging_groups(FORMATS, packaging)
+        models, outs_g, enc_s, nbytes = [], [], 0.0, 0
         for gi, g in enumerate(groups):
             fm = [FORMATS[t] for t in g]
-            d = nt.configs.desc_for(w, fm, side=side)
+            d = nt.configs.desc_for(wl, fm, side=side)
             cres, eres = nt.configs.res_lists(d)
+            seed = rank_material_seed(rank) + (0 if packaging == "aggressive" else 17 * (gi + 1))
             pc = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(d, "color"), nt.configs.mlp_dims(d, "endpoint"),
-                                   rank_material_seed(rank) + 17 * (gi + 1))
+                                   seed)
             mc = nt.Model(d)
             mc.set_params(torch.from_numpy(nt.configs.flatten(d, pc)).to(dev))
-            mat_c = nt.Material.make(side, side, fm, [tex_d[t] for t in g], [refs[t] for t in g])
-            cfg_c = nt.TrainConfig.make(steps=main_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1, grid_bits=8,
-                                        seed=rank, precision=nt.TRAIN_BF16)
+            mat_g = nt.Material.make(side, side, fm, [tex_d[t] for t in g], [refs[t] for t in g])
+            cfg_g = nt.TrainConfig.make(steps=main_steps, batch_texels=BATCH_TEXELS, qat_fraction=0.1,
+                                        grid_bits=grid_bits, seed=rank, precision=nt.TRAIN_BF16)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            mc.train(mat_c, cfg_c)
-            c_train_s += time.perf_counter() - t0
-            mc.export(grid_bits=8, weight_prec=nt.PREC_FP16)
-            c_bytes += mc.blob_size()
-            c_models.append(mc)
-            c_outs.append([torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in g])
+            mc.train(mat_g, cfg_g)
+            enc_s += time.perf_counter() - t0
+            mc.export(grid_bits=grid_bits, weight_prec=nt.PREC_FP16)
+            nbytes += mc.blob_size()
+            models.append(mc)
+            outs_g.append([torch.empty(nblk * 8, dtype=torch.uint8, device=dev) for _ in g])
+        by_tex = [None] * len(FORMATS)
+        for g, o in zip(groups, outs_g):
+            for t, oo in zip(g, o):
+                by_tex[t] = oo
+        return groups, models, outs_g, by_tex, enc_s, nbytes
+
+    def quality(by_tex):
+        return psnr_list(nt, torch, mat, by_tex, side), ssim_list(nt, torch, mat, by_tex, side)
+
+    packages = {"aggressive_u8": {"storage_bytes": int(model.blob_size()), "encode_s": round(train_s, 2),
+                                  "psnr_db": ours_psnr, "ssim": ours_ssim}}
+    conservative = None
+    if not args.no_conservative:
+        groups, c_models, c_outs, by_tex, c_train_s, c_bytes = encode_package("conservative", 8)
         c_batch = nt.Batch(c_models, c_outs)
         c_batch.infer()
         torch.cuda.synchronize()
         c_times = time_events(torch, c_batch.infer, max(3, args.steps // 2), flush=flush)
         c_ms = float(np.mean(c_times))
-        by_tex = [None] * len(FORMATS)
-        for g, o in zip(groups, c_outs):
-            for t, oo in zip(g, o):
-                by_tex[t] = oo
+        c_psnr, c_ssim = quality(by_tex)
         conservative = {"models": len(groups), "textures_per_model": [len(g) for g in groups],
                         "encode_s_measured": round(c_train_s, 2), "infer_ms": round(c_ms, 4),
                         "infer_value": round(tex_blocks / (c_ms * 1e-3) / 1e6, 3), "unit": "Mblocks/s",
-                        "psnr_db": psnr_list(nt, torch, mat, by_tex, side),
+                        "psnr_db": c_psnr, "ssim": c_ssim,
                         "storage_bytes": int(c_bytes), "aggressive_storage_bytes": int(model.blob_size())}
+        packages["conservative_u8"] = {"storage_bytes": int(c_bytes), "encode_s": round(c_train_s, 2),
+                                       "psnr_db": c_psnr, "ssim": c_ssim}
         c_batch.close()
         for mc in c_models:
             mc.close()
+
+    # ---- quality / storage study (Fig. average): each packaging's mean decoded PSNR and SSIM
+    # as a ratio of the reference BC's, against its stored bytes; 8-bit and 4-bit QAT grids
+    study = None
+    if not args.no_study:
+        for packaging in ("aggressive", "conservative"):
+            if packaging == "conservative" and args.no_conservative:
+                continue
+            groups, ms_, outs_g, by_tex, enc_s, nbytes = encode_package(packaging, 4)
+            for mm, o in zip(ms_, outs_g):
+                mm.infer_to_bc(o)
+            torch.cuda.synchronize()
+            q_psnr, q_ssim = quality(by_tex)
+            packages[packaging + "_u4"] = {"storage_bytes": int(nbytes), "encode_s": round(enc_s, 2),
+                                           "psnr_db": q_psnr, "ssim": q_ssim}
+            for mm in ms_:
+                mm.close()
+        ref_bytes = nblk * 8 * len(FORMATS)
+        p_ref, s_ref = float(np.mean(ref_psnr)), float(np.mean(ref_ssim))
+        study = {"reference_bc": {"storage_bytes": int(ref_bytes), "psnr_db_mean": round(p_ref, 3),
+                                  "ssim_mean": round(s_ref, 4), "refine_steps": REF_REFINE}}
+        for name, e in packages.items():
+            study[name] = dict(e, storage_ratio=round(e["storage_bytes"] / ref_bytes, 4),
+                               psnr_ratio=round(float(np.mean(e["psnr_db"])) / p_ref, 4),
+                               ssim_ratio=round(float(np.mean(e["ssim"])) / s_ref, 4))
 
     # ---- plain FP32 PyTorch path on the same GPU and weights
     plain = None
@@ -663,8 +714,9 @@ def main():
                                f"3x64 SELU, FP16 weights", "texture_blocks": tex_blocks, "block_positions": nblk,
                    "l2": "flushed (256 MiB write) between timed iterations", "parallelism": f"replicas x{world}"},
         "block_positions_per_s_M": round(nblk * world / (ms * 1e-3) / 1e6, 3),
-        "ssim": {"ntbc": ssim_list(nt, torch, mat, outs, side), "reference_bc": ssim_list(nt, torch, mat, refs, side)},
+        "ssim": {"ntbc": ours_ssim, "reference_bc": ref_ssim},
         "psnr_db": {"ntbc": ours_psnr, "untrained": untrained_psnr, "reference_bc": ref_psnr,
+                    "reference_bc_unrefined": ref_psnr_unrefined,
                     "e2e": e2e_psnr, "plain_fp32": plain["psnr_db"] if plain else None},
         "encode": {"precision": "bf16 tensor-core MMA operands, fp32 accumulate / loss / Adam",
                    "ms_per_step": round(ms_per_train_step, 3), "steps_run": total_steps,
@@ -677,6 +729,7 @@ def main():
                    "fp32_kernels": fp32_encode},
         "plain_fp32_gpu": plain,
         "conservative": conservative,
+        "quality_storage": study,
         "storage": {"ntbc_blob_bytes": int(model.blob_size()), "bc_bytes": int(nblk * 8 * len(FORMATS)),
                     "weights": "FP16", "grids": "u8"},
         "roofline": roofline,

@@ -230,8 +230,11 @@ ntbc_status ntbc_model_blob_size(const ntbc_model* model, size_t* size);
 
 /*
  * Stored model blob (the on-disk form the paper loads at texture-load time):
- * exported grid codes (or FP32 grid), per-level (s, z), MLP weights in the
- * export precision. ntbc_model_save copies device -> host `blob` (host,
+ * exported grid codes (8-bit: one per byte; 4-bit: two per byte, the lower-indexed
+ * code in the low nibble; or the FP32 grid), per-level (s, z), MLP weights in the
+ * export precision. A 4-bit blob is packed and unpacked on the device (one kernel
+ * each way). Loading a blob whose header is not this ABI version, describes another
+ * model or names an unknown grid width / precision returns NTBC_EINVAL. ntbc_model_save copies device -> host `blob` (host,
  * blob_size bytes; synchronises the stream); ntbc_model_load copies host `blob`
  * (pinned host memory recommended) -> the model's device buffers, asynchronously.
  */

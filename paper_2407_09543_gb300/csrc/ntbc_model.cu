@@ -165,6 +165,27 @@ __global__ void round_half_kernel(const float* __restrict__ src, float* __restri
     }
 }
 
+// 4-bit grid codes in the blob: two per byte, the lower-indexed code in the low nibble
+__global__ void pack_nibbles_kernel(const uint8_t* __restrict__ codes, uint8_t* __restrict__ packed, long long n) {
+    const long long pairs = (n + 1) / 2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += (long long)gridDim.x * blockDim.x) {
+        uint8_t lo = codes[2 * i] & 15, hi = 2 * i + 1 < n ? codes[2 * i + 1] & 15 : 0;
+        packed[i] = (uint8_t)(lo | (hi << 4));
+    }
+}
+
+__global__ void unpack_nibbles_kernel(const uint8_t* __restrict__ packed, uint8_t* __restrict__ codes, long long n) {
+    const long long pairs = (n + 1) / 2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += (long long)gridDim.x * blockDim.x) {
+        uint8_t b = packed[i];
+        codes[2 * i] = b & 15;
+        if (2 * i + 1 < n) codes[2 * i + 1] = b >> 4;
+    }
+}
+
+// the packed staging area of 4-bit blobs sits behind the codes in the same allocation
+static size_t qgrid_codes_bytes(const ntbc_layout& L) { return (L.grid_floats + 15) & ~(size_t)15; }
+
 __global__ void half_to_float_kernel(const __half* __restrict__ h, float* __restrict__ dst, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = __half2float(h[i]);
@@ -407,7 +428,7 @@ static ntbc_status ensure_export_buffers(ntbc_model* m) {
     const ntbc_layout& L = m->layout;
     int levels = m->desc.color_levels + m->desc.endpoint_levels;
     ntbc_status st = NTBC_OK;
-    if (!m->qgrid) st = device_alloc((void**)&m->qgrid, L.grid_floats, "grid codes");
+    if (!m->qgrid) st = device_alloc((void**)&m->qgrid, qgrid_codes_bytes(L) + (L.grid_floats + 1) / 2, "grid codes");
     if (st == NTBC_OK && !m->qscale) st = device_alloc((void**)&m->qscale, levels * sizeof(float) * 2 + 2 * levels * sizeof(unsigned), "grid scales");
     if (st == NTBC_OK && !m->qzero) m->qzero = m->qscale + levels;
     if (st == NTBC_OK && !m->infer_params) st = device_alloc((void**)&m->infer_params, L.total * sizeof(float), "inference parameters");
@@ -491,7 +512,8 @@ static size_t blob_parts(const ntbc_model* m, size_t* grid_b, size_t* sz_b, size
     const ntbc_layout& L = m->layout;
     int levels = m->desc.color_levels + m->desc.endpoint_levels;
     *sz_b = 2 * levels * sizeof(float);
-    *grid_b = m->grid_bits > 0 ? L.grid_floats : L.grid_floats * sizeof(float);
+    *grid_b = m->grid_bits == 4 ? (L.grid_floats + 1) / 2
+                                : (m->grid_bits > 0 ? L.grid_floats : L.grid_floats * sizeof(float));
     size_t nw = L.total - L.grid_floats;
     if (m->weight_prec == NTBC_PREC_FP8)
         *w_b = 2 * NTBC_MAX_MLP_LAYERS * sizeof(int) + nw;        // exponents, then codes
@@ -526,7 +548,13 @@ ntbc_status ntbc_model_save(const ntbc_model* m, uint8_t* blob, size_t size, voi
     h.weight_prec = m->weight_prec;
     memcpy(blob, &h, sizeof(h));
     uint8_t* p = blob + sizeof(h);
-    if (m->grid_bits > 0) {
+    if (m->grid_bits == 4) {
+        uint8_t* packed = m->qgrid + qgrid_codes_bytes(m->layout);
+        pack_nibbles_kernel<<<grid_blocks((long long)gb), 256, 0, s>>>(m->qgrid, packed, (long long)m->layout.grid_floats);
+        NTBC_CHECK_LAUNCH("pack 4-bit grid codes");
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(p, m->qscale, zb, cudaMemcpyDeviceToHost, s));
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb, packed, gb, cudaMemcpyDeviceToHost, s));
+    } else if (m->grid_bits > 0) {
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p, m->qscale, zb, cudaMemcpyDeviceToHost, s));
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb, m->qgrid, gb, cudaMemcpyDeviceToHost, s));
     } else {
@@ -554,6 +582,9 @@ ntbc_status ntbc_model_load(ntbc_model* m, const uint8_t* blob, size_t size, voi
     memcpy(&h, blob, sizeof(h));
     if (memcmp(h.magic, "NTBC", 4) != 0 || h.version != ntbc_abi_version()) return fail(NTBC_EINVAL, "not an NTBC blob of this version");
     if (memcmp(&h.desc, &m->desc, sizeof(ntbc_model_desc)) != 0) return fail(NTBC_EINVAL, "blob describes a different model");
+    if (h.grid_bits != 0 && h.grid_bits != 4 && h.grid_bits != 8) return fail(NTBC_EINVAL, "blob has grid_bits %d", h.grid_bits);
+    if (h.weight_prec < NTBC_PREC_FP32 || h.weight_prec > NTBC_PREC_FP8)
+        return fail(NTBC_EINVAL, "blob has weight precision %d", h.weight_prec);
     ntbc_status st = ensure_export_buffers(m);
     if (st != NTBC_OK) return st;
     m->grid_bits = h.grid_bits;
@@ -564,7 +595,13 @@ ntbc_status ntbc_model_load(ntbc_model* m, const uint8_t* blob, size_t size, voi
     cudaStream_t s = (cudaStream_t)stream;
     const uint8_t* p = blob + sizeof(h);
     const ntbc_layout& L = m->layout;
-    if (m->grid_bits > 0) {
+    if (m->grid_bits == 4) {
+        uint8_t* packed = m->qgrid + qgrid_codes_bytes(L);
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(m->qscale, p, zb, cudaMemcpyHostToDevice, s));
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(packed, p + zb, gb, cudaMemcpyHostToDevice, s));
+        unpack_nibbles_kernel<<<grid_blocks((long long)gb), 256, 0, s>>>(packed, m->qgrid, (long long)L.grid_floats);
+        NTBC_CHECK_LAUNCH("unpack 4-bit grid codes");
+    } else if (m->grid_bits > 0) {
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->qscale, p, zb, cudaMemcpyHostToDevice, s));
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->qgrid, p + zb, gb, cudaMemcpyHostToDevice, s));
     } else {

@@ -155,6 +155,34 @@ def test_blob_roundtrip_reproduces_blocks():
         np.testing.assert_array_equal(a, b)
 
 
+def test_blob_u4_packed_two_codes_per_byte():
+    # a 4-bit export stores two grid codes per byte (low nibble first): the blob is half a
+    # byte per grid value smaller than the 8-bit one, its packed part matches the exported
+    # codes, and a fresh model loaded from it reproduces the blocks
+    import ctypes
+    mat, desc, odesc, params = make_case(side=64, levels=3, lo=4, hi=16)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    size8 = model.blob_size()
+    model.export(grid_bits=4, weight_prec=nt.PREC_FP16)
+    lay = model.layout
+    assert size8 - model.blob_size() == lay.grid_floats - (lay.grid_floats + 1) // 2
+    before = gpu_blocks(model, desc)
+    blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
+    model.save(blob)
+    levels = desc.color_levels + desc.endpoint_levels
+    head = 8 + ctypes.sizeof(nt.ModelDesc) + 8 + 8 * levels
+    packed = blob.numpy()[head:head + (lay.grid_floats + 1) // 2]
+    oc, _, _ = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 4)
+    codes = np.concatenate([c.reshape(-1) for c in oc]).astype(np.uint8)
+    assert codes.size == lay.grid_floats and codes.max() <= 15
+    np.testing.assert_array_equal(packed & 15, codes[0::2])
+    np.testing.assert_array_equal(packed[:codes[1::2].size] >> 4, codes[1::2])
+    other = nt.Model(desc)
+    other.load(blob)
+    for a, b in zip(before, gpu_blocks(other, desc)):
+        np.testing.assert_array_equal(a, b)
+
+
 def _blob_fp8_part(model, desc, n_layers):
     """(per-layer exponents, codes in parameter-layout order) from a saved FP8 blob: header
     (magic, version, desc, grid_bits, weight_prec), (s, z) per level, grid codes, then the
