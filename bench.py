@@ -298,6 +298,10 @@ def run_reference(args):
 
 MUFU_PER_SM_PER_CLK = 16        # exp2 results per clock per SM (CUDA arithmetic-instruction throughput table)
 SM_COUNT = 152
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# infer_tc_kernel<SPLIT=true> on the 4096^2 four-texture material, from one ncu capture of the
+# current kernel; None for any other workload or precision
+INFER_TC_DRAM_BYTES_MAT4K = 16_955_392
 SM_MAX_GHZ = 2.07
 
 
@@ -320,7 +324,7 @@ def encode_roofline(nt, desc, ms_step):
             "frac_of_measured": round(max(t_tc, t_hbm) / ms_step, 4)}
 
 
-def inference_roofline(nt, desc, ms):
+def inference_roofline(nt, desc, ms, traffic=None):
     """Governing roofline of one inference pass: max of tensor (FP16 dense), MUFU (one exp2 per
     SELU unit and per sigmoid output) and HBM (grid codes read once + blocks written) times."""
     import json as _json
@@ -340,7 +344,7 @@ def inference_roofline(nt, desc, ms):
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
     sec = ms * 1e-3
     roofline = {"bound": "alu", "achieved": round(exps / sec / 1e12, 4), "peak": round(mufu_peak / 1e12, 4),
-                "unit": "Texp/s", "frac": round(t_xu / sec, 4), "traffic": None,
+                "unit": "Texp/s", "frac": round(t_xu / sec, 4), "traffic": traffic,
                 "kernel": "infer_tc_kernel<SPLIT=true>",
                 "peak_kind": "MUFU exp2: 152 SM x 16/clk x 2.07 GHz (derived); tensor/HBM peaks of measured"}
     terms = {"t_tensor_ms": round(t_tc * 1e3, 4), "t_mufu_ms": round(t_xu * 1e3, 4), "t_hbm_ms": round(t_hbm * 1e3, 4),
@@ -552,7 +556,8 @@ def main():
     e2e_psnr = psnr_list(nt, torch, mat, host_out, side)
 
     # ---- roofline of the inference kernel (algorithmic counts per block position)
-    roofline, terms = inference_roofline(nt, desc, ms)
+    roofline, terms = inference_roofline(
+        nt, desc, ms, INFER_TC_DRAM_BYTES_MAT4K if side == 4096 and args.prec == 1 else None)
     encode_terms = encode_roofline(nt, desc, ms_per_train_step)
 
     # ---- the same inference in the other modes (pure FP16 activations; FP32 SIMT kernel)
