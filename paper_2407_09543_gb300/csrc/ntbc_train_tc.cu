@@ -112,10 +112,17 @@ __device__ __forceinline__ float rcp_fast(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float sqrt_fast(float x) {
+__device__ __forceinline__ float rsqrt_fast(float x) {
     float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+// ||x - P_n|| and its guarded inverse 1 / max(||x - P_n||, 1e-6) from the squared distance
+// with one reciprocal square root: r = 1 / sqrt(max(sq, 1e-12)), norm = sq r (below the
+// guard the norm itself is < 1e-6 and only enters the softmax, where 1e-6 / T is negligible)
+__device__ __forceinline__ float norm_and_inverse(float sq, float& inv) {
+    inv = rsqrt_fast(fmaxf(sq, kNormGuard * kNormGuard));
+    return sq * inv;
 }
 __device__ __forceinline__ float act_fast(float z, int act) {
     if (act != NTBC_ACT_SELU) return fmaxf(z, 0.f);
@@ -172,7 +179,7 @@ __device__ __forceinline__ int palette_distances(int fmt, const float* e0, const
 #pragma unroll
     for (int n = 0; n < (C == 3 ? 4 : 8); ++n) a8[n] = b8[n] = c8[n] = 0.f;       // BC1 fills only n < 4
     int K = palette_coeffs(fmt, e0[0] > e1[0], a8, b8, c8);
-    float bestv = -3.0e38f;
+    float bestsq = 3.0e38f;
     best = 0;
 #pragma unroll
     for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
@@ -183,11 +190,10 @@ __device__ __forceinline__ int palette_distances(int fmt, const float* e0, const
             float df = x[q] - P[n][q];
             sq = fmaf(df, df, sq);
         }
-        float nrm = sqrt_fast(sq);
+        float nrm = norm_and_inverse(sq, inv[n]);
         d[n] = n < K ? -nrm : -3.0e38f;
-        inv[n] = rcp_fast(fmaxf(nrm, kNormGuard));
-        if (d[n] > bestv) {
-            bestv = d[n];
+        if (n < K && sq < bestsq) {           // argmax of -||.|| = argmin of the squared distance
+            bestsq = sq;
             best = n;
         }
     }
@@ -337,7 +343,7 @@ __device__ __forceinline__ void endpoint_item(const TrArgs& a, int fmt, int b, i
 #pragma unroll
         for (int q = 0; q < C; ++q) c[q] = (float)tp[q] * (1.f / 255.f);
         float d[8], inv[8];
-        float bestv = -3.0e38f;
+        float bestsq = 3.0e38f;
         int best = 0;
 #pragma unroll
         for (int n = 0; n < KM; ++n) {
@@ -347,11 +353,9 @@ __device__ __forceinline__ void endpoint_item(const TrArgs& a, int fmt, int b, i
                 float df = c[q] - Ph[n][q];
                 sq = fmaf(df, df, sq);
             }
-            float nrm = sqrt_fast(sq);
-            d[n] = -nrm;
-            inv[n] = rcp_fast(fmaxf(nrm, kNormGuard));
-            if (d[n] > bestv) {
-                bestv = d[n];
+            d[n] = -norm_and_inverse(sq, inv[n]);
+            if (sq < bestsq) {                // argmax of -||.|| = argmin of the squared distance
+                bestsq = sq;
                 best = n;
             }
         }
@@ -409,6 +413,28 @@ __device__ __forceinline__ void endpoint_block_row(const TrArgs& a, int s, bool 
 
 // grid features of one sample (FP32 master grid, QAT fake quantisation while active)
 // straight into the BF16 X row: level l -> columns 2l, 2l + 1
+// the two features of level l at (u, v) (bilinear over the FP32 grid, fake-quantised in the
+// QAT phase) as one BF16 pair in row r of the X tile
+__device__ __forceinline__ void gather_level_train(const NetView& nv, const GridSrc& src, int l, float u, float v,
+                                                   unsigned char* X, int r, int K0, int qat_bits) {
+    Bilinear bl = bilinear_at(nv.res[l], u, v);
+    const float* gp = src.f32 + nv.grid_off[l] + bl.base;
+    float2 p00 = __ldg(reinterpret_cast<const float2*>(gp));
+    float2 p01 = __ldg(reinterpret_cast<const float2*>(gp + 2));
+    float2 p10 = __ldg(reinterpret_cast<const float2*>(gp + bl.row));
+    float2 p11 = __ldg(reinterpret_cast<const float2*>(gp + bl.row + 2));
+    if (qat_bits > 0) {
+        float sc = src.scale[l], z = src.zero[l], qm = (float)((1 << qat_bits) - 1);
+        p00 = make_float2(fake_quant(p00.x, sc, z, qm), fake_quant(p00.y, sc, z, qm));
+        p01 = make_float2(fake_quant(p01.x, sc, z, qm), fake_quant(p01.y, sc, z, qm));
+        p10 = make_float2(fake_quant(p10.x, sc, z, qm), fake_quant(p10.y, sc, z, qm));
+        p11 = make_float2(fake_quant(p11.x, sc, z, qm), fake_quant(p11.y, sc, z, qm));
+    }
+    float f0 = bl.w00 * p00.x + bl.w01 * p01.x + bl.w10 * p10.x + bl.w11 * p11.x;
+    float f1 = bl.w00 * p00.y + bl.w01 * p01.y + bl.w10 * p10.y + bl.w11 * p11.y;
+    *reinterpret_cast<uint32_t*>(X + chunk_byte(r, (2 * l) >> 3, K0) + ((2 * l) & 7) * 2) = pack_bf16x2(f0, f1);
+}
+
 __device__ __forceinline__ void gather_row_train(const NetView& nv, const GridSrc& src, float u, float v,
                                                  unsigned char* X, int r, int K0) {
     const int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
@@ -419,24 +445,7 @@ __device__ __forceinline__ void gather_row_train(const NetView& nv, const GridSr
         prefetch_l1(gp + bl.row);
     }
 #pragma unroll 4
-    for (int l = 0; l < nv.levels; ++l) {
-        Bilinear bl = bilinear_at(nv.res[l], u, v);
-        const float* gp = src.f32 + nv.grid_off[l] + bl.base;
-        float2 p00 = __ldg(reinterpret_cast<const float2*>(gp));
-        float2 p01 = __ldg(reinterpret_cast<const float2*>(gp + 2));
-        float2 p10 = __ldg(reinterpret_cast<const float2*>(gp + bl.row));
-        float2 p11 = __ldg(reinterpret_cast<const float2*>(gp + bl.row + 2));
-        if (qat_bits > 0) {
-            float sc = src.scale[l], z = src.zero[l], qm = (float)((1 << qat_bits) - 1);
-            p00 = make_float2(fake_quant(p00.x, sc, z, qm), fake_quant(p00.y, sc, z, qm));
-            p01 = make_float2(fake_quant(p01.x, sc, z, qm), fake_quant(p01.y, sc, z, qm));
-            p10 = make_float2(fake_quant(p10.x, sc, z, qm), fake_quant(p10.y, sc, z, qm));
-            p11 = make_float2(fake_quant(p11.x, sc, z, qm), fake_quant(p11.y, sc, z, qm));
-        }
-        float f0 = bl.w00 * p00.x + bl.w01 * p01.x + bl.w10 * p10.x + bl.w11 * p11.x;
-        float f1 = bl.w00 * p00.y + bl.w01 * p01.y + bl.w10 * p10.y + bl.w11 * p11.y;
-        *reinterpret_cast<uint32_t*>(X + chunk_byte(r, (2 * l) >> 3, K0) + ((2 * l) & 7) * 2) = pack_bf16x2(f0, f1);
-    }
+    for (int l = 0; l < nv.levels; ++l) gather_level_train(nv, src, l, u, v, X, r, K0, qat_bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -509,6 +518,7 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
     const int od = net.out_dim;
     float* Ys = reinterpret_cast<float*>(smem + sl.stage_off);   // endpoint only
     float* Gs = Ys + kTrRows * od;
+    float2* UV = reinterpret_cast<float2*>(Gs + kTrRows * od);    // endpoint only: block coordinates
     uint32_t phase = 0;
     bool ok = true, first = true;
     float loss0 = 0.f, loss1 = 0.f;
@@ -520,9 +530,24 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
         const bool valid = s_raw < a.B;
         const int s = valid ? s_raw : a.B - 1;
 
+        if (!COLOR) {
+            // ---- gather of the tile's 128 blocks, one (block, level) item per thread over all
+            // 16 warps; the blocks' coordinates stay in shared memory for the scatter
+            const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+            for (int p = threadIdx.x; p < kTrRows * nv.levels; p += blockDim.x) {
+                const int rr = p % kTrRows, lv = p / kTrRows, sb = tile * kTrRows + rr;
+                float u, v;
+                int x, y;
+                sample_coords(a.mv, false, a.ids, sb < a.B ? sb : a.B - 1, u, v, x, y);
+                if (lv == 0) UV[rr] = make_float2(u, v);
+                gather_level_train(nv, a.src, lv, u, v, G.X, rr, net.K0, qat_bits);
+            }
+            proxy_fence();
+            __syncthreads();
+        }
         if (tile_thread && ok) {
             // ---- gather
-            {
+            if (COLOR) {
                 float u, v;
                 int x, y;
                 sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
@@ -707,11 +732,9 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
             for (int p = threadIdx.x; p < kTrRows * nv.levels; p += blockDim.x) {
                 const int rr = p % kTrRows, lv = p / kTrRows, sb = tile * kTrRows + rr;
                 const bool pv = sb < a.B;
-                float u, v;
-                int x, y;
-                sample_coords(a.mv, false, a.ids, pv ? sb : a.B - 1, u, v, x, y);
-                scatter_level(nv, false, lv, u, v, rr, pv, gs_all[rr * 33 + 2 * lv], gs_all[rr * 33 + 2 * lv + 1], a.src,
-                              qat_bits, a.grads);
+                const float2 uv = UV[rr];
+                scatter_level(nv, false, lv, uv.x, uv.y, rr, pv, gs_all[rr * 33 + 2 * lv], gs_all[rr * 33 + 2 * lv + 1],
+                              a.src, qat_bits, a.grads);
             }
             __syncthreads();                // staging reused by the next tile
         } else if (!ok) {
@@ -746,12 +769,21 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
     }
 
     // ---- weight gradients: this group's TMEM accumulators -> its row of partial sums (plain
-    // stores; a second kernel adds the rows of all groups, so no address sees contention)
+    // stores; a second kernel adds the rows of all groups, so no address sees contention).
+    // Layer 0 holds dW_0 (lane = unit o, column = input i, the bias at i = in); later layers
+    // hold dW_l^T (lane = input i, the bias at i = in, column = unit o). Warps whose 32 lanes
+    // hold nothing skip the layer; the others read only the columns that hold gradients.
     if (tile_thread && ok) {
         float* part = a.partials + (long long)(blockIdx.x * a.groups + G.g) * net.mlp_params;
+        const int lane0 = r & ~31;
         for (int l = 0; l < L; ++l) {
             const TrLayer& Ly = net.layer[l];
-            const int ncol = l == 0 ? net.K0 : Ly.N;
+            const int lanes = l == 0 ? Ly.out : Ly.in + 1;
+            if (lane0 >= lanes) continue;                    // warp-uniform
+            const int ncol = l == 0 ? Ly.in + 1 : Ly.out;
+            const bool lane_ok = r < lanes;
+            float* wrow = part + (Ly.w_off - net.mlp_base) + (l == 0 ? (long long)r * Ly.in : (long long)r);
+            float* brow = part + (Ly.b_off - net.mlp_base);
             for (int c0 = 0; c0 < ncol; c0 += 16) {
                 float v[16];
                 if (!first) {
@@ -761,16 +793,22 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = 0.f;      // a group without tiles adds nothing
                 }
+                if (!lane_ok) continue;
+                if (l == 0) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    int c = c0 + j;
-                    if (l == 0) {             // lane = unit o, column = input i
-                        if (r < Ly.out && c < Ly.in) part[Ly.w_off - net.mlp_base + (long long)r * Ly.in + c] = v[j];
-                        else if (r < Ly.out && c == Ly.in) part[Ly.b_off - net.mlp_base + r] = v[j];
-                    } else {                  // lane = input i (64 = bias), column = unit o
-                        if (c < Ly.out && r < Ly.in) part[Ly.w_off - net.mlp_base + (long long)c * Ly.in + r] = v[j];
-                        else if (c < Ly.out && r == Ly.in) part[Ly.b_off - net.mlp_base + c] = v[j];
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = c0 + j;
+                        if (c < Ly.in) wrow[c] = v[j];
+                        else if (c == Ly.in) brow[r] = v[j];
                     }
+                } else if (r < Ly.in) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < Ly.out) wrow[(long long)(c0 + j) * Ly.in] = v[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < Ly.out) brow[c0 + j] = v[j];
                 }
             }
         }
@@ -907,7 +945,7 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
     smem = (size_t)a.sl.group_off + (size_t)a.groups * a.sl.group_bytes;
     if (!color) {
         a.sl.stage_off = (int)smem;
-        smem += 2 * (size_t)kTrRows * net.out_dim * sizeof(float);
+        smem += 2 * (size_t)kTrRows * net.out_dim * sizeof(float) + (size_t)kTrRows * sizeof(float2);
     }
     if (smem + 1024 > 227 * 1024) return fail(NTBC_EUNSUPPORTED, "tensor-core training: shared memory too small");
     smem = std::max(smem, (size_t)116 * 1024);     // one CTA per SM: each CTA allocates all 512 TMEM columns
