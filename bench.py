@@ -190,13 +190,17 @@ def ssim_gpu(torch, a, b):
     import torch.nn.functional as F
     g = torch.exp(-((torch.arange(11, device=a.device, dtype=torch.float64) - 5.0) ** 2) / (2 * 1.5 ** 2))
     g = g / g.sum()
-    win = (g[:, None] * g[None, :])[None, None]
+    gx, gy = g.view(1, 1, 1, 11), g.view(1, 1, 11, 1)
+
+    def win(t):                      # the separable 11 x 11 Gaussian window, valid region
+        return F.conv2d(F.conv2d(t, gx), gy)
+
     x = a.double().permute(2, 0, 1)[:, None] / 255.0
     y = b.double().permute(2, 0, 1)[:, None] / 255.0
-    mx, my = F.conv2d(x, win), F.conv2d(y, win)
-    sxx = F.conv2d(x * x, win) - mx * mx
-    syy = F.conv2d(y * y, win) - my * my
-    sxy = F.conv2d(x * y, win) - mx * my
+    mx, my = win(x), win(y)
+    sxx = win(x * x) - mx * mx
+    syy = win(y * y) - my * my
+    sxy = win(x * y) - mx * my
     c1, c2 = 0.01 ** 2, 0.03 ** 2
     m = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
     return float(m.mean(dim=(1, 2, 3)).mean())

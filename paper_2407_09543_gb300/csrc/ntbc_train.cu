@@ -30,6 +30,12 @@ struct StepState {
     int qat;                 // 1 while the QAT phase fake-quantises the grids
 };
 
+// The scheduled quantities of one step (what step_begin_kernel writes into StepState).
+struct StepSchedule {
+    float lr_grid, lr_mlp, bc1, bc2;
+    int qat;
+};
+
 struct NetBuffers {
     int cap;                 // sample capacity
     float* X;                // [32][cap] grid features
@@ -57,6 +63,8 @@ struct ntbc_train_state {
     float* tc_part = nullptr;         // weight-gradient partial sums of the tensor-core pass
     int tc_part_rows = 0;
     int* tc_err = nullptr;            // set when a bounded wait of the tensor-core training gives up
+    ntbc::StepSchedule* sched = nullptr;   // per-step schedule of the current ntbc_train call
+    long long sched_cap = 0;
 };
 
 namespace ntbc {
@@ -95,11 +103,10 @@ __global__ void sample_kernel(uint64_t seed, const StepState* __restrict__ st, l
 // step bookkeeping: schedule, bias corrections, QAT phase flag
 // ---------------------------------------------------------------------------
 
-__global__ void step_begin_kernel(StepState* st, long long explicit_step, long long main_steps, long long total_steps,
-                                  float lr_grid, float lr_mlp, int warmup, int qat_bits) {
-    if (threadIdx.x != 0) return;
-    long long t = explicit_step >= 0 ? explicit_step : st->step;
-    st->step = t;
+// LR (linear warm-up, then cosine to 0 over all steps, Sec. 3.4), Adam bias corrections and
+// the QAT flag of step t
+__device__ __forceinline__ StepSchedule schedule_of(long long t, long long main_steps, long long total_steps,
+                                                    float lr_grid, float lr_mlp, int warmup, int qat_bits) {
     double f;
     if (t < warmup) {
         f = (double)(t + 1) / warmup;
@@ -107,11 +114,38 @@ __global__ void step_begin_kernel(StepState* st, long long explicit_step, long l
         long long span = total_steps - warmup > 0 ? total_steps - warmup : 1;
         f = 0.5 * (1.0 + cos(3.14159265358979323846 * (double)(t - warmup) / (double)span));
     }
-    st->lr_grid = (float)(lr_grid * f);
-    st->lr_mlp = (float)(lr_mlp * f);
-    st->bc1 = (float)(1.0 - pow(kAdamB1, (double)(t + 1)));
-    st->bc2 = (float)(1.0 - pow(kAdamB2, (double)(t + 1)));
-    st->qat = (qat_bits > 0 && t >= main_steps) ? 1 : 0;
+    StepSchedule q;
+    q.lr_grid = (float)(lr_grid * f);
+    q.lr_mlp = (float)(lr_mlp * f);
+    q.bc1 = (float)(1.0 - pow(kAdamB1, (double)(t + 1)));
+    q.bc2 = (float)(1.0 - pow(kAdamB2, (double)(t + 1)));
+    q.qat = (qat_bits > 0 && t >= main_steps) ? 1 : 0;
+    return q;
+}
+
+// every step's schedule at once (one thread per step), before the step loop
+__global__ void schedule_kernel(StepSchedule* tab, long long main_steps, long long total_steps, float lr_grid,
+                                float lr_mlp, int warmup, int qat_bits) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total_steps;
+         t += (long long)gridDim.x * blockDim.x)
+        tab[t] = schedule_of(t, main_steps, total_steps, lr_grid, lr_mlp, warmup, qat_bits);
+}
+
+// Step t = explicit_step (>= 0) or the running counter: its schedule from the table when one
+// is given, else computed here.
+__global__ void step_begin_kernel(StepState* st, const StepSchedule* tab, long long explicit_step, long long main_steps,
+                                  long long total_steps, float lr_grid, float lr_mlp, int warmup, int qat_bits) {
+    if (threadIdx.x != 0) return;
+    long long t = explicit_step >= 0 ? explicit_step : st->step;
+    st->step = t;
+    StepSchedule q = tab && t >= 0 && t < total_steps
+                         ? tab[t]
+                         : schedule_of(t, main_steps, total_steps, lr_grid, lr_mlp, warmup, qat_bits);
+    st->lr_grid = q.lr_grid;
+    st->lr_mlp = q.lr_mlp;
+    st->bc1 = q.bc1;
+    st->bc2 = q.bc2;
+    st->qat = q.qat;
 }
 
 __global__ void step_end_kernel(StepState* st) {
@@ -526,6 +560,7 @@ void ntbc_train_release(ntbc_model* m) {
     cudaFree(ts->qscale);
     cudaFree(ts->tc_img);
     cudaFree(ts->tc_part);
+    cudaFree(ts->sched);
     delete ts;
     m->train = nullptr;
 }
@@ -835,7 +870,8 @@ ntbc_status ntbc_adam_step(ntbc_model* m, const float* grads, long step, long to
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), s));
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), s));
     }
-    step_begin_kernel<<<1, 32, 0, s>>>(m->train->st, step, total_steps, total_steps, cfg->lr_grid, cfg->lr_mlp, cfg->warmup, 0);
+    step_begin_kernel<<<1, 32, 0, s>>>(m->train->st, nullptr, step, total_steps, total_steps, cfg->lr_grid, cfg->lr_mlp,
+                                       cfg->warmup, 0);
     NTBC_CHECK_LAUNCH("step begin");
     return adam_launch(m, grads, s);
 }
@@ -869,11 +905,26 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), cap));
     NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), cap));
     NTBC_CHECK_CUDA(cudaMemsetAsync(ts->st, 0, sizeof(StepState), cap));
+    if (ts->sched_cap < total) {
+        cudaFree(ts->sched);
+        ts->sched = nullptr;
+        ts->sched_cap = 0;
+        st = device_alloc((void**)&ts->sched, (size_t)total * sizeof(StepSchedule), "step schedule");
+        if (st != NTBC_OK) {
+            cudaStreamDestroy(cap);
+            return st;
+        }
+        ts->sched_cap = total;
+    }
+    schedule_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 1024), 256, 0, cap>>>(
+        ts->sched, cfg->steps, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup, qbits);
+    NTBC_CHECK_LAUNCH("step schedule");
     // capture one step; every quantity that changes per step lives in StepState
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     NTBC_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    step_begin_kernel<<<1, 32, 0, cap>>>(ts->st, -1, cfg->steps, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup, qbits);
+    step_begin_kernel<<<1, 32, 0, cap>>>(ts->st, ts->sched, -1, cfg->steps, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup,
+                                         qbits);
     sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, 0, nb, n_blocks, ts->ids);
     st = grads_on_ids(m, mat, ts->ids, nb, qbits, true, cfg->temperature, cfg->precision, ts->grads, cap);
     if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap);

@@ -824,12 +824,27 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
     if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(512));
 }
 
-// grads[mlp_base + j] += sum over the groups' partial rows
-__global__ void reduce_partials_kernel(const float* __restrict__ part, int rows, int n, float* __restrict__ grads) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        float acc = 0.f;
-        for (int p = 0; p < rows; ++p) acc += part[(long long)p * n + j];
-        grads[j] += acc;
+// grads[mlp_base + j] += sum over the groups' partial rows. A CTA owns 32 columns (one per
+// lane, so every row read is one 128-byte line); its 8 warps split the rows, then warp 0
+// adds the 8 partial sums.
+constexpr int kReduceWarps = 8;
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(const float* __restrict__ part, int rows,
+                                                                            int n, float* __restrict__ grads) {
+    __shared__ float sums[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
+    float acc = 0.f;
+    if (j < n) {
+#pragma unroll 4
+        for (int p = w; p < rows; p += kReduceWarps) acc += __ldcs(part + (long long)p * n + j);
+    }
+    sums[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && j < n) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < kReduceWarps; ++q) t += sums[q][lane];
+        grads[j] += t;
     }
 }
 
@@ -963,7 +978,7 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
         train_tc_kernel<false><<<grid, kTrEndpointThreads, smem, s>>>(a);
     }
     NTBC_CHECK_LAUNCH(color ? "tensor-core training (colour)" : "tensor-core training (endpoint)");
-    reduce_partials_kernel<<<(net.mlp_params + 255) / 256, 256, 0, s>>>(partials, grid * a.groups, net.mlp_params,
+    reduce_partials_kernel<<<(net.mlp_params + 31) / 32, 32 * kReduceWarps, 0, s>>>(partials, grid * a.groups, net.mlp_params,
                                                                       grads + net.mlp_base);
     NTBC_CHECK_LAUNCH("weight-gradient partials");
     return NTBC_OK;
