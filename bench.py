@@ -51,7 +51,7 @@ METRIC = "NTBC infer Mblocks/s (4k material, 4 textures) + 4k-material encode s,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--train-steps", type=int, default=FULL_MAIN_STEPS,
@@ -122,6 +122,14 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def wait_first_sample(self, timeout_s=5.0):
+        """Block until nvidia-smi has written its first sample (it takes a moment to start)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < timeout_s:
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -520,6 +528,9 @@ def main():
     def infer():
         model.infer_to_bc(outs)
 
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.wait_first_sample()
     for _ in range(args.warmup):
         flush()
         infer()
@@ -527,8 +538,6 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     times = time_events(torch, infer, args.steps, flush=flush)
     torch.cuda.synchronize()
     clk = clocks.stop()
