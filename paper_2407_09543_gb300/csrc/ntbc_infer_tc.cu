@@ -74,16 +74,67 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return e;
 }
 
-// SELU on a pair of units with packed FP32 (two lanes per instruction)
+// SELU on a pair of units with packed FP32 (two lanes per instruction):
+// lambda max(a, 0) + lambda alpha L (2^min(a, 0) - 1), with max(a, 0) formed as a - min(a, 0)
+// (exact) so that one min per unit serves both branches
 __device__ __forceinline__ float2 selu2_l2(float2 a) {
-    float2 e = make_float2(ex2_approx(fminf(a.x, 0.f)), ex2_approx(fminf(a.y, 0.f)));
+    const float2 m = make_float2(fminf(a.x, 0.f), fminf(a.y, 0.f));
+    float2 e = make_float2(ex2_approx(m.x), ex2_approx(m.y));
     float2 t = __ffma2_rn(make_float2(kSeluLA * kLog2e, kSeluLA * kLog2e), e,
                           make_float2(-kSeluLA * kLog2e, -kSeluLA * kLog2e));
-    return __ffma2_rn(make_float2(kSeluLambda, kSeluLambda), make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)), t);
+    return __ffma2_rn(make_float2(kSeluLambda, kSeluLambda), __ffma2_rn(m, make_float2(-1.f, -1.f), a), t);
 }
 
 // sigmoid(z) from a = z L
 __device__ __forceinline__ float sigmoid_l2(float a) { return __fdividef(1.f, 1.f + ex2_approx(-a)); }
+
+// The decisions of choose_code_bc1 / choose_code_bc4 (least squared FP32 distance, channels
+// summed in order, ties to the lowest code) with two palette entries per packed instruction;
+// each lane of a packed op rounds exactly like the scalar op, and p * -1 + x is x - p rounded
+// once, so the distances and the codes are bit-identical.
+__device__ __forceinline__ int choose_code_bc1_x2(const BlockPalette& bp, float r, float g, float b) {
+    if (bp.solid) return 0;
+    float d[4];
+#pragma unroll
+    for (int k = 0; k < 4; k += 2) {
+        const float2 m1 = make_float2(-1.f, -1.f);
+        float2 dr = __ffma2_rn(make_float2(bp.pal[k][0], bp.pal[k + 1][0]), m1, make_float2(r, r));
+        float2 dg = __ffma2_rn(make_float2(bp.pal[k][1], bp.pal[k + 1][1]), m1, make_float2(g, g));
+        float2 db = __ffma2_rn(make_float2(bp.pal[k][2], bp.pal[k + 1][2]), m1, make_float2(b, b));
+        float2 s2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dr, dr), __fmul2_rn(dg, dg)), __fmul2_rn(db, db));
+        d[k] = s2.x;
+        d[k + 1] = s2.y;
+    }
+    int best = 0;
+    float bestd = d[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (d[k] < bestd) {
+            bestd = d[k];
+            best = k;
+        }
+    return best;
+}
+
+__device__ __forceinline__ int choose_code_bc4_x2(const BlockPalette& bp, float v) {
+    float d[8];
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        float2 dv = __ffma2_rn(make_float2(bp.pal[k][0], bp.pal[k + 1][0]), make_float2(-1.f, -1.f), make_float2(v, v));
+        float2 s2 = __fmul2_rn(dv, dv);
+        d[k] = s2.x;
+        d[k + 1] = s2.y;
+    }
+    int best = 0;
+    float bestd = d[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k)
+        if (d[k] < bestd) {
+            bestd = d[k];
+            best = k;
+        }
+    return best;
+}
 
 struct TcLayer {
     int K;           // total K of the MMA (multiple of 16, bias column included)
@@ -556,7 +607,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                                           *reinterpret_cast<const uint32_t*>(pb + 8)};
 #pragma unroll
                         for (int q = 0; q < 12; ++q) bp.pal[q / 3][q % 3] = tab[(wv[q / 4] >> (8 * (q % 4))) & 255];
-                        uint32_t w = (uint32_t)choose_code_bc1(bp, sigmoid_l2(cv[t][0]), sigmoid_l2(cv[t][1]),
+                        uint32_t w = (uint32_t)choose_code_bc1_x2(bp, sigmoid_l2(cv[t][0]), sigmoid_l2(cv[t][1]),
                                                                sigmoid_l2(cv[t][2])) << (2 * i);
 #pragma unroll
                         for (int o = 8; o > 0; o >>= 1) w |= __shfl_xor_sync(0xffffffffu, w, o);
@@ -566,7 +617,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                         uint32_t w1 = *reinterpret_cast<const uint32_t*>(pb + 4);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) bp.pal[q][0] = tab[((q < 4 ? w0 : w1) >> (8 * (q % 4))) & 255];
-                        bits = (uint64_t)choose_code_bc4(bp, sigmoid_l2(cv[t][0])) << (3 * i);
+                        bits = (uint64_t)choose_code_bc4_x2(bp, sigmoid_l2(cv[t][0])) << (3 * i);
 #pragma unroll
                         for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
                     }
