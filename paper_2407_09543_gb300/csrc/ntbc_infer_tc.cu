@@ -42,6 +42,19 @@ __device__ __forceinline__ void st_row8(unsigned char* tile, int r, int kg, int 
     *reinterpret_cast<uint4*>(tile + (((r >> 3) * (K >> 3) + kg) * 128 + (r & 7) * 16)) = u;
 }
 
+// x - (float)h for both halves of h (low half with x.x): one mixed-precision FMA per value,
+// h * -1 + x with the half operand widened exactly and a single rounding (the residual of an
+// FP16 rounding is exact in FP32, so no rounding happens at all)
+__device__ __forceinline__ float2 residual_f16x2(__half2 h, float2 x) {
+    float2 r;
+    const uint32_t hb = *reinterpret_cast<uint32_t*>(&h);
+    asm("{\n\t.reg .b16 hl, hu, m1;\n\tmov.b32 {hl, hu}, %2;\n\tmov.b16 m1, 0xBC00;\n\t"
+        "fma.rn.f32.f16 %0, hl, m1, %3;\n\tfma.rn.f32.f16 %1, hu, m1, %4;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "r"(hb), "f"(x.x), "f"(x.y));
+    return r;
+}
+
 // store 8 values as FP16 hi (and, when split, the FP16 rounding of the residual in lo)
 template <bool SPLIT>
 __device__ __forceinline__ void st_row8_split(unsigned char* hi_tile, unsigned char* lo_tile, int r, int kg, int K,
@@ -54,7 +67,7 @@ __device__ __forceinline__ void st_row8_split(unsigned char* hi_tile, unsigned c
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         __half2 h = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-        float2 r = __ffma2_rn(__half22float2(h), make_float2(-1.f, -1.f), make_float2(v[2 * j], v[2 * j + 1]));
+        float2 r = residual_f16x2(h, make_float2(v[2 * j], v[2 * j + 1]));
         __half2 lo = __floats2half2_rn(r.x, r.y);
         hw[j] = *reinterpret_cast<uint32_t*>(&h);
         lw[j] = *reinterpret_cast<uint32_t*>(&lo);
