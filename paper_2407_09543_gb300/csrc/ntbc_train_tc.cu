@@ -545,13 +545,13 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
             proxy_fence();
             __syncthreads();
         }
+        float su = 0.f, sv = 0.f;                 // the colour sample's coordinates (gather, scatter)
         if (tile_thread && ok) {
             // ---- gather
             if (COLOR) {
-                float u, v;
                 int x, y;
-                sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
-                gather_row_train(nv, a.src, u, v, G.X, r, net.K0);
+                sample_coords(a.mv, COLOR, a.ids, s, su, sv, x, y);
+                gather_row_train(nv, a.src, su, sv, G.X, r, net.K0);
             }
             // ---- forward
             for (int l = 0; l < L; ++l) {
@@ -709,14 +709,11 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
 #pragma unroll
                     for (int j = 0; j < 32; ++j) gs[j] = gx[j];
                     if (COLOR) {          // texels: warp-aggregated along the block's rows and columns
-                        float u, v;
-                        int x, y;
-                        sample_coords(a.mv, COLOR, a.ids, s, u, v, x, y);
                         const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
-                        const Neighbours nbr = neighbours(u, v);
+                        const Neighbours nbr = neighbours(su, sv);
 #pragma unroll 1
                         for (int lv = 0; lv < nv.levels; ++lv)
-                            scatter_level(nv, COLOR, lv, u, v, r, valid, gs[2 * lv], gs[2 * lv + 1], a.src, qat_bits,
+                            scatter_level(nv, COLOR, lv, su, sv, r, valid, gs[2 * lv], gs[2 * lv + 1], a.src, qat_bits,
                                           a.grads, nbr);
                     }
                 }
