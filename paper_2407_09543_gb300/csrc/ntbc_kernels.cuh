@@ -15,10 +15,9 @@ struct LevelTable {
 };
 
 LevelTable level_table(const ntbc_model_desc& d, const ntbc_layout& L);
-// per-level QAT scale / zero point; with `active` (device flag) the kernels do nothing
-// while the flag is zero (outside the QAT phase of a captured training step)
+// per-level QAT scale / zero point
 ntbc_status launch_level_scale_zero(const float* grid, const LevelTable& lt, int bits, unsigned* mm, float* scale,
-                                    float* zero, cudaStream_t s, const int* active = nullptr);
+                                    float* zero, cudaStream_t s);
 
 // Where a network's grid comes from.
 //   f32:  FP32 features (parameter buffer), optional QAT fake quantisation (qat_bits > 0 with
@@ -31,7 +30,6 @@ struct GridSrc {
     const float* scale;      // indexed by level (already offset for the network)
     const float* zero;
     int qat_bits;
-    const int* qat_active;   // optional device flag: fake quantisation only while it is non-zero
 };
 
 // Corner-aligned bilinear lookup of level l at normalised (u, v):
@@ -65,7 +63,7 @@ __device__ __forceinline__ float fake_quant(float r, float s, float z, float qma
 
 // features of every level, level-major, 2 per level, into out[0 .. 2*levels)
 __device__ __forceinline__ void grid_features(const NetView& nv, const GridSrc& src, float u, float v, float* out) {
-    int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+    const int qat_bits = src.qat_bits;
 #pragma unroll
     for (int l = 0; l < NTBC_MAX_LEVELS; ++l) {
         if (l >= nv.levels) break;

@@ -98,9 +98,7 @@ __device__ __forceinline__ float dec_f(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
 }
 
-__global__ void level_minmax_kernel(const float* __restrict__ grid, LevelTable lt, unsigned* __restrict__ mm,
-                                    const int* __restrict__ active) {
-    if (active && *active == 0) return;
+__global__ void level_minmax_kernel(const float* __restrict__ grid, LevelTable lt, unsigned* __restrict__ mm) {
     int l = blockIdx.y;
     long long n = lt.count[l];
     const float* g = grid + lt.offset[l];
@@ -120,16 +118,14 @@ __global__ void level_minmax_kernel(const float* __restrict__ grid, LevelTable l
     }
 }
 
-__global__ void level_minmax_init_kernel(unsigned* mm, int levels, const int* __restrict__ active) {
-    if (active && *active == 0) return;
+__global__ void level_minmax_init_kernel(unsigned* mm, int levels) {
     int i = threadIdx.x;
     if (i < 2 * levels) mm[i] = enc_f(0.f);
 }
 
 // s = (beta - alpha) / (2^b - 1), z = round(-alpha / s); all-zero level: s = 1, z = 0
 __global__ void level_scale_zero_kernel(const unsigned* __restrict__ mm, int levels, int bits,
-                                        float* __restrict__ scale, float* __restrict__ zero, const int* __restrict__ active) {
-    if (active && *active == 0) return;
+                                        float* __restrict__ scale, float* __restrict__ zero) {
     int l = threadIdx.x;
     if (l >= levels) return;
     float a = dec_f(mm[2 * l]), b = dec_f(mm[2 * l + 1]);
@@ -207,11 +203,11 @@ LevelTable level_table(const ntbc_model_desc& d, const ntbc_layout& L) {
 }
 
 ntbc_status launch_level_scale_zero(const float* grid, const LevelTable& lt, int bits, unsigned* mm, float* scale,
-                                    float* zero, cudaStream_t s, const int* active) {
-    level_minmax_init_kernel<<<1, 64, 0, s>>>(mm, lt.levels, active);
+                                    float* zero, cudaStream_t s) {
+    level_minmax_init_kernel<<<1, 64, 0, s>>>(mm, lt.levels);
     dim3 g(64, lt.levels);
-    level_minmax_kernel<<<g, 256, 0, s>>>(grid, lt, mm, active);
-    level_scale_zero_kernel<<<1, 32, 0, s>>>(mm, lt.levels, bits, scale, zero, active);
+    level_minmax_kernel<<<g, 256, 0, s>>>(grid, lt, mm);
+    level_scale_zero_kernel<<<1, 32, 0, s>>>(mm, lt.levels, bits, scale, zero);
     NTBC_CHECK_LAUNCH("grid level scale / zero point");
     return NTBC_OK;
 }

@@ -27,13 +27,11 @@ struct StepState {
     long long step;          // current step index (0-based)
     float lr_grid, lr_mlp;   // scheduled learning rates of this step
     float bc1, bc2;          // Adam bias corrections 1 - beta^(step+1)
-    int qat;                 // 1 while the QAT phase fake-quantises the grids
 };
 
-// The scheduled quantities of one step (what step_begin_kernel writes into StepState).
+// The scheduled quantities of one step, copied into StepState at the start of the step.
 struct StepSchedule {
     float lr_grid, lr_mlp, bc1, bc2;
-    int qat;
 };
 
 struct NetBuffers {
@@ -58,7 +56,6 @@ struct ntbc_train_state {
     float* qscale = nullptr;          // [levels] QAT scale / zero of this step
     float* qzero = nullptr;
     unsigned* qmm = nullptr;
-    int* qat_flag = nullptr;          // points at st->qat
     unsigned char* tc_img = nullptr;  // BF16 weight images of both networks (tensor-core training)
     float* tc_part = nullptr;         // weight-gradient partial sums of the tensor-core pass
     int tc_part_rows = 0;
@@ -88,11 +85,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-__global__ void sample_kernel(uint64_t seed, const StepState* __restrict__ st, long long explicit_step, int n,
-                              int n_blocks, int32_t* __restrict__ ids) {
+// With a schedule table (a captured training step) thread 0 also publishes the step's LR and
+// bias corrections into the step state before anything of the step reads them.
+__global__ void sample_kernel(uint64_t seed, StepState* __restrict__ st, const StepSchedule* __restrict__ tab,
+                              long long total_steps, long long explicit_step, int n, int n_blocks,
+                              int32_t* __restrict__ ids) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     long long step = st ? st->step : explicit_step;
+    if (tab && i == 0 && step >= 0 && step < total_steps) {
+        const StepSchedule q = tab[step];
+        st->lr_grid = q.lr_grid;
+        st->lr_mlp = q.lr_mlp;
+        st->bc1 = q.bc1;
+        st->bc2 = q.bc2;
+    }
     uint4 w = philox4x32_10(make_uint4((uint32_t)(i >> 2), (uint32_t)step, 0u, 0u),
                             make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
     uint32_t word = (i & 3) == 0 ? w.x : (i & 3) == 1 ? w.y : (i & 3) == 2 ? w.z : w.w;
@@ -100,13 +107,13 @@ __global__ void sample_kernel(uint64_t seed, const StepState* __restrict__ st, l
 }
 
 // ---------------------------------------------------------------------------
-// step bookkeeping: schedule, bias corrections, QAT phase flag
+// step bookkeeping: schedule and bias corrections
 // ---------------------------------------------------------------------------
 
-// LR (linear warm-up, then cosine to 0 over all steps, Sec. 3.4), Adam bias corrections and
-// the QAT flag of step t
-__device__ __forceinline__ StepSchedule schedule_of(long long t, long long main_steps, long long total_steps,
-                                                    float lr_grid, float lr_mlp, int warmup, int qat_bits) {
+// LR (linear warm-up, then cosine to 0 over all steps, Sec. 3.4) and Adam bias corrections
+// of step t
+__device__ __forceinline__ StepSchedule schedule_of(long long t, long long total_steps, float lr_grid, float lr_mlp,
+                                                    int warmup) {
     double f;
     if (t < warmup) {
         f = (double)(t + 1) / warmup;
@@ -119,42 +126,28 @@ __device__ __forceinline__ StepSchedule schedule_of(long long t, long long main_
     q.lr_mlp = (float)(lr_mlp * f);
     q.bc1 = (float)(1.0 - pow(kAdamB1, (double)(t + 1)));
     q.bc2 = (float)(1.0 - pow(kAdamB2, (double)(t + 1)));
-    q.qat = (qat_bits > 0 && t >= main_steps) ? 1 : 0;
     return q;
 }
 
 // every step's schedule at once (one thread per step), before the step loop
-__global__ void schedule_kernel(StepSchedule* tab, long long main_steps, long long total_steps, float lr_grid,
-                                float lr_mlp, int warmup, int qat_bits) {
+__global__ void schedule_kernel(StepSchedule* tab, long long total_steps, float lr_grid, float lr_mlp, int warmup) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total_steps;
          t += (long long)gridDim.x * blockDim.x)
-        tab[t] = schedule_of(t, main_steps, total_steps, lr_grid, lr_mlp, warmup, qat_bits);
+        tab[t] = schedule_of(t, total_steps, lr_grid, lr_mlp, warmup);
 }
 
-// Step t = explicit_step (>= 0) or the running counter: its schedule from the table when one
-// is given, else computed here.
-__global__ void step_begin_kernel(StepState* st, const StepSchedule* tab, long long explicit_step, long long main_steps,
-                                  long long total_steps, float lr_grid, float lr_mlp, int warmup, int qat_bits) {
+// The schedule of step t = explicit_step into the step state (the single-step Adam call).
+__global__ void step_begin_kernel(StepState* st, long long explicit_step, long long total_steps, float lr_grid,
+                                  float lr_mlp, int warmup) {
     if (threadIdx.x != 0) return;
-    long long t = explicit_step >= 0 ? explicit_step : st->step;
-    st->step = t;
-    StepSchedule q = tab && t >= 0 && t < total_steps
-                         ? tab[t]
-                         : schedule_of(t, main_steps, total_steps, lr_grid, lr_mlp, warmup, qat_bits);
+    st->step = explicit_step;
+    const StepSchedule q = schedule_of(explicit_step, total_steps, lr_grid, lr_mlp, warmup);
     st->lr_grid = q.lr_grid;
     st->lr_mlp = q.lr_mlp;
     st->bc1 = q.bc1;
     st->bc2 = q.bc2;
-    st->qat = q.qat;
 }
 
-__global__ void step_end_kernel(StepState* st) {
-    if (threadIdx.x == 0) st->step += 1;
-}
-
-__global__ void set_qat_kernel(StepState* st, int on) {
-    if (threadIdx.x == 0) st->qat = on;
-}
 
 // ---------------------------------------------------------------------------
 // batch gather of grid features
@@ -498,8 +491,10 @@ __device__ __forceinline__ void adam4(float4& P, float4 G, float4& M, float4& V,
 
 // dense Adam over all parameters, two float4 of every array in flight per thread; the
 // streams are touched once per step, so they bypass L2 retention (evict-first hints)
+// advance: a captured training step, whose last kernel this is, moves the step counter on
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, long long n, long long grid_floats, const StepState* __restrict__ st) {
+                            float* __restrict__ v, long long n, long long grid_floats, StepState* __restrict__ st,
+                            int advance) {
     const float inv_bc1 = 1.f / st->bc1, rsb2 = rsqrtf(st->bc2);
     const float step_g = st->lr_grid * inv_bc1, step_m = st->lr_mlp * inv_bc1;
     const long long n4 = n / 4;
@@ -533,6 +528,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
         long long e = 4 * n4 + threadIdx.x;
         adam_one(p[e], g[e], m[e], v[e], e < grid_floats ? step_g : step_m, rsb2);
     }
+    if (advance && blockIdx.x == 0 && threadIdx.x == 0) st->step += 1;   // nothing of this kernel reads it
 }
 
 // ---------------------------------------------------------------------------
@@ -599,7 +595,6 @@ static ntbc_status ensure_train_state(ntbc_model* m, int n_blocks) {
         ts->losses = reinterpret_cast<float*>(ts->loss_acc + 6);
         ts->qzero = ts->qscale + levels;
         ts->qmm = reinterpret_cast<unsigned*>(ts->qscale + 2 * levels);
-        ts->qat_flag = &ts->st->qat;
         NTBC_CHECK_CUDA(cudaMemset(ts->st, 0, sizeof(StepState)));
         ModelView mv = make_view(m->desc, m->layout);
         size_t img = (size_t)train_tc_net_desc(mv, true).img_bytes + train_tc_net_desc(mv, false).img_bytes;
@@ -726,18 +721,16 @@ __global__ void vjp_seed_kernel(const float* __restrict__ Y, int out, int B, con
 }
 
 // grid sources of the FP32 master parameters, with static QAT fake quantisation
-static ntbc_status train_sources(ntbc_model* m, int qat_bits, bool dynamic_qat, GridSrc& csrc, GridSrc& esrc,
+static ntbc_status train_sources(ntbc_model* m, int qat_bits, GridSrc& csrc, GridSrc& esrc,
                                  cudaStream_t s) {
     ntbc_train_state* ts = m->train;
     memset(&csrc, 0, sizeof(csrc));
     csrc.f32 = m->params;
     csrc.qat_bits = qat_bits;
-    csrc.qat_active = dynamic_qat ? ts->qat_flag : nullptr;
     esrc = csrc;
     if (qat_bits > 0) {
         LevelTable lt = level_table(m->desc, m->layout);
-        ntbc_status st = launch_level_scale_zero(m->params, lt, qat_bits, ts->qmm, ts->qscale, ts->qzero, s,
-                                                 dynamic_qat ? ts->qat_flag : nullptr);
+        ntbc_status st = launch_level_scale_zero(m->params, lt, qat_bits, ts->qmm, ts->qscale, ts->qzero, s);
         if (st != NTBC_OK) return st;
         csrc.scale = ts->qscale;
         csrc.zero = ts->qzero;
@@ -748,7 +741,7 @@ static ntbc_status train_sources(ntbc_model* m, int qat_bits, bool dynamic_qat, 
 }
 
 static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const int32_t* ids, int nb, int qat_bits,
-                                bool dynamic_qat, float T, int precision, float* grads, cudaStream_t s) {
+                                float T, int precision, float* grads, cudaStream_t s) {
     ntbc_train_state* ts = m->train;
     ModelView mv = make_view(m->desc, m->layout);
     TexPtrs tp;
@@ -758,7 +751,7 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
         tp.blocks[t] = mat->ref_blocks[t];
     }
     GridSrc csrc, esrc;
-    ntbc_status st0 = train_sources(m, qat_bits, dynamic_qat, csrc, esrc, s);
+    ntbc_status st0 = train_sources(m, qat_bits, csrc, esrc, s);
     if (st0 != NTBC_OK) return st0;
     NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
     NTBC_CHECK_CUDA(cudaMemsetAsync(ts->loss_acc, 0, 6 * sizeof(double), s));
@@ -785,11 +778,35 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
     return NTBC_OK;
 }
 
-static ntbc_status adam_launch(ntbc_model* m, const float* grads, cudaStream_t s) {
+static ntbc_status adam_launch(ntbc_model* m, const float* grads, cudaStream_t s, int advance = 0) {
     long long n = (long long)m->layout.total;
     unsigned g = (unsigned)std::min<long long>(blocks_for(n, 256), 152LL * 16);
-    adam_kernel<<<g, 256, 0, s>>>(m->params, grads, m->adam_m, m->adam_v, n, (long long)m->layout.grid_floats, m->train->st);
+    adam_kernel<<<g, 256, 0, s>>>(m->params, grads, m->adam_m, m->adam_v, n, (long long)m->layout.grid_floats, m->train->st,
+                                  advance);
     NTBC_CHECK_LAUNCH("adam");
+    return NTBC_OK;
+}
+
+// Capture one training step (qbits > 0: a QAT-phase step) as a graph on `cap`.
+static ntbc_status capture_step(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, int nb,
+                                int n_blocks, long long total, int qbits, cudaStream_t cap, cudaGraphExec_t* exec) {
+    ntbc_train_state* ts = m->train;
+    cudaGraph_t graph = nullptr;
+    NTBC_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, ts->sched, total, 0, nb, n_blocks, ts->ids);
+    ntbc_status st = grads_on_ids(m, mat, ts->ids, nb, qbits, cfg->temperature, cfg->precision, ts->grads, cap);
+    if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap, 1);
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (st != NTBC_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return st != NTBC_OK ? st : cuda_fail(ce, "cudaStreamEndCapture");
+    }
+    ce = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        *exec = nullptr;
+        return cuda_fail(ce, "cudaGraphInstantiate");
+    }
     return NTBC_OK;
 }
 
@@ -803,7 +820,7 @@ ntbc_status ntbc_sample_blocks(uint64_t seed, long step, int n, int n_blocks, in
     clear_error();
     if (!ids || n < 0 || n_blocks <= 0) return fail(NTBC_EINVAL, "need ids, n >= 0 and n_blocks > 0");
     if (n == 0) return NTBC_OK;
-    sample_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(seed, nullptr, step, n, n_blocks, ids);
+    sample_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(seed, nullptr, nullptr, 0, step, n, n_blocks, ids);
     NTBC_CHECK_LAUNCH("sample blocks");
     return NTBC_OK;
 }
@@ -821,7 +838,7 @@ ntbc_status ntbc_train_grads(ntbc_model* m, const ntbc_material* mat, const int3
     st = ensure_train_state(m, n_blocks);
     if (st != NTBC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    st = grads_on_ids(m, mat, block_ids, n_blocks, qat_bits, false, temperature, precision, grads, s);
+    st = grads_on_ids(m, mat, block_ids, n_blocks, qat_bits, temperature, precision, grads, s);
     if (st != NTBC_OK) return st;
     if (losses) NTBC_CHECK_CUDA(cudaMemcpyAsync(losses, m->train->losses, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return NTBC_OK;
@@ -839,7 +856,7 @@ ntbc_status ntbc_vjp(ntbc_model* m, const int32_t* block_ids, int n_blocks, int 
     if (st != NTBC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     GridSrc csrc, esrc;
-    st = train_sources(m, qat_bits, false, csrc, esrc, s);
+    st = train_sources(m, qat_bits, csrc, esrc, s);
     if (st != NTBC_OK) return st;
     ModelView mv = make_view(m->desc, m->layout);
     if (g_e) NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
@@ -870,8 +887,7 @@ ntbc_status ntbc_adam_step(ntbc_model* m, const float* grads, long step, long to
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), s));
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), s));
     }
-    step_begin_kernel<<<1, 32, 0, s>>>(m->train->st, nullptr, step, total_steps, total_steps, cfg->lr_grid, cfg->lr_mlp,
-                                       cfg->warmup, 0);
+    step_begin_kernel<<<1, 32, 0, s>>>(m->train->st, step, total_steps, cfg->lr_grid, cfg->lr_mlp, cfg->warmup);
     NTBC_CHECK_LAUNCH("step begin");
     return adam_launch(m, grads, s);
 }
@@ -917,34 +933,23 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
         ts->sched_cap = total;
     }
     schedule_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 1024), 256, 0, cap>>>(
-        ts->sched, cfg->steps, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup, qbits);
+        ts->sched, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup);
     NTBC_CHECK_LAUNCH("step schedule");
-    // capture one step; every quantity that changes per step lives in StepState
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    NTBC_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    step_begin_kernel<<<1, 32, 0, cap>>>(ts->st, ts->sched, -1, cfg->steps, total, cfg->lr_grid, cfg->lr_mlp, cfg->warmup,
-                                         qbits);
-    sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, 0, nb, n_blocks, ts->ids);
-    st = grads_on_ids(m, mat, ts->ids, nb, qbits, true, cfg->temperature, cfg->precision, ts->grads, cap);
-    if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap);
-    step_end_kernel<<<1, 32, 0, cap>>>(ts->st);
-    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    if (st != NTBC_OK || ce != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cap);
-        return st != NTBC_OK ? st : cuda_fail(ce, "cudaStreamEndCapture");
+    // one graph per phase (the main phase without the QAT kernels, the QAT phase with them),
+    // each launched once per step; every quantity that changes per step lives in StepState
+    cudaGraphExec_t exec_main = nullptr, exec_qat = nullptr;
+    st = capture_step(m, mat, cfg, nb, n_blocks, total, 0, cap, &exec_main);
+    if (st == NTBC_OK && qat_steps > 0) st = capture_step(m, mat, cfg, nb, n_blocks, total, qbits, cap, &exec_qat);
+    cudaError_t ce = cudaSuccess;
+    if (st == NTBC_OK) {
+        for (long long t = 0; t < cfg->steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_main, cap);
+        for (long long t = 0; t < qat_steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_qat, cap);
     }
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) {
-        cudaStreamDestroy(cap);
-        return cuda_fail(ce, "cudaGraphInstantiate");
-    }
-    for (long long t = 0; t < total && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec, cap);
     cudaError_t se = cudaStreamSynchronize(cap);
-    cudaGraphExecDestroy(exec);
+    if (exec_main) cudaGraphExecDestroy(exec_main);
+    if (exec_qat) cudaGraphExecDestroy(exec_qat);
     cudaStreamDestroy(cap);
+    if (st != NTBC_OK) return st;
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphLaunch");
     if (se != cudaSuccess) return cuda_fail(se, "training steps");
     int tc_err = 0;

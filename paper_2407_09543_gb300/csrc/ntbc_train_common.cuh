@@ -225,7 +225,7 @@ __device__ __forceinline__ void scatter_sample(const ModelView& mv, bool color, 
     float u, v;
     int x, y;
     sample_coords(mv, color, ids, kc, u, v, x, y);
-    int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+    const int qat_bits = src.qat_bits;
     const Neighbours nb = color ? neighbours(u, v) : Neighbours();
 #pragma unroll
     for (int l = 0; l < NTBC_MAX_LEVELS; ++l) {              // unrolled: g stays in registers

@@ -437,7 +437,7 @@ __device__ __forceinline__ void gather_level_train(const NetView& nv, const Grid
 
 __device__ __forceinline__ void gather_row_train(const NetView& nv, const GridSrc& src, float u, float v,
                                                  unsigned char* X, int r, int K0) {
-    const int qat_bits = src.qat_active ? (*src.qat_active ? src.qat_bits : 0) : src.qat_bits;
+    const int qat_bits = src.qat_bits;
     for (int l = 0; l < nv.levels; ++l) {               // both corner rows of every level into L1
         Bilinear bl = bilinear_at(nv.res[l], u, v);
         const float* gp = src.f32 + nv.grid_off[l] + bl.base;
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
         if (!COLOR) {
             // ---- gather of the tile's 128 blocks, one (block, level) item per thread over all
             // 16 warps; the blocks' coordinates stay in shared memory for the scatter
-            const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+            const int qat_bits = a.src.qat_bits;
             for (int p = threadIdx.x; p < kTrRows * nv.levels; p += blockDim.x) {
                 const int rr = p % kTrRows, lv = p / kTrRows, sb = tile * kTrRows + rr;
                 float u, v;
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
 #pragma unroll
                     for (int j = 0; j < 32; ++j) gs[j] = gx[j];
                     if (COLOR) {          // texels: warp-aggregated along the block's rows and columns
-                        const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+                        const int qat_bits = a.src.qat_bits;
                         const Neighbours nbr = neighbours(su, sv);
 #pragma unroll 1
                         for (int lv = 0; lv < nv.levels; ++lv)
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
             // blocks: the (sample, level) scatter items spread over all 16 warps
             __syncthreads();
             if (abort[0]) break;
-            const int qat_bits = a.src.qat_active ? (*a.src.qat_active ? a.src.qat_bits : 0) : a.src.qat_bits;
+            const int qat_bits = a.src.qat_bits;
             const float* gs_all = reinterpret_cast<const float*>(G.D);
             for (int p = threadIdx.x; p < kTrRows * nv.levels; p += blockDim.x) {
                 const int rr = p % kTrRows, lv = p / kTrRows, sb = tile * kTrRows + rr;
