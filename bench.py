@@ -195,13 +195,19 @@ def ssim_gpu(torch, a, b):
     """Mean SSIM (Wang et al. 2004; Sec. 4.1 reports it beside PSNR) of two H x W x C uint8
     images on the GPU: 11 x 11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2 on values
     in [0, 1], valid region only, averaged over the channels."""
-    import torch.nn.functional as F
     g = torch.exp(-((torch.arange(11, device=a.device, dtype=torch.float64) - 5.0) ** 2) / (2 * 1.5 ** 2))
     g = g / g.sum()
-    gx, gy = g.view(1, 1, 1, 11), g.view(1, 1, 11, 1)
+    taps = [float(w) for w in g.cpu()]
 
-    def win(t):                      # the separable 11 x 11 Gaussian window, valid region
-        return F.conv2d(F.conv2d(t, gx), gy)
+    def blur(t, dim):                # one 11-tap pass along `dim`, valid region (FP64 adds)
+        n = t.shape[dim] - 10
+        acc = t.narrow(dim, 0, n) * taps[0]
+        for k in range(1, 11):
+            acc = acc + t.narrow(dim, k, n) * taps[k]
+        return acc
+
+    def win(t):                      # the separable 11 x 11 Gaussian window
+        return blur(blur(t, 3), 2)
 
     x = a.double().permute(2, 0, 1)[:, None] / 255.0
     y = b.double().permute(2, 0, 1)[:, None] / 255.0
