@@ -255,6 +255,20 @@ ntbc_status ntbc_model_load(ntbc_model* model, const uint8_t* blob, size_t size,
 ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out, void* stream);
 
 /*
+ * The same inference with the blocks delivered to HOST memory: the material's blocks are
+ * produced in `chunks` (1..16) consecutive ranges of whole 128-block work units, and each
+ * range is copied device -> host (one copy per texture, on a copy stream the model keeps)
+ * while the next range is computed, so the transfer hides behind the inference.
+ *   host_out  host array of n_textures HOST pointers, each (w/4)*(h/4)*8 bytes; pinned
+ *             memory lets the copies overlap the compute (pageable memory still works)
+ * Everything is ordered before later work on `stream`: the blocks are in host_out once
+ * `stream` has been synchronised. The first call allocates a device staging area of the
+ * material's block bytes, the block ids 0..n-1, a stream and events, all kept by the model
+ * until ntbc_model_free; calls on one model must not overlap.
+ */
+ntbc_status ntbc_infer_to_host(ntbc_model* model, uint8_t* const* host_out, int chunks, void* stream);
+
+/*
  * The same with a block stride per texture: block b of texture t is written at
  * blocks_out[t] + b * block_stride[t] (a positive multiple of 8; NULL means 8 for all). With
  * stride 16 two textures of the model fill one 16-byte-block texture: a BC4 alpha texture

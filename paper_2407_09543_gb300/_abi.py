@@ -115,6 +115,7 @@ _SIGS = {
     "ntbc_infer_to_bc": (c_int, [_P, ctypes.POINTER(_P), _P]),
     "ntbc_forward": (c_int, [_P, _P, c_int, _P, _P, _P]),
     "ntbc_infer_to_bc_strided": (c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(c_int), _P]),
+    "ntbc_infer_to_host": (c_int, [_P, ctypes.POINTER(_P), c_int, _P]),
     "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, c_int, _P, _P, _P]),
     "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
                                          c_float, _P, _P, _P]),
@@ -254,6 +255,12 @@ class Model:
         else:
             st = (c_int * len(strides))(*strides)
             _check(lib.ntbc_infer_to_bc_strided(self.handle, arr, st, _stream(stream)))
+
+    def infer_to_host(self, host_out, chunks=4, stream=None):
+        """host_out: per texture a host tensor (pinned for overlap) or int address of its first
+        block; the blocks are there once the stream has been synchronised."""
+        arr = (_P * len(host_out))(*[_ptr(b) for b in host_out])
+        _check(lib.ntbc_infer_to_host(self.handle, arr, chunks, _stream(stream)))
 
     def forward(self, block_ids, e_hat, c_hat, stream=None):
         _check(lib.ntbc_forward(self.handle, _ptr(block_ids), block_ids.numel(), _ptr(e_hat), _ptr(c_hat),

@@ -270,6 +270,70 @@ static ntbc_status launch_simt(const ntbc_model* m, const OutPtrs& outs, const i
     return NTBC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// host delivery (ntbc_infer_to_host): device staging of the blocks, block ids 0 .. n-1 for
+// the ranged launches, a copy stream and its events, kept by the model
+// ---------------------------------------------------------------------------
+
+constexpr int kHostIoMaxChunks = 16;
+
+}  // namespace ntbc
+
+struct ntbc_host_io {
+    uint8_t* stage = nullptr;                         // n_textures x n blocks x 8 bytes
+    int32_t* ids = nullptr;                           // 0 .. n - 1
+    cudaStream_t copy = nullptr;
+    cudaEvent_t done[ntbc::kHostIoMaxChunks] = {};    // range c computed
+    cudaEvent_t copied = nullptr;                     // every range on the host
+};
+
+namespace ntbc {
+
+__global__ void iota_kernel(int32_t* __restrict__ ids, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) ids[i] = i;
+}
+
+static void host_io_destroy(ntbc_host_io* io) {
+    if (!io) return;
+    if (io->copy) {
+        cudaStreamSynchronize(io->copy);
+        cudaStreamDestroy(io->copy);
+    }
+    for (int c = 0; c < kHostIoMaxChunks; ++c)
+        if (io->done[c]) cudaEventDestroy(io->done[c]);
+    if (io->copied) cudaEventDestroy(io->copied);
+    cudaFree(io->stage);
+    cudaFree(io->ids);
+    delete io;
+}
+
+void host_io_release(ntbc_model* m) {
+    host_io_destroy(m->host_io);
+    m->host_io = nullptr;
+}
+
+static ntbc_status host_io_prepare(ntbc_model* m, int n, cudaStream_t s) {
+    if (m->host_io) return NTBC_OK;
+    ntbc_host_io* io = new ntbc_host_io();
+    ntbc_status st = device_alloc((void**)&io->stage, (size_t)m->desc.n_textures * n * 8, "host-delivery staging");
+    if (st == NTBC_OK) st = device_alloc((void**)&io->ids, (size_t)n * sizeof(int32_t), "block ids");
+    cudaError_t e = cudaSuccess;
+    if (st == NTBC_OK) e = cudaStreamCreateWithFlags(&io->copy, cudaStreamNonBlocking);
+    for (int c = 0; c < kHostIoMaxChunks && st == NTBC_OK && e == cudaSuccess; ++c)
+        e = cudaEventCreateWithFlags(&io->done[c], cudaEventDisableTiming);
+    if (st == NTBC_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&io->copied, cudaEventDisableTiming);
+    if (st == NTBC_OK && e == cudaSuccess) {
+        iota_kernel<<<(unsigned)std::min((n + 255) / 256, 152 * 8), 256, 0, s>>>(io->ids, n);
+        e = cudaGetLastError();
+    }
+    if (st != NTBC_OK || e != cudaSuccess) {
+        host_io_destroy(io);
+        return st != NTBC_OK ? st : cuda_fail(e, "host-delivery set-up");
+    }
+    m->host_io = io;
+    return NTBC_OK;
+}
+
 }  // namespace ntbc
 
 using namespace ntbc;
@@ -302,6 +366,68 @@ ntbc_status ntbc_infer_to_bc_strided(const ntbc_model* m, uint8_t* const* blocks
 
 ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, void* stream) {
     return ntbc_infer_to_bc_strided(m, blocks_out, nullptr, stream);
+}
+
+ntbc_status ntbc_infer_to_host(ntbc_model* m, uint8_t* const* host_out, int chunks, void* stream) {
+    clear_error();
+    if (!m || !host_out) return fail(NTBC_EINVAL, "null argument");
+    if (chunks < 1 || chunks > kHostIoMaxChunks) return fail(NTBC_EINVAL, "chunks must be 1..%d", kHostIoMaxChunks);
+    if (m->grid_bits < 0) return fail(NTBC_EINVAL, "model has not been exported (call ntbc_model_export or ntbc_model_load)");
+    for (int t = 0; t < m->desc.n_textures; ++t)
+        if (!host_out[t]) return fail(NTBC_EINVAL, "null output pointer for texture %d", t);
+    const int n = (m->desc.width / 4) * (m->desc.height / 4);
+    cudaStream_t s = (cudaStream_t)stream;
+    ntbc_status st = host_io_prepare(m, n, s);
+    if (st != NTBC_OK) return st;
+    ntbc_host_io* io = m->host_io;
+    const int T = m->desc.n_textures;
+    uint8_t* stage[NTBC_MAX_TEXTURES];
+    int strides[NTBC_MAX_TEXTURES];
+    for (int t = 0; t < T; ++t) {
+        stage[t] = io->stage + (size_t)t * n * 8;
+        strides[t] = 8;
+    }
+    // ranges of whole work units (128 blocks); on the tensor-core path every range but the
+    // last is a whole number of rounds of the units in flight, so the ranged launches take no
+    // more rounds than one launch over the material would
+    const int units = (n + 127) / 128;
+    int per_units = (units + chunks - 1) / chunks;
+    const int flight = m->weight_prec != NTBC_PREC_FP32 ? tc_units_in_flight(m) : 0;
+    if (flight > 0) {
+        const int rounds = (units + flight - 1) / flight;
+        per_units = (rounds + chunks - 1) / chunks * flight;
+    }
+    const int per = per_units * 128;
+    GridSrc csrc, esrc;
+    if (m->weight_prec != NTBC_PREC_FP32) {
+        st = grid_sources(m, csrc, esrc);
+        if (st != NTBC_OK) return st;
+    }
+    int c = 0;
+    for (int first = 0; first < n; first += per, ++c) {
+        const int cnt = std::min(per, n - first);
+        if (m->weight_prec != NTBC_PREC_FP32) {
+            st = tc_launch(m, stage, strides, io->ids + first, cnt, nullptr, nullptr, csrc, esrc, s);
+        } else {
+            OutPtrs outs;
+            memset(&outs, 0, sizeof(outs));
+            for (int t = 0; t < T; ++t) {
+                outs.p[t] = stage[t];
+                outs.stride[t] = 8;
+            }
+            st = launch_simt<MODE_PACK>(m, outs, io->ids + first, cnt, nullptr, nullptr, s);
+        }
+        if (st != NTBC_OK) return st;
+        // this range's blocks go to the host on the copy stream while the next range runs
+        NTBC_CHECK_CUDA(cudaEventRecord(io->done[c], s));
+        NTBC_CHECK_CUDA(cudaStreamWaitEvent(io->copy, io->done[c], 0));
+        for (int t = 0; t < T; ++t)
+            NTBC_CHECK_CUDA(cudaMemcpyAsync(host_out[t] + (size_t)first * 8, stage[t] + (size_t)first * 8,
+                                            (size_t)cnt * 8, cudaMemcpyDeviceToHost, io->copy));
+    }
+    NTBC_CHECK_CUDA(cudaEventRecord(io->copied, io->copy));
+    NTBC_CHECK_CUDA(cudaStreamWaitEvent(s, io->copied, 0));
+    return NTBC_OK;
 }
 
 ntbc_status ntbc_forward(const ntbc_model* m, const int32_t* block_ids, int n, float* e_hat, float* c_hat, void* stream) {

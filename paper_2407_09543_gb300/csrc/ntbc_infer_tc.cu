@@ -746,10 +746,14 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
 // bias in column `in` (layer 0) or column 64 (the extra K block of later layers)
 // ---------------------------------------------------------------------------
 
+// Every element of every tile is written (weights, the bias column, zeros elsewhere); only the
+// padding behind the last tile is zeroed separately, so any number of CTAs can share the work.
 __global__ void build_image_kernel(const float* __restrict__ params, TcArgs args, ModelView mv, __half* __restrict__ img) {
-    int total = args.img_bytes / 2;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) img[e] = __float2half(0.f);
-    __syncthreads();
+    const TcNet& last_net = args.net[1];
+    const TcLayer& last = last_net.layer[last_net.n_layers - 1];
+    const int tiles_end = (last.img + last.N * last.K * 2) / 2, total = args.img_bytes / 2;
+    for (int e = tiles_end + blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x)
+        img[e] = __float2half(0.f);
     // one pass per (net, layer): element (n, k)
     for (int net = 0; net < 2; ++net) {
         const NetView& nv = net ? mv.endpoint : mv.color;
@@ -820,9 +824,19 @@ ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s) {
     }
     m->tc_err = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(m->umma_img) + a.img_bytes);
     NTBC_CHECK_CUDA(cudaMemsetAsync(m->tc_err, 0, sizeof(int), s));
-    build_image_kernel<<<1, 1024, 0, s>>>(m->infer_params, a, a.mv, m->umma_img);
+    build_image_kernel<<<32, 256, 0, s>>>(m->infer_params, a, a.mv, m->umma_img);
     NTBC_CHECK_LAUNCH("tensor-core weight image");
     return NTBC_OK;
+}
+
+int tc_units_in_flight(const ntbc_model* m) {
+    TcArgs a = tc_args(m);
+    size_t smem = 0;
+    const int groups = tc_groups(a, m->desc.n_textures, m->weight_prec != NTBC_PREC_FP16_FAST, &smem);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return groups * sms;
 }
 
 ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,

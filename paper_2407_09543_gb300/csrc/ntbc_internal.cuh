@@ -73,6 +73,7 @@ struct ntbc_model {
     __half* umma_img = nullptr;         // FP16 weights in the tensor-core shared-memory layout
     int* tc_err = nullptr;              // set by the tensor-core kernel when a bounded wait gives up
     struct ntbc_train_state* train = nullptr;   // training scratch (allocated on first use)
+    struct ntbc_host_io* host_io = nullptr;     // staging of ntbc_infer_to_host (allocated on first use)
 };
 
 namespace ntbc {
@@ -102,6 +103,7 @@ struct ModelView {
 };
 
 ModelView make_view(const ntbc_model_desc& d, const ntbc_layout& L);
+void host_io_release(ntbc_model* m);
 
 // ---------------------------------------------------------------------------
 // device helpers: SELU, sigmoid, BC palettes, packing, output decisions

@@ -393,6 +393,7 @@ void ntbc_model_free(ntbc_model* m) {
     cudaFree(m->w8);                     // also holds w8_exp
     cudaFree(m->umma_img);               // also holds tc_err
     ntbc_train_release(m);
+    host_io_release(m);
     delete m;
 }
 

@@ -155,6 +155,38 @@ def test_blob_roundtrip_reproduces_blocks():
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("side,height,chunks,prec", [(68, 60, 1, 1), (68, 60, 3, 1), (256, 256, 16, 1),
+                                                     (256, 192, 5, 2), (132, 100, 4, 0)])
+def test_infer_to_host_matches_device(side, height, chunks, prec):
+    # blocks delivered to pinned host memory range by range equal the device-resident result;
+    # 68 x 60 is 255 blocks (a ragged last work unit), 256^2 with 16 ranges of 256 blocks
+    mat, desc, odesc, params = make_case(side=side, height=height, levels=3, lo=4, hi=16)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=prec)
+    want = gpu_blocks(model, desc)
+    n = (desc.width // 4) * (desc.height // 4)
+    host = [torch.zeros(n * 8, dtype=torch.uint8).pin_memory() for _ in range(desc.n_textures)]
+    model.infer_to_host(host, chunks=chunks)
+    torch.cuda.synchronize()
+    for a, h in zip(want, host):
+        np.testing.assert_array_equal(a, h.numpy().reshape(-1, 8))
+    # a second call reuses the staging the model keeps
+    for h in host:
+        h.zero_()
+    model.infer_to_host(host, chunks=chunks)
+    torch.cuda.synchronize()
+    for a, h in zip(want, host):
+        np.testing.assert_array_equal(a, h.numpy().reshape(-1, 8))
+
+
+def test_infer_to_host_rejects_bad_chunks():
+    mat, desc, odesc, params = make_case(side=64, levels=3, lo=4, hi=16)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    host = [torch.zeros(16 * 16 * 8, dtype=torch.uint8) for _ in range(desc.n_textures)]
+    for bad in (0, 17):
+        with pytest.raises(nt.NTBCError):
+            model.infer_to_host(host, chunks=bad)
+
+
 def test_blob_u4_packed_two_codes_per_byte():
     # a 4-bit export stores two grid codes per byte (low nibble first): the blob is half a
     # byte per grid value smaller than the 8-bit one, its packed part matches the exported
