@@ -269,6 +269,15 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out
 ntbc_status ntbc_infer_to_host(ntbc_model* model, uint8_t* const* host_out, int chunks, void* stream);
 
 /*
+ * Failure-path check of the bounded device waits: one thread polls an mbarrier that nothing
+ * will complete, with the wait loop of the tensor-core kernels limited to `polls` polls
+ * (1 .. the kernels' own limit, 2^18, about one second). Returns NTBC_ETIMEOUT when the wait gave up (the
+ * expected outcome; the GPU context stays usable) and the wait's duration in *seconds
+ * (optional). Synchronises `stream`.
+ */
+ntbc_status ntbc_wait_probe(long long polls, double* seconds, void* stream);
+
+/*
  * The same with a block stride per texture: block b of texture t is written at
  * blocks_out[t] + b * block_stride[t] (a positive multiple of 8; NULL means 8 for all). With
  * stride 16 two textures of the model fill one 16-byte-block texture: a BC4 alpha texture

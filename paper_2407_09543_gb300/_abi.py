@@ -116,6 +116,7 @@ _SIGS = {
     "ntbc_forward": (c_int, [_P, _P, c_int, _P, _P, _P]),
     "ntbc_infer_to_bc_strided": (c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(c_int), _P]),
     "ntbc_infer_to_host": (c_int, [_P, ctypes.POINTER(_P), c_int, _P]),
+    "ntbc_wait_probe": (c_int, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
     "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, c_int, _P, _P, _P]),
     "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
                                          c_float, _P, _P, _P]),
@@ -185,6 +186,14 @@ def ntbc_model_layout(desc: ModelDesc) -> Layout:
 
 def ntbc_sample_blocks(seed, step, n, n_blocks, ids, stream=None):
     _check(lib.ntbc_sample_blocks(seed, step, n, n_blocks, _ptr(ids), _stream(stream)))
+
+
+def ntbc_wait_probe(polls, stream=None):
+    """Bounded-wait failure path: returns (status, seconds); NTBC_ETIMEOUT (4) is the expected
+    status (the wait on an mbarrier that nothing completes gave up)."""
+    sec = ctypes.c_double(0.0)
+    status = lib.ntbc_wait_probe(polls, ctypes.byref(sec), _stream(stream))
+    return status, sec.value
 
 
 NOALLOC_MAX_BLOCKS = 128

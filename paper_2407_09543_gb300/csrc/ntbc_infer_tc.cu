@@ -742,6 +742,27 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
 }
 
 // ---------------------------------------------------------------------------
+// bounded-wait probe: an mbarrier that expects one arrival that never comes, polled with the
+// waits of the tensor-core kernels under a given poll limit; records that the wait gave up
+// and how long it took (the failure path of every MMA wait, without any GPU fault)
+// ---------------------------------------------------------------------------
+
+__global__ void wait_probe_kernel(long long polls, int* __restrict__ gave_up, unsigned long long* __restrict__ ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = global_ns();
+        const bool done = mbar_wait(&bar, 0, polls);
+        *ns = global_ns() - t0;
+        *gave_up = done ? 0 : 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // weight image: every layer's B tile [N][K] (FP16, core-matrix layout) with the
 // bias in column `in` (layer 0) or column 64 (the extra K block of later layers)
 // ---------------------------------------------------------------------------
@@ -900,6 +921,28 @@ static ntbc_status batch_fail_free(ntbc_batch* b, ntbc_status st) {
 }  // namespace ntbc
 
 extern "C" {
+
+ntbc_status ntbc_wait_probe(long long polls, double* seconds, void* stream) {
+    using namespace ntbc;
+    clear_error();
+    if (polls < 1 || polls > ntbc::kTcWaitLimit) return fail(NTBC_EINVAL, "polls must be 1..%lld", ntbc::kTcWaitLimit);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* d = nullptr;
+    ntbc_status st = device_alloc((void**)&d, 2 * sizeof(unsigned long long), "wait probe");
+    if (st != NTBC_OK) return st;
+    ntbc::wait_probe_kernel<<<1, 32, 0, s>>>(polls, reinterpret_cast<int*>(d + 1), d);
+    cudaError_t e = cudaGetLastError();
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+    const double sec = (double)h[0] * 1e-9;
+    if (seconds) *seconds = sec;
+    const int gave_up = *reinterpret_cast<const int*>(&h[1]);
+    if (gave_up) return fail(NTBC_ETIMEOUT, "bounded wait gave up after %lld polls (%.3f s)", polls, sec);
+    return NTBC_OK;
+}
 
 ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out, ntbc_batch** out) {
     using namespace ntbc;

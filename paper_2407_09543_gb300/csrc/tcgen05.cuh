@@ -8,8 +8,9 @@
 namespace ntbc {
 
 // polls of an mbarrier before a wait gives up (the caller then records an error,
-// lets in-flight MMAs land and returns instead of hanging the GPU)
-constexpr long long kTcWaitLimit = 1LL << 26;
+// lets in-flight MMAs land and returns instead of hanging the GPU); an unsuccessful
+// try_wait suspends the thread for ~3.8 us on GB300, so the limit is about one second
+constexpr long long kTcWaitLimit = 1LL << 18;
 
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -45,9 +46,9 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long long limit = kTcWaitLimit) {
     uint32_t done = 0;
-    for (long long it = 0; it < kTcWaitLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(smem_u32(bar)), "r"(phase));

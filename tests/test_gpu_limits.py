@@ -151,3 +151,28 @@ def test_empty_block_list():
     m.forward(torch.empty(0, dtype=torch.int32, device=DEV), e, c)
     torch.cuda.synchronize()
     assert float(e.abs().sum()) == 0.0 and float(c.abs().sum()) == 0.0
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    # the failure path of every MMA wait: an mbarrier that nothing completes, polled with the
+    # kernels' bounded loop under a small limit, gives up with NTBC_ETIMEOUT, and the GPU
+    # context stays usable (a normal inference right after matches one from before)
+    desc = nt.configs.model_desc([nt.BC1, nt.BC4], 64, 3, 4, 16, 2, nt.ACT_SELU)
+    cres, eres = nt.configs.res_lists(desc)
+    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
+    model = nt.Model(desc)
+    model.set_params(torch.from_numpy(nt.configs.flatten(desc, synth.random_params_like(p0, seed=1))).to("cuda"))
+    model.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+    outs = [torch.empty(16 * 16 * 8, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    model.infer_to_bc(outs)
+    before = [o.clone() for o in outs]
+    for polls in (1, 1 << 12, 1 << 16):
+        status, sec = nt.ntbc_wait_probe(polls)
+        assert status == 4, nt.STATUS_NAMES.get(status, status)
+        assert 0.0 <= sec < 10.0
+    for o in outs:
+        o.zero_()
+    model.infer_to_bc(outs)
+    torch.cuda.synchronize()
+    for a, b in zip(before, outs):
+        assert torch.equal(a, b)
