@@ -86,10 +86,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // With a schedule table (a captured training step) thread 0 also publishes the step's LR and
-// bias corrections into the step state before anything of the step reads them.
+// bias corrections into the step state and clears the step's six loss accumulators, before
+// anything of the step reads them.
 __global__ void sample_kernel(uint64_t seed, StepState* __restrict__ st, const StepSchedule* __restrict__ tab,
                               long long total_steps, long long explicit_step, int n, int n_blocks,
-                              int32_t* __restrict__ ids) {
+                              int32_t* __restrict__ ids, double* __restrict__ loss_acc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     long long step = st ? st->step : explicit_step;
@@ -99,6 +100,7 @@ __global__ void sample_kernel(uint64_t seed, StepState* __restrict__ st, const S
         st->lr_mlp = q.lr_mlp;
         st->bc1 = q.bc1;
         st->bc2 = q.bc2;
+        for (int k = 0; k < 6; ++k) loss_acc[k] = 0.0;
     }
     uint4 w = philox4x32_10(make_uint4((uint32_t)(i >> 2), (uint32_t)step, 0u, 0u),
                             make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
@@ -740,8 +742,10 @@ static ntbc_status train_sources(ntbc_model* m, int qat_bits, GridSrc& csrc, Gri
     return NTBC_OK;
 }
 
+// in_step: inside a captured training step, whose sampler clears the loss accumulators and
+// whose losses are turned into floats once after the last step
 static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const int32_t* ids, int nb, int qat_bits,
-                                float T, int precision, float* grads, cudaStream_t s) {
+                                float T, int precision, float* grads, cudaStream_t s, bool in_step = false) {
     ntbc_train_state* ts = m->train;
     ModelView mv = make_view(m->desc, m->layout);
     TexPtrs tp;
@@ -754,14 +758,13 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
     ntbc_status st0 = train_sources(m, qat_bits, csrc, esrc, s);
     if (st0 != NTBC_OK) return st0;
     NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
-    NTBC_CHECK_CUDA(cudaMemsetAsync(ts->loss_acc, 0, 6 * sizeof(double), s));
+    if (!in_step) NTBC_CHECK_CUDA(cudaMemsetAsync(ts->loss_acc, 0, 6 * sizeof(double), s));
     ntbc_status st;
     if (precision == NTBC_TRAIN_BF16) {
         TrNet cn = train_tc_net_desc(mv, true), en = train_tc_net_desc(mv, false);
         unsigned char* cimg = ts->tc_img;
         unsigned char* eimg = ts->tc_img + cn.img_bytes;
-        st = train_tc_image(m->params, cn, cimg, s);
-        if (st == NTBC_OK) st = train_tc_image(m->params, en, eimg, s);
+        st = train_tc_images(m->params, cn, cimg, en, eimg, s);
         if (st == NTBC_OK)
             st = train_tc_launch(mv, true, cn, cimg, csrc, tp, ids, nb * 16, T, grads, ts->loss_acc, ts->tc_err,
                                  ts->tc_part, ts->tc_part_rows, s);
@@ -773,6 +776,7 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
         if (st == NTBC_OK) st = run_net(m, mv, false, tp, ids, nb, esrc, T, grads, ts->loss_acc, s);
     }
     if (st != NTBC_OK) return st;
+    if (in_step) return NTBC_OK;
     loss_finalize_kernel<<<1, 32, 0, s>>>(ts->loss_acc, ts->losses);
     NTBC_CHECK_LAUNCH("loss finalize");
     return NTBC_OK;
@@ -793,8 +797,9 @@ static ntbc_status capture_step(ntbc_model* m, const ntbc_material* mat, const n
     ntbc_train_state* ts = m->train;
     cudaGraph_t graph = nullptr;
     NTBC_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, ts->sched, total, 0, nb, n_blocks, ts->ids);
-    ntbc_status st = grads_on_ids(m, mat, ts->ids, nb, qbits, cfg->temperature, cfg->precision, ts->grads, cap);
+    sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, ts->sched, total, 0, nb, n_blocks, ts->ids,
+                                                        ts->loss_acc);
+    ntbc_status st = grads_on_ids(m, mat, ts->ids, nb, qbits, cfg->temperature, cfg->precision, ts->grads, cap, true);
     if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap, 1);
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (st != NTBC_OK || ce != cudaSuccess) {
@@ -820,7 +825,8 @@ ntbc_status ntbc_sample_blocks(uint64_t seed, long step, int n, int n_blocks, in
     clear_error();
     if (!ids || n < 0 || n_blocks <= 0) return fail(NTBC_EINVAL, "need ids, n >= 0 and n_blocks > 0");
     if (n == 0) return NTBC_OK;
-    sample_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(seed, nullptr, nullptr, 0, step, n, n_blocks, ids);
+    sample_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(seed, nullptr, nullptr, 0, step, n, n_blocks, ids,
+                                                                        nullptr);
     NTBC_CHECK_LAUNCH("sample blocks");
     return NTBC_OK;
 }
@@ -944,6 +950,10 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     if (st == NTBC_OK) {
         for (long long t = 0; t < cfg->steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_main, cap);
         for (long long t = 0; t < qat_steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_qat, cap);
+        if (ce == cudaSuccess) {              // the last step's losses
+            loss_finalize_kernel<<<1, 32, 0, cap>>>(ts->loss_acc, ts->losses);
+            ce = cudaGetLastError();
+        }
     }
     cudaError_t se = cudaStreamSynchronize(cap);
     if (exec_main) cudaGraphExecDestroy(exec_main);

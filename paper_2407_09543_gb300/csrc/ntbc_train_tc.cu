@@ -845,9 +845,13 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
     }
 }
 
-// BF16 weight image of one network: per layer the [N][K] tile (W in columns 0..in-1, the
-// bias in column `in`, zeros elsewhere), canonical K-major core-matrix layout
-__global__ void train_image_kernel(const float* __restrict__ params, TrNet net, __nv_bfloat16* __restrict__ img) {
+// BF16 weight images of both networks (blockIdx.y: colour, endpoint): per layer the [N][K]
+// tile (W in columns 0..in-1, the bias in column `in`, zeros elsewhere), canonical K-major
+// core-matrix layout
+__global__ void train_image_kernel(const float* __restrict__ params, TrNet net0, TrNet net1,
+                                   __nv_bfloat16* __restrict__ img0, __nv_bfloat16* __restrict__ img1) {
+    const TrNet& net = blockIdx.y ? net1 : net0;
+    __nv_bfloat16* img = blockIdx.y ? img1 : img0;
     for (int l = 0; l < net.n_layers; ++l) {
         const TrLayer& Ly = net.layer[l];
         __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(img) + Ly.img);
@@ -918,9 +922,11 @@ static TrSmem train_tc_smem(const TrNet& n) {
     return s;
 }
 
-ntbc_status train_tc_image(const float* params, const TrNet& net, unsigned char* img, cudaStream_t s) {
-    train_image_kernel<<<64, 256, 0, s>>>(params, net, reinterpret_cast<__nv_bfloat16*>(img));
-    NTBC_CHECK_LAUNCH("training weight image");
+ntbc_status train_tc_images(const float* params, const TrNet& cnet, unsigned char* cimg, const TrNet& enet,
+                            unsigned char* eimg, cudaStream_t s) {
+    train_image_kernel<<<dim3(32, 2), 256, 0, s>>>(params, cnet, enet, reinterpret_cast<__nv_bfloat16*>(cimg),
+                                                   reinterpret_cast<__nv_bfloat16*>(eimg));
+    NTBC_CHECK_LAUNCH("training weight images");
     return NTBC_OK;
 }
 

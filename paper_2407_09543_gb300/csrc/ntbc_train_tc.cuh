@@ -52,7 +52,8 @@ TrNet train_tc_net_desc(const ModelView& mv, bool color);
 // TMEM columns one warpgroup needs (data accumulator + every weight-gradient accumulator)
 int train_tc_tmem_cols(const TrNet& n);
 // BF16 weight image of the network from the FP32 master parameters (device img, img_bytes)
-ntbc_status train_tc_image(const float* params, const TrNet& net, unsigned char* img, cudaStream_t s);
+ntbc_status train_tc_images(const float* params, const TrNet& cnet, unsigned char* cimg, const TrNet& enet,
+                            unsigned char* eimg, cudaStream_t s);
 // rows of the partial-sum scratch a launch may use (one per warpgroup)
 int train_tc_max_partial_rows();
 // forward + loss + backward of B samples; adds into grads and the loss accumulators;
