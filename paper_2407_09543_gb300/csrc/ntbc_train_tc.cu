@@ -137,37 +137,35 @@ __device__ __forceinline__ float sigmoid_fast(float z) { return rcp_fast(1.f + e
 // ---------------------------------------------------------------------------
 
 // Softmax-expectation backward of the hard decode (App. A, corrected form):
-// g_d[n] = (1/T) sigma_n sum_c g_dec[c] (P[n][c] - sum_i sigma_i P[i][c]), sigma = softmax(d / T)
+// g_d[n] = (1/T) sigma_n sum_c g_dec[c] (P[n][c] - sum_i sigma_i P[i][c]), sigma = softmax(d / T),
+// evaluated as (1/T) sigma_n (v_n - sum_i sigma_i v_i) with v_n = sum_c g_dec[c] P[n][c].
+// Returned already divided by the guarded distance: s_n = g_d[n] inv[n], since every caller
+// goes on through d d_n / d P_n = (x - P_n) / max(||x - P_n||, 1e-6).
 template <int C>
 __device__ __forceinline__ void ste_fast(int K, const float d[8], const float P[8][C], const float g_dec[C], float invT,
-                                         float g_d[8]) {
+                                         const float inv[8], float s[8]) {
+    constexpr int KM = C == 3 ? 4 : 8;
     float m = d[0];
 #pragma unroll
-    for (int n = 1; n < (C == 3 ? 4 : 8); ++n)
+    for (int n = 1; n < KM; ++n)
         if (n < K) m = fmaxf(m, d[n]);
-    float sig[8], sum = 0.f;
+    const float k = invT * kL2e, mk = m * k;
+    float e[8], v[8], sum = 0.f, vbar = 0.f;
 #pragma unroll
-    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
-        sig[n] = n < K ? ex2_fast((d[n] - m) * (invT * kL2e)) : 0.f;
-        sum += sig[n];
-    }
-    const float inv = rcp_fast(sum);
-    float pbar[C];
-#pragma unroll
-    for (int q = 0; q < C; ++q) pbar[q] = 0.f;
-#pragma unroll
-    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
-        sig[n] *= inv;
-#pragma unroll
-        for (int q = 0; q < C; ++q) pbar[q] = fmaf(sig[n], P[n][q], pbar[q]);
-    }
-#pragma unroll
-    for (int n = 0; n < (C == 3 ? 4 : 8); ++n) {
+    for (int n = 0; n < KM; ++n) {
+        e[n] = n < K ? ex2_fast(fmaf(d[n], k, -mk)) : 0.f;
+        sum += e[n];
         float t = 0.f;
 #pragma unroll
-        for (int q = 0; q < C; ++q) t = fmaf(g_dec[q], P[n][q] - pbar[q], t);
-        g_d[n] = sig[n] * t * invT;
+        for (int q = 0; q < C; ++q) t = fmaf(g_dec[q], P[n][q], t);
+        v[n] = t;
+        vbar = fmaf(e[n], t, vbar);
     }
+    const float r = rcp_fast(sum);
+    vbar *= r;
+    const float c = r * invT;
+#pragma unroll
+    for (int n = 0; n < KM; ++n) s[n] = e[n] * c * (v[n] - vbar) * inv[n];
 }
 
 // linear palette P_n = a_n e0 + b_n e1 + c_n (Eq. palette / Eq. weightBC4), distances
@@ -231,12 +229,12 @@ __device__ __forceinline__ void color_texture(int fmt, const float* ch, const fl
         g_dec[q] = -2.f * rr * inv_n;
         g[q] = 2.f * e * inv_n;
     }
-    float g_d[8];
-    ste_fast<C>(K, d, P, g_dec, invT, g_d);
+    float sd[8];
+    ste_fast<C>(K, d, P, g_dec, invT, inv, sd);
 #pragma unroll
     for (int n = 0; n < (C == 3 ? 4 : 8); ++n)
 #pragma unroll
-        for (int q = 0; q < C; ++q) g[q] -= g_d[n] * (ch[q] - P[n][q]) * inv[n];
+        for (int q = 0; q < C; ++q) g[q] = fmaf(-sd[n], ch[q] - P[n][q], g[q]);
 #pragma unroll
     for (int q = 0; q < C; ++q) dz[q] = valid ? g[q] * ch[q] * (1.f - ch[q]) : 0.f;
 }
@@ -367,13 +365,13 @@ __device__ __forceinline__ void endpoint_item(const TrArgs& a, int fmt, int b, i
             if (valid) lcd = fmaf(rr, rr, lcd);
             g_dec[q] = valid ? -2.f * rr * inv_ncd : 0.f;
         }
-        float g_d[8];
-        ste_fast<C>(K, d, Pr, g_dec, invT, g_d);
+        float sd[8];
+        ste_fast<C>(K, d, Pr, g_dec, invT, inv, sd);
 #pragma unroll
         for (int n = 0; n < KM; ++n)
 #pragma unroll
             for (int q = 0; q < C; ++q) {
-                float gp = g_d[n] * (c[q] - Ph[n][q]) * inv[n];   // d d_n / d P_n = (c - P_n) / ||.||
+                float gp = sd[n] * (c[q] - Ph[n][q]);   // d d_n / d P_n = (c - P_n) / ||.||
                 g0[q] = fmaf(ah[n], gp, g0[q]);
                 g1[q] = fmaf(bh[n], gp, g1[q]);
             }
