@@ -1,10 +1,10 @@
 // Tensor-core (tcgen05) form of the fused NTBC inference kernel (Sec. 3.2,
 // Fig. NTBC (a); Sec. 4.4) for FP16 weights, FP32 accumulation in TMEM.
 //
-// One persistent CTA per SM holds up to three independent warpgroups. A
+// One persistent CTA per SM holds up to four independent warpgroups. A
 // warpgroup owns one work unit at a time: 128 consecutive blocks. It runs the
 // endpoint MLP on the 128 blocks as one M = 128 MMA chain, turns the sigmoid
-// outputs into quantised endpoints and FP32 palettes (kept in shared memory),
+// outputs into quantised endpoints and integer palettes (kept in shared memory),
 // then runs the colour MLP on the unit's 2048 texels as 16 tiles of 128 texels
 // (8 blocks each), picks each texel's code and packs the 16 codes of a block
 // with shuffles inside the half-warp that holds the block.
