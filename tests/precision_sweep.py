@@ -35,7 +35,7 @@ def run_sweep(args):
     nblk = (side // 4) ** 2
     mat, desc, p0, tex_d, refs = build_workload(nt, torch, side, seed=0, dev=dev)
     for t, fmt in enumerate(mat.formats):
-        nt.bc_reference_encode(fmt, tex_d[t], side, side, refs[t])
+        nt.bc_reference_encode(fmt, tex_d[t], side, side, refs[t], refine=bench.REF_REFINE)
     torch.cuda.synchronize()
     ref_psnr = bench.psnr_list(nt, torch, mat, refs, side)
     material = nt.Material.make(side, side, mat.formats, tex_d, refs)
