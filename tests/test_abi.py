@@ -76,6 +76,17 @@ def test_host_validation_errors():
         nt.ntbc_level_resolutions(0, 16, 32)
     with pytest.raises(nt.NTBCError):
         nt.ntbc_sample_blocks(0, 0, 10, 0, 1, stream=0)
+    # refinement steps outside 0..16 (valid dummy pointers: nothing is launched)
+    with pytest.raises(nt.NTBCError) as e:
+        nt.bc_reference_encode(1, 16, 8, 8, 16, stream=0, refine=17)
+    assert e.value.status == 1 and "0..16" in str(e.value)
+    # the bounded-wait probe's poll count is checked before anything runs
+    for bad in (0, (1 << 18) + 1):
+        status, _ = nt.ntbc_wait_probe(bad)
+        assert status == 1
+    # host delivery: no model
+    arr = (ctypes.c_void_p * 1)(16)
+    assert nt.lib.ntbc_infer_to_host(None, arr, 4, None) == 1
 
 
 def test_injected_allocation_failure_reports_enomem():
