@@ -791,6 +791,17 @@ static ntbc_status adam_launch(ntbc_model* m, const float* grads, cudaStream_t s
     return NTBC_OK;
 }
 
+// A stream created for one call: drained and destroyed on every return path.
+struct OwnedStream {
+    cudaStream_t s = nullptr;
+    ~OwnedStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+};
+
 // Capture one training step (qbits > 0: a QAT-phase step) as a graph on `cap`.
 static ntbc_status capture_step(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, int nb,
                                 int n_blocks, long long total, int qbits, cudaStream_t cap, cudaGraphExec_t* exec) {
@@ -921,8 +932,9 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     if (st != NTBC_OK) return st;
     ntbc_train_state* ts = m->train;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaStream_t cap;
-    NTBC_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    OwnedStream owned;
+    NTBC_CHECK_CUDA(cudaStreamCreateWithFlags(&owned.s, cudaStreamNonBlocking));
+    cudaStream_t cap = owned.s;
     NTBC_CHECK_CUDA(cudaStreamSynchronize(s));
     NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), cap));
     NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), cap));
@@ -932,10 +944,7 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
         ts->sched = nullptr;
         ts->sched_cap = 0;
         st = device_alloc((void**)&ts->sched, (size_t)total * sizeof(StepSchedule), "step schedule");
-        if (st != NTBC_OK) {
-            cudaStreamDestroy(cap);
-            return st;
-        }
+        if (st != NTBC_OK) return st;
         ts->sched_cap = total;
     }
     schedule_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 1024), 256, 0, cap>>>(
@@ -958,7 +967,6 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     cudaError_t se = cudaStreamSynchronize(cap);
     if (exec_main) cudaGraphExecDestroy(exec_main);
     if (exec_qat) cudaGraphExecDestroy(exec_qat);
-    cudaStreamDestroy(cap);
     if (st != NTBC_OK) return st;
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphLaunch");
     if (se != cudaSuccess) return cuda_fail(se, "training steps");
