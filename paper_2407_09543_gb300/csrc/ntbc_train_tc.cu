@@ -768,7 +768,20 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
     // Layer 0 holds dW_0 (lane = unit o, column = input i, the bias at i = in); later layers
     // hold dW_l^T (lane = input i, the bias at i = in, column = unit o). Warps whose 32 lanes
     // hold nothing skip the layer; the others read only the columns that hold gradients.
-    if (tile_thread && ok) {
+    // In the endpoint kernel the four warps that reach one TMEM lane quarter (w, w + 4,
+    // w + 8, w + 12) share the column chunks, so all 16 warps flush.
+    bool flush = tile_thread && ok, no_tiles = first;
+    int part_id = 0, nparts = 1;
+    if (!COLOR) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        flush = abort[0] == 0;
+        no_tiles = (int)blockIdx.x >= a.tiles;
+        part_id = threadIdx.x / kTrRows;
+        nparts = blockDim.x / kTrRows;
+    }
+    if (flush) {
         float* part = a.partials + (long long)(blockIdx.x * a.groups + G.g) * net.mlp_params;
         const int lane0 = r & ~31;
         for (int l = 0; l < L; ++l) {
@@ -779,9 +792,10 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
             const bool lane_ok = r < lanes;
             float* wrow = part + (Ly.w_off - net.mlp_base) + (l == 0 ? (long long)r * Ly.in : (long long)r);
             float* brow = part + (Ly.b_off - net.mlp_base);
-            for (int c0 = 0; c0 < ncol; c0 += 16) {
+            for (int c0 = 0, ci = 0; c0 < ncol; c0 += 16, ++ci) {
+                if (ci % nparts != part_id) continue;            // warp-uniform
                 float v[16];
-                if (!first) {
+                if (!no_tiles) {
                     tmem_ld16(G.row + (uint32_t)Ly.dw_col + c0, v);
                     tmem_wait_ld_regs<16>(v);
                 } else {
