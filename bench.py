@@ -115,14 +115,16 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.out = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
+            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -136,17 +138,21 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            if self.out is not None:
+                self.out.close()
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        self.out.close()
         rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
@@ -326,6 +332,15 @@ INFER_TC_DRAM_BYTES_MAT4K = 16_966_144
 SM_MAX_GHZ = 2.07
 
 
+def measured_peaks():
+    """The machine's measured HBM copy and bf16 GEMM peaks, else the recipe's fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(path):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}
+    with open(path) as f:
+        return json.load(f)
+
+
 def encode_roofline(nt, desc, ms_step):
     """Bounds of one encode step at BATCH_TEXELS: tensor time of the forward + backward MLP
     FLOPs (3x the forward, BF16 dense peak) and HBM time of the dense Adam pass (read p, g,
@@ -336,8 +351,7 @@ def encode_roofline(nt, desc, ms_step):
     mac_e = lay.in_endpoint * 64 + (hl - 1) * 64 * 64 + 64 * lay.out_endpoint
     flops = 3 * 2.0 * (BATCH_TEXELS * mac_c + BATCH_TEXELS // 16 * mac_e)
     bytes_ = lay.total * 4.0 * (7 + 1 + 1)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}
+    peaks = measured_peaks()
     t_tc = flops / (peaks["bf16_tflops"] * 1e12) * 1e3
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9) * 1e3
     return {"flop_per_step": flops, "hbm_bytes_per_step": bytes_, "t_tensor_ms": round(t_tc, 4),
@@ -348,7 +362,6 @@ def encode_roofline(nt, desc, ms_step):
 def inference_roofline(nt, desc, ms, traffic=None):
     """Governing roofline of one inference pass: max of tensor (FP16 dense), MUFU (one exp2 per
     SELU unit and per sigmoid output) and HBM (grid codes read once + blocks written) times."""
-    import json as _json
     lay = nt.ntbc_model_layout(desc)
     n_pos = (desc.width // 4) * (desc.height // 4)
     hl = desc.hidden_layers
@@ -357,8 +370,7 @@ def inference_roofline(nt, desc, ms, traffic=None):
     flops = 2.0 * (16 * mac_c + mac_e) * n_pos
     exps = (16 * (hl * 64 + lay.out_color) + hl * 64 + lay.out_endpoint) * float(n_pos)
     bytes_ = lay.grid_floats * 1 + 8.0 * n_pos * desc.n_textures
-    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}
+    peaks = measured_peaks()
     mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * SM_MAX_GHZ * 1e9
     t_tc = flops / (peaks["bf16_tflops"] * 1e12)
     t_xu = exps / mufu_peak

@@ -17,7 +17,8 @@ nt = pytest.importorskip("paper_2407_09543_gb300")
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "ntbc.h")).read()
+    with open(os.path.join(ROOT, "include", "ntbc.h")) as f:
+        text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(\w+)\s*\([^;{]*\)\s*;", text, flags=re.M)
     return sorted(set(names))

@@ -43,8 +43,8 @@ def test_plain_losses_and_autograd_match_oracle(qat):
         (le + lc).backward()
     finally:
         torch.set_default_dtype(old)
-    assert float(le) == pytest.approx(L["L_endpoint"], rel=1e-6)
-    assert float(lc) == pytest.approx(L["L_color"], rel=1e-6)
+    assert le.item() == pytest.approx(L["L_endpoint"], rel=1e-6)
+    assert lc.item() == pytest.approx(L["L_color"], rel=1e-6)
     for a, b in zip(pm.color_grid + pm.endpoint_grid, g["color_grid"] + g["endpoint_grid"]):
         assert np.linalg.norm(a.grad.numpy() - b) <= 1e-5 * np.linalg.norm(b)
     for (W, bb), (gW, gb) in zip(pm.color_mlp + pm.endpoint_mlp, g["color_mlp"] + g["endpoint_mlp"]):
