@@ -10,6 +10,7 @@ import sys
 import numpy as np
 import pytest
 
+import descs
 from conftest import ROOT, golden
 from oracle import ntbc as ont
 
@@ -39,10 +40,8 @@ def test_level_resolutions_agree_with_oracle():
 def test_layout_counts_agree_with_oracle_storage():
     g = golden("paper_numbers.txt")
     for formats in ([1, 1, 4, 4, 4, 4], [1, 1], [4, 4, 4, 4], [1, 4]):
-        desc = nt.configs.model_desc(formats, 4096, 8, 16, 2048)
+        desc, od = descs.case_descs(nt, formats, 4096, 8, 16, 2048, 3, "selu")
         lay = nt.ntbc_model_layout(desc)
-        cres, eres = nt.configs.res_lists(desc)
-        od = ont.ModelDesc(4096, 4096, formats, cres, eres)
         # FP32 everywhere: storage_bytes with 32-bit grids and 4-byte weights is 4 * layout.total
         assert ont.storage_bytes(od, grid_bits=32, weight_bytes=4) == 4 * lay.total
         assert lay.in_color == int(g["color_input_dims"][0])

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import ntbc as ont
 
@@ -20,12 +21,8 @@ def rel_err(a, b):
 
 def case(side=32, kinds=("sine_rgb", "sine_r", "sine_rgb"), levels=3, lo=4, hi=9, hidden=2, act="selu", seed=3):
     mat = synth.make_material("vjp", side, list(kinds), seed)
-    acti = nt.ACT_SELU if act == "selu" else nt.ACT_RELU
-    desc = nt.configs.model_desc(mat.formats, side, levels, lo, hi, hidden, acti)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
-    params = synth.random_params_like(p0, seed=seed + 1)
-    odesc = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=hidden, activation=act)
+    desc, odesc = descs.case_descs(nt, mat.formats, side, levels, lo, hi, hidden, act)
+    params = synth.random_params_like(descs.init_params(odesc, seed), seed=seed + 1)
     return desc, odesc, params
 
 
@@ -106,11 +103,8 @@ def test_full_model_on_a_64x64_crop():
     # 2 BC1 + 2 BC4, 8-bit QAT) at the 16 x 16 blocks covering texels [1024, 1088)^2
     w = nt.configs.WORKLOADS["mat4k"]
     formats = [1, 1, 4, 4]
-    desc = nt.configs.desc_for(w, formats)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 9)
-    params = synth.random_params_like(p0, seed=10)
-    odesc = ont.ModelDesc(4096, 4096, formats, cres, eres, hidden_layers=3, activation="selu")
+    desc, odesc = descs.case_descs(nt, formats, 4096, w.levels, w.min_res, w.max_res, 3, "selu")
+    params = synth.random_params_like(descs.init_params(odesc, 9), seed=10)
     bx, by = np.meshgrid(np.arange(256, 272), np.arange(256, 272))
     ids = (by * 1024 + bx).ravel()
     rng = np.random.default_rng(2)

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 
 nt = pytest.importorskip("paper_2407_09543_gb300")
@@ -17,9 +18,8 @@ SPECS = [(64, [1, 4]), (132, [4, 1, 1]), (256, [1, 1, 4, 4, 4]), (96, [4, 4])]
 def _models(prec):
     models, outs, descs = [], [], []
     for i, (side, formats) in enumerate(SPECS):
-        desc = nt.configs.model_desc(formats, side, 4, 8, max(side // 2, 16), 3, nt.ACT_SELU)
-        cres, eres = nt.configs.res_lists(desc)
-        p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), i)
+        desc, odesc = descs.case_descs(nt, formats, side, 4, 8, max(side // 2, 16), 3, "selu")
+        p0 = descs.init_params(odesc, i)
         params = synth.random_params_like(p0, seed=10 + i)
         m = nt.Model(desc)
         m.set_params(torch.from_numpy(nt.configs.flatten(desc, params)).to(DEV))

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import bc as obc, ntbc as ont
 
@@ -26,12 +27,8 @@ def make_case(side=64, kinds=("sine_rgb", "sine_r"), levels=3, lo=4, hi=16, hidd
               height=None):
     mat = synth.make_material(f"inf{side}", side, list(kinds), seed)
     h = height or side
-    acti = nt.ACT_SELU if act == "selu" else nt.ACT_RELU
-    desc = nt.configs.model_desc(mat.formats, side, levels, lo, hi, hidden, acti, height=h)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
-    params = synth.random_params_like(p0, seed=seed + 1)
-    odesc = ont.ModelDesc(side, h, mat.formats, cres, eres, hidden_layers=hidden, activation=act)
+    desc, odesc = descs.case_descs(nt, mat.formats, side, levels, lo, hi, hidden, act, height=h)
+    params = synth.random_params_like(descs.init_params(odesc, seed), seed=seed + 1)
     return mat, desc, odesc, params
 
 
@@ -269,11 +266,8 @@ def test_full_size_4k_sampled():
     # the oracle evaluates a seeded sample of blocks one by one
     w = nt.configs.WORKLOADS["mat4k"]
     formats = [1, 1, 4, 4]
-    desc = nt.configs.desc_for(w, formats)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 3)
-    params = synth.random_params_like(p0, seed=4)
-    odesc = ont.ModelDesc(4096, 4096, formats, cres, eres, hidden_layers=3, activation="selu")
+    desc, odesc = descs.case_descs(nt, formats, 4096, w.levels, w.min_res, w.max_res, 3, "selu")
+    params = synth.random_params_like(descs.init_params(odesc, 3), seed=4)
     model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
     oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], 8)
     deq = ont.dequantize_grid(oc, os_, oz)
@@ -331,14 +325,12 @@ def _oracle_trained(bits, seed=5):
     realistic, sharper weights than random ones, and none of it comes from the CUDA path."""
     from oracle import philox
     mat = synth.make_material("trained", 64, ["sine_rgb", "sine_r", "sine_rgb"], seed)
-    desc = nt.configs.model_desc(mat.formats, 64, 4, 8, 32, 3, nt.ACT_SELU)
-    cres, eres = nt.configs.res_lists(desc)
-    odesc = ont.ModelDesc(64, 64, mat.formats, cres, eres, hidden_layers=3, activation="selu")
-    p0 = synth.init_params(cres, eres, 2, odesc.mlp_dims("color"), odesc.mlp_dims("endpoint"), seed)
+    desc, odesc = descs.case_descs(nt, mat.formats, 64, 4, 8, 32, 3, "selu")
+    p0 = descs.init_params(odesc, seed)
     refs = [obc.encode(f, t, 64, 64) for f, t in zip(mat.formats, mat.textures)]
     cfg = ont.TrainConfig(steps=200, batch_texels=1024, qat_fraction=0.1, grid_bits=bits)
     p1, _ = ont.train(odesc, p0, mat.textures, refs, cfg, lambda s: philox.sample_blocks(1, s, 64, odesc.n_blocks))
-    p32 = nt.configs.unflatten(desc, nt.configs.flatten(desc, p1))          # the float32 weights both sides use
+    p32 = descs.as_float32(p1)          # the float32 weights both sides use
     return mat, desc, odesc, p32
 
 

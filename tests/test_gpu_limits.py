@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import bc as obc, ntbc as ont
 
@@ -22,12 +23,9 @@ def max_case(seed=0):
     side = 64
     mat = synth.make_material("limits", side, KINDS, seed)
     assert len(mat.formats) == nt.MAX_TEXTURES
-    desc = nt.configs.model_desc(mat.formats, side, nt.MAX_LEVELS, 4, 64, 3, nt.ACT_SELU)
+    desc, odesc = descs.case_descs(nt, mat.formats, side, nt.MAX_LEVELS, 4, 64, 3, "selu")
     assert desc.color_levels == nt.MAX_LEVELS
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
-    params = synth.random_params_like(p0, seed=seed + 1)
-    odesc = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=3, activation="selu")
+    params = synth.random_params_like(descs.init_params(odesc, seed), seed=seed + 1)
     return mat, desc, odesc, params
 
 
@@ -157,9 +155,8 @@ def test_bounded_wait_gives_up_and_context_survives():
     # the failure path of every MMA wait: an mbarrier that nothing completes, polled with the
     # kernels' bounded loop under a small limit, gives up with NTBC_ETIMEOUT, and the GPU
     # context stays usable (a normal inference right after matches one from before)
-    desc = nt.configs.model_desc([nt.BC1, nt.BC4], 64, 3, 4, 16, 2, nt.ACT_SELU)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
+    desc, odesc = descs.case_descs(nt, [nt.BC1, nt.BC4], 64, 3, 4, 16, 2, "selu")
+    p0 = descs.init_params(odesc, 0)
     model = nt.Model(desc)
     model.set_params(torch.from_numpy(nt.configs.flatten(desc, synth.random_params_like(p0, seed=1))).to("cuda"))
     model.export(grid_bits=8, weight_prec=nt.PREC_FP16)

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import bc as obc, ntbc as ont
 
@@ -23,9 +24,8 @@ def trained():
     w = nt.configs.WORKLOADS["mat1k"]
     mat = synth.material_1k(seed=0)
     side = mat.width
-    desc = nt.configs.desc_for(w, mat.formats)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
+    desc, odesc = descs.case_descs(nt, mat.formats, side, w.levels, w.min_res, w.max_res, 3, "selu")
+    p0 = descs.init_params(odesc, 0)
     tex_d = [_dev(t) for t in mat.textures]
     nblk = (side // 4) ** 2
     refs = [torch.empty(nblk * 8, dtype=torch.uint8, device=DEV) for _ in mat.formats]
@@ -51,7 +51,7 @@ def trained():
         assert all(np.isfinite(losses))
         models[prec] = m
     ref = [obc.psnr(obc.decode(f, r.cpu().numpy(), side, side), t) for f, r, t in zip(mat.formats, refs, mat.textures)]
-    return dict(mat=mat, desc=desc, models=models, psnrs=psnrs, untrained=untrained, ref=ref, keep=(tex_d, refs))
+    return dict(mat=mat, desc=desc, odesc=odesc, models=models, psnrs=psnrs, untrained=untrained, ref=ref, keep=(tex_d, refs))
 
 
 def test_encode_fp32_and_bf16_gain_and_agree(trained):
@@ -68,9 +68,8 @@ def test_inference_fp32_and_fp16_match_oracle_on_trained_weights(trained):
     m = trained["models"][nt.TRAIN_BF16]
     flat = torch.empty(m.n_params, device=DEV)
     m.get_params(flat)
-    params = nt.configs.unflatten(desc, flat.cpu().numpy())
-    cres, eres = nt.configs.res_lists(desc)
-    odesc = ont.ModelDesc(mat.width, mat.height, mat.formats, cres, eres, hidden_layers=3, activation="selu")
+    odesc = trained["odesc"]
+    params = descs.params_from_flat(odesc, flat.cpu().numpy())
     ids = np.sort(np.random.default_rng(1).choice(odesc.n_blocks, 500, replace=False))
     out = {}
     for prec in (nt.PREC_FP32, nt.PREC_FP16):

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import bc as obc, ntbc as ont
 
@@ -22,11 +23,8 @@ def _dev(a):
 def test_single_format_model_matches_oracle(kinds):
     side = 64
     mat = synth.make_material("pkg", side, list(kinds), 2)
-    desc = nt.configs.model_desc(mat.formats, side, 4, 4, 32, 3, nt.ACT_SELU)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 2)
-    params = synth.random_params_like(p0, seed=3)
-    odesc = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=3, activation="selu")
+    desc, odesc = descs.case_descs(nt, mat.formats, side, 4, 4, 32, 3, "selu")
+    params = synth.random_params_like(descs.init_params(odesc, 2), seed=3)
     m = nt.Model(desc)
     m.set_params(_dev(nt.configs.flatten(desc, params)))
     m.export(grid_bits=8, weight_prec=nt.PREC_FP16)
@@ -71,9 +69,8 @@ def test_conservative_encode_and_batched_decode():
     models, outs, before = [], [], {}
     for g in groups:
         fm = [mat.formats[t] for t in g]
-        desc = nt.configs.model_desc(fm, side, 4, 8, 64, 3, nt.ACT_SELU)
-        cres, eres = nt.configs.res_lists(desc)
-        p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 7)
+        desc, odesc = descs.case_descs(nt, fm, side, 4, 8, 64, 3, "selu")
+        p0 = descs.init_params(odesc, 7)
         m = nt.Model(desc)
         m.set_params(_dev(nt.configs.flatten(desc, p0)))
         o = [torch.empty((side // 4) ** 2 * 8, dtype=torch.uint8, device=DEV) for _ in g]

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import bc as obc, ntbc as ont, philox
 
@@ -20,12 +21,9 @@ def _dev(a):
 def setup(side=32, kinds=("sine_rgb", "sine_r", "sine_r", "sine_rgb"), levels=3, lo=4, hi=9, hidden=2, act="selu",
           seed=3, grid_scale=0.5):
     mat = synth.make_material("trn", side, list(kinds), seed)
-    acti = nt.ACT_SELU if act == "selu" else nt.ACT_RELU
-    desc = nt.configs.model_desc(mat.formats, side, levels, lo, hi, hidden, acti)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
+    desc, odesc = descs.case_descs(nt, mat.formats, side, levels, lo, hi, hidden, act)
+    p0 = descs.init_params(odesc, seed)
     params = synth.random_params_like(p0, seed=seed + 1, grid_scale=grid_scale) if grid_scale else p0
-    odesc = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=hidden, activation=act)
     refs = [obc.encode(f, t, side, side) for f, t in zip(mat.formats, mat.textures)]
     tex_d = [_dev(t) for t in mat.textures]
     ref_d = [_dev(r) for r in refs]
@@ -99,9 +97,8 @@ def test_training_gains_over_untrained_network():
     # below the reference BC encoder (the ordering of every row of the paper's tables)
     mat = synth.tiny_material()
     w = nt.configs.WORKLOADS["tiny256"]
-    desc = nt.configs.desc_for(w, mat.formats)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
+    desc, odesc = descs.case_descs(nt, mat.formats, mat.width, w.levels, w.min_res, w.max_res, w.hidden_layers, "relu")
+    p0 = descs.init_params(odesc, 0)
     tex_d = [_dev(t) for t in mat.textures]
     refs = [torch.empty(64 * 64 * 8, dtype=torch.uint8, device=DEV) for _ in mat.formats]
     for t, fmt in enumerate(mat.formats):

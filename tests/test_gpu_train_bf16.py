@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import bc as obc, ntbc as ont
 
@@ -31,12 +32,8 @@ def _dev(a):
 def setup(side=32, kinds=("sine_rgb", "sine_r", "sine_r", "sine_rgb"), levels=3, lo=4, hi=9, hidden=2, act="selu",
           seed=3):
     mat = synth.make_material("trn", side, list(kinds), seed)
-    acti = nt.ACT_SELU if act == "selu" else nt.ACT_RELU
-    desc = nt.configs.model_desc(mat.formats, side, levels, lo, hi, hidden, acti)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
-    params = synth.random_params_like(p0, seed=seed + 1, grid_scale=0.5)
-    odesc = ont.ModelDesc(side, side, mat.formats, cres, eres, hidden_layers=hidden, activation=act)
+    desc, odesc = descs.case_descs(nt, mat.formats, side, levels, lo, hi, hidden, act)
+    params = synth.random_params_like(descs.init_params(odesc, seed), seed=seed + 1, grid_scale=0.5)
     refs = [obc.encode(f, t, side, side) for f, t in zip(mat.formats, mat.textures)]
     tex_d = [_dev(t) for t in mat.textures]
     ref_d = [_dev(r) for r in refs]
@@ -96,9 +93,8 @@ def test_bf16_many_tiles_per_group():
 def test_bf16_training_gains_over_untrained_network():
     mat = synth.tiny_material()
     w = nt.configs.WORKLOADS["tiny256"]
-    desc = nt.configs.desc_for(w, mat.formats)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
+    desc, odesc = descs.case_descs(nt, mat.formats, mat.width, w.levels, w.min_res, w.max_res, w.hidden_layers, "relu")
+    p0 = descs.init_params(odesc, 0)
     tex_d = [_dev(t) for t in mat.textures]
     refs = [torch.empty(64 * 64 * 8, dtype=torch.uint8, device=DEV) for _ in mat.formats]
     for t, fmt in enumerate(mat.formats):

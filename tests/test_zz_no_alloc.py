@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import descs
 import synth
 from oracle import bc as obc
 
@@ -27,9 +28,8 @@ def _dev(a):
 
 def _case(seed=3):
     mat = synth.make_material("noalloc", 64, ["sine_rgb", "sine_r", "sine_r", "sine_rgb"], seed)
-    desc = nt.configs.model_desc(mat.formats, 64, 3, 4, 16, hidden_layers=3, activation=nt.ACT_SELU)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), seed)
+    desc, odesc = descs.case_descs(nt, mat.formats, 64, 3, 4, 16, 3, "selu")
+    p0 = descs.init_params(odesc, seed)
     params = synth.random_params_like(p0, seed=seed + 1, grid_scale=0.5)
     refs = [obc.encode(f, t, 64, 64) for f, t in zip(mat.formats, mat.textures)]
     tex_d = [_dev(t) for t in mat.textures]
