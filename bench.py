@@ -48,6 +48,7 @@ REF_REFINE = 2
 # end-to-end leg: blocks delivered to pinned host memory in this many ranges, each range's
 # copy overlapping the inference of the next
 E2E_CHUNKS = 4
+KIND_FORMAT = {"diffuse": 1, "normal": 1, "roughness": 4, "ao": 4}
 METRIC = "NTBC infer Mblocks/s (4k material, 4 textures) + 4k-material encode s, vs plain FP32 GPU, at decoded-PSNR parity"
 
 
@@ -257,73 +258,243 @@ def psnr_list(nt, torch, mat, blocks, side):
     return out
 
 
-def cpu_oracle_inference(nt, desc, flat_params, grid_bits, budget_s=12.0, seed=0):
-    """Time the FP64 oracle's NTBC inference on a bounded sample of blocks (single thread)."""
+# ----------------------------------------------------------------------------
+# the CPU oracle across the host cores (cpu_baseline, full-material parity, reference arm)
+# ----------------------------------------------------------------------------
+
+def workload_spec(side, seed=0, params_path=None, grid_bits=8):
+    """What an oracle worker needs to rebuild the model on its own: the 4k workload's shape
+    (Sec. 3.4 model configuration) and either a file of flat FP32 parameters or a seed."""
+    return dict(formats=list(FORMATS), side=side, levels=12, lo=16, hi=2048, hidden=3, act="selu",
+                grid_bits=grid_bits, params=params_path, seed=seed)
+
+
+def oracle_desc_of(spec):
     from oracle import ntbc as ont
-    params = nt.configs.unflatten(desc, flat_params)
-    p16 = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"])
-    for k in ("color_mlp", "endpoint_mlp"):
-        p16[k] = [(W.astype(np.float16).astype(np.float64), b.astype(np.float16).astype(np.float64)) for W, b in params[k]]
-    cres, eres = nt.configs.res_lists(desc)
-    od = ont.ModelDesc(desc.width, desc.height, [desc.formats[i] for i in range(desc.n_textures)], cres, eres,
-                       hidden_layers=desc.hidden_layers, activation="selu" if desc.activation == 0 else "relu")
-    codes, sc, zr = ont.export_grid(params["color_grid"] + params["endpoint_grid"], grid_bits)
+    cres = ont.level_resolutions(spec["levels"], spec["lo"], spec["hi"])
+    eres = ont.endpoint_resolutions(cres, spec["side"] // 4)
+    return ont.ModelDesc(spec["side"], spec["side"], spec["formats"], cres, eres, hidden_layers=spec["hidden"],
+                         activation=spec["act"])
+
+
+def oracle_random_params(od, seed):
+    """The seeded random-init weights (Sec. 3.4 initialisation, then spread over (0, 1) outputs)."""
+    p0 = synth.init_params(od.color_res, od.endpoint_res, od.features, od.mlp_dims("color"),
+                           od.mlp_dims("endpoint"), seed)
+    return synth.random_params_like(p0, seed=seed + 1)
+
+
+_ORACLE = {}
+
+
+def _oracle_init(spec, compare=None):
+    """Worker set-up: the exported model as the oracle computes it (its own QAT export of the
+    grids, MLP weights rounded to FP16), and for the comparison pass memory maps of the source
+    textures and of both block sets."""
+    from oracle import ntbc as ont
+    od = oracle_desc_of(spec)
+    if spec["params"]:
+        p = ont.params_from_flat(od, np.load(spec["params"], mmap_mode="r"))
+    else:
+        p = oracle_random_params(od, spec["seed"])
+    nc = len(od.color_res)
+    codes, sc, zr = ont.export_grid(p["color_grid"] + p["endpoint_grid"], spec["grid_bits"])
     deq = ont.dequantize_grid(codes, sc, zr)
-    nc = desc.color_levels
-    rng = np.random.default_rng(seed)
-    n = 64
-    t0 = time.perf_counter()
-    ont.infer_blocks(od, p16, block_ids=rng.choice(od.n_blocks, n, replace=False), color_grid=deq[:nc], endpoint_grid=deq[nc:])
-    per_block = (time.perf_counter() - t0) / n
-    n = int(max(64, min(od.n_blocks, budget_s / max(per_block, 1e-9))))
-    ids = np.sort(rng.choice(od.n_blocks, n, replace=False))
-    t0 = time.perf_counter()
-    ont.infer_blocks(od, p16, block_ids=ids, color_grid=deq[:nc], endpoint_grid=deq[nc:])
-    dt = time.perf_counter() - t0
-    return n, dt
+    p16 = dict(color_grid=[], endpoint_grid=[])
+    for k in ("color_mlp", "endpoint_mlp"):
+        p16[k] = [(W.astype(np.float16).astype(np.float64), b.astype(np.float16).astype(np.float64)) for W, b in p[k]]
+    _ORACLE.update(od=od, p16=p16, cgrid=deq[:nc], egrid=deq[nc:])
+    if compare:
+        _ORACLE["cmp"] = {k: [np.load(p, mmap_mode="r") for p in v] if isinstance(v, list) else np.load(v, mmap_mode="r")
+                          for k, v in compare.items()}
+
+
+def _oracle_blocks(rng):
+    """NTBC inference to blocks (Sec. 3.2) of block ids [start, stop): [textures, n, 8] uint8."""
+    from oracle import ntbc as ont
+    start, stop = rng
+    o = _ORACLE
+    blocks = ont.infer_blocks(o["od"], o["p16"], block_ids=np.arange(start, stop), color_grid=o["cgrid"],
+                              endpoint_grid=o["egrid"])
+    return start, np.stack(blocks)
+
+
+def _oracle_compare(rng):
+    """Per texture, over whole block rows [start, stop): squared error of the decoded oracle and
+    GPU blocks against the source (in [0, 1] units), and mismatched endpoint / index fields."""
+    from oracle import bc as obc
+    start, stop = rng
+    od, c = _ORACLE["od"], _ORACLE["cmp"]
+    bw = od.blocks_x
+    y0, y1 = 4 * (start // bw), 4 * (stop // bw)
+    out = []
+    for t, fmt in enumerate(od.formats):
+        ours = np.asarray(c["gpu"][t, start:stop])
+        ref = np.asarray(c["oracle"][t, start:stop])
+        src = np.asarray(c["tex"][t][y0:y1], np.float64) / 255.0
+        unpack = obc.bc1_unpack if fmt == 1 else obc.bc4_unpack
+        fo, fr = unpack(ours), unpack(ref)
+        ep = int((fo[0] != fr[0]).sum() + (fo[1] != fr[1]).sum())
+        ix = int((fo[2] != fr[2]).sum())
+        sse = []
+        for b in (ours, ref):
+            d = obc.decode(fmt, b, od.width, y1 - y0).astype(np.float64) / 255.0
+            sse.append(float(((d - src.reshape(d.shape)) ** 2).sum()))
+        out.append((sse[0], sse[1], ep, ix))
+    return start, out
+
+
+class OraclePool:
+    """The FP64 oracle in one spawned process per host core (spawn: safe after CUDA is up;
+    single-threaded BLAS in every worker so the processes do not oversubscribe the cores)."""
+
+    def __init__(self, spec, compare=None, cores=None):
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.cores = cores or len(os.sched_getaffinity(0))
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init, initargs=(spec, compare))
+        self.od = oracle_desc_of(spec)
+        # every worker finished its set-up before anything is timed
+        self.pool.map(_oracle_blocks, [(0, 1)] * self.cores, chunksize=1)
+
+    def ranges(self, start_row, rows, rows_per_task=1):
+        bw = self.od.blocks_x
+        return [(r * bw, min(start_row + rows, r + rows_per_task) * bw)
+                for r in range(start_row, start_row + rows, rows_per_task)]
+
+    def blocks(self, start_row=0, rows=None):
+        """Oracle blocks of block rows [start_row, start_row + rows): ([T, n, 8], wall seconds)."""
+        rows = self.od.blocks_y - start_row if rows is None else rows
+        rngs = self.ranges(start_row, rows)
+        out = np.empty((len(self.od.formats), rows * self.od.blocks_x, 8), np.uint8)
+        base = start_row * self.od.blocks_x
+        t0 = time.perf_counter()
+        for s, b in self.pool.imap_unordered(_oracle_blocks, rngs):
+            out[:, s - base:s - base + b.shape[1]] = b
+        return out, time.perf_counter() - t0
+
+    def compare(self):
+        res = [r for _, r in sorted(self.pool.imap_unordered(_oracle_compare, self.ranges(0, self.od.blocks_y, 4)))]
+        return [tuple(sum(r[t][k] for r in res) for k in range(4)) for t in range(len(self.od.formats))]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def full_material_oracle(side, flat_params, gpu_blocks, textures):
+    """The oracle over every block of the material with the GPU arm's exported model (u8 QAT
+    grids, FP16 MLP weights): timed across the host cores (the CPU baseline), then checked
+    against the GPU blocks on the spec bars: decoded PSNR within 0.05 dB of the FP64-oracle
+    network per texture and at most 0.1 % of endpoint or index fields differing."""
+    tmp = tempfile.mkdtemp(prefix="ntbc_oracle_")
+    paths = {"params": os.path.join(tmp, "params.npy"), "gpu": os.path.join(tmp, "gpu.npy"),
+             "oracle": os.path.join(tmp, "oracle.npy")}
+    try:
+        np.save(paths["params"], np.asarray(flat_params, np.float32))
+        np.save(paths["gpu"], np.stack([np.asarray(b).reshape(-1, 8) for b in gpu_blocks]))
+        tex_paths = []
+        for t, tex in enumerate(textures):
+            tex_paths.append(os.path.join(tmp, f"tex{t}.npy"))
+            np.save(tex_paths[-1], np.ascontiguousarray(tex))
+        spec = workload_spec(side, params_path=paths["params"])
+        compare = {"gpu": paths["gpu"], "oracle": paths["oracle"], "tex": tex_paths}
+        # the comparison reads the oracle's blocks from a file the first pass writes
+        pool = OraclePool(spec)
+        blocks, dt = pool.blocks()
+        pool.close()
+        np.save(paths["oracle"], blocks)
+        pool = OraclePool(spec, compare=compare, cores=pool.cores)
+        sums = pool.compare()
+        pool.close()
+    finally:
+        for p in list(paths.values()) + [os.path.join(tmp, f) for f in os.listdir(tmp) if f.startswith("tex")]:
+            if os.path.exists(p):
+                os.unlink(p)
+        os.rmdir(tmp)
+    od = oracle_desc_of(spec)
+    n = od.n_blocks
+    psnr_g, psnr_o, diff = [], [], []
+    ep_m = ix_m = ep_f = ix_f = 0
+    for t, (sse_g, sse_o, ep, ix) in enumerate(sums):
+        vals = side * side * od.channels[t]
+        pg, po = (10.0 * np.log10(vals / s) if s > 0 else float("inf") for s in (sse_g, sse_o))
+        psnr_g.append(round(float(pg), 4))
+        psnr_o.append(round(float(po), 4))
+        diff.append(round(float(pg - po), 4))
+        ep_m, ix_m = ep_m + ep, ix_m + ix
+        ep_f, ix_f = ep_f + 2 * n, ix_f + 16 * n
+    rate = (ep_m + ix_m) / (ep_f + ix_f)
+    parity = {"blocks": n, "textures": len(od.formats), "psnr_db_gpu": psnr_g, "psnr_db_oracle": psnr_o,
+              "psnr_diff_db": diff, "endpoint_field_mismatch": ep_m, "index_field_mismatch": ix_m,
+              "field_mismatch_rate": round(rate, 7),
+              "bar": "|PSNR diff| <= 0.05 dB per texture and <= 0.1 % fields differ",
+              "pass": bool(max(abs(d) for d in diff) <= 0.05 and rate <= 0.001)}
+    cpu = {"value": round(n * len(od.formats) / dt / 1e6, 6), "unit": "Mblocks/s", "cores": pool.cores,
+           "kind": "oracle",
+           "sample": f"the whole {side}x{side} material ({n} block positions x {len(od.formats)} textures), "
+                     f"FP64 numpy, {pool.cores} processes, {dt:.1f} s"}
+    return parity, cpu
 
 
 # ----------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ----------------------------------------------------------------------------
 
+def workload_config(side, world):
+    return {"workload": f"mat4k {side}x{side}, 4 textures (2 BC1 + 2 BC4), 12 levels 16..2048 u8 QAT, "
+                        f"3x64 SELU, FP16 weights", "texture_blocks": (side // 4) ** 2 * len(FORMATS),
+            "block_positions": (side // 4) ** 2, "l2": "flushed (256 MiB write) between timed iterations",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
+    """The oracle (FP64 numpy, no product code) on the host cores: every step decodes a run of
+    block rows of the 4k material to BC blocks, sized from the warm-up rate so the whole run
+    takes about two minutes (the whole material per step when the cores allow it)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import paper_2407_09543_gb300 as nt
     side = args.side
-    w = nt.configs.WORKLOADS["mat4k"]
-    desc = nt.configs.desc_for(w, FORMATS, side=side)
-    cres, eres = nt.configs.res_lists(desc)
-    p0 = synth.init_params(cres, eres, 2, nt.configs.mlp_dims(desc, "color"), nt.configs.mlp_dims(desc, "endpoint"), 0)
-    params = synth.random_params_like(p0, seed=1)
-    flat = nt.configs.flatten(desc, params)
-    budget = 120.0 / max(1, args.steps + args.warmup)
+    pool = OraclePool(workload_spec(side, seed=0))
+    od = pool.od
+    rows_total = od.blocks_y
+    rows = max(1, min(rows_total, 2 * pool.cores))
     rates = []
-    samples = []
-    for i in range(args.warmup + args.steps):
-        n, dt = cpu_oracle_inference(nt, desc, flat, 8, budget_s=budget, seed=i)
-        if i >= args.warmup:
-            rates.append(n * len(FORMATS) / dt / 1e6)
-            samples.append(n)
-    value = float(np.mean(rates))
+    for i in range(args.warmup):
+        _, dt = pool.blocks((i * rows) % max(1, rows_total - rows + 1), rows)
+        rates.append(rows / dt)
+    per_step_s = 120.0 / max(1, args.steps)
+    rows = int(max(1, min(rows_total, (np.median(rates) if rates else rows) * per_step_s)))
+    times = []
+    for i in range(args.steps):
+        start = (i * rows) % max(1, rows_total - rows + 1)
+        _, dt = pool.blocks(start, rows)
+        times.append(dt)
+    pool.close()
+    ms = 1e3 * float(np.mean(times))
+    tex_blocks = rows * od.blocks_x * len(FORMATS)
+    value = tex_blocks / (ms * 1e-3) / 1e6
+    sample = (f"{rows} of {rows_total} block rows per step ({rows * od.blocks_x} block positions x {len(FORMATS)} "
+              f"textures), FP64 numpy, {pool.cores} processes")
     line = {
-        "metric": METRIC, "value": value, "unit": "Mblocks/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * (desc.width // 4) ** 2 * len(FORMATS) / (value * 1e6),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference",
-        "config": {"workload": f"mat4k {side}x{side}, 4 textures (2 BC1 + 2 BC4), 12 levels 16..2048 u8, 3x64 SELU",
-                   "l2": "oracle on CPU", "parallelism": "single process, CPU"},
-        "cpu_baseline": {"value": value, "unit": "Mblocks/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{int(np.mean(samples))} random blocks of the 4k material per step (FP64 numpy)"},
-        "e2e": {"value": value, "unit": "Mblocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "metric": METRIC, "value": round(value, 6), "unit": "Mblocks/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": workload_config(side, world),
+        "weights": "seeded random-init (the timed work does not depend on the weight values)",
+        "cpu_baseline": {"value": round(value, 6), "unit": "Mblocks/s", "cores": pool.cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "Mblocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-MUFU_PER_SM_PER_CLK = 16        # exp2 results per clock per SM (CUDA arithmetic-instruction throughput table)
+# exp2 results per clock per SM: measured on GB300 by ntbc_ex2_rate_probe (31.9 at 2.07 GHz);
+# used only when no live measurement is given
+MUFU_PER_SM_PER_CLK = 32
 SM_COUNT = 152
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # infer_tc_kernel<SPLIT=true> on the 4096^2 four-texture material, from one ncu capture of the
@@ -359,9 +530,11 @@ def encode_roofline(nt, desc, ms_step):
             "frac_of_measured": round(max(t_tc, t_hbm) / ms_step, 4)}
 
 
-def inference_roofline(nt, desc, ms, traffic=None):
+def inference_roofline(nt, desc, ms, traffic=None, mufu_peak=None):
     """Governing roofline of one inference pass: max of tensor (FP16 dense), MUFU (one exp2 per
-    SELU unit and per sigmoid output) and HBM (grid codes read once + blocks written) times."""
+    SELU unit and per sigmoid output) and HBM (grid codes read once + blocks written) times.
+    mufu_peak: exp2 per second measured on the device (ntbc_ex2_rate_probe), else the per-SM
+    rate measured on GB300 at the maximum SM clock."""
     lay = nt.ntbc_model_layout(desc)
     n_pos = (desc.width // 4) * (desc.height // 4)
     hl = desc.hidden_layers
@@ -371,15 +544,19 @@ def inference_roofline(nt, desc, ms, traffic=None):
     exps = (16 * (hl * 64 + lay.out_color) + hl * 64 + lay.out_endpoint) * float(n_pos)
     bytes_ = lay.grid_floats * 1 + 8.0 * n_pos * desc.n_textures
     peaks = measured_peaks()
-    mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * SM_MAX_GHZ * 1e9
+    measured = mufu_peak is not None
+    if not measured:
+        mufu_peak = SM_COUNT * MUFU_PER_SM_PER_CLK * SM_MAX_GHZ * 1e9
     t_tc = flops / (peaks["bf16_tflops"] * 1e12)
     t_xu = exps / mufu_peak
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
     sec = ms * 1e-3
+    kind = ("MUFU exp2 measured live by ntbc_ex2_rate_probe" if measured else
+            "MUFU exp2: 152 SM x 32/clk (measured per-SM rate) x 2.07 GHz")
     roofline = {"bound": "alu", "achieved": round(exps / sec / 1e12, 4), "peak": round(mufu_peak / 1e12, 4),
                 "unit": "Texp/s", "frac": round(t_xu / sec, 4), "traffic": traffic,
                 "kernel": "infer_tc_kernel<SPLIT=true>",
-                "peak_kind": "MUFU exp2: 152 SM x 16/clk x 2.07 GHz (derived); tensor/HBM peaks of measured"}
+                "peak_kind": kind + "; tensor / HBM terms against MEASURED_PEAKS (of measured)"}
     terms = {"t_tensor_ms": round(t_tc * 1e3, 4), "t_mufu_ms": round(t_xu * 1e3, 4), "t_hbm_ms": round(t_hbm * 1e3, 4),
              "tensor_frac_of_measured": round(t_tc / sec, 4), "hbm_frac_of_measured": round(t_hbm / sec, 4),
              "flop_per_pass": flops, "exp_per_pass": exps, "hbm_bytes_per_pass": bytes_}
@@ -565,6 +742,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     ms = max_over_ranks(float(np.mean(times)), world, dev)
+    headline_blocks = [o.cpu().numpy() for o in outs]          # for the full-material oracle check
     ours_psnr = psnr_list(nt, torch, mat, outs, side)
     ours_ssim = ssim_list(nt, torch, mat, outs, side)
     value = job_throughput(tex_blocks, world, ms)
@@ -586,11 +764,39 @@ def main():
     e2e_times = time_events(torch, e2e, args.steps, flush=flush)
     e2e_ms = max_over_ranks(float(np.mean(e2e_times)), world, dev)
     e2e_value = job_throughput(tex_blocks, world, e2e_ms)
+    # where the end-to-end time goes: the blob upload, the inference with the blocks delivered
+    # to host memory (copies overlapping the compute), and the raw copy rates of the same bytes
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    up, rest = [], []
+    for _ in range(max(3, args.steps // 4)):
+        flush()
+        ev[0].record(stream)
+        e2e_model.load(blob)
+        ev[1].record(stream)
+        e2e_model.infer_to_host(host_out, chunks=E2E_CHUNKS)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        up.append(ev[0].elapsed_time(ev[1]))
+        rest.append(ev[1].elapsed_time(ev[2]))
+    blob_dev = torch.empty(blob.numel(), dtype=torch.uint8, device=dev)
+    raw_h2d = time_events(torch, lambda: blob_dev.copy_(blob, non_blocking=True), 5, flush=flush)
+    raw_d2h = time_events(torch, lambda: [h.copy_(o, non_blocking=True) for h, o in zip(host_out, outs)], 5,
+                          flush=flush)
+    d2h_bytes = nblk * 8 * len(FORMATS)
+    e2e_parts = {"blob_upload_ms": round(float(np.median(up)), 4),
+                 "infer_and_delivery_ms": round(float(np.median(rest)), 4),
+                 "raw_h2d_gbs": round(blob.numel() / (float(np.median(raw_h2d)) * 1e-3) / 1e9, 1),
+                 "raw_d2h_gbs": round(d2h_bytes / (float(np.median(raw_d2h)) * 1e-3) / 1e9, 1),
+                 "e2e_ms_min_median_max": [round(float(np.min(e2e_times)), 4), round(float(np.median(e2e_times)), 4),
+                                           round(float(np.max(e2e_times)), 4)],
+                 "chunks": E2E_CHUNKS}
+    del blob_dev
     e2e_psnr = psnr_list(nt, torch, mat, host_out, side)
 
     # ---- roofline of the inference kernel (algorithmic counts per block position)
+    mufu_peak = nt.ntbc_ex2_rate_probe()
     roofline, terms = inference_roofline(
-        nt, desc, ms, INFER_TC_DRAM_BYTES_MAT4K if side == 4096 and args.prec == 1 else None)
+        nt, desc, ms, INFER_TC_DRAM_BYTES_MAT4K if side == 4096 and args.prec == 1 else None, mufu_peak=mufu_peak)
     encode_terms = encode_roofline(nt, desc, ms_per_train_step)
 
     # ---- the same inference in the other modes (pure FP16 activations; FP32 SIMT kernel)
@@ -735,22 +941,19 @@ def main():
                  "train_ms_per_step": round(p_train_ms, 3),
                  "encode_s_extrapolated": round(p_train_ms * (FULL_MAIN_STEPS + FULL_QAT_STEPS) / 1e3, 1)}
 
-    # ---- CPU oracle on a bounded sample
-    cpu = None
+    # ---- the CPU oracle over the whole material on the host cores: the CPU baseline, and the
+    # spec parity of the headline blocks (PSNR per texture, field mismatch)
+    cpu = oracle_parity = None
     if not args.no_cpu and rank == 0 and world == 1:
         flat = torch.empty(model.n_params, device=dev)
         model.get_params(flat)
-        n, dt = cpu_oracle_inference(nt, desc, flat.cpu().numpy(), 8, budget_s=12.0)
-        cpu = {"value": round(n * len(FORMATS) / dt / 1e6, 6), "unit": "Mblocks/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} random blocks of the 4k material, FP64 numpy, {dt:.1f} s"}
+        oracle_parity, cpu = full_material_oracle(side, flat.cpu().numpy(), headline_blocks, mat.textures)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mblocks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp16 tensor-core MMA (split hi+lo activations), fp32 accumulate; u8 grids", "data": "synthetic",
-        "config": {"workload": f"mat4k {side}x{side}, 4 textures (2 BC1 + 2 BC4), 12 levels 16..2048 u8 QAT, "
-                               f"3x64 SELU, FP16 weights", "texture_blocks": tex_blocks, "block_positions": nblk,
-                   "l2": "flushed (256 MiB write) between timed iterations", "parallelism": f"replicas x{world}"},
+        "config": workload_config(side, world),
         "block_positions_per_s_M": round(nblk * world / (ms * 1e-3) / 1e6, 3),
         "ssim": {"ntbc": ours_ssim, "reference_bc": ref_ssim},
         "psnr_db": {"ntbc": ours_psnr, "untrained": untrained_psnr, "reference_bc": ref_psnr,
@@ -774,8 +977,10 @@ def main():
         "roofline_terms": terms,
         "other_modes": modes,
         "cpu_baseline": cpu,
+        "oracle_parity": oracle_parity,
         "e2e": {"value": round(e2e_value, 3), "unit": "Mblocks/s", "ms_per_step": round(e2e_ms, 4),
-                "h2d_bytes_per_step": int(blob.numel()), "d2h_bytes_per_step": int(nblk * 8 * len(FORMATS))},
+                "h2d_bytes_per_step": int(blob.numel()), "d2h_bytes_per_step": int(nblk * 8 * len(FORMATS)),
+                **e2e_parts},
         "clocks": clk,
         "gpu_launches": args.steps,
     }

@@ -278,6 +278,15 @@ ntbc_status ntbc_infer_to_host(ntbc_model* model, uint8_t* const* host_out, int 
 ntbc_status ntbc_wait_probe(long long polls, double* seconds, void* stream);
 
 /*
+ * Measurement utility; the paper has no counterpart. The exp2 throughput of the device
+ * (ex2.approx results per second over all SMs: 8 independent dependency chains per thread,
+ * 8 CTAs of 256 threads per SM), the MUFU peak against which the inference kernel's roofline
+ * is reported (its SELU and sigmoid evaluate one exp2 per unit). About 10 ms of device work;
+ * allocates a small scratch buffer; synchronises `stream`.
+ */
+ntbc_status ntbc_ex2_rate_probe(double* ex2_per_s, void* stream);
+
+/*
  * The same with a block stride per texture: block b of texture t is written at
  * blocks_out[t] + b * block_stride[t] (a positive multiple of 8; NULL means 8 for all). With
  * stride 16 two textures of the model fill one 16-byte-block texture: a BC4 alpha texture
@@ -396,8 +405,11 @@ ntbc_status ntbc_vjp(ntbc_model* model, const int32_t* block_ids, int n_blocks, 
  * device array of NTBC_NOALLOC_MAX_BLOCKS blocks' worth (about 3.3 MB) that every
  * GPU loading the library holds until the process exits.
  *   desc, params  model description (host) and FP32 parameters (device, layout of
- *                 ntbc_model_layout); the other arguments as in ntbc_train_grads,
- *                 with `losses` required.
+ *                 ntbc_model_layout); block_ids, qat_bits, temperature, grads and
+ *                 losses as in ntbc_train_grads, with `losses` required. There is no
+ *                 precision argument: this call always runs the FP32 layer-by-layer
+ *                 kernels (NTBC_TRAIN_FP32), the same launches ntbc_train_grads makes
+ *                 for that precision.
  *   n_blocks      1..NTBC_NOALLOC_MAX_BLOCKS, else NTBC_EINVAL before any launch.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before

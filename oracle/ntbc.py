@@ -764,6 +764,33 @@ def unflatten_like(params, flat):
     return out
 
 
+def params_from_flat(desc, flat):
+    """Parameters from one flat vector in the order of the C ABI's parameter layout: colour-
+    grid levels ([res][res][F] each, row = y), endpoint-grid levels, colour MLP (W [out][in]
+    then b [out] per layer), endpoint MLP. Sizes come from `desc`; the vector must be consumed
+    exactly. Arrays are float64 views of the values."""
+    flat = np.asarray(flat)
+    off = 0
+
+    def take(shape):
+        nonlocal off
+        n = int(np.prod(shape))
+        if off + n > flat.size:
+            raise ValueError("flat parameter vector too short for this model")
+        a = flat[off:off + n].astype(np.float64).reshape(shape)
+        off += n
+        return a
+
+    out = dict(color_grid=[take((r, r, desc.features)) for r in desc.color_res],
+               endpoint_grid=[take((r, r, desc.features)) for r in desc.endpoint_res])
+    for which in ("color", "endpoint"):
+        dims = desc.mlp_dims(which)
+        out[which + "_mlp"] = [(take((dims[l + 1], dims[l])), take((dims[l + 1],))) for l in range(len(dims) - 1)]
+    if off != flat.size:
+        raise ValueError(f"flat parameter vector has {flat.size} values, the model {off}")
+    return out
+
+
 def is_grid_index(params, i):
     return i < len(params["color_grid"]) + len(params["endpoint_grid"])
 

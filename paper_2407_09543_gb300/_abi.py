@@ -117,6 +117,7 @@ _SIGS = {
     "ntbc_infer_to_bc_strided": (c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(c_int), _P]),
     "ntbc_infer_to_host": (c_int, [_P, ctypes.POINTER(_P), c_int, _P]),
     "ntbc_wait_probe": (c_int, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
+    "ntbc_ex2_rate_probe": (c_int, [ctypes.POINTER(ctypes.c_double), _P]),
     "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, c_int, _P, _P, _P]),
     "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
                                          c_float, _P, _P, _P]),
@@ -194,6 +195,13 @@ def ntbc_wait_probe(polls, stream=None):
     sec = ctypes.c_double(0.0)
     status = lib.ntbc_wait_probe(polls, ctypes.byref(sec), _stream(stream))
     return status, sec.value
+
+
+def ntbc_ex2_rate_probe(stream=None):
+    """exp2 results per second of the whole device (the MUFU peak of the inference roofline)."""
+    rate = ctypes.c_double(0.0)
+    _check(lib.ntbc_ex2_rate_probe(ctypes.byref(rate), _stream(stream)))
+    return rate.value
 
 
 NOALLOC_MAX_BLOCKS = 128

@@ -763,6 +763,28 @@ __global__ void wait_probe_kernel(long long polls, int* __restrict__ gave_up, un
 }
 
 // ---------------------------------------------------------------------------
+// exp2 throughput probe: the MUFU peak of the inference roofline, measured on the device the
+// library runs on (every thread runs 8 independent chains x = 2^-x, one ex2.approx per step)
+// ---------------------------------------------------------------------------
+
+constexpr int kEx2Chains = 8;
+
+__global__ void ex2_rate_kernel(float* __restrict__ out, int iters) {
+    float a[kEx2Chains];
+#pragma unroll
+    for (int k = 0; k < kEx2Chains; ++k) a[k] = 0.5f + 0.01f * (float)k + 1e-7f * (float)threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kEx2Chains; ++k)
+            asm volatile("{\n\t.reg .f32 t;\n\tneg.f32 t, %0;\n\tex2.approx.ftz.f32 %0, t;\n\t}" : "+f"(a[k]));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kEx2Chains; ++k) s += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
 // weight image: every layer's B tile [N][K] (FP16, core-matrix layout) with the
 // bias in column `in` (layer 0) or column 64 (the extra K block of later layers)
 // ---------------------------------------------------------------------------
@@ -941,6 +963,42 @@ ntbc_status ntbc_wait_probe(long long polls, double* seconds, void* stream) {
     if (seconds) *seconds = sec;
     const int gave_up = *reinterpret_cast<const int*>(&h[1]);
     if (gave_up) return fail(NTBC_ETIMEOUT, "bounded wait gave up after %lld polls (%.3f s)", polls, sec);
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_ex2_rate_probe(double* ex2_per_s, void* stream) {
+    using namespace ntbc;
+    clear_error();
+    if (!ex2_per_s) return fail(NTBC_EINVAL, "null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    NTBC_CHECK_CUDA(cudaGetDevice(&dev));
+    NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256, iters = 4096, reps = 5;
+    float* d = nullptr;
+    ntbc_status st = device_alloc((void**)&d, (size_t)blocks * threads * sizeof(float), "exp2 probe");
+    if (st != NTBC_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int w = 0; w < 3 && e == cudaSuccess; ++w) {
+        ntbc::ex2_rate_kernel<<<blocks, threads, 0, s>>>(d, iters);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        ntbc::ex2_rate_kernel<<<blocks, threads, 0, s>>>(d, iters);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "exp2 probe");
+    *ex2_per_s = (double)blocks * threads * iters * ntbc::kEx2Chains * reps / ((double)ms * 1e-3);
     return NTBC_OK;
 }
 

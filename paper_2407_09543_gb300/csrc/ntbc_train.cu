@@ -652,7 +652,7 @@ static ntbc_status check_material(const ntbc_model* m, const ntbc_material* mat)
 
 // gather + dense layers of one network on the batch: features in nb.X, hidden
 // activations in nb.A, sigmoid outputs in nb.Y (feature-major)
-static void net_forward(const ntbc_model* m, const ModelView& mv, bool color, NetBuffers& nb, const int32_t* ids,
+static void net_forward(const float* params, const ModelView& mv, bool color, NetBuffers& nb, const int32_t* ids,
                         int B, GridSrc src, cudaStream_t s) {
     const NetView& nv = color ? mv.color : mv.endpoint;
     const int thr = 128;
@@ -665,16 +665,16 @@ static void net_forward(const ntbc_model* m, const ModelView& mv, bool color, Ne
         float* outbuf = last ? nb.Y : nb.A[l];
         int act = last ? 2 : mv.activation;
         if (l == 0)
-            dense_fwd_kernel<kMaxIn><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, m->params + nv.w_off[l], m->params + nv.b_off[l], nv.layer_out[l], act, outbuf);
+            dense_fwd_kernel<kMaxIn><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, params + nv.w_off[l], params + nv.b_off[l], nv.layer_out[l], act, outbuf);
         else
-            dense_fwd_kernel<kHidden><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, m->params + nv.w_off[l], m->params + nv.b_off[l], nv.layer_out[l], act, outbuf);
+            dense_fwd_kernel<kHidden><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, params + nv.w_off[l], params + nv.b_off[l], nv.layer_out[l], act, outbuf);
         prev = outbuf;
     }
 }
 
 // backward from the output-layer deltas in nb.D0 (d loss / d pre-sigmoid): weight and
 // bias gradients, input gradients, and the grid scatter-add (through the QAT mask)
-static void net_backward(const ntbc_model* m, const ModelView& mv, bool color, NetBuffers& nb, const int32_t* ids,
+static void net_backward(const float* params, const ModelView& mv, bool color, NetBuffers& nb, const int32_t* ids,
                          int B, GridSrc src, float* grads, cudaStream_t s) {
     const NetView& nv = color ? mv.color : mv.endpoint;
     const int thr = 128;
@@ -685,7 +685,7 @@ static void net_backward(const ntbc_model* m, const ModelView& mv, bool color, N
     for (int l = nv.n_layers - 1; l >= 0; --l) {
         const float* Ain = l == 0 ? nb.X : nb.A[l - 1];
         dense_bwd_weight_kernel<<<gw, 256, 0, s>>>(D, nv.layer_out[l], Ain, nv.layer_in[l], B, grads + nv.w_off[l], grads + nv.b_off[l]);
-        dense_bwd_data_kernel<<<g, thr, 0, s>>>(D, nv.layer_out[l], B, m->params + nv.w_off[l], nv.layer_in[l],
+        dense_bwd_data_kernel<<<g, thr, 0, s>>>(D, nv.layer_out[l], B, params + nv.w_off[l], nv.layer_in[l],
                                                  l == 0 ? nullptr : nb.A[l - 1], mv.activation, Dn);
         float* t = D;
         D = Dn;
@@ -694,17 +694,22 @@ static void net_backward(const ntbc_model* m, const ModelView& mv, bool color, N
     grid_scatter_kernel<<<g, thr, 0, s>>>(mv, color, ids, B, D, src, grads);
 }
 
-// one network's forward + loss + backward on the gathered batch
-static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const TexPtrs& tp, const int32_t* ids, int B,
-                           GridSrc src, float T, float* grads, double* acc, cudaStream_t s) {
-    NetBuffers& nb = color ? m->train->color : m->train->endpoint;
-    net_forward(m, mv, color, nb, ids, B, src, s);
+// one network's forward + loss + backward on the gathered batch, on given parameters and
+// buffers (the model's training state, or the allocation-free entry point's scratch)
+static void net_step(const float* params, const ModelView& mv, bool color, const TexPtrs& tp, const int32_t* ids,
+                     int B, GridSrc src, float T, NetBuffers& nb, float* grads, double* acc, cudaStream_t s) {
+    net_forward(params, mv, color, nb, ids, B, src, s);
     const int thr = 128;
     if (color)
         color_loss_kernel<<<blocks_for(B, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, nb.D0, acc);
     else
         endpoint_loss_kernel<<<blocks_for((long long)B * 16, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, nb.D0, acc);
-    net_backward(m, mv, color, nb, ids, B, src, grads, s);
+    net_backward(params, mv, color, nb, ids, B, src, grads, s);
+}
+
+static ntbc_status run_net(ntbc_model* m, const ModelView& mv, bool color, const TexPtrs& tp, const int32_t* ids, int B,
+                           GridSrc src, float T, float* grads, double* acc, cudaStream_t s) {
+    net_step(m->params, mv, color, tp, ids, B, src, T, color ? m->train->color : m->train->endpoint, grads, acc, s);
     NTBC_CHECK_LAUNCH(color ? "colour network step" : "endpoint network step");
     return NTBC_OK;
 }
@@ -882,10 +887,10 @@ ntbc_status ntbc_vjp(ntbc_model* m, const int32_t* block_ids, int n_blocks, int 
         NetBuffers& nb = color ? m->train->color : m->train->endpoint;
         const int B = color ? n_blocks * 16 : n_blocks;
         const int out = color ? m->layout.out_color : m->layout.out_endpoint;
-        net_forward(m, mv, color, nb, block_ids, B, color ? csrc : esrc, s);
+        net_forward(m->params, mv, color, nb, block_ids, B, color ? csrc : esrc, s);
         vjp_seed_kernel<<<blocks_for((long long)B * out, 256), 256, 0, s>>>(nb.Y, out, B, color ? g_c : g_e, nb.D0,
                                                                             color ? c_hat : e_hat);
-        if (g_e) net_backward(m, mv, color, nb, block_ids, B, color ? csrc : esrc, grads, s);
+        if (g_e) net_backward(m->params, mv, color, nb, block_ids, B, color ? csrc : esrc, grads, s);
         NTBC_CHECK_LAUNCH(color ? "colour network vjp" : "endpoint network vjp");
     }
     return NTBC_OK;
@@ -1046,45 +1051,6 @@ static NetBuffers carve_net(float*& cursor, int cap, int out) {
     return nb;
 }
 
-// forward + loss + backward of one network on given buffers (same launches as the
-// model-based path)
-static void noalloc_net(const ModelView& mv, const float* params, bool color, const TexPtrs& tp, const int32_t* ids,
-                        int B, const GridSrc& src, float T, NetBuffers& nb, float* grads, double* acc, cudaStream_t s) {
-    const NetView& nv = color ? mv.color : mv.endpoint;
-    const int thr = 128;
-    unsigned g = blocks_for(B, thr);
-    gather_kernel<<<g, thr, 0, s>>>(mv, color, src, ids, B, nb.X);
-    const float* prev = nb.X;
-    int nl = nv.n_layers;
-    for (int l = 0; l < nl; ++l) {
-        bool last = l + 1 == nl;
-        float* outbuf = last ? nb.Y : nb.A[l];
-        int act = last ? 2 : mv.activation;
-        if (l == 0)
-            dense_fwd_kernel<kMaxIn><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, params + nv.w_off[l], params + nv.b_off[l], nv.layer_out[l], act, outbuf);
-        else
-            dense_fwd_kernel<kHidden><<<g, thr, 0, s>>>(prev, nv.layer_in[l], B, params + nv.w_off[l], params + nv.b_off[l], nv.layer_out[l], act, outbuf);
-        prev = outbuf;
-    }
-    float* D = nb.D0;
-    float* Dn = nb.D1;
-    if (color)
-        color_loss_kernel<<<g, thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
-    else
-        endpoint_loss_kernel<<<blocks_for((long long)B * 16, thr), thr, 0, s>>>(mv, tp, ids, B, nb.Y, T, D, acc);
-    unsigned gw = blocks_for(B, kWgChunk);
-    for (int l = nl - 1; l >= 0; --l) {
-        const float* Ain = l == 0 ? nb.X : nb.A[l - 1];
-        dense_bwd_weight_kernel<<<gw, 256, 0, s>>>(D, nv.layer_out[l], Ain, nv.layer_in[l], B, grads + nv.w_off[l], grads + nv.b_off[l]);
-        dense_bwd_data_kernel<<<g, thr, 0, s>>>(D, nv.layer_out[l], B, params + nv.w_off[l], nv.layer_in[l],
-                                                 l == 0 ? nullptr : nb.A[l - 1], mv.activation, Dn);
-        float* t = D;
-        D = Dn;
-        Dn = t;
-    }
-    grid_scatter_kernel<<<g, thr, 0, s>>>(mv, color, ids, B, D, src, grads);
-}
-
 }  // namespace ntbc
 
 extern "C" {
@@ -1143,8 +1109,8 @@ ntbc_status ntbc_train_grads_noalloc(const ntbc_model_desc* desc, const float* p
     // the array keeps the previous call's contents: clear what accumulates
     NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, L.total * sizeof(float), s));
     NTBC_CHECK_CUDA(cudaMemsetAsync(acc, 0, 6 * sizeof(double), s));
-    noalloc_net(mv, params, true, tp, block_ids, n_blocks * 16, csrc, temperature, cbuf, grads, acc, s);
-    noalloc_net(mv, params, false, tp, block_ids, n_blocks, esrc, temperature, ebuf, grads, acc, s);
+    net_step(params, mv, true, tp, block_ids, n_blocks * 16, csrc, temperature, cbuf, grads, acc, s);
+    net_step(params, mv, false, tp, block_ids, n_blocks, esrc, temperature, ebuf, grads, acc, s);
     loss_finalize_kernel<<<1, 32, 0, s>>>(acc, losses);
     NTBC_CHECK_LAUNCH("allocation-free training gradients");
     return NTBC_OK;

@@ -40,28 +40,8 @@ def init_params(od, seed):
 
 
 def params_from_flat(od, flat):
-    """Split a flat parameter vector in the C ABI's order (colour-grid levels [res][res][F],
-    endpoint-grid levels, colour MLP W [out][in] then b [out] per layer, endpoint MLP) by the
-    oracle's sizes; the whole vector must be consumed."""
-    import numpy as np
-
-    flat = np.asarray(flat)
-    off = 0
-
-    def take(shape):
-        nonlocal off
-        n = int(np.prod(shape))
-        a = flat[off:off + n].reshape(shape)
-        off += n
-        return a
-
-    out = dict(color_grid=[take((r, r, od.features)) for r in od.color_res],
-               endpoint_grid=[take((r, r, od.features)) for r in od.endpoint_res])
-    for which in ("color", "endpoint"):
-        dims = od.mlp_dims(which)
-        out[which + "_mlp"] = [(take((dims[l + 1], dims[l])), take((dims[l + 1],))) for l in range(len(dims) - 1)]
-    assert off == flat.size, (off, flat.size)
-    return out
+    """A flat parameter vector (the C ABI's order) split by the oracle's own reader."""
+    return ont.params_from_flat(od, flat)
 
 
 def as_float32(params):

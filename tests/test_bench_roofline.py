@@ -28,8 +28,10 @@ def test_inference_counts_per_block():
     # grid codes read once (one byte per feature) + 8-byte blocks of four textures
     lay = nt.ntbc_model_layout(_desc())
     assert terms["hbm_bytes_per_pass"] == lay.grid_floats + 32 * n_pos
-    # MUFU peak: 152 SMs x 16 exp2 per clock x 2.07 GHz
-    assert roof["peak"] == pytest.approx(152 * 16 * 2.07e9 / 1e12, rel=1e-4)
+    # MUFU peak without a live measurement: 152 SMs x 32 exp2 per clock (the rate measured on
+    # GB300) x 2.07 GHz; a live measurement replaces it
+    assert roof["peak"] == pytest.approx(152 * 32 * 2.07e9 / 1e12, rel=1e-4)
+    assert bench.inference_roofline(nt, _desc(), 2.0, mufu_peak=9.5e12)[0]["peak"] == pytest.approx(9.5)
     assert roof["bound"] == "alu" and roof["unit"] == "Texp/s"
     assert roof["achieved"] == pytest.approx(3_408 * n_pos / 2.0e-3 / 1e12, rel=1e-3)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"], rel=1e-3)

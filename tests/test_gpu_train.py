@@ -51,7 +51,7 @@ def test_grads_match_oracle(act, hidden, qat):
     got_l = losses.cpu().numpy()
     want_l = [L["L_e"], L["L_cd_endpoint"], L["L_c"], L["L_cd_color"], L["L_endpoint"], L["L_color"]]
     np.testing.assert_allclose(got_l, want_l, rtol=2e-4)
-    gg = nt.configs.unflatten(s["desc"], grads.cpu().numpy())
+    gg = descs.params_from_flat(s["odesc"], grads.cpu().numpy())
     for key in ("color_grid", "endpoint_grid"):
         for a, b in zip(gg[key], g[key]):
             assert rel_err(a, b) < 2e-3, key

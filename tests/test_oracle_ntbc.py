@@ -547,3 +547,28 @@ def test_backward_through_activation_output_equals_through_preactivation(act):
     for (a, b), (c, d) in zip(g1, g0):
         np.testing.assert_allclose(a, c, rtol=1e-12, atol=1e-13)
         np.testing.assert_allclose(b, d, rtol=1e-12, atol=1e-13)
+
+
+def test_params_from_flat_inverts_the_canonical_order():
+    # the flat reader takes exactly the values of flatten_params, in that order, and its size is
+    # the paper-pinned parameter count (4096^2 material, 8 levels 16..2048: the storage figure of
+    # Sec. 4.3 counts the same values)
+    cres = ntbc.level_resolutions(4, 4, 16)
+    desc = ntbc.ModelDesc(32, 32, [1, 4], cres, ntbc.endpoint_resolutions(cres, 8), hidden_layers=2)
+    p = synth.random_params_like(synth.init_params(cres, desc.endpoint_res, 2, desc.mlp_dims("color"),
+                                                   desc.mlp_dims("endpoint"), seed=4), seed=5)
+    flat = np.concatenate([np.asarray(a, np.float64).ravel() for a in ntbc.flatten_params(p)])
+    q = ntbc.params_from_flat(desc, flat)
+    for a, b in zip(ntbc.flatten_params(p), ntbc.flatten_params(q)):
+        assert a.shape == b.shape and np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        ntbc.params_from_flat(desc, flat[:-1])
+    with pytest.raises(ValueError):
+        ntbc.params_from_flat(desc, np.concatenate([flat, [0.0]]))
+    big = ntbc.ModelDesc(4096, 4096, [1, 1, 4, 4, 4, 4], ntbc.level_resolutions(8, 16, 2048),
+                         ntbc.endpoint_resolutions(ntbc.level_resolutions(8, 16, 2048), 1024))
+    n = sum(r * r * 2 for r in big.color_res + big.endpoint_res)
+    for which in ("color", "endpoint"):
+        d = big.mlp_dims(which)
+        n += sum(d[i] * d[i + 1] + d[i + 1] for i in range(len(d) - 1))
+    assert ntbc.storage_bytes(big, grid_bits=32, weight_bytes=4) == 4 * n
