@@ -122,15 +122,6 @@ __device__ __forceinline__ void red_add_f32x2(float* addr, float2 v) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
-// One straight-through factor per corner value: 1 where the QAT code was not clamped.
-__device__ __forceinline__ float2 ste_mask(float2 add, const float* f32, long long corner, float s, float z, float qm) {
-    float2 r = *reinterpret_cast<const float2*>(f32 + corner);
-    float q0 = roundf(__fdiv_rn(r.x, s)) + z, q1 = roundf(__fdiv_rn(r.y, s)) + z;
-    if (q0 < 0.f || q0 > qm) add.x = 0.f;
-    if (q1 < 0.f || q1 > qm) add.y = 0.f;
-    return add;
-}
-
 // Bilinear adjoint: d loss / d features back to the 4 corners of every level.
 // Colour network: the 16 texels of a block sit in one half-warp and their corner
 // indices are non-decreasing in x (lane & 3) and in y (lane >> 2), so equal corners form
@@ -182,9 +173,11 @@ __device__ __forceinline__ void scatter_level(const NetView& nv, bool color, int
     for (int j = 0; j < 4; ++j) {
         int cx = ix + (j & 1), cy = iy + (j >> 1);
         long long corner = nv.grid_off[l] + ((long long)cy * res + cx) * 2;
+        // QAT (Sec. 3.3): the straight-through factor is 1 where the quantiser does not clamp.
+        // alpha and beta are this level's own min and max, recomputed every step, so no grid
+        // value is ever clamped and the factor is 1 throughout; testing the clamp in FP32 instead
+        // could mark a level's maximum as clamped (round(beta / s) + z rounding to 2^b).
         float2 add = make_float2(w[j] * g0, w[j] * g1);
-        if (qat_bits > 0 && valid)
-            add = ste_mask(add, src.f32, corner, src.scale[l], src.zero[l], (float)((1 << qat_bits) - 1));
         bool issue = valid;
         if (color) {
             const int dx = j & 1, dy = j >> 1;

@@ -16,7 +16,7 @@ SPECS = [(64, [1, 4]), (132, [4, 1, 1]), (256, [1, 1, 4, 4, 4]), (96, [4, 4])]
 
 
 def _models(prec):
-    models, outs, descs = [], [], []
+    models, outs, dlist = [], [], []
     for i, (side, formats) in enumerate(SPECS):
         desc, odesc = descs.case_descs(nt, formats, side, 4, 8, max(side // 2, 16), 3, "selu")
         p0 = descs.init_params(odesc, i)
@@ -27,13 +27,13 @@ def _models(prec):
         nb = (side // 4) ** 2
         models.append(m)
         outs.append([torch.full((nb * 8,), 0xAB, dtype=torch.uint8, device=DEV) for _ in formats])
-        descs.append(desc)
-    return models, outs, descs
+        dlist.append(desc)
+    return models, outs, dlist
 
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_batch_equals_single_launches_and_replays(prec):
-    models, outs, descs = _models(prec)
+    models, outs, dlist = _models(prec)
     batch = nt.Batch(models, outs)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -59,7 +59,7 @@ def test_batch_equals_single_launches_and_replays(prec):
 
 
 def test_batch_rejects_fp32_models():
-    models, outs, descs = _models(1)
+    models, outs, dlist = _models(1)
     models[1].export(grid_bits=8, weight_prec=nt.PREC_FP32)
     with pytest.raises(nt.NTBCError):
         nt.Batch(models, outs)
