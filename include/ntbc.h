@@ -313,11 +313,17 @@ ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int 
  *   ntbc_batch_create  models: host array of n models; blocks_out: host array of n host
  *                      arrays, each holding that material's per-texture DEVICE outputs.
  *                      Uploads the launch description (allocates; not capturable).
- *   ntbc_batch_infer   one counter reset and one kernel launch on `stream`; may be
- *                      captured in a CUDA graph and replayed.
- *   ntbc_batch_times   synchronises `stream`; ms (host double[n]) = each material's
- *                      completion time after the start of the last launch
- *                      (device global timer); NTBC_ETIMEOUT if a bounded wait gave up.
+ *   ntbc_batch_infer   one reset of the launch's counters and one kernel launch on
+ *                      `stream`; may be captured in a CUDA graph and replayed. The persistent
+ *                      CTAs take work from a device queue of CTA-units (one 128-block work unit
+ *                      per warpgroup), the materials queued largest first. A claim outside the
+ *                      queue does no work; after 2^16 of them a CTA gives up and the launch
+ *                      reports NTBC_ETIMEOUT through ntbc_batch_times (host-side fault
+ *                      injection NTBC_FAULT=ticket starts the counter negative to test this).
+ *   ntbc_batch_times   synchronises `stream`; ms (host double[n], in the order of `models`)
+ *                      = each material's completion time after the start of the last launch
+ *                      (device global timer); NTBC_ETIMEOUT if a bounded wait or the bounded
+ *                      claim loop gave up.
  */
 typedef struct ntbc_batch ntbc_batch;
 ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out,

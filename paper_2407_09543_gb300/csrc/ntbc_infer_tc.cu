@@ -16,6 +16,8 @@
 // 128 threads read their row of the accumulator (tcgen05.ld 32x32b) and apply
 // SELU (or the sigmoid on the output layer). The other warpgroups of the CTA
 // keep the SM busy while one waits on its MMA.
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "ntbc_internal.cuh"
@@ -130,23 +132,20 @@ __device__ __forceinline__ int choose_code_bc1_x2(const BlockPalette& bp, float 
 }
 
 __device__ __forceinline__ int choose_code_bc4_x2(const BlockPalette& bp, float v) {
-    float d[8];
+    float2 d[4];
 #pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-        float2 dv = __ffma2_rn(make_float2(bp.pal[k][0], bp.pal[k + 1][0]), make_float2(-1.f, -1.f), make_float2(v, v));
-        float2 s2 = __fmul2_rn(dv, dv);
-        d[k] = s2.x;
-        d[k + 1] = s2.y;
+    for (int k = 0; k < 4; ++k) {
+        float2 dv = __ffma2_rn(make_float2(bp.pal[2 * k][0], bp.pal[2 * k + 1][0]), make_float2(-1.f, -1.f),
+                               make_float2(v, v));
+        d[k] = __fmul2_rn(dv, dv);
     }
-    int best = 0;
-    float bestd = d[0];
-#pragma unroll
-    for (int k = 1; k < 8; ++k)
-        if (d[k] < bestd) {
-            bestd = d[k];
-            best = k;
-        }
-    return best;
+    // tournament: the right entry wins only when strictly smaller, so equal distances keep the
+    // lowest code, as a first-minimum scan does
+    int i0 = d[0].y < d[0].x, i1 = 2 + (d[1].y < d[1].x), i2 = 4 + (d[2].y < d[2].x), i3 = 6 + (d[3].y < d[3].x);
+    float m0 = fminf(d[0].x, d[0].y), m1 = fminf(d[1].x, d[1].y), m2 = fminf(d[2].x, d[2].y), m3 = fminf(d[3].x, d[3].y);
+    if (m1 < m0) { m0 = m1; i0 = i1; }
+    if (m3 < m2) { m2 = m3; i2 = i3; }
+    return m2 < m0 ? i2 : i0;
 }
 
 struct TcLayer {
@@ -201,7 +200,7 @@ __host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int s
     s.ones_off = (img_bytes + 127) & ~127;
     s.table_off = s.ones_off + 2 * kTcRows * 16 * 2;             // two constant tiles: L high, L low
     s.lvl_off = s.table_off + 256 * 4;
-    s.group_off = (s.lvl_off + 2 * 2 * NTBC_MAX_LEVELS * 4 + 127) & ~127;
+    s.group_off = (s.lvl_off + 2 * 4 * NTBC_MAX_LEVELS * 4 + 127) & ~127;
     s.a_off = 0;
     s.lo_off = kTcRows * 64 * 2;
     s.pal_off = s.lo_off + (split ? kTcRows * 64 * 2 : 0);
@@ -225,21 +224,22 @@ __device__ __forceinline__ float2 corner_codes(uint32_t word) {
                       make_float2(-8388608.f, -8388608.f));
 }
 
-// corner-aligned bilinear set-up of level l (same arithmetic as bilinear_at, with the
-// per-level constants precomputed as floats)
+// corner-aligned bilinear set-up of level l: p = (u, v) (res - 1); floor(p) as p + 2^23
+// rounded down, the integer then sits in the low mantissa bits (no float-to-int conversion on
+// the XU pipe); p < res - 1 for every texel and block centre (checked on the host), so
+// floor(p) <= res - 2 needs no clamp
 __device__ __forceinline__ Bilinear bilinear_tc(const NetView& nv, int l, float u, float v) {
     float2 p = __fmul2_rn(make_float2(u, v), make_float2(nv.resm1[l], nv.resm1[l]));
-    int res = nv.res[l];
-    int ix = min((int)p.x, res - 2), iy = min((int)p.y, res - 2);    // p >= 0: truncation is floor
-    float2 fl = __fadd2_rn(make_float2(__int_as_float(ix + 0x4B000000), __int_as_float(iy + 0x4B000000)),
-                           make_float2(-8388608.f, -8388608.f));
+    const float tx = __fadd_rd(p.x, 8388608.f), ty = __fadd_rd(p.y, 8388608.f);
+    float2 fl = __fadd2_rn(make_float2(tx, ty), make_float2(-8388608.f, -8388608.f));
     float2 f = __fadd2_rn(p, make_float2(-fl.x, -fl.y));                 // (fx, fy)
     float2 g = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-f.x, -f.y)); // (1 - fx, 1 - fy)
     float2 w0 = __fmul2_rn(make_float2(g.y, g.y), make_float2(g.x, f.x));  // (w00, w01)
     float2 w1 = __fmul2_rn(make_float2(f.y, f.y), make_float2(g.x, f.x));  // (w10, w11)
+    const int ix = __float_as_int(tx) - 0x4B000000, iy = __float_as_int(ty) - 0x4B000000;
     Bilinear b;
-    b.base = ((long long)iy * res + ix) * 2;
-    b.row = res * 2;
+    b.base = (long long)((iy * nv.res[l] + ix) * 2);
+    b.row = nv.res[l] * 2;
     b.w00 = w0.x;
     b.w01 = w0.y;
     b.w10 = w1.x;
@@ -256,7 +256,7 @@ __device__ __forceinline__ uint32_t ld_u16(const uint8_t* p) {
 // split). Exported grids: bilinear interpolation of the exact codes, then the
 // dequantisation s (q - z) L as one FMA with the per-level constants in lvl.
 template <bool SPLIT>
-__device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src, const float2* lvl, float u, float v,
+__device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src, const float4* lvl, float u, float v,
                                            int K0, unsigned char* A, unsigned char* Alo, int r, bool valid) {
     float f[2 * NTBC_MAX_LEVELS];
 #pragma unroll
@@ -272,8 +272,8 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
                 y = __ffma2_rn(make_float2(b.w01, b.w01), corner_codes(c), y);
                 y = __ffma2_rn(make_float2(b.w10, b.w10), corner_codes(d), y);
                 y = __ffma2_rn(make_float2(b.w11, b.w11), corner_codes(e), y);
-                float2 k = lvl[l];
-                float2 f = __ffma2_rn(make_float2(k.x, k.x), y, make_float2(k.y, k.y));
+                const float4 k = lvl[l];
+                float2 f = __ffma2_rn(make_float2(k.x, k.y), y, make_float2(k.z, k.w));
                 f0 = f.x;
                 f1 = f.y;
             } else {
@@ -314,17 +314,17 @@ struct TcGroup {
     int g, r;
 };
 
-// Per-level dequantisation constants of both grids: (s L, -s z L).
+// Per-level dequantisation constants of both grids as pairs: (s L, s L, -s z L, -s z L).
 __device__ __forceinline__ void load_level_constants(const ModelView& mv, const GridSrc& csrc, const GridSrc& esrc,
-                                                     float2* lvl) {
+                                                     float4* lvl) {
     for (int i = threadIdx.x; i < 2 * NTBC_MAX_LEVELS; i += blockDim.x) {
         int net = i / NTBC_MAX_LEVELS, l = i % NTBC_MAX_LEVELS;
         const GridSrc& src = net ? esrc : csrc;
         int L = net ? mv.endpoint.levels : mv.color.levels;
-        float2 k = make_float2(0.f, 0.f);
+        float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
         if (src.codes && l < L) {
             float sc = src.scale[l], z = src.zero[l];
-            k = make_float2(sc * kLog2e, -sc * z * kLog2e);
+            k = make_float4(sc * kLog2e, sc * kLog2e, -sc * z * kLog2e, -sc * z * kLog2e);
         }
         lvl[i] = k;
     }
@@ -394,20 +394,23 @@ __device__ __forceinline__ void teardown_groups(const TcGroup& G, int groups, bo
 template <bool SPLIT>
 __device__ __forceinline__ void issue_steps(const TcLayer& L, int l, unsigned char* smem, unsigned char* A,
                                             const TcSmem& sl, uint32_t tmem_d, int kc0, int kc1, bool bias) {
-    uint32_t idesc = umma_idesc(L.N);
-    uint32_t a_base = smem_u32(A), b_base = smem_u32(smem + L.img);
-    int Ka = l == 0 ? L.K : 64;
+    // descriptors built once; the K step advances only the start-address field (16-byte units,
+    // no carry out of the field for shared-memory addresses), so each MMA adds to the low word
+    const uint32_t idesc = umma_idesc(L.N);
+    const int Ka = l == 0 ? L.K : 64;
+    const uint64_t a0 = umma_desc(smem_u32(A), 128, (Ka / 8) * 128);
+    const uint64_t b0 = umma_desc(smem_u32(smem + L.img), 128, (L.K / 8) * 128);
+    const uint32_t a_lo = (uint32_t)a0, a_hi = (uint32_t)(a0 >> 32);
+    const uint32_t b_lo = (uint32_t)b0, b_hi = (uint32_t)(b0 >> 32);
+    const uint32_t lo_step = (uint32_t)(sl.lo_off - sl.a_off) >> 4;
     for (int kc = kc0; kc < kc1; ++kc) {
-        uint64_t ad = umma_desc(a_base + kc * 256, 128, (Ka / 8) * 128);
-        uint64_t bd = umma_desc(b_base + kc * 256, 128, (L.K / 8) * 128);
-        umma_f16(tmem_d, ad, bd, idesc, kc > 0);
-        if (SPLIT) {
-            uint64_t lo = umma_desc(a_base + (sl.lo_off - sl.a_off) + kc * 256, 128, (Ka / 8) * 128);
-            umma_f16(tmem_d, lo, bd, idesc, 1);
-        }
+        const uint32_t ka = a_lo + (uint32_t)kc * 16u, kb = b_lo + (uint32_t)kc * 16u;
+        const uint64_t bd = ((uint64_t)b_hi << 32) | kb;
+        umma_f16(tmem_d, ((uint64_t)a_hi << 32) | ka, bd, idesc, kc > 0);
+        if (SPLIT) umma_f16(tmem_d, ((uint64_t)a_hi << 32) | (ka + lo_step), bd, idesc, 1);
     }
     if (bias) {
-        uint64_t bd = umma_desc(b_base + (Ka / 16) * 256, 128, (L.K / 8) * 128);
+        const uint64_t bd = ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)(Ka / 16) * 16u);
         umma_f16(tmem_d, umma_desc(smem_u32(smem + sl.ones_off), 128, 256), bd, idesc, 1);
         if (SPLIT) umma_f16(tmem_d, umma_desc(smem_u32(smem + sl.ones_off + kTcRows * 32), 128, 256), bd, idesc, 1);
     }
@@ -503,7 +506,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
     uint64_t* bar = G.bar;
     const uint32_t tmem = G.tmem, tmem_row = G.tmem_row;
     const float* tab = reinterpret_cast<const float*>(smem + sl.table_off);
-    const float2* lvl = reinterpret_cast<const float2*>(smem + sl.lvl_off);
+    const float4* lvl = reinterpret_cast<const float4*>(smem + sl.lvl_off);
     const int T = mv.n_textures;
     bool ok = true;
         // ================= endpoint network: row r = block r of the unit
@@ -658,7 +661,7 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
     const TcSmem sl = tc_smem_layout(args.img_bytes, args.mv.n_textures, SPLIT);
     for (int i = threadIdx.x; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
     load_constants(smem, sl);
-    load_level_constants(args.mv, csrc, esrc, reinterpret_cast<float2*>(smem + sl.lvl_off));
+    load_level_constants(args.mv, csrc, esrc, reinterpret_cast<float4*>(smem + sl.lvl_off));
     TcGroup G = setup_groups(smem, sl, args.groups, &tmem_slot, abort_flag);
     uint32_t phase = 0, region = 0;
     bool ok = true;
@@ -686,6 +689,8 @@ struct TcBatchHeader {
     int* done;                   // [n_mats] units completed
     unsigned long long* stamps;  // [n_mats + 1]: kernel start, then each material's completion (globaltimer, ns)
     int* err;
+    int* ticket;                 // work queue: the next CTA-unit to claim
+    long long claim_limit;       // claims outside the queue a CTA makes before it gives up
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -694,10 +699,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// The grid strides over CTA-units; all groups of a CTA work on the same material, so the
-// weight image is reloaded (after a CTA barrier) only when the CTA crosses into the next
-// material. A group that gave up keeps walking the CTA-units (skipping the work) so that
-// the CTA barriers stay uniform.
+// A device work queue of CTA-units (one work unit per warpgroup, all from one material; the
+// materials ordered largest first): thread 0 claims the next CTA-unit from the ticket counter
+// and the CTA works on it, so CTAs that finish early take more work instead of idling at the
+// end of a static share. All groups of a CTA work on the same material, so the weight image
+// is reloaded (after a CTA barrier) only when the CTA crosses into the next material. A claim
+// outside the queue (a negative ticket: the counter was corrupted) does no work; after
+// claim_limit of them the CTA records the error and stops, so a bad counter ends the launch
+// with NTBC_ETIMEOUT instead of spinning. A group that gave up keeps claiming with its CTA
+// (skipping the work) so that the CTA barriers stay uniform.
 template <bool SPLIT>
 __global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
 infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
@@ -705,6 +715,7 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag[kTcMaxGroups];
     __shared__ TcMat cur;
+    __shared__ int claim[2];
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr.stamps[0] = global_ns();
     const TcSmem sl = tc_smem_layout(hdr.img_bytes, hdr.max_textures, SPLIT);
     load_constants(smem, sl);
@@ -712,17 +723,31 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
     uint32_t phase = 0, region = 0;
     bool ok = true;
     int m = -1;
-    for (int j = blockIdx.x; j < hdr.total_cta_units; j += gridDim.x) {
+    long long bad = 0;
+    for (int it = 0;; ++it) {
+        // double-buffered by iteration: the slot written here was last read before the
+        // previous iteration's barrier
+        if (threadIdx.x == 0) claim[it & 1] = atomicAdd(hdr.ticket, 1);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int j = claim[it & 1];
+        if (j >= hdr.total_cta_units) break;
+        if (j < 0) {
+            if (++bad >= hdr.claim_limit) {
+                if (threadIdx.x == 0) atomicExch(hdr.err, 1);
+                break;
+            }
+            continue;
+        }
         int mj = m < 0 ? 0 : m;
         while (mj + 1 < hdr.n_mats && mats[mj + 1].first_cta_unit <= j) ++mj;
         if (mj != m) {                                   // uniform across the CTA
-            tc_fence_before();
-            __syncthreads();
             if (threadIdx.x == 0) cur = mats[mj];
             __syncthreads();
             for (int i = threadIdx.x; i < cur.args.img_bytes / 16; i += blockDim.x)
                 reinterpret_cast<uint4*>(smem)[i] = cur.img[i];
-            load_level_constants(cur.args.mv, cur.csrc, cur.esrc, reinterpret_cast<float2*>(smem + sl.lvl_off));
+            load_level_constants(cur.args.mv, cur.csrc, cur.esrc, reinterpret_cast<float4*>(smem + sl.lvl_off));
             proxy_fence();
             __syncthreads();
             tc_fence_after();
@@ -844,6 +869,24 @@ static TcArgs tc_args(const ntbc_model* m) {
 
 // static_bytes: the kernel's static shared variables (the batch kernel keeps a copy of
 // the current material's launch description)
+// The tensor-core gather takes floor(p) for p = t (res - 1) without clamping it to res - 2:
+// true when the largest texel or block centre coordinate t_max (computed in FP32 as the kernel
+// does) keeps p below res - 1, which holds unless (res - 1) / extent falls under FP32 rounding
+// of res - 1. Checked for every level of both grids before a launch.
+static bool floor_in_range(const NetView& nv, int extent, float inv) {
+    const float t_max = ((float)(extent - 1) + 0.5f) * inv;
+    for (int l = 0; l < nv.levels; ++l) {
+        const float p = t_max * nv.resm1[l];
+        if (!(std::floor(p) <= (float)(nv.res[l] - 2))) return false;
+    }
+    return true;
+}
+
+static bool tc_coords_ok(const TcArgs& a) {
+    return floor_in_range(a.mv.color, a.mv.width, a.inv_w) && floor_in_range(a.mv.color, a.mv.height, a.inv_h) &&
+           floor_in_range(a.mv.endpoint, a.mv.bw, a.inv_bw) && floor_in_range(a.mv.endpoint, a.mv.bh, a.inv_bh);
+}
+
 static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, size_t static_bytes = 256) {
     for (int groups = kTcMaxGroups; groups >= 1; --groups) {
         TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split);
@@ -889,6 +932,7 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
     const bool split = m->weight_prec != NTBC_PREC_FP16_FAST;     // FP16 and FP8 weights
     a.groups = tc_groups(a, m->desc.n_textures, split, &smem);
     if (a.groups == 0) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: shared memory too small for this model");
+    if (!tc_coords_ok(a)) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: a grid level is too fine for the texture extent");
     a.n = n;
     a.ids = ids;
     a.mode = blocks_out ? 0 : 1;
@@ -926,7 +970,8 @@ struct ntbc_batch {
     size_t smem = 0;
     ntbc::TcBatchHeader hdr{};
     ntbc::TcMat* d_mats = nullptr;
-    unsigned char* d_mem = nullptr;     // done counters, stamps, error flag
+    unsigned char* d_mem = nullptr;     // stamps, done counters, error flag, ticket counter
+    std::vector<int> order;             // queue position -> the caller's material index
 };
 
 namespace ntbc {
@@ -1020,6 +1065,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         TcMat& t = mats[i];
         memset(&t, 0, sizeof(t));
         t.args = tc_args(m);
+        if (!tc_coords_ok(t.args)) return fail(NTBC_EUNSUPPORTED, "material %d: a grid level is too fine for the texture extent", i);
         t.args.n = (m->desc.width / 4) * (m->desc.height / 4);
         t.args.mode = 0;
         t.img = reinterpret_cast<const uint4*>(m->umma_img);
@@ -1035,8 +1081,17 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         max_tex = std::max(max_tex, m->desc.n_textures);
         max_img = std::max(max_img, t.args.img_bytes);
     }
+    // the queue holds the materials largest first, so the last claims are the small units of
+    // the small materials and the CTAs finish close together
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mats[a].units > mats[b].units; });
+    std::vector<TcMat> sorted(n);
+    for (int i = 0; i < n; ++i) sorted[i] = mats[order[i]];
+    mats.swap(sorted);
     ntbc_batch* b = new ntbc_batch();
     b->n = n;
+    b->order = order;
     b->split = prec == NTBC_PREC_FP16;
     TcArgs probe;
     memset(&probe, 0, sizeof(probe));
@@ -1048,7 +1103,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         mats[i].args.groups = b->groups;
         total += (mats[i].units + b->groups - 1) / b->groups;
     }
-    size_t mem = (size_t)n * sizeof(int) + (size_t)(n + 1) * sizeof(unsigned long long) + 16;
+    size_t mem = (size_t)(n + 1) * sizeof(unsigned long long) + (size_t)(n + 2) * sizeof(int);
     ntbc_status st = device_alloc((void**)&b->d_mats, (size_t)n * sizeof(TcMat), "batch descriptors");
     if (st == NTBC_OK) st = device_alloc((void**)&b->d_mem, mem, "batch counters");
     if (st != NTBC_OK) return batch_fail_free(b, st);
@@ -1060,6 +1115,8 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
     b->hdr.stamps = reinterpret_cast<unsigned long long*>(b->d_mem);
     b->hdr.done = reinterpret_cast<int*>(b->d_mem + (size_t)(n + 1) * sizeof(unsigned long long));
     b->hdr.err = b->hdr.done + n;
+    b->hdr.ticket = b->hdr.err + 1;
+    b->hdr.claim_limit = 1 << 16;
     for (int i = 0; i < n; ++i) mats[i].args.err = b->hdr.err;
     cudaError_t e = cudaMemcpy(b->d_mats, mats.data(), (size_t)n * sizeof(TcMat), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_mem, 0, mem);
@@ -1080,7 +1137,11 @@ ntbc_status ntbc_batch_infer(ntbc_batch* b, void* stream) {
     clear_error();
     if (!b) return fail(NTBC_EINVAL, "null batch");
     cudaStream_t s = (cudaStream_t)stream;
-    NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.done, 0, (size_t)b->n * sizeof(int), s));
+    // completion counters, the error flag and the ticket counter start at zero every launch;
+    // NTBC_FAULT=ticket corrupts the ticket counter instead (a negative start), which the
+    // kernel's bounded claim loop turns into NTBC_ETIMEOUT
+    NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.done, 0, (size_t)(b->n + 2) * sizeof(int), s));
+    if (fault_injected("ticket")) NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.ticket, 0x80, sizeof(int), s));
     if (b->split)
         infer_tc_batch_kernel<true><<<b->grid, kTcRows * b->groups, b->smem, s>>>(b->hdr, b->d_mats);
     else
@@ -1098,8 +1159,8 @@ ntbc_status ntbc_batch_times(const ntbc_batch* b, double* ms, void* stream) {
     int err = 0;
     NTBC_CHECK_CUDA(cudaMemcpy(st.data(), b->hdr.stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     NTBC_CHECK_CUDA(cudaMemcpy(&err, b->hdr.err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) return fail(NTBC_ETIMEOUT, "a bounded wait in the batched inference gave up");
-    for (int i = 0; i < b->n; ++i) ms[i] = st[i + 1] >= st[0] ? (double)(st[i + 1] - st[0]) * 1e-6 : -1.0;
+    if (err) return fail(NTBC_ETIMEOUT, "a bounded wait or the bounded work-queue claim loop of the batched inference gave up");
+    for (int i = 0; i < b->n; ++i) ms[b->order[i]] = st[i + 1] >= st[0] ? (double)(st[i + 1] - st[0]) * 1e-6 : -1.0;
     return NTBC_OK;
 }
 
