@@ -439,11 +439,13 @@ const char* ntbc_last_error(void) { return g_last_error.c_str(); }
 int ntbc_abi_version(void) { return 1; }
 
 ntbc_status bc_reference_encode(int fmt, const uint8_t* texels, int w, int h, uint8_t* blocks, void* stream) {
+    ntbc::NvtxRange nvtx_range("bc_reference_encode");
     return bc_reference_encode_refined(fmt, texels, w, h, 0, blocks, stream);
 }
 
 ntbc_status bc_reference_encode_refined(int fmt, const uint8_t* texels, int w, int h, int refine, uint8_t* blocks,
                                         void* stream) {
+    ntbc::NvtxRange nvtx_range("bc_reference_encode_refined");
     clear_error();
     ntbc_status st = check_texture_args(fmt, texels, blocks, w, h);
     if (st != NTBC_OK) return st;
@@ -468,6 +470,7 @@ ntbc_status bc_reference_encode_refined(int fmt, const uint8_t* texels, int w, i
 }
 
 ntbc_status bc_decode(int fmt, const uint8_t* blocks, int w, int h, uint8_t* texels, void* stream) {
+    ntbc::NvtxRange nvtx_range("bc_decode");
     clear_error();
     ntbc_status st = check_texture_args(fmt, blocks, texels, w, h);
     if (st != NTBC_OK) return st;

@@ -342,6 +342,7 @@ extern "C" {
 
 ntbc_status ntbc_infer_to_bc_strided(const ntbc_model* m, uint8_t* const* blocks_out, const int* block_stride,
                                      void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_infer_to_bc_strided");
     clear_error();
     if (!m || !blocks_out) return fail(NTBC_EINVAL, "null argument");
     OutPtrs outs;
@@ -369,6 +370,7 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* m, uint8_t* const* blocks_out, vo
 }
 
 ntbc_status ntbc_infer_to_host(ntbc_model* m, uint8_t* const* host_out, int chunks, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_infer_to_host");
     clear_error();
     if (!m || !host_out) return fail(NTBC_EINVAL, "null argument");
     if (chunks < 1 || chunks > kHostIoMaxChunks) return fail(NTBC_EINVAL, "chunks must be 1..%d", kHostIoMaxChunks);
@@ -387,17 +389,18 @@ ntbc_status ntbc_infer_to_host(ntbc_model* m, uint8_t* const* host_out, int chun
         stage[t] = io->stage + (size_t)t * n * 8;
         strides[t] = 8;
     }
-    // ranges of whole work units (128 blocks); on the tensor-core path every range but the
-    // last is a whole number of rounds of the units in flight, so the ranged launches take no
-    // more rounds than one launch over the material would
-    const int units = (n + 127) / 128;
+    // ranges of whole work units (128 blocks, or the tensor-core kernel's unit size); on the
+    // tensor-core path every range but the last is a whole number of rounds of the units in
+    // flight, so the ranged launches take no more rounds than one launch over the material would
+    int ub = 128;
+    const int flight = m->weight_prec != NTBC_PREC_FP32 ? tc_units_in_flight(m, &ub) : 0;
+    const int units = (n + ub - 1) / ub;
     int per_units = (units + chunks - 1) / chunks;
-    const int flight = m->weight_prec != NTBC_PREC_FP32 ? tc_units_in_flight(m) : 0;
     if (flight > 0) {
         const int rounds = (units + flight - 1) / flight;
         per_units = (rounds + chunks - 1) / chunks * flight;
     }
-    const int per = per_units * 128;
+    const int per = per_units * ub;
     GridSrc csrc, esrc;
     if (m->weight_prec != NTBC_PREC_FP32) {
         st = grid_sources(m, csrc, esrc);
@@ -431,6 +434,7 @@ ntbc_status ntbc_infer_to_host(ntbc_model* m, uint8_t* const* host_out, int chun
 }
 
 ntbc_status ntbc_forward(const ntbc_model* m, const int32_t* block_ids, int n, float* e_hat, float* c_hat, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_forward");
     clear_error();
     if (!m) return fail(NTBC_EINVAL, "null model");
     if (n < 0) return fail(NTBC_EINVAL, "negative count");

@@ -27,8 +27,10 @@
 namespace ntbc {
 
 constexpr int kTcRows = 128;               // M of every MMA: blocks (endpoint) or texels (colour)
+// Work unit: kTcUnitBlocks consecutive blocks (the endpoint MMA's 128 rows), or half of that
+// when the palettes of a material with many textures would leave room for fewer warpgroups
+// (the endpoint MMA then runs with 64 valid rows)
 constexpr int kTcUnitBlocks = 128;
-constexpr int kTcTiles = kTcUnitBlocks * 16 / kTcRows;   // 16 colour tiles per unit
 constexpr int kTcMaxGroups = 4;
 constexpr int kTcColsPerGroup = 128;           // two 64-column accumulator regions per group
 constexpr int kTcPalBytes = 12;            // integer palette bytes per block per texture
@@ -168,6 +170,7 @@ struct TcArgs {
     int n;                    // blocks to process
     const int32_t* ids;       // optional block ids (else 0..n-1)
     int mode;                 // 0 pack, 1 raw outputs
+    int ub;                   // blocks per work unit (128, or 64)
     int* err;
     float inv_w, inv_h, inv_bw, inv_bh;   // reciprocals of the texel and block extents
 };
@@ -195,7 +198,7 @@ struct TcSmem {
 // constants. Per group: A tile (FP16 activations), the low-half tile when split, the
 // unit's integer palettes (12 bytes per block and texture) and quantised endpoints,
 // and the group's mbarrier.
-__host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int split) {
+__host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int split, int ub) {
     TcSmem s;
     s.ones_off = (img_bytes + 127) & ~127;
     s.table_off = s.ones_off + 2 * kTcRows * 16 * 2;             // two constant tiles: L high, L low
@@ -204,8 +207,8 @@ __host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int s
     s.a_off = 0;
     s.lo_off = kTcRows * 64 * 2;
     s.pal_off = s.lo_off + (split ? kTcRows * 64 * 2 : 0);
-    s.ep_off = s.pal_off + ((n_tex * kTcUnitBlocks * kTcPalBytes + 15) & ~15);
-    s.bar_off = s.ep_off + n_tex * kTcUnitBlocks * 4;
+    s.ep_off = s.pal_off + ((n_tex * ub * kTcPalBytes + 15) & ~15);
+    s.bar_off = s.ep_off + n_tex * ub * 4;
     s.group_bytes = (s.bar_off + 16 + 127) & ~127;
     return s;
 }
@@ -491,8 +494,8 @@ __device__ __forceinline__ bool run_mlp(const TcNet& net, int act, unsigned char
     return abort_flag[G.g] == 0;
 }
 
-// One work unit (128 blocks): endpoint network, palettes, then 16 colour tiles.
-template <bool SPLIT>
+// One work unit (UB blocks, 128 or 64): endpoint network, palettes, then UB / 8 colour tiles.
+template <bool SPLIT, int UB>
 __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& csrc, const GridSrc& esrc, const TcOut& outs,
                                           float* __restrict__ e_out, float* __restrict__ c_out, int unit,
                                           unsigned char* smem, const TcSmem& sl, const TcGroup& G, uint32_t& phase,
@@ -508,12 +511,13 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
     const float* tab = reinterpret_cast<const float*>(smem + sl.table_off);
     const float4* lvl = reinterpret_cast<const float4*>(smem + sl.lvl_off);
     const int T = mv.n_textures;
+    constexpr int ub = UB;
     bool ok = true;
         // ================= endpoint network: row r = block r of the unit
         {
             const TcNet& net = args.net[1];
-            int k = unit * kTcUnitBlocks + r;
-            bool valid = k < args.n;
+            int k = unit * ub + r;
+            bool valid = r < ub && k < args.n;
             int b = valid ? (args.ids ? args.ids[k] : k) : 0;
             int bx, by;
             block_xy(b, mv.bw, args.inv_bw, bx, by);
@@ -532,9 +536,9 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                     }
                     continue;
                 }
-                for (int t = 0; t < T; ++t) {
+                for (int t = 0; t < T && r < ub; ++t) {
                     int eo = mv.eoff[t];
-                    uint8_t* pb = palb + (t * kTcUnitBlocks + r) * kTcPalBytes;
+                    uint8_t* pb = palb + (t * ub + r) * kTcPalBytes;
                     float e[6];
                     if (mv.formats[t] == NTBC_BC1) {
 #pragma unroll
@@ -557,7 +561,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                         for (int q = 0; q < 4; ++q)
 #pragma unroll
                             for (int ch = 0; ch < 3; ++ch) pb[q * 3 + ch] = (uint8_t)p[q][ch];
-                        eps[t * kTcUnitBlocks + r] = c0 | (c1 << 16);
+                        eps[t * ub + r] = c0 | (c1 << 16);
                     } else {
                         e[0] = tmem_ld1(tmem_row + eo);
                         e[1] = tmem_ld1(tmem_row + eo + 1);
@@ -568,16 +572,16 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                         bc4_palette(r0, r1, p);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) pb[q] = (uint8_t)p[q];
-                        eps[t * kTcUnitBlocks + r] = (uint32_t)r0 | ((uint32_t)r1 << 8);
+                        eps[t * ub + r] = (uint32_t)r0 | ((uint32_t)r1 << 8);
                     }
                 }
             }
         }
         // ================= colour network: 16 tiles of 8 blocks x 16 texels
-        for (int tile = 0; tile < kTcTiles && ok; ++tile) {
+        for (int tile = 0; tile < ub / 8 && ok; ++tile) {
             const TcNet& net = args.net[0];
             int blk = tile * 8 + r / 16, i = r & 15;
-            int k = unit * kTcUnitBlocks + blk;
+            int k = unit * ub + blk;
             bool valid = k < args.n;
             int b = valid ? (args.ids ? args.ids[k] : k) : 0;
             int bx, by;
@@ -613,8 +617,8 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
 #pragma unroll
                 for (int t = 0; t < NTBC_MAX_TEXTURES; ++t) {
                     if (t >= T) break;
-                    const uint8_t* pb = palb + (t * kTcUnitBlocks + blk) * kTcPalBytes;
-                    uint32_t ep = eps[t * kTcUnitBlocks + blk];
+                    const uint8_t* pb = palb + (t * ub + blk) * kTcPalBytes;
+                    uint32_t ep = eps[t * ub + blk];
                     BlockPalette bp;
                     uint64_t bits;
                     if (mv.formats[t] == NTBC_BC1) {           // 2-bit codes: the block's 32 bits in one word
@@ -651,23 +655,23 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
     return ok;
 }
 
-template <bool SPLIT>
+template <bool SPLIT, int UB>
 __global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
 infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSrc esrc, TcOut outs,
                 float* __restrict__ e_out, float* __restrict__ c_out) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag[kTcMaxGroups];
-    const TcSmem sl = tc_smem_layout(args.img_bytes, args.mv.n_textures, SPLIT);
+    const TcSmem sl = tc_smem_layout(args.img_bytes, args.mv.n_textures, SPLIT, UB);
     for (int i = threadIdx.x; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
     load_constants(smem, sl);
     load_level_constants(args.mv, csrc, esrc, reinterpret_cast<float4*>(smem + sl.lvl_off));
     TcGroup G = setup_groups(smem, sl, args.groups, &tmem_slot, abort_flag);
     uint32_t phase = 0, region = 0;
     bool ok = true;
-    const int n_units = (args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
+    const int n_units = (args.n + UB - 1) / UB;
     for (int unit = blockIdx.x * args.groups + G.g; unit < n_units && ok; unit += gridDim.x * args.groups)
-        ok = process_unit<SPLIT>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, region, abort_flag);
+        ok = process_unit<SPLIT, UB>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, region, abort_flag);
     teardown_groups(G, args.groups, ok, phase, args.err, tmem_slot);
 }
 
@@ -685,7 +689,7 @@ struct TcMat {
 };
 
 struct TcBatchHeader {
-    int n_mats, total_cta_units, groups, img_bytes, max_textures;
+    int n_mats, total_cta_units, groups, img_bytes, max_textures, ub;
     int* done;                   // [n_mats] units completed
     unsigned long long* stamps;  // [n_mats + 1]: kernel start, then each material's completion (globaltimer, ns)
     int* err;
@@ -708,7 +712,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // claim_limit of them the CTA records the error and stops, so a bad counter ends the launch
 // with NTBC_ETIMEOUT instead of spinning. A group that gave up keeps claiming with its CTA
 // (skipping the work) so that the CTA barriers stay uniform.
-template <bool SPLIT>
+template <bool SPLIT, int UB>
 __global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
 infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -717,7 +721,7 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
     __shared__ TcMat cur;
     __shared__ int claim[2];
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr.stamps[0] = global_ns();
-    const TcSmem sl = tc_smem_layout(hdr.img_bytes, hdr.max_textures, SPLIT);
+    const TcSmem sl = tc_smem_layout(hdr.img_bytes, hdr.max_textures, SPLIT, UB);
     load_constants(smem, sl);
     TcGroup G = setup_groups(smem, sl, hdr.groups, &tmem_slot, abort_flag);
     uint32_t phase = 0, region = 0;
@@ -755,7 +759,7 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
         }
         int unit = (j - cur.first_cta_unit) * hdr.groups + G.g;
         if (ok && unit < cur.units) {
-            ok = process_unit<SPLIT>(cur.args, cur.csrc, cur.esrc, cur.outs, nullptr, nullptr, unit, smem, sl, G, phase,
+            ok = process_unit<SPLIT, UB>(cur.args, cur.csrc, cur.esrc, cur.outs, nullptr, nullptr, unit, smem, sl, G, phase,
                                      region, abort_flag);
             if (ok && G.r == 0) {
                 __threadfence();
@@ -867,8 +871,6 @@ static TcArgs tc_args(const ntbc_model* m) {
     return a;
 }
 
-// static_bytes: the kernel's static shared variables (the batch kernel keeps a copy of
-// the current material's launch description)
 // The tensor-core gather takes floor(p) for p = t (res - 1) without clamping it to res - 2:
 // true when the largest texel or block centre coordinate t_max (computed in FP32 as the kernel
 // does) keeps p below res - 1, which holds unless (res - 1) / extent falls under FP32 rounding
@@ -887,9 +889,12 @@ static bool tc_coords_ok(const TcArgs& a) {
            floor_in_range(a.mv.endpoint, a.mv.bw, a.inv_bw) && floor_in_range(a.mv.endpoint, a.mv.bh, a.inv_bh);
 }
 
-static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, size_t static_bytes = 256) {
+// static_bytes: the kernel's static shared variables (the batch kernel keeps a copy of
+// the current material's launch description). Returns the warpgroups per CTA and sets the
+// work-unit size: 128 blocks, unless 64-block units (half the palette space) fit more groups.
+static int tc_groups_ub(const TcArgs& a, int n_tex, int split, int ub, size_t* smem_bytes, size_t static_bytes) {
     for (int groups = kTcMaxGroups; groups >= 1; --groups) {
-        TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split);
+        TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split, ub);
         size_t bytes = (size_t)sl.group_off + (size_t)groups * sl.group_bytes;
         if (bytes + static_bytes <= 227 * 1024) {
             // more than two groups allocate all 512 TMEM columns: ask for enough shared
@@ -900,6 +905,20 @@ static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, 
         }
     }
     return 0;
+}
+
+static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, int* ub, size_t static_bytes = 256) {
+    size_t s128 = 0, s64 = 0;
+    const int g128 = tc_groups_ub(a, n_tex, split, kTcUnitBlocks, &s128, static_bytes);
+    const int g64 = g128 == kTcMaxGroups ? 0 : tc_groups_ub(a, n_tex, split, kTcUnitBlocks / 2, &s64, static_bytes);
+    if (g64 > g128) {
+        *smem_bytes = s64;
+        *ub = kTcUnitBlocks / 2;
+        return g64;
+    }
+    *smem_bytes = s128;
+    *ub = kTcUnitBlocks;
+    return g128;
 }
 
 ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s) {
@@ -915,10 +934,12 @@ ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s) {
     return NTBC_OK;
 }
 
-int tc_units_in_flight(const ntbc_model* m) {
+int tc_units_in_flight(const ntbc_model* m, int* unit_blocks) {
     TcArgs a = tc_args(m);
     size_t smem = 0;
-    const int groups = tc_groups(a, m->desc.n_textures, m->weight_prec != NTBC_PREC_FP16_FAST, &smem);
+    int ub = kTcUnitBlocks;
+    const int groups = tc_groups(a, m->desc.n_textures, m->weight_prec != NTBC_PREC_FP16_FAST, &smem, &ub);
+    if (unit_blocks) *unit_blocks = ub;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
@@ -930,7 +951,7 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
     TcArgs a = tc_args(m);
     size_t smem = 0;
     const bool split = m->weight_prec != NTBC_PREC_FP16_FAST;     // FP16 and FP8 weights
-    a.groups = tc_groups(a, m->desc.n_textures, split, &smem);
+    a.groups = tc_groups(a, m->desc.n_textures, split, &smem, &a.ub);
     if (a.groups == 0) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: shared memory too small for this model");
     if (!tc_coords_ok(a)) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: a grid level is too fine for the texture extent");
     a.n = n;
@@ -947,17 +968,18 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
     int dev = 0, sms = 0;
     NTBC_CHECK_CUDA(cudaGetDevice(&dev));
     NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int units = (n + kTcUnitBlocks - 1) / kTcUnitBlocks;
+    int units = (n + a.ub - 1) / a.ub;
     int grid = std::min(sms, (units + a.groups - 1) / a.groups);
     if (grid < 1) return NTBC_OK;
     const uint4* img = reinterpret_cast<const uint4*>(m->umma_img);
-    if (split) {
-        NTBC_CHECK_CUDA(cudaFuncSetAttribute(infer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        infer_tc_kernel<true><<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
-    } else {
-        NTBC_CHECK_CUDA(cudaFuncSetAttribute(infer_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        infer_tc_kernel<false><<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
-    }
+    auto launch = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) kernel<<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
+        return e;
+    };
+    const bool half = a.ub != kTcUnitBlocks;
+    NTBC_CHECK_CUDA(split ? (half ? launch(infer_tc_kernel<true, kTcUnitBlocks / 2>) : launch(infer_tc_kernel<true, kTcUnitBlocks>))
+                          : (half ? launch(infer_tc_kernel<false, kTcUnitBlocks / 2>) : launch(infer_tc_kernel<false, kTcUnitBlocks>)));
     NTBC_CHECK_LAUNCH("ntbc inference (tcgen05)");
     return NTBC_OK;
 }
@@ -975,6 +997,16 @@ struct ntbc_batch {
 };
 
 namespace ntbc {
+
+static cudaError_t batch_set_smem(const ntbc_batch* b) {
+    const int bytes = (int)b->smem;
+    const bool half = b->hdr.ub != kTcUnitBlocks;
+    if (b->split)
+        return half ? cudaFuncSetAttribute(infer_tc_batch_kernel<true, kTcUnitBlocks / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                    : cudaFuncSetAttribute(infer_tc_batch_kernel<true, kTcUnitBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return half ? cudaFuncSetAttribute(infer_tc_batch_kernel<false, kTcUnitBlocks / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                : cudaFuncSetAttribute(infer_tc_batch_kernel<false, kTcUnitBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 static ntbc_status batch_fail_free(ntbc_batch* b, ntbc_status st) {
     if (b) {
@@ -1077,7 +1109,6 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
             t.outs.p[k] = o;
             t.outs.stride[k] = 8;
         }
-        t.units = (t.args.n + kTcUnitBlocks - 1) / kTcUnitBlocks;
         max_tex = std::max(max_tex, m->desc.n_textures);
         max_img = std::max(max_img, t.args.img_bytes);
     }
@@ -1085,7 +1116,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
     // the small materials and the CTAs finish close together
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mats[a].units > mats[b].units; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mats[a].args.n > mats[b].args.n; });
     std::vector<TcMat> sorted(n);
     for (int i = 0; i < n; ++i) sorted[i] = mats[order[i]];
     mats.swap(sorted);
@@ -1096,8 +1127,13 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
     TcArgs probe;
     memset(&probe, 0, sizeof(probe));
     probe.img_bytes = max_img;
-    b->groups = tc_groups(probe, max_tex, b->split, &b->smem, sizeof(TcMat) + 256);
+    int ub = kTcUnitBlocks;
+    b->groups = tc_groups(probe, max_tex, b->split, &b->smem, &ub, sizeof(TcMat) + 256);
     if (b->groups == 0) return batch_fail_free(b, fail(NTBC_EUNSUPPORTED, "batch: shared memory too small"));
+    for (int i = 0; i < n; ++i) {
+        mats[i].args.ub = ub;
+        mats[i].units = (mats[i].args.n + ub - 1) / ub;
+    }
     for (int i = 0; i < n; ++i) {
         mats[i].first_cta_unit = total;
         mats[i].args.groups = b->groups;
@@ -1112,6 +1148,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
     b->hdr.groups = b->groups;
     b->hdr.img_bytes = max_img;
     b->hdr.max_textures = max_tex;
+    b->hdr.ub = ub;
     b->hdr.stamps = reinterpret_cast<unsigned long long*>(b->d_mem);
     b->hdr.done = reinterpret_cast<int*>(b->d_mem + (size_t)(n + 1) * sizeof(unsigned long long));
     b->hdr.err = b->hdr.done + n;
@@ -1124,8 +1161,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = b->split ? cudaFuncSetAttribute(infer_tc_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem)
-                     : cudaFuncSetAttribute(infer_tc_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        e = batch_set_smem(b);
     if (e != cudaSuccess) return batch_fail_free(b, cuda_fail(e, "batch set-up"));
     b->grid = std::min(sms, total);
     *out = b;
@@ -1133,6 +1169,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
 }
 
 ntbc_status ntbc_batch_infer(ntbc_batch* b, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_batch_infer");
     using namespace ntbc;
     clear_error();
     if (!b) return fail(NTBC_EINVAL, "null batch");
@@ -1142,10 +1179,15 @@ ntbc_status ntbc_batch_infer(ntbc_batch* b, void* stream) {
     // kernel's bounded claim loop turns into NTBC_ETIMEOUT
     NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.done, 0, (size_t)(b->n + 2) * sizeof(int), s));
     if (fault_injected("ticket")) NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.ticket, 0x80, sizeof(int), s));
-    if (b->split)
-        infer_tc_batch_kernel<true><<<b->grid, kTcRows * b->groups, b->smem, s>>>(b->hdr, b->d_mats);
-    else
-        infer_tc_batch_kernel<false><<<b->grid, kTcRows * b->groups, b->smem, s>>>(b->hdr, b->d_mats);
+    const bool half = b->hdr.ub != kTcUnitBlocks;
+    const dim3 grid(b->grid), block(kTcRows * b->groups);
+    if (b->split) {
+        if (half) infer_tc_batch_kernel<true, kTcUnitBlocks / 2><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
+        else infer_tc_batch_kernel<true, kTcUnitBlocks><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
+    } else {
+        if (half) infer_tc_batch_kernel<false, kTcUnitBlocks / 2><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
+        else infer_tc_batch_kernel<false, kTcUnitBlocks><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
+    }
     NTBC_CHECK_LAUNCH("batched ntbc inference (tcgen05)");
     return NTBC_OK;
 }

@@ -3,6 +3,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdarg>
@@ -37,6 +38,15 @@ bool fault_injected(const char* what);   // NTBC_FAULT=alloc|launch|... host-sid
     } while (0)
 
 ntbc_status device_alloc(void** ptr, size_t bytes, const char* what);
+
+// NVTX range over one C-ABI call (host timeline of a profiler; the NVTX v3 calls are no-ops
+// unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 inline int channels_of(int fmt) { return fmt == NTBC_BC1 ? 3 : (fmt == NTBC_BC4 ? 1 : 0); }
 

@@ -109,8 +109,9 @@ ntbc_status grid_sources(const ntbc_model* m, GridSrc& csrc, GridSrc& esrc);
 
 // tensor-core inference (FP16 weights): weight image preparation and launch
 ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s);
-// work units (128 blocks) the tensor-core inference processes at once (groups x SMs); 0 on error
-int tc_units_in_flight(const ntbc_model* m);
+// work units the tensor-core inference processes at once (groups x SMs; 0 on error) and the
+// blocks per work unit (unit_blocks, optional)
+int tc_units_in_flight(const ntbc_model* m, int* unit_blocks);
 // blocks_out: per texture the first block; strides: bytes between its blocks (NULL: 8)
 ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
                       float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s);

@@ -439,6 +439,7 @@ static ntbc_status ensure_export_buffers(ntbc_model* m) {
 }
 
 ntbc_status ntbc_model_export(ntbc_model* m, int grid_bits, int weight_prec, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_model_export");
     clear_error();
     if (!m) return fail(NTBC_EINVAL, "null model");
     if (grid_bits != 0 && grid_bits != 8 && grid_bits != 4) return fail(NTBC_EINVAL, "grid_bits must be 0, 4 or 8");
@@ -572,6 +573,7 @@ ntbc_status ntbc_model_save(const ntbc_model* m, uint8_t* blob, size_t size, voi
 }
 
 ntbc_status ntbc_model_load(ntbc_model* m, const uint8_t* blob, size_t size, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_model_load");
     clear_error();
     if (!m || !blob) return fail(NTBC_EINVAL, "null argument");
     if (size < sizeof(BlobHeader)) return fail(NTBC_EINVAL, "blob too small");

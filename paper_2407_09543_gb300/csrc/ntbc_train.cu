@@ -849,6 +849,7 @@ ntbc_status ntbc_sample_blocks(uint64_t seed, long step, int n, int n_blocks, in
 
 ntbc_status ntbc_train_grads(ntbc_model* m, const ntbc_material* mat, const int32_t* block_ids, int n_blocks,
                              int qat_bits, float temperature, int precision, float* grads, float* losses, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_train_grads");
     clear_error();
     if (!m || !block_ids || !grads) return fail(NTBC_EINVAL, "null argument");
     ntbc_status st = check_material(m, mat);
@@ -916,6 +917,7 @@ ntbc_status ntbc_adam_step(ntbc_model* m, const float* grads, long step, long to
 
 ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, float* losses_out,
                        void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_train");
     clear_error();
     if (!m || !cfg) return fail(NTBC_EINVAL, "null argument");
     ntbc_status st = check_material(m, mat);
@@ -967,6 +969,9 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
         if (ce == cudaSuccess) {              // the last step's losses
             loss_finalize_kernel<<<1, 32, 0, cap>>>(ts->loss_acc, ts->losses);
             ce = cudaGetLastError();
+            // host-side fault injection of a diverged encode: NTBC_FAULT=nan overwrites the
+            // finalised losses with NaN, so the non-finite check below is exercised
+            if (ce == cudaSuccess && fault_injected("nan")) ce = cudaMemsetAsync(ts->losses, 0xFF, 6 * sizeof(float), cap);
         }
     }
     cudaError_t se = cudaStreamSynchronize(cap);

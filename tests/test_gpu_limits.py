@@ -173,3 +173,29 @@ def test_bounded_wait_gives_up_and_context_survives():
     torch.cuda.synchronize()
     for a, b in zip(before, outs):
         assert torch.equal(a, b)
+
+
+def test_nonfinite_loss_is_reported_and_the_next_encode_works():
+    # a diverged encode, injected on the host (NTBC_FAULT=nan poisons the finalised losses):
+    # ntbc_train returns NTBC_ENONFINITE instead of a silent NaN model; without the injection
+    # the same call on a fresh model succeeds with finite losses
+    import os
+    mat = synth.make_material("nan", 32, ["sine_rgb", "sine_r"], 0)
+    desc, odesc = descs.case_descs(nt, mat.formats, 32, 3, 4, 8, 2, "selu")
+    p0 = descs.init_params(odesc, 0)
+    tex = [_dev(t) for t in mat.textures]
+    refs = [_dev(obc.encode(f, t, 32, 32)) for f, t in zip(mat.formats, mat.textures)]
+    material = nt.Material.make(32, 32, mat.formats, tex, refs)
+    cfg = nt.TrainConfig.make(steps=3, batch_texels=256, seed=0, precision=nt.TRAIN_BF16)
+    m = nt.Model(desc)
+    m.set_params(_dev(nt.configs.flatten(desc, p0)))
+    os.environ["NTBC_FAULT"] = "nan"
+    try:
+        with pytest.raises(nt.NTBCError) as e:
+            m.train(material, cfg)
+        assert e.value.status == 5 and "non-finite" in str(e.value)
+    finally:
+        del os.environ["NTBC_FAULT"]
+    m2 = nt.Model(desc)
+    m2.set_params(_dev(nt.configs.flatten(desc, p0)))
+    assert all(np.isfinite(m2.train(material, cfg)))
