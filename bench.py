@@ -499,7 +499,7 @@ SM_COUNT = 152
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # infer_tc_kernel<SPLIT=true> on the 4096^2 four-texture material, from one ncu capture of the
 # current kernel; None for any other workload or precision
-INFER_TC_DRAM_BYTES_MAT4K = 16_966_144
+INFER_TC_DRAM_BYTES_MAT4K = 16_961_536
 SM_MAX_GHZ = 2.07
 
 
