@@ -8,17 +8,19 @@ One timed step = one NTBC inference pass over the whole material (all 4 textures
 1,048,576 block positions, 4,194,304 texture blocks) through the C ABI, inputs
 resident in HBM; the L2 is flushed (256 MiB write) between timed iterations, each
 iteration bracketed by its own CUDA events on the launching stream.
-Also reported: the encode (training) time per step and the full-schedule encode
-seconds (BF16 tensor-core training; the FP32-kernel encode beside it for decoded-PSNR
-parity), the same metric end to end with host
-buffers (model blob H2D, blocks D2H), the plain FP32 PyTorch path on the same GPU,
-the CPU oracle on a bounded sample (cpu_baseline), and a quality / storage study
-(Fig. average: mean decoded PSNR and SSIM as ratios of the reference BC's against stored
-bytes, aggressive and conservative packaging, 8-bit and 4-bit QAT grids). The reference
-BC targets are the range-fit encoder with two least-squares endpoint refits.
+Also reported: the roofline of the inference kernel against the exp2 rate measured in the
+same run; the encode (training) time per step and the full-schedule encode seconds (BF16
+tensor-core training; the FP32-kernel encode beside it for decoded-PSNR parity); the same
+metric end to end with host buffers (model blob H2D, blocks D2H) and its parts; the plain
+FP32 PyTorch path on the same GPU; the 16-material batched launch; the FP64 oracle over the
+whole material on all host cores (cpu_baseline) with the accuracy bars checked on the GPU's
+blocks against it; and a quality / storage study (Fig. average: mean decoded PSNR and SSIM as
+ratios of the reference BC's against stored bytes, aggressive and conservative packaging,
+8-bit and 4-bit QAT grids). The reference BC targets are the range-fit encoder with two
+least-squares endpoint refits.
 
---impl reference times the CPU oracle (the reference arm of this build) on a
-bounded sample of the same workload.
+--impl reference times the FP64 oracle alone on all host cores (the paper has no code, so its
+reference arm is the oracle): runs of block rows of the same workload, no product code.
 """
 from __future__ import annotations
 
@@ -386,7 +388,7 @@ class OraclePool:
 def full_material_oracle(side, flat_params, gpu_blocks, textures):
     """The oracle over every block of the material with the GPU arm's exported model (u8 QAT
     grids, FP16 MLP weights): timed across the host cores (the CPU baseline), then checked
-    against the GPU blocks on the spec bars: decoded PSNR within 0.05 dB of the FP64-oracle
+    against the GPU blocks on the accuracy bars: decoded PSNR within 0.05 dB of the FP64-oracle
     network per texture and at most 0.1 % of endpoint or index fields differing."""
     tmp = tempfile.mkdtemp(prefix="ntbc_oracle_")
     paths = {"params": os.path.join(tmp, "params.npy"), "gpu": os.path.join(tmp, "gpu.npy"),
@@ -504,7 +506,7 @@ SM_MAX_GHZ = 2.07
 
 
 def measured_peaks():
-    """The machine's measured HBM copy and bf16 GEMM peaks, else the recipe's fallback figures."""
+    """The measured HBM copy and bf16 GEMM peaks of these GPUs (MEASURED_PEAKS.json), else fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if not os.path.exists(path):
         return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}
@@ -952,7 +954,7 @@ def main():
                  "encode_s_extrapolated": round(p_train_ms * (FULL_MAIN_STEPS + FULL_QAT_STEPS) / 1e3, 1)}
 
     # ---- the CPU oracle over the whole material on the host cores: the CPU baseline, and the
-    # spec parity of the headline blocks (PSNR per texture, field mismatch)
+    # accuracy parity of the headline blocks (PSNR per texture, field mismatch)
     cpu = oracle_parity = None
     if not args.no_cpu and rank == 0 and world == 1:
         flat = torch.empty(model.n_params, device=dev)

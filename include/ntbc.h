@@ -403,6 +403,33 @@ ntbc_status ntbc_vjp(ntbc_model* model, const int32_t* block_ids, int n_blocks, 
                      void* stream);
 
 /*
+ * Steps [first_step, last_step) of the encode that ntbc_train runs in one call (the schedule of
+ * `cfg`: cfg->steps main steps, then ceil(qat_fraction * steps) QAT steps, the LR warm-up and
+ * cosine over all of them, batches sampled by (seed, step)). first_step = 0 starts a fresh
+ * encode (Adam moments zeroed); first_step > 0 continues from the model's current parameters
+ * and Adam moments, as left by the previous range or by ntbc_checkpoint_load, so an encode can
+ * be split at any step and resumed in another process. Synchronises the stream at the end;
+ * losses_out (host float[6], may be NULL): the last step's losses; NTBC_ENONFINITE if they are
+ * not finite. A resumed encode matches an uninterrupted one up to the rounding order of the
+ * grid scatter's floating-point atomics (two uninterrupted encodes differ as much).
+ */
+ntbc_status ntbc_train_range(ntbc_model* model, const ntbc_material* mat, const ntbc_train_config* cfg,
+                             long first_step, long last_step, float* losses_out, void* stream);
+
+/*
+ * Training checkpoint of a model: its description, the step a resumed encode starts at, the FP32
+ * master parameters and both Adam moments (3 x layout.total floats after a small header).
+ * ntbc_checkpoint_save copies device -> host `buf` (host, ntbc_checkpoint_size bytes) and
+ * synchronises `stream`; ntbc_checkpoint_load copies it back into a model of the same
+ * description (NTBC_EINVAL otherwise, or for a header of another ABI version), synchronises, and
+ * returns the step to resume at in *next_step (optional). The resumed encode is then
+ * ntbc_train_range(model, mat, cfg, next_step, total, ...) with the same cfg.
+ */
+ntbc_status ntbc_checkpoint_size(const ntbc_model* model, size_t* size);
+ntbc_status ntbc_checkpoint_save(ntbc_model* model, uint8_t* buf, size_t size, void* stream);
+ntbc_status ntbc_checkpoint_load(ntbc_model* model, const uint8_t* buf, size_t size, long* next_step, void* stream);
+
+/*
  * Allocation-free variant of ntbc_train_grads. The paper has no counterpart.
  * For callers that cannot allocate device memory: an engine's texture-streaming
  * thread working inside a fixed, pre-reserved VRAM budget, or a real-time thread

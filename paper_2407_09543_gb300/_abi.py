@@ -117,6 +117,11 @@ _SIGS = {
     "ntbc_infer_to_bc_strided": (c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(c_int), _P]),
     "ntbc_infer_to_host": (c_int, [_P, ctypes.POINTER(_P), c_int, _P]),
     "ntbc_wait_probe": (c_int, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
+    "ntbc_train_range": (c_int, [_P, ctypes.POINTER(Material), ctypes.POINTER(TrainConfig), ctypes.c_long,
+                                 ctypes.c_long, _P, _P]),
+    "ntbc_checkpoint_size": (c_int, [_P, ctypes.POINTER(c_size_t)]),
+    "ntbc_checkpoint_save": (c_int, [_P, _P, c_size_t, _P]),
+    "ntbc_checkpoint_load": (c_int, [_P, _P, c_size_t, ctypes.POINTER(ctypes.c_long), _P]),
     "ntbc_ex2_rate_probe": (c_int, [ctypes.POINTER(ctypes.c_double), _P]),
     "ntbc_train_grads": (c_int, [_P, ctypes.POINTER(Material), _P, c_int, c_int, c_float, c_int, _P, _P, _P]),
     "ntbc_train_grads_noalloc": (c_int, [ctypes.POINTER(ModelDesc), _P, ctypes.POINTER(Material), _P, c_int, c_int,
@@ -299,6 +304,27 @@ class Model:
         out = (c_float * 6)()
         _check(lib.ntbc_train(self.handle, ctypes.byref(material), ctypes.byref(cfg), out, _stream(stream)))
         return list(out)
+
+    def train_range(self, material: Material, cfg: TrainConfig, first_step, last_step, stream=None):
+        out = (c_float * 6)()
+        _check(lib.ntbc_train_range(self.handle, ctypes.byref(material), ctypes.byref(cfg), first_step, last_step, out,
+                                    _stream(stream)))
+        return list(out)
+
+    def checkpoint_size(self):
+        n = c_size_t()
+        _check(lib.ntbc_checkpoint_size(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def checkpoint_save(self, host_buf, stream=None):
+        _check(lib.ntbc_checkpoint_save(self.handle, _ptr(host_buf), host_buf.numel(), _stream(stream)))
+
+    def checkpoint_load(self, host_buf, stream=None):
+        """Returns the step a resumed encode starts at."""
+        step = ctypes.c_long(0)
+        _check(lib.ntbc_checkpoint_load(self.handle, _ptr(host_buf), host_buf.numel(), ctypes.byref(step),
+                                        _stream(stream)))
+        return step.value
 
 
 class Batch:

@@ -83,6 +83,7 @@ struct ntbc_model {
     __half* umma_img = nullptr;         // FP16 weights in the tensor-core shared-memory layout
     int* tc_err = nullptr;              // set by the tensor-core kernel when a bounded wait gives up
     struct ntbc_train_state* train = nullptr;   // training scratch (allocated on first use)
+    long long next_step = 0;            // the encode step a resumed ntbc_train_range starts at
     struct ntbc_host_io* host_io = nullptr;     // staging of ntbc_infer_to_host (allocated on first use)
 };
 

@@ -915,9 +915,9 @@ ntbc_status ntbc_adam_step(ntbc_model* m, const float* grads, long step, long to
     return adam_launch(m, grads, s);
 }
 
-ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, float* losses_out,
-                       void* stream) {
-    ntbc::NvtxRange nvtx_range("ntbc_train");
+ntbc_status ntbc_train_range(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, long first_step,
+                             long last_step, float* losses_out, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_train_range");
     clear_error();
     if (!m || !cfg) return fail(NTBC_EINVAL, "null argument");
     ntbc_status st = check_material(m, mat);
@@ -934,6 +934,11 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     long long qat_steps = cfg->qat_fraction > 0.f ? (long long)std::ceil((double)cfg->qat_fraction * (double)cfg->steps) : 0;
     long long total = cfg->steps + qat_steps;
     int qbits = qat_steps > 0 ? cfg->grid_bits : 0;
+    if (first_step < 0 || last_step <= first_step || last_step > total)
+        return fail(NTBC_EINVAL, "step range [%ld, %ld) outside the schedule's %lld steps", first_step, last_step, total);
+    if (first_step > 0 && !m->adam_m)
+        return fail(NTBC_EINVAL, "resuming at step %ld needs the Adam state (train the earlier steps or load a checkpoint)",
+                    first_step);
     st = ensure_train_state(m, nb);
     if (st == NTBC_OK) st = ensure_adam(m);
     if (st != NTBC_OK) return st;
@@ -943,9 +948,17 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     NTBC_CHECK_CUDA(cudaStreamCreateWithFlags(&owned.s, cudaStreamNonBlocking));
     cudaStream_t cap = owned.s;
     NTBC_CHECK_CUDA(cudaStreamSynchronize(s));
-    NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), cap));
-    NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), cap));
-    NTBC_CHECK_CUDA(cudaMemsetAsync(ts->st, 0, sizeof(StepState), cap));
+    if (first_step == 0) {          // a fresh encode: Adam moments start at zero
+        NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), cap));
+        NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), cap));
+    }
+    {                               // the step counter the sampler, schedule and Adam read
+        StepState st0;
+        memset(&st0, 0, sizeof(st0));
+        st0.step = first_step;
+        NTBC_CHECK_CUDA(cudaMemcpyAsync(ts->st, &st0, sizeof(StepState), cudaMemcpyHostToDevice, cap));
+        NTBC_CHECK_CUDA(cudaStreamSynchronize(cap));
+    }
     if (ts->sched_cap < total) {
         cudaFree(ts->sched);
         ts->sched = nullptr;
@@ -960,12 +973,15 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     // one graph per phase (the main phase without the QAT kernels, the QAT phase with them),
     // each launched once per step; every quantity that changes per step lives in StepState
     cudaGraphExec_t exec_main = nullptr, exec_qat = nullptr;
-    st = capture_step(m, mat, cfg, nb, n_blocks, total, 0, cap, &exec_main);
-    if (st == NTBC_OK && qat_steps > 0) st = capture_step(m, mat, cfg, nb, n_blocks, total, qbits, cap, &exec_qat);
+    // the main-phase steps of the range, then its QAT-phase steps
+    const long long main_n = std::max(0LL, std::min((long long)last_step, (long long)cfg->steps) - first_step);
+    const long long qat_n = (long long)last_step - first_step - main_n;
+    if (main_n > 0) st = capture_step(m, mat, cfg, nb, n_blocks, total, 0, cap, &exec_main);
+    if (st == NTBC_OK && qat_n > 0) st = capture_step(m, mat, cfg, nb, n_blocks, total, qbits, cap, &exec_qat);
     cudaError_t ce = cudaSuccess;
     if (st == NTBC_OK) {
-        for (long long t = 0; t < cfg->steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_main, cap);
-        for (long long t = 0; t < qat_steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_qat, cap);
+        for (long long t = 0; t < main_n && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_main, cap);
+        for (long long t = 0; t < qat_n && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec_qat, cap);
         if (ce == cudaSuccess) {              // the last step's losses
             loss_finalize_kernel<<<1, 32, 0, cap>>>(ts->loss_acc, ts->losses);
             ce = cudaGetLastError();
@@ -986,8 +1002,95 @@ ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train
     float host_losses[6];
     NTBC_CHECK_CUDA(cudaMemcpy(host_losses, ts->losses, sizeof(host_losses), cudaMemcpyDeviceToHost));
     if (losses_out) memcpy(losses_out, host_losses, sizeof(host_losses));
+    m->next_step = last_step;
     for (int i = 0; i < 6; ++i)
         if (!std::isfinite(host_losses[i])) return fail(NTBC_ENONFINITE, "non-finite loss after training");
+    return NTBC_OK;
+}
+
+
+ntbc_status ntbc_train(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, float* losses_out,
+                       void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_train");
+    clear_error();
+    if (!cfg) return fail(NTBC_EINVAL, "null argument");
+    const long long qat_steps =
+        cfg->qat_fraction > 0.f ? (long long)std::ceil((double)cfg->qat_fraction * (double)cfg->steps) : 0;
+    return ntbc_train_range(m, mat, cfg, 0, (long)(cfg->steps + qat_steps), losses_out, stream);
+}
+
+namespace {
+
+// Training checkpoint: header, then the FP32 master parameters, Adam m and Adam v.
+struct CheckpointHeader {
+    char magic[4];               // "NTCK"
+    int version;                 // ntbc_abi_version()
+    ntbc_model_desc desc;        // the model it belongs to
+    unsigned long long total;    // floats per array
+    long long next_step;         // the step a resumed encode starts at
+};
+
+}  // namespace
+
+ntbc_status ntbc_checkpoint_size(const ntbc_model* m, size_t* size) {
+    clear_error();
+    if (!m || !size) return fail(NTBC_EINVAL, "null argument");
+    *size = sizeof(CheckpointHeader) + 3 * m->layout.total * sizeof(float);
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_checkpoint_save(ntbc_model* m, uint8_t* buf, size_t size, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_checkpoint_save");
+    clear_error();
+    size_t need = 0;
+    ntbc_status st = ntbc_checkpoint_size(m, &need);
+    if (st != NTBC_OK) return st;
+    if (!buf || size != need) return fail(NTBC_EINVAL, "checkpoint buffer must be %zu bytes", need);
+    st = ensure_adam(m);               // a model that never trained saves zero moments
+    if (st != NTBC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CheckpointHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "NTCK", 4);
+    h.version = ntbc_abi_version();
+    h.desc = m->desc;
+    h.total = m->layout.total;
+    h.next_step = m->next_step;
+    const size_t bytes = m->layout.total * sizeof(float);
+    memcpy(buf, &h, sizeof(h));
+    uint8_t* p = buf + sizeof(h);
+    NTBC_CHECK_CUDA(cudaMemcpyAsync(p, m->params, bytes, cudaMemcpyDeviceToHost, s));
+    NTBC_CHECK_CUDA(cudaMemcpyAsync(p + bytes, m->adam_m, bytes, cudaMemcpyDeviceToHost, s));
+    NTBC_CHECK_CUDA(cudaMemcpyAsync(p + 2 * bytes, m->adam_v, bytes, cudaMemcpyDeviceToHost, s));
+    NTBC_CHECK_CUDA(cudaStreamSynchronize(s));
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_checkpoint_load(ntbc_model* m, const uint8_t* buf, size_t size, long* next_step, void* stream) {
+    ntbc::NvtxRange nvtx_range("ntbc_checkpoint_load");
+    clear_error();
+    size_t need = 0;
+    ntbc_status st = ntbc_checkpoint_size(m, &need);
+    if (st != NTBC_OK) return st;
+    if (!buf || size != need) return fail(NTBC_EINVAL, "checkpoint must be %zu bytes", need);
+    CheckpointHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.magic, "NTCK", 4) != 0 || h.version != ntbc_abi_version())
+        return fail(NTBC_EINVAL, "not an NTBC checkpoint of this version");
+    if (memcmp(&h.desc, &m->desc, sizeof(ntbc_model_desc)) != 0 || h.total != m->layout.total)
+        return fail(NTBC_EINVAL, "the checkpoint belongs to another model");
+    if (h.next_step < 0) return fail(NTBC_EINVAL, "bad step in checkpoint");
+    st = ensure_adam(m);
+    if (st != NTBC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = m->layout.total * sizeof(float);
+    const uint8_t* p = buf + sizeof(h);
+    NTBC_CHECK_CUDA(cudaMemcpyAsync(m->params, p, bytes, cudaMemcpyHostToDevice, s));
+    NTBC_CHECK_CUDA(cudaMemcpyAsync(m->adam_m, p + bytes, bytes, cudaMemcpyHostToDevice, s));
+    NTBC_CHECK_CUDA(cudaMemcpyAsync(m->adam_v, p + 2 * bytes, bytes, cudaMemcpyHostToDevice, s));
+    NTBC_CHECK_CUDA(cudaStreamSynchronize(s));
+    m->next_step = h.next_step;
+    if (next_step) *next_step = (long)h.next_step;
     return NTBC_OK;
 }
 

@@ -26,7 +26,7 @@ DEV = "cuda"
 SIDE = 4096
 STEPS = 20000
 # largest relative output error against the FP64 oracle with the same stored weights, and the
-# field-mismatch bar, per mode (the split and FP32 modes hold the spec bars; FP16
+# field-mismatch bar, per mode (the split and FP32 modes hold the 1e-3 and 0.1 % bars; FP16
 # activations carry four FP16 roundings amplified by the trained network: about 1e-2 measured)
 BARS = {"fp32": (1e-3, 0.001), "fp16": (1e-3, 0.001), "fp16_fast": (2.5e-2, 0.02), "fp8_e4m3": (1e-3, 0.001)}
 

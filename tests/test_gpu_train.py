@@ -122,3 +122,54 @@ def test_training_gains_over_untrained_network():
     assert all(np.isfinite(losses))
     for b, a, r in zip(before, after, ref):
         assert a > b + 5.0 and a < r
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_matches_uninterrupted_encode(precision):
+    """An encode split at a step, its checkpoint (FP32 master parameters, Adam moments, step)
+    written out and loaded into a fresh model, then resumed, ends where an uninterrupted encode
+    ends, up to the rounding order of the grid scatter's floating-point atomics, which makes two
+    uninterrupted encodes differ too; the checkpoint round trip itself is exact."""
+    s = setup(grid_scale=0)
+    desc, material = s["desc"], s["material"]
+    flat0 = _dev(nt.configs.flatten(desc, s["params"]))
+    cfg = nt.TrainConfig.make(steps=40, batch_texels=512, qat_fraction=0.1, grid_bits=8, seed=5, precision=precision)
+    total = 44
+
+    def fresh():
+        m = nt.Model(desc)
+        m.set_params(flat0)
+        return m
+
+    def params(m):
+        out = torch.empty(m.n_params, device=DEV)
+        m.get_params(out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64)
+
+    a, c = fresh(), fresh()
+    a.train(material, cfg)
+    c.train(material, cfg)
+    first = fresh()
+    first.train_range(material, cfg, 0, 20)
+    ck = torch.empty(first.checkpoint_size(), dtype=torch.uint8)
+    first.checkpoint_save(ck)
+    b = nt.Model(desc)
+    assert b.checkpoint_load(ck) == 20
+    ck2 = torch.empty_like(ck)
+    b.checkpoint_save(ck2)
+    assert torch.equal(ck, ck2)
+    losses = b.train_range(material, cfg, 20, total)
+    assert all(np.isfinite(losses))
+    pa, pb, pc = params(a), params(b), params(c)
+    noise = np.linalg.norm(pa - pc) / np.linalg.norm(pa)
+    resumed = np.linalg.norm(pa - pb) / np.linalg.norm(pa)
+    assert resumed <= 5 * noise + 1e-6, (resumed, noise)
+    # a checkpoint of another model, or with a damaged header, is refused
+    other = nt.Model(nt.configs.model_desc(list(s["mat"].formats), 64, 3, 4, 9, 2, nt.ACT_SELU))
+    with pytest.raises(nt.NTBCError):
+        other.checkpoint_load(ck)
+    bad = ck.clone()
+    bad[0] = 0
+    with pytest.raises(nt.NTBCError):
+        b.checkpoint_load(bad)
