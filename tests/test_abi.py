@@ -97,3 +97,14 @@ def test_injected_allocation_failure_reports_enomem():
     env = dict(os.environ, NTBC_FAULT="alloc", PYTHONPATH=ROOT)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
     assert out.stdout.strip().splitlines()[-1] == "2", out.stdout + out.stderr
+
+
+def test_smallest_material():
+    # one 4x4 block leaves the endpoint grid no level (every level has res >= 2 > 1 block per
+    # side), so the description is refused before anything is allocated; 8x8 (2x2 blocks) is the
+    # smallest material with an endpoint grid
+    with pytest.raises(nt.NTBCError) as e:
+        nt.ntbc_model_layout(nt.configs.model_desc([1, 4], 4, 2, 2, 4, 2, nt.ACT_SELU))
+    assert e.value.status == 1
+    d = nt.configs.model_desc([1, 4], 8, 2, 2, 8, 2, nt.ACT_SELU)
+    assert d.endpoint_levels == 1 and nt.ntbc_model_layout(d).in_endpoint == 2

@@ -199,3 +199,25 @@ def test_nonfinite_loss_is_reported_and_the_next_encode_works():
     m2 = nt.Model(desc)
     m2.set_params(_dev(nt.configs.flatten(desc, p0)))
     assert all(np.isfinite(m2.train(material, cfg)))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_smallest_material_matches_oracle(prec):
+    # 8x8 texels = 2x2 blocks: one partial 8-block tile of one partial work unit
+    mat = synth.make_material("tiny8", 8, ["sine_rgb", "sine_r"], 4)
+    desc, odesc = descs.case_descs(nt, mat.formats, 8, 2, 2, 8, 2, "selu")
+    params = synth.random_params_like(descs.init_params(odesc, 4), seed=5)
+    m = nt.Model(desc)
+    m.set_params(_dev(nt.configs.flatten(desc, params)))
+    m.export(grid_bits=0, weight_prec=prec)
+    outs = [torch.empty(4 * 8, dtype=torch.uint8, device=DEV) for _ in mat.formats]
+    m.infer_to_bc(outs)
+    torch.cuda.synchronize()
+    pw = dict(params)
+    if prec:
+        for k in ("color_mlp", "endpoint_mlp"):
+            pw[k] = [(W.astype(np.float16).astype(np.float64), b.astype(np.float16).astype(np.float64)) for W, b in params[k]]
+    ref = ont.infer_blocks(odesc, pw)
+    got = [o.cpu().numpy().reshape(-1, 8) for o in outs]
+    mm, ff = mismatch(mat.formats, got, ref)
+    assert mm <= (0.005 if prec == 2 else 0.001) * ff + 1, (mm, ff)
