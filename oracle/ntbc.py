@@ -45,7 +45,11 @@ Readings where the paper is silent or garbled (each one is listed in the design 
   * one LR schedule spans the main and the QAT phase;
   * FP8 weights (an extension for the precision study; the paper stores FP16): E4M3
     round to nearest even, saturating; one power-of-two scale per layer shared by its
-    weights and bias.
+    weights and bias;
+  * FP8 arithmetic (the same study): each layer's input rounded to E4M3 at a per-layer
+    power-of-two scale calibrated on a fixed sample of the material (one binade of
+    headroom above the sampled maximum), exact products and sums, the bias added
+    exactly.
 """
 from __future__ import annotations
 
@@ -417,6 +421,57 @@ def fp8_params(params):
     return out, exps, codes
 
 
+# FP8 arithmetic (an extension for the precision study, like the FP8 weights): activations
+# in E4M3 too. Layer l's input x (the grid features for l = 0, the previous layer's
+# activation otherwise) is rounded to E4M3 at the layer's scale 2^e_l,
+# x -> e4m3_round(x 2^-e_l) 2^e_l; the weights are the FP8 ones (fp8_params); products and
+# sums are exact and the bias is added exactly. The exponents come from a calibration
+# sample of the material: FP8_CALIB_BLOCKS blocks at ids i * FP8_CALIB_STRIDE mod n_blocks
+# (distinct for i < n_blocks, the stride being a prime above any block count), the endpoint
+# network on their centres and the colour network on their 16 texel centres, in the
+# network with the FP8 weights and exact activations; e_l is the smallest integer with
+# 2 max|x_l| <= 448 2^e_l over the sample (one binade of headroom above the sampled maximum,
+# for inputs outside the sample).
+
+FP8_CALIB_BLOCKS = 2048
+FP8_CALIB_STRIDE = 2654435761          # prime
+
+
+def mlp_forward_fp8(layers, x, kind, act_exps):
+    """Outputs of an MLP in the FP8 arithmetic: act_exps[l] is layer l's input exponent."""
+    h = np.asarray(x, np.float64)
+    for i, (W, b) in enumerate(layers):
+        e = int(act_exps[i])
+        hq = np.ldexp(e4m3_round(np.ldexp(h, -e)), e)
+        z = hq @ np.asarray(W, np.float64).T + np.asarray(b, np.float64)
+        h = _act(z, kind) if i + 1 < len(layers) else sigmoid(z)
+    return h
+
+
+def fp8_calibration_ids(n_blocks, count=FP8_CALIB_BLOCKS):
+    """Block ids of the calibration sample (int64)."""
+    k = min(int(n_blocks), int(count))
+    return (np.arange(k, dtype=np.int64) * FP8_CALIB_STRIDE) % int(n_blocks)
+
+
+def fp8_activation_exponents(desc, params, color_grid=None, endpoint_grid=None):
+    """Activation exponents of the FP8 arithmetic, colour layers then endpoint layers.
+    params: the parameters with the FP8 weights (fp8_params); grids: the ones inference
+    reads (dequantised exported grids), defaulting to the parameter grids."""
+    ids = fp8_calibration_ids(desc.n_blocks)
+    s, t = block_coords(desc.blocks_x, desc.blocks_y, ids % desc.blocks_x, ids // desc.blocks_x)
+    xs, ys = block_texel_xy(desc, ids)
+    u, v = texel_coords(desc.width, desc.height, xs.ravel(), ys.ravel())
+    cg = color_grid if color_grid is not None else params["color_grid"]
+    eg = endpoint_grid if endpoint_grid is not None else params["endpoint_grid"]
+    exps = []
+    for key, grid, (a, b) in (("color_mlp", cg, (u, v)), ("endpoint_mlp", eg, (s, t))):
+        x, _ = grid_lookup(_as64(grid), a, b)
+        _, cache = mlp_forward(params[key], x, desc.activation)
+        exps += [fp8_layer_exponent(2.0 * h) for h, _ in cache]
+    return exps
+
+
 # ----------------------------------------------------------------------------
 # forward over a material
 # ----------------------------------------------------------------------------
@@ -425,20 +480,24 @@ def _as64(levels):
     return [np.asarray(g, np.float64) for g in levels]
 
 
-def endpoint_forward(desc, params, bxs, bys, grid=None):
+def _net_forward(desc, layers, x, act_exps):
+    if act_exps is None:
+        return mlp_forward(layers, x, desc.activation)[0]
+    return mlp_forward_fp8(layers, x, desc.activation, act_exps)
+
+
+def endpoint_forward(desc, params, bxs, bys, grid=None, act_exps=None):
     s, t = block_coords(desc.blocks_x, desc.blocks_y, bxs, bys)
     levels = _as64(grid if grid is not None else params["endpoint_grid"])
     x, _ = grid_lookup(levels, s, t)
-    y, _ = mlp_forward(params["endpoint_mlp"], x, desc.activation)
-    return y
+    return _net_forward(desc, params["endpoint_mlp"], x, act_exps)
 
 
-def color_forward(desc, params, xs, ys, grid=None):
+def color_forward(desc, params, xs, ys, grid=None, act_exps=None):
     u, v = texel_coords(desc.width, desc.height, xs, ys)
     levels = _as64(grid if grid is not None else params["color_grid"])
     x, _ = grid_lookup(levels, u, v)
-    y, _ = mlp_forward(params["color_mlp"], x, desc.activation)
-    return y
+    return _net_forward(desc, params["color_mlp"], x, act_exps)
 
 
 def block_texel_xy(desc, block_ids):
@@ -450,12 +509,16 @@ def block_texel_xy(desc, block_ids):
     return 4 * bx[:, None] + (i % 4)[None, :], 4 * by[:, None] + (i // 4)[None, :]
 
 
-def forward_blocks(desc, params, block_ids, color_grid=None, endpoint_grid=None):
-    """Network outputs for the given blocks: e_hat [nb, out_e], c_hat [nb, 16, out_c] (FP64)."""
+def forward_blocks(desc, params, block_ids, color_grid=None, endpoint_grid=None, fp8_act=None):
+    """Network outputs for the given blocks: e_hat [nb, out_e], c_hat [nb, 16, out_c] (FP64).
+    fp8_act: activation exponents (colour layers, then endpoint layers) of the FP8
+    arithmetic, or None for exact activations."""
     block_ids = np.asarray(block_ids, np.int64)
-    e_hat = endpoint_forward(desc, params, block_ids % desc.blocks_x, block_ids // desc.blocks_x, endpoint_grid)
+    nc = len(params["color_mlp"])
+    ce, ee = (None, None) if fp8_act is None else (list(fp8_act[:nc]), list(fp8_act[nc:]))
+    e_hat = endpoint_forward(desc, params, block_ids % desc.blocks_x, block_ids // desc.blocks_x, endpoint_grid, ee)
     xs, ys = block_texel_xy(desc, block_ids)
-    c_hat = color_forward(desc, params, xs.ravel(), ys.ravel(), color_grid)
+    c_hat = color_forward(desc, params, xs.ravel(), ys.ravel(), color_grid, ce)
     return e_hat, c_hat.reshape(len(block_ids), 16, desc.out_color)
 
 
@@ -516,11 +579,11 @@ def outputs_to_blocks(fmt, e_hat, c_hat):
     return _bc.bc4_pack(r0, r1, codes)
 
 
-def infer_blocks(desc, params, block_ids=None, color_grid=None, endpoint_grid=None):
+def infer_blocks(desc, params, block_ids=None, color_grid=None, endpoint_grid=None, fp8_act=None):
     """NTBC inference to BC blocks for every texture: list of [nb, 8] uint8 (row-major blocks)."""
     if block_ids is None:
         block_ids = np.arange(desc.n_blocks)
-    e_hat, c_hat = forward_blocks(desc, params, block_ids, color_grid, endpoint_grid)
+    e_hat, c_hat = forward_blocks(desc, params, block_ids, color_grid, endpoint_grid, fp8_act)
     out = []
     for t, fmt in enumerate(desc.formats):
         ch = desc.channels[t]

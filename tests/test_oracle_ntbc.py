@@ -448,6 +448,115 @@ def test_fp8_params_error_bound():
 
 
 # ----------------------------------------------------------------------------
+# FP8 arithmetic (E4M3 activations, precision study)
+# ----------------------------------------------------------------------------
+
+def _one(w, b):
+    return [(np.array([[float(w)]]), np.array([float(b)]))]
+
+
+def test_fp8_forward_rounds_inputs_to_nearest_even():
+    # 1 + 1/16 lies half-way between 1 (mantissa 000) and 1.125 (001): to 1; 1 + 3/16 half-way
+    # between 1.125 (001) and 1.25 (010): to 1.25; one layer w = 1, b = 0 -> sigmoid(x_q)
+    y = ntbc.mlp_forward_fp8(_one(1, 0), np.array([[1.0625], [1.1875], [1.0]]), "selu", [0])
+    np.testing.assert_allclose(y[:, 0], 1 / (1 + np.exp(-np.array([1.0, 1.25, 1.0]))), rtol=0, atol=1e-15)
+
+
+def test_fp8_forward_applies_the_scale_and_saturates():
+    # 1000 2^-2 = 250 -> 256 (spacing 16 in [128, 256)) -> 1024; 1000 2^-3 = 125 -> 128
+    # (spacing 8) -> 1024; unscaled, 1000 saturates to 448; b = -1024 centres the sigmoid
+    x = np.array([[1000.0]])
+    assert ntbc.mlp_forward_fp8(_one(1, -1024), x, "selu", [2])[0, 0] == 0.5
+    assert ntbc.mlp_forward_fp8(_one(1, -1024), x, "selu", [3])[0, 0] == 0.5
+    assert ntbc.mlp_forward_fp8(_one(1, -1024), x, "selu", [0])[0, 0] < 1e-200
+    # below the normal range: 2^-9 spacing at scale 1, so 3e-3 -> 2^-9 * 2 (3e-3 / 2^-9 = 1.536)
+    y = ntbc.mlp_forward_fp8(_one(1, 0), np.array([[3e-3]]), "selu", [0])[0, 0]
+    assert y == 1 / (1 + math.exp(-2.0 ** -8))
+
+
+def test_fp8_forward_uses_each_layers_own_exponent():
+    # ReLU, x = 3 -> layer 0 (w 100): h = 300 (3 2^7 = 384 is exact, e0 = -7 keeps it;
+    # e0 = -8 gives 768 -> 448 -> 1.75, h = 175 -> 176 at e1 = 0, spacing 16); layer 1 rounds
+    # h: 300 -> 288 at e1 = 0 or 1 (spacing 32 / 16), -> 448 2^-1 = 224 at e1 = -1
+    # (saturated); b1 = -288 centres the output
+    layers = [(np.array([[100.0]]), np.array([0.0])), (np.array([[1.0]]), np.array([-288.0]))]
+    f = lambda e: ntbc.mlp_forward_fp8(layers, np.array([[3.0]]), "relu", e)[0, 0]
+    assert f([-7, 0]) == 0.5 and f([-7, 1]) == 0.5 and f([0, 0]) == 0.5
+    assert f([-7, -1]) == pytest.approx(1 / (1 + math.exp(64.0)), rel=1e-12)
+    assert f([-8, 0]) == pytest.approx(1 / (1 + math.exp(288.0 - 176.0)), rel=1e-12)
+
+
+def test_fp8_forward_exact_on_representable_activations():
+    """A ReLU network whose inputs and activations are small integers (every integer up to 16
+    is an E4M3 value) computes exactly what the exact-activation network does."""
+    rng = np.random.default_rng(3)
+    W0 = rng.integers(-1, 2, (8, 4)).astype(np.float64)
+    W1 = rng.integers(0, 2, (3, 8)).astype(np.float64) * 0.5
+    layers = [(W0, np.zeros(8)), (W1, np.array([0.25, -0.5, 0.0]))]
+    x = rng.integers(0, 3, (50, 4)).astype(np.float64)
+    h = np.maximum(x @ W0.T, 0.0)
+    assert h.max() <= 16
+    want, _ = ntbc.mlp_forward(layers, x, "relu")
+    np.testing.assert_array_equal(ntbc.mlp_forward_fp8(layers, x, "relu", [0, 0]), want)
+
+
+def test_fp8_forward_error_bound_against_exact_activations():
+    """Forward error bound of the E4M3 input roundings, propagated with absolute values: a
+    rounding of y has error <= 2^-4 |y| + 2^(e - 10) (relative half-spacing 2^-4 for normal
+    values, absolute 2^-10 2^e below the normal range at scale 2^e); a layer maps input
+    errors d to pre-activation errors |W| d; SELU is Lipschitz with lambda alpha, the
+    sigmoid with 1/4. The FP8 outputs lie within the bound, and differ from the exact ones
+    (the rounding is applied)."""
+    rng = np.random.default_rng(4)
+    layers = [(rng.standard_normal((64, 16)) * 0.4, rng.standard_normal(64) * 0.1),
+              (rng.standard_normal((64, 64)) * 0.15, rng.standard_normal(64) * 0.1),
+              (rng.standard_normal((8, 64)) * 0.15, np.zeros(8))]
+    x = rng.standard_normal((500, 16))
+    want, cache = ntbc.mlp_forward(layers, x, "selu")
+    exps = [ntbc.fp8_layer_exponent(2.0 * h) for h, _ in cache]
+    got = ntbc.mlp_forward_fp8(layers, x, "selu", exps)
+    err = np.zeros_like(x)
+    for l, ((W, _), (h, _)) in enumerate(zip(layers, cache)):
+        rounded = err + 2.0 ** -4 * (np.abs(h) + err) + 2.0 ** (exps[l] - 10)
+        zerr = rounded @ np.abs(W).T
+        err = zerr * (ntbc.SELU_LAMBDA * ntbc.SELU_ALPHA if l + 1 < len(layers) else 0.25)
+    d = np.abs(got - want)
+    assert np.all(d <= err)
+    assert d.max() > 1e-4
+
+
+def test_fp8_calibration_ids():
+    # 2654435761 = 7 * 379205108 + 5, so the ids for 7 blocks are 5 i mod 7; = 1 mod 10
+    np.testing.assert_array_equal(ntbc.fp8_calibration_ids(7), [0, 5, 3, 1, 6, 4, 2])
+    np.testing.assert_array_equal(ntbc.fp8_calibration_ids(10), np.arange(10))
+    ids = ntbc.fp8_calibration_ids(1024 * 1024)
+    assert ids.size == ntbc.FP8_CALIB_BLOCKS == len(np.unique(ids)) and ids.min() >= 0 and ids.max() < 1024 * 1024
+
+
+def test_fp8_activation_exponents_no_sample_input_saturates():
+    """With the calibrated exponents every sampled layer input sits at or below half the E4M3
+    maximum after scaling, and above a quarter of it (the exponent is the smallest such)."""
+    cres = [4, 8]
+    desc = ntbc.ModelDesc(32, 32, [1, 4], cres, ntbc.endpoint_resolutions(cres, 8), hidden_layers=2)
+    p0 = synth.init_params(cres, desc.endpoint_res, 2, desc.mlp_dims("color"), desc.mlp_dims("endpoint"), 0)
+    params = ntbc.fp8_params(synth.random_params_like(p0, seed=1))[0]
+    exps = ntbc.fp8_activation_exponents(desc, params)
+    assert len(exps) == 6
+    ids = np.arange(desc.n_blocks)                  # 64 blocks: the sample is every block
+    xs, ys = ntbc.block_texel_xy(desc, ids)
+    u, v = ntbc.texel_coords(32, 32, xs.ravel(), ys.ravel())
+    s, t = ntbc.block_coords(8, 8, ids % 8, ids // 8)
+    for k, (key, grid, a, b) in enumerate((("color_mlp", "color_grid", u, v), ("endpoint_mlp", "endpoint_grid", s, t))):
+        x, _ = ntbc.grid_lookup(params[grid], a, b)
+        h = x
+        for l, (W, bias) in enumerate(params[key]):
+            m = np.abs(h).max() * 2.0 ** -exps[3 * k + l]
+            assert 112.0 < m <= 224.0, (key, l, m)
+            z = h @ W.T + bias
+            h = ntbc.selu(z)
+
+
+# ----------------------------------------------------------------------------
 # vector-Jacobian product of the raw outputs (the differentiable-function form)
 # ----------------------------------------------------------------------------
 
