@@ -808,9 +808,10 @@ def main():
         nt, desc, ms, INFER_TC_DRAM_BYTES_MAT4K if side == 4096 and args.prec == 1 else None, mufu_peak=mufu_peak)
     encode_terms = encode_roofline(nt, desc, ms_per_train_step)
 
-    # ---- the same inference in the other modes (pure FP16 activations; FP32 SIMT kernel)
+    # ---- the same inference in the other modes (pure FP16 activations; FP8 arithmetic with
+    # E4M3 activations on kind::f8f6f4 MMAs; FP32 SIMT kernel)
     modes = {}
-    for name, prec in (("fp16_fast", nt.PREC_FP16_FAST), ("fp32_simt", nt.PREC_FP32)):
+    for name, prec in (("fp16_fast", nt.PREC_FP16_FAST), ("fp8_e4m3_mma", nt.PREC_FP8_MMA), ("fp32_simt", nt.PREC_FP32)):
         model.export(grid_bits=8, weight_prec=prec)
         model.infer_to_bc(outs)
         torch.cuda.synchronize()

@@ -67,9 +67,24 @@ enum { NTBC_ACT_SELU = 0, NTBC_ACT_RELU = 1 };
  *                        q * 2^e are exact in FP16 and run on the NTBC_PREC_FP16 path (split
  *                        activations), so the outputs stay within 1e-3 relative of an FP64
  *                        evaluation with the same FP8 weights. The paper stores FP16 weights;
- *                        this mode is an extension for the weight-precision study.
+ *                        this mode is an extension for the weight-precision study (FP8
+ *                        storage, FP16 arithmetic).
+ *   NTBC_PREC_FP8_MMA    FP8 arithmetic: the NTBC_PREC_FP8 weights, and every layer's input
+ *                        (grid features, hidden activations) rounded to E4M3 (nearest even,
+ *                        saturating) at a per-layer power-of-two scale 2^a; the MMAs are
+ *                        tcgen05 kind::f8f6f4 (E4M3 x E4M3, FP32 accumulation in TMEM), the
+ *                        biases (the FP8 values) are added in FP32 after the MMA. a is the
+ *                        smallest integer with 2 max|x| <= 448 * 2^a over a calibration sample
+ *                        taken at export: 2048 blocks (all, if fewer) at ids
+ *                        i * 2654435761 mod n_blocks, the endpoint network on their centres
+ *                        and the colour network on their 16 texels, evaluated in FP32 with the
+ *                        FP8 weights and unrounded activations. Outputs match an FP64
+ *                        evaluation of the same arithmetic except where an FP32 activation
+ *                        lands on the other side of an E4M3 rounding boundary; against exact
+ *                        activations they differ by a few per cent. An extension for the
+ *                        precision study, like NTBC_PREC_FP8.
  */
-enum { NTBC_PREC_FP32 = 0, NTBC_PREC_FP16 = 1, NTBC_PREC_FP16_FAST = 2, NTBC_PREC_FP8 = 3 };
+enum { NTBC_PREC_FP32 = 0, NTBC_PREC_FP16 = 1, NTBC_PREC_FP16_FAST = 2, NTBC_PREC_FP8 = 3, NTBC_PREC_FP8_MMA = 4 };
 
 #define NTBC_MAX_TEXTURES 8
 #define NTBC_MAX_LEVELS 16
@@ -213,7 +228,9 @@ ntbc_status ntbc_model_get_params(const ntbc_model* model, float* dst, size_t co
  * half precision (round to nearest even) and prepares the tensor-core weight image;
  * NTBC_PREC_FP8 quantises them to E4M3 with per-layer power-of-two scales (layers in
  * the order colour 0.., endpoint 0..; a layer's weights and bias share its scale);
- * NTBC_PREC_FP32 keeps them.
+ * NTBC_PREC_FP8_MMA does the same and then calibrates the per-layer activation scales
+ * on the exported grids (one small kernel; the calibration sample is described with
+ * the precision modes); NTBC_PREC_FP32 keeps them.
  */
 ntbc_status ntbc_model_export(ntbc_model* model, int grid_bits, int weight_prec, void* stream);
 
@@ -232,7 +249,8 @@ ntbc_status ntbc_model_blob_size(const ntbc_model* model, size_t* size);
  * Stored model blob (the on-disk form the paper loads at texture-load time):
  * exported grid codes (8-bit: one per byte; 4-bit: two per byte, the lower-indexed
  * code in the low nibble; or the FP32 grid), per-level (s, z), MLP weights in the
- * export precision. A 4-bit blob is packed and unpacked on the device (one kernel
+ * export precision (FP8: 2 * NTBC_MAX_MLP_LAYERS int32 weight exponents, then for
+ * NTBC_PREC_FP8_MMA as many activation exponents, then one E4M3 code per parameter). A 4-bit blob is packed and unpacked on the device (one kernel
  * each way). Loading a blob whose header is not this ABI version, describes another
  * model or names an unknown grid width / precision returns NTBC_EINVAL. ntbc_model_save copies device -> host `blob` (host,
  * blob_size bytes; synchronises the stream); ntbc_model_load copies host `blob`
@@ -309,7 +327,8 @@ ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int 
  * Batched load-time inference (Sec. 4.4: inference runs once per material when it is
  * loaded): many materials, each with its own model, decoded to BC blocks in one
  * persistent launch. Every model must be exported for the same tensor-core kernel:
- * all NTBC_PREC_FP16 / NTBC_PREC_FP8 (split activations), or all NTBC_PREC_FP16_FAST.
+ * all NTBC_PREC_FP16 / NTBC_PREC_FP8 (split activations), all NTBC_PREC_FP16_FAST, or all
+ * NTBC_PREC_FP8_MMA.
  *   ntbc_batch_create  models: host array of n models; blocks_out: host array of n host
  *                      arrays, each holding that material's per-texture DEVICE outputs.
  *                      Uploads the launch description (allocates; not capturable).

@@ -10,7 +10,7 @@ library_path = os.path.join(HERE, "libntbc.so")
 BC1, BC4 = 1, 4
 BC3, BC5 = 3, 5
 ACT_SELU, ACT_RELU = 0, 1
-PREC_FP32, PREC_FP16, PREC_FP16_FAST, PREC_FP8 = 0, 1, 2, 3
+PREC_FP32, PREC_FP16, PREC_FP16_FAST, PREC_FP8, PREC_FP8_MMA = 0, 1, 2, 3, 4
 TRAIN_FP32, TRAIN_BF16 = 0, 1
 MAX_TEXTURES, MAX_LEVELS, MAX_MLP_LAYERS = 8, 16, 4
 STATUS_NAMES = {0: "NTBC_OK", 1: "NTBC_EINVAL", 2: "NTBC_ENOMEM", 3: "NTBC_ECUDA", 4: "NTBC_ETIMEOUT",

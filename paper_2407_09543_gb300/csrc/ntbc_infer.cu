@@ -271,6 +271,98 @@ static ntbc_status launch_simt(const ntbc_model* m, const OutPtrs& outs, const i
 }
 
 // ---------------------------------------------------------------------------
+// calibration of the FP8 activation scales (NTBC_PREC_FP8_MMA): the largest |input| of every
+// layer over a fixed sample of the material, in FP32 with the FP8 weights and unrounded
+// activations; then per layer the smallest a with 2 max|x| <= 448 2^a
+// ---------------------------------------------------------------------------
+
+constexpr int kFp8CalibBlocks = 2048;
+constexpr unsigned long long kFp8CalibStride = 2654435761ull;     // prime: the sampled ids are distinct
+
+// One thread per sample row: rows [0, count) run the endpoint network on the sampled blocks'
+// centres, rows [count, 17 count) the colour network on their 16 texels. amax: per network
+// (colour, endpoint) and layer the largest |input| as FP32 bits (non-negative floats order
+// like their bit patterns).
+__global__ void __launch_bounds__(128) fp8_calib_kernel(ModelView mv, const float* __restrict__ params, GridSrc csrc,
+                                                        GridSrc esrc, int count, unsigned* __restrict__ amax) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = row < 17 * count;
+    const bool endpoint = row < count;
+    float m[NTBC_MAX_MLP_LAYERS];
+#pragma unroll
+    for (int l = 0; l < NTBC_MAX_MLP_LAYERS; ++l) m[l] = 0.f;
+    if (valid) {
+        const int k = endpoint ? row : (row - count) / 16, i = endpoint ? 0 : (row - count) % 16;
+        const unsigned long long nb = (unsigned long long)mv.bw * (unsigned long long)mv.bh;
+        const long long b = (long long)((unsigned long long)k * kFp8CalibStride % nb);
+        const int bx = (int)(b % mv.bw), by = (int)(b / mv.bw);
+        const NetView& nv = endpoint ? mv.endpoint : mv.color;
+        float u, v;
+        if (endpoint) {
+            u = ((float)bx + 0.5f) / (float)mv.bw;
+            v = ((float)by + 0.5f) / (float)mv.bh;
+        } else {
+            u = ((float)(4 * bx + (i & 3)) + 0.5f) / (float)mv.width;
+            v = ((float)(4 * by + (i >> 2)) + 0.5f) / (float)mv.height;
+        }
+        float f[kMaxIn], x[kHidden], y[kHidden];
+        grid_features(nv, endpoint ? esrc : csrc, u, v, f);
+        for (int j = 0; j < kHidden; ++j) x[j] = j < nv.in_dim ? f[j] : 0.f;
+        for (int l = 0; l < nv.n_layers; ++l) {
+            const int in = nv.layer_in[l], out = nv.layer_out[l];
+            float mx = 0.f;
+            for (int j = 0; j < in; ++j) mx = fmaxf(mx, fabsf(x[j]));
+            m[l] = mx;
+            if (l + 1 == nv.n_layers) break;                 // the output layer's result feeds no layer
+            for (int o = 0; o < out; ++o) {
+                float acc = params[nv.b_off[l] + o];
+                for (int j = 0; j < in; ++j) acc = fmaf(params[nv.w_off[l] + (long long)o * in + j], x[j], acc);
+                y[o] = act_f(acc, mv.activation);
+            }
+            for (int o = 0; o < out; ++o) x[o] = y[o];
+        }
+    }
+    for (int net = 0; net < 2; ++net)
+#pragma unroll
+        for (int l = 0; l < NTBC_MAX_MLP_LAYERS; ++l) {
+            unsigned w = valid && endpoint == (net == 1) ? __float_as_uint(m[l]) : 0u;
+            w = __reduce_max_sync(0xffffffffu, w);
+            if ((threadIdx.x & 31) == 0 && w) atomicMax(amax + net * NTBC_MAX_MLP_LAYERS + l, w);
+        }
+}
+
+// aexp[net * n_layers + l] (the order of the FP8 weight exponents): smallest a with
+// 2 max <= 448 2^a, compared exactly (powers of two scale exactly); 0 for an all-zero input
+__global__ void fp8_act_exponent_kernel(const unsigned* __restrict__ amax, int n_layers, int* __restrict__ aexp) {
+    for (int net = 0; net < 2; ++net)
+        for (int l = 0; l < n_layers; ++l) {
+            const float m = 2.f * __uint_as_float(amax[net * NTBC_MAX_MLP_LAYERS + l]);
+            int e = 0;
+            if (m > 0.f) {
+                e = ilogbf(fminf(m, 3.0e38f)) - 8;
+                for (int it = 0; it < 64 && m > ldexpf(448.f, e); ++it) ++e;
+                for (int it = 0; it < 64 && m <= ldexpf(448.f, e - 1); ++it) --e;
+            }
+            aexp[net * n_layers + l] = e;
+        }
+}
+
+ntbc_status fp8_calibrate(ntbc_model* m, cudaStream_t s) {
+    GridSrc csrc, esrc;
+    ntbc_status st = grid_sources(m, csrc, esrc);
+    if (st != NTBC_OK) return st;
+    const ModelView mv = make_view(m->desc, m->layout);
+    const long long nb = (long long)mv.bw * mv.bh;
+    const int count = (int)std::min<long long>(nb, kFp8CalibBlocks);
+    NTBC_CHECK_CUDA(cudaMemsetAsync(m->w8_amax, 0, 2 * NTBC_MAX_MLP_LAYERS * sizeof(unsigned), s));
+    const int rows = 17 * count;
+    fp8_calib_kernel<<<(rows + 127) / 128, 128, 0, s>>>(mv, m->infer_params, csrc, esrc, count, m->w8_amax);
+    fp8_act_exponent_kernel<<<1, 1, 0, s>>>(m->w8_amax, mv.color.n_layers, m->w8_aexp);
+    NTBC_CHECK_LAUNCH("FP8 activation calibration");
+    return NTBC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // host delivery (ntbc_infer_to_host): device staging of the blocks, block ids 0 .. n-1 for
 // the ranged launches, a copy stream and its events, kept by the model
 // ---------------------------------------------------------------------------

@@ -16,6 +16,12 @@
 // 128 threads read their row of the accumulator (tcgen05.ld 32x32b) and apply
 // SELU (or the sigmoid on the output layer). The other warpgroups of the CTA
 // keep the SM busy while one waits on its MMA.
+//
+// The FP8 arithmetic (NTBC_PREC_FP8_MMA) runs the same schedule with E4M3 tiles and
+// kind::f8f6f4 MMAs (K = 32 per MMA): the A tile holds each layer's input scaled by the
+// layer's 2^-a and rounded to E4M3, the B tile the E4M3 weight codes; the accumulator is
+// then (x W) 2^-(a + w), so the epilogue forms z L = acc L 2^(a + w) + b L with the FP32
+// bias from shared memory (no bias K block) and writes SELU(z) 2^-a' for the next layer.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -34,6 +40,11 @@ constexpr int kTcUnitBlocks = 128;
 constexpr int kTcMaxGroups = 4;
 constexpr int kTcColsPerGroup = 128;           // two 64-column accumulator regions per group
 constexpr int kTcPalBytes = 12;            // integer palette bytes per block per texture
+// A-operand (activation) formats: FP16; FP16 high + low halves (two MMAs per K block); E4M3
+// at per-layer power-of-two scales (kind::f8f6f4)
+enum { kActF16 = 0, kActSplit = 1, kActE4M3 = 2 };
+
+__host__ __device__ constexpr int tc_a_bytes(int act) { return act == kActE4M3 ? 1 : 2; }
 // store 8 FP16 values (k-group kg) of row r
 __device__ __forceinline__ void st_row8(unsigned char* tile, int r, int kg, int K, const float* v) {
     __half2 h0 = __floats2half2_rn(v[0], v[1]), h1 = __floats2half2_rn(v[2], v[3]);
@@ -81,6 +92,21 @@ __device__ __forceinline__ void st_row8_split(unsigned char* hi_tile, unsigned c
     *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
+// two values as E4M3 codes (nearest even, saturating at +-448): lo in the low byte
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+    unsigned short d;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// store 16 values as E4M3 (k-group kg of 16 one-byte elements) of row r
+__device__ __forceinline__ void st_row16_e4m3(unsigned char* tile, int r, int kg, int K, const float* v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = e4m3x2(v[4 * j], v[4 * j + 1]) | (e4m3x2(v[4 * j + 2], v[4 * j + 3]) << 16);
+    *reinterpret_cast<uint4*>(tile + core_byte8(r, 16 * kg, K)) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // Activations travel scaled by L = log2(e): every accumulator holds z L (the layer-0
 // features and both bias inputs carry the factor), so the exponentials are plain ex2.
 constexpr float kLog2e = 1.4426950408889634f;
@@ -104,6 +130,15 @@ __device__ __forceinline__ float2 selu2_l2(float2 a) {
 
 // sigmoid(z) from a = z L
 __device__ __forceinline__ float sigmoid_l2(float a) { return __fdividef(1.f, 1.f + ex2_approx(-a)); }
+
+// The same SELU with the output scaled: c1 (a - min(a, 0)) + c2 (2^min(a, 0) - 1), which is
+// SELU(z) 2^-a' for c1 = lambda 2^-a' / L and c2 = lambda alpha 2^-a' (ReLU: c1 max(a, 0), c2 = 0)
+__device__ __forceinline__ float2 selu2_scaled(float2 a, float c1, float c2) {
+    const float2 m = make_float2(fminf(a.x, 0.f), fminf(a.y, 0.f));
+    float2 e = make_float2(ex2_approx(m.x), ex2_approx(m.y));
+    float2 t = __ffma2_rn(make_float2(c2, c2), e, make_float2(-c2, -c2));
+    return __ffma2_rn(make_float2(c1, c1), __ffma2_rn(m, make_float2(-1.f, -1.f), a), t);
+}
 
 // The decisions of choose_code_bc1 / choose_code_bc4 (least squared FP32 distance, channels
 // summed in order, ties to the lowest code) with two palette entries per packed instruction;
@@ -151,10 +186,21 @@ __device__ __forceinline__ int choose_code_bc4_x2(const BlockPalette& bp, float 
 }
 
 struct TcLayer {
-    int K;           // total K of the MMA (multiple of 16, bias column included)
+    int K;           // total K of the MMA (FP16: multiple of 16, bias column included; E4M3: 32 or 64)
     int N;           // padded output width (multiple of 16)
     int out;         // real output width
     int img;         // byte offset of the B tile in the weight image
+    int bias;        // E4M3: byte offset of the N FP32 values b L in the weight image
+};
+
+// E4M3: per network and layer (colour 0.., endpoint 0..) the FP32 constants
+// (L 2^(a + w), c1, c2 of the scaled SELU writing the next layer's input, and for layer 0
+// the grid-feature scale 2^-a), at byte ftab of the weight image. A ReLU hidden layer keeps
+// L out of it (s = 2^(a + w - a'), bias b 2^-a'): every scaling is then a power of two, so
+// an activation that is exactly an E4M3 rounding tie (common in a ReLU network, whose
+// values are dyadic) reaches the rounding unperturbed.
+struct TcLayerConst {
+    float s, c1, c2, fscale;
 };
 
 struct TcNet {
@@ -171,6 +217,8 @@ struct TcArgs {
     const int32_t* ids;       // optional block ids (else 0..n-1)
     int mode;                 // 0 pack, 1 raw outputs
     int ub;                   // blocks per work unit (128, or 64)
+    int act;                  // A-operand format (kActF16, kActSplit, kActE4M3)
+    int ftab;                 // E4M3: byte offset of the TcLayerConst table in the weight image
     int* err;
     float inv_w, inv_h, inv_bw, inv_bh;   // reciprocals of the texel and block extents
 };
@@ -195,18 +243,18 @@ struct TcSmem {
 };
 
 // Shared: weight image, ones tile (bias K block), k/255 table, per-level dequantisation
-// constants. Per group: A tile (FP16 activations), the low-half tile when split, the
-// unit's integer palettes (12 bytes per block and texture) and quantised endpoints,
+// constants. Per group: A tile (FP16 or E4M3 activations), the low-half tile when split,
+// the unit's integer palettes (12 bytes per block and texture) and quantised endpoints,
 // and the group's mbarrier.
-__host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int split, int ub) {
+__host__ __device__ inline TcSmem tc_smem_layout(int img_bytes, int n_tex, int act, int ub) {
     TcSmem s;
     s.ones_off = (img_bytes + 127) & ~127;
     s.table_off = s.ones_off + 2 * kTcRows * 16 * 2;             // two constant tiles: L high, L low
     s.lvl_off = s.table_off + 256 * 4;
     s.group_off = (s.lvl_off + 2 * 4 * NTBC_MAX_LEVELS * 4 + 127) & ~127;
     s.a_off = 0;
-    s.lo_off = kTcRows * 64 * 2;
-    s.pal_off = s.lo_off + (split ? kTcRows * 64 * 2 : 0);
+    s.lo_off = kTcRows * 64 * tc_a_bytes(act);
+    s.pal_off = s.lo_off + (act == kActSplit ? kTcRows * 64 * 2 : 0);
     s.ep_off = s.pal_off + ((n_tex * ub * kTcPalBytes + 15) & ~15);
     s.bar_off = s.ep_off + n_tex * ub * 4;
     s.group_bytes = (s.bar_off + 16 + 127) & ~127;
@@ -256,11 +304,13 @@ __device__ __forceinline__ uint32_t ld_u16(const uint8_t* p) {
 
 // Grid features of one row (texel or block), level-major, 2 per level, followed by the
 // constant 1 of the layer-0 bias column; stored as FP16 chunks (high, and low halves when
-// split). Exported grids: bilinear interpolation of the exact codes, then the
-// dequantisation s (q - z) L as one FMA with the per-level constants in lvl.
-template <bool SPLIT>
-__device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src, const float4* lvl, float u, float v,
-                                           int K0, unsigned char* A, unsigned char* Alo, int r, bool valid) {
+// split), or for E4M3 as 32 codes of the features times 2^-a (no bias column). Exported
+// grids: bilinear interpolation of the exact codes, then the dequantisation s (q - z) fs as
+// one FMA with the per-level constants in lvl; FP32 grids: the interpolation times fs.
+// fs = L, or 2^-a for E4M3.
+template <int ACT>
+__device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src, const float4* lvl, float fs, float u,
+                                           float v, int K0, unsigned char* A, unsigned char* Alo, int r, bool valid) {
     float f[2 * NTBC_MAX_LEVELS];
 #pragma unroll
     for (int l = 0; l < NTBC_MAX_LEVELS; ++l) {
@@ -285,12 +335,17 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
                 float2 c = __ldg(reinterpret_cast<const float2*>(gp + 2));
                 float2 d = __ldg(reinterpret_cast<const float2*>(gp + b.row));
                 float2 e = __ldg(reinterpret_cast<const float2*>(gp + b.row + 2));
-                f0 = (b.w00 * a.x + b.w01 * c.x + b.w10 * d.x + b.w11 * e.x) * kLog2e;
-                f1 = (b.w00 * a.y + b.w01 * c.y + b.w10 * d.y + b.w11 * e.y) * kLog2e;
+                f0 = (b.w00 * a.x + b.w01 * c.x + b.w10 * d.x + b.w11 * e.x) * fs;
+                f1 = (b.w00 * a.y + b.w01 * c.y + b.w10 * d.y + b.w11 * e.y) * fs;
             }
         }
         f[2 * l] = f0;
         f[2 * l + 1] = f1;
+    }
+    if constexpr (ACT == kActE4M3) {              // K0 = 32 = 2 NTBC_MAX_LEVELS
+        st_row16_e4m3(A, r, 0, 32, f);
+        st_row16_e4m3(A, r, 1, 32, f + 16);
+        return;
     }
 #pragma unroll
     for (int kg = 0; kg < 6; ++kg) {
@@ -302,7 +357,7 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
             float x = i < 2 * NTBC_MAX_LEVELS ? f[i] : 0.f;
             v8[j] = i == nv.in_dim ? kLog2e : x;
         }
-        st_row8_split<SPLIT>(A, Alo, r, kg, K0, v8);
+        st_row8_split<ACT == kActSplit>(A, Alo, r, kg, K0, v8);
     }
 }
 
@@ -317,17 +372,19 @@ struct TcGroup {
     int g, r;
 };
 
-// Per-level dequantisation constants of both grids as pairs: (s L, s L, -s z L, -s z L).
+// Per-level dequantisation constants of both grids as pairs: (s fs, s fs, -s z fs, -s z fs)
+// with the feature scale fs of the network (L, or 2^-a for E4M3: fs_c colour, fs_e endpoint).
 __device__ __forceinline__ void load_level_constants(const ModelView& mv, const GridSrc& csrc, const GridSrc& esrc,
-                                                     float4* lvl) {
+                                                     float4* lvl, float fs_c = kLog2e, float fs_e = kLog2e) {
     for (int i = threadIdx.x; i < 2 * NTBC_MAX_LEVELS; i += blockDim.x) {
         int net = i / NTBC_MAX_LEVELS, l = i % NTBC_MAX_LEVELS;
         const GridSrc& src = net ? esrc : csrc;
         int L = net ? mv.endpoint.levels : mv.color.levels;
+        const float fs = net ? fs_e : fs_c;
         float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
         if (src.codes && l < L) {
             float sc = src.scale[l], z = src.zero[l];
-            k = make_float4(sc * kLog2e, sc * kLog2e, -sc * z * kLog2e, -sc * z * kLog2e);
+            k = make_float4(sc * fs, sc * fs, -sc * z * fs, -sc * z * fs);
         }
         lvl[i] = k;
     }
@@ -393,29 +450,36 @@ __device__ __forceinline__ void teardown_groups(const TcGroup& G, int groups, bo
 
 // MMAs of K blocks kc0 .. kc1-1 of layer l (A tile of K0 columns for layer 0, 64
 // afterwards; when split each block twice, high and low halves) and, with `bias`, the
-// bias K block from the constant tiles, into the accumulator at tmem_d.
-template <bool SPLIT>
+// bias K block from the constant tiles, into the accumulator at tmem_d. A K block is 32
+// bytes of every row: 16 FP16 values (kind::f16) or 32 E4M3 values (kind::f8f6f4, no bias
+// block).
+template <int ACT>
 __device__ __forceinline__ void issue_steps(const TcLayer& L, int l, unsigned char* smem, unsigned char* A,
                                             const TcSmem& sl, uint32_t tmem_d, int kc0, int kc1, bool bias) {
     // descriptors built once; the K step advances only the start-address field (16-byte units,
     // no carry out of the field for shared-memory addresses), so each MMA adds to the low word
-    const uint32_t idesc = umma_idesc(L.N);
+    constexpr int EPC = 16 / tc_a_bytes(ACT);               // elements per core-matrix row
+    const uint32_t idesc = ACT == kActE4M3 ? umma_idesc_e4m3(L.N) : umma_idesc(L.N);
     const int Ka = l == 0 ? L.K : 64;
-    const uint64_t a0 = umma_desc(smem_u32(A), 128, (Ka / 8) * 128);
-    const uint64_t b0 = umma_desc(smem_u32(smem + L.img), 128, (L.K / 8) * 128);
+    const uint64_t a0 = umma_desc(smem_u32(A), 128, (Ka / EPC) * 128);
+    const uint64_t b0 = umma_desc(smem_u32(smem + L.img), 128, (L.K / EPC) * 128);
     const uint32_t a_lo = (uint32_t)a0, a_hi = (uint32_t)(a0 >> 32);
     const uint32_t b_lo = (uint32_t)b0, b_hi = (uint32_t)(b0 >> 32);
     const uint32_t lo_step = (uint32_t)(sl.lo_off - sl.a_off) >> 4;
     for (int kc = kc0; kc < kc1; ++kc) {
         const uint32_t ka = a_lo + (uint32_t)kc * 16u, kb = b_lo + (uint32_t)kc * 16u;
         const uint64_t bd = ((uint64_t)b_hi << 32) | kb;
-        umma_f16(tmem_d, ((uint64_t)a_hi << 32) | ka, bd, idesc, kc > 0);
-        if (SPLIT) umma_f16(tmem_d, ((uint64_t)a_hi << 32) | (ka + lo_step), bd, idesc, 1);
+        if constexpr (ACT == kActE4M3) {
+            umma_f8(tmem_d, ((uint64_t)a_hi << 32) | ka, bd, idesc, kc > 0);
+        } else {
+            umma_f16(tmem_d, ((uint64_t)a_hi << 32) | ka, bd, idesc, kc > 0);
+            if (ACT == kActSplit) umma_f16(tmem_d, ((uint64_t)a_hi << 32) | (ka + lo_step), bd, idesc, 1);
+        }
     }
-    if (bias) {
+    if (ACT != kActE4M3 && bias) {
         const uint64_t bd = ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)(Ka / 16) * 16u);
         umma_f16(tmem_d, umma_desc(smem_u32(smem + sl.ones_off), 128, 256), bd, idesc, 1);
-        if (SPLIT) umma_f16(tmem_d, umma_desc(smem_u32(smem + sl.ones_off + kTcRows * 32), 128, 256), bd, idesc, 1);
+        if (ACT == kActSplit) umma_f16(tmem_d, umma_desc(smem_u32(smem + sl.ones_off + kTcRows * 32), 128, 256), bd, idesc, 1);
     }
 }
 
@@ -434,14 +498,41 @@ __device__ __forceinline__ void wait_mma(uint64_t* bar, uint32_t& phase, int g, 
     tc_fence_after();
 }
 
-// 32 accumulator columns (c0 .. c0 + 31) -> activation -> A columns c0 .. c0 + 31
-template <bool SPLIT>
+// 32 accumulator columns (c0 .. c0 + 31) -> activation -> A columns c0 .. c0 + 31. E4M3:
+// the accumulator is first turned into z L = acc s + b L (ReLU: z 2^-a' = acc s + b 2^-a';
+// lc: the layer's constants, bias: its bias column in shared memory) and the activation is
+// written scaled for the next layer.
+template <int ACT>
 __device__ __forceinline__ void epilogue_half(uint32_t src_row, int c0, unsigned char* A, unsigned char* Alo, int r,
-                                              int act) {
+                                              int act, const TcLayerConst& lc, const float* bias) {
     float v[32];
     tmem_ld16(src_row + c0, v);
     tmem_ld16(src_row + c0 + 16, v + 16);
     tmem_wait_ld();
+    if constexpr (ACT == kActE4M3) {
+        const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            const float4 b = b4[j / 4];
+            float2 a0 = __ffma2_rn(make_float2(v[j], v[j + 1]), make_float2(lc.s, lc.s), make_float2(b.x, b.y));
+            float2 a1 = __ffma2_rn(make_float2(v[j + 2], v[j + 3]), make_float2(lc.s, lc.s), make_float2(b.z, b.w));
+            float2 y0, y1;
+            if (act == NTBC_ACT_SELU) {
+                y0 = selu2_scaled(a0, lc.c1, lc.c2);
+                y1 = selu2_scaled(a1, lc.c1, lc.c2);
+            } else {                             // ReLU: a is already z 2^-a'
+                y0 = make_float2(fmaxf(a0.x, 0.f), fmaxf(a0.y, 0.f));
+                y1 = make_float2(fmaxf(a1.x, 0.f), fmaxf(a1.y, 0.f));
+            }
+            v[j] = y0.x;
+            v[j + 1] = y0.y;
+            v[j + 2] = y1.x;
+            v[j + 3] = y1.y;
+        }
+        st_row16_e4m3(A, r, c0 / 16, 64, v);
+        st_row16_e4m3(A, r, c0 / 16 + 1, 64, v + 16);
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < 32; j += 2) {
         float2 y = act == NTBC_ACT_SELU ? selu2_l2(make_float2(v[j], v[j + 1]))
@@ -450,40 +541,53 @@ __device__ __forceinline__ void epilogue_half(uint32_t src_row, int c0, unsigned
         v[j + 1] = y.y;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st_row8_split<SPLIT>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
+    for (int q = 0; q < 4; ++q) st_row8_split<ACT == kActSplit>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
+}
+
+// E4M3: the constants of layer l of network `net` (0 colour, 1 endpoint) in the image copy
+__device__ __forceinline__ TcLayerConst layer_const(const unsigned char* smem, int ftab, int net, int l) {
+    return reinterpret_cast<const TcLayerConst*>(smem + ftab)[net * NTBC_MAX_MLP_LAYERS + l];
 }
 
 // All layers of one MLP on the A tile the gather wrote. Accumulators alternate between the
 // group's two TMEM regions, and each hidden epilogue runs in two halves: once the first 32
-// activations of every row are in shared memory, the next layer's first two K blocks are
+// activations of every row are in shared memory, the next layer's K blocks over them are
 // issued, so they run on the tensor core while the second half is computed. Leaves the
 // output layer's accumulator row at *out_row.
-template <bool SPLIT>
-__device__ __forceinline__ bool run_mlp(const TcNet& net, int act, unsigned char* smem, const TcSmem& sl,
-                                        const TcGroup& G, uint32_t& phase, uint32_t& region, volatile int* abort_flag,
-                                        uint32_t* out_row) {
+template <int ACT>
+__device__ __forceinline__ bool run_mlp(const TcNet& net, int which, int ftab, int act, unsigned char* smem,
+                                        const TcSmem& sl, const TcGroup& G, uint32_t& phase, uint32_t& region,
+                                        volatile int* abort_flag, uint32_t* out_row) {
+    constexpr int KB = ACT == kActE4M3 ? 32 : 16;        // K per MMA
+    constexpr int KH = 32 / KB;                           // MMAs per half of a hidden layer
     if (!group_barrier(G.g, abort_flag)) return false;
     uint32_t cur = region;
     if (G.r == 0) {
         tc_fence_after();
-        issue_steps<SPLIT>(net.layer[0], 0, smem, G.A, sl, G.tmem + 64 * cur, 0, net.layer[0].K / 16, false);
+        issue_steps<ACT>(net.layer[0], 0, smem, G.A, sl, G.tmem + 64 * cur, 0, net.layer[0].K / KB, false);
         umma_commit(G.bar);
     }
     wait_mma(G.bar, phase, G.g, abort_flag);
     for (int l = 1; l < net.n_layers; ++l) {
         uint32_t nxt = cur ^ 1;
         uint32_t src_row = G.tmem_row + 64 * cur;
-        epilogue_half<SPLIT>(src_row, 0, G.A, G.Alo, G.r, act);
-        if (!group_barrier(G.g, abort_flag)) return false;
-        if (G.r == 0) {
-            tc_fence_after();
-            issue_steps<SPLIT>(net.layer[l], l, smem, G.A, sl, G.tmem + 64 * nxt, 0, 2, false);
+        TcLayerConst lc{};
+        const float* bias = nullptr;
+        if constexpr (ACT == kActE4M3) {
+            lc = layer_const(smem, ftab, which, l - 1);
+            bias = reinterpret_cast<const float*>(smem + net.layer[l - 1].bias);
         }
-        epilogue_half<SPLIT>(src_row, 32, G.A, G.Alo, G.r, act);
+        epilogue_half<ACT>(src_row, 0, G.A, G.Alo, G.r, act, lc, bias);
         if (!group_barrier(G.g, abort_flag)) return false;
         if (G.r == 0) {
             tc_fence_after();
-            issue_steps<SPLIT>(net.layer[l], l, smem, G.A, sl, G.tmem + 64 * nxt, 2, 4, true);
+            issue_steps<ACT>(net.layer[l], l, smem, G.A, sl, G.tmem + 64 * nxt, 0, KH, false);
+        }
+        epilogue_half<ACT>(src_row, 32, G.A, G.Alo, G.r, act, lc, bias);
+        if (!group_barrier(G.g, abort_flag)) return false;
+        if (G.r == 0) {
+            tc_fence_after();
+            issue_steps<ACT>(net.layer[l], l, smem, G.A, sl, G.tmem + 64 * nxt, KH, 2 * KH, true);
             umma_commit(G.bar);
         }
         wait_mma(G.bar, phase, G.g, abort_flag);
@@ -495,7 +599,7 @@ __device__ __forceinline__ bool run_mlp(const TcNet& net, int act, unsigned char
 }
 
 // One work unit (UB blocks, 128 or 64): endpoint network, palettes, then UB / 8 colour tiles.
-template <bool SPLIT, int UB>
+template <int ACT, int UB>
 __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& csrc, const GridSrc& esrc, const TcOut& outs,
                                           float* __restrict__ e_out, float* __restrict__ c_out, int unit,
                                           unsigned char* smem, const TcSmem& sl, const TcGroup& G, uint32_t& phase,
@@ -513,6 +617,21 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
     const int T = mv.n_textures;
     constexpr int ub = UB;
     bool ok = true;
+    // E4M3: the output layers' z L = acc s + b L (FP16 paths: the accumulator already holds z L)
+    float fs[2] = {kLog2e, kLog2e}, os[2] = {1.f, 1.f};
+    const float* ob[2] = {nullptr, nullptr};
+    if constexpr (ACT == kActE4M3) {
+        for (int w = 0; w < 2; ++w) {
+            const TcNet& tn = args.net[w];
+            fs[w] = layer_const(smem, args.ftab, w, 0).fscale;
+            os[w] = layer_const(smem, args.ftab, w, tn.n_layers - 1).s;
+            ob[w] = reinterpret_cast<const float*>(smem + tn.layer[tn.n_layers - 1].bias);
+        }
+    }
+    auto zl = [&](int w, float acc, int col) -> float {
+        if constexpr (ACT == kActE4M3) return fmaf(acc, os[w], ob[w][col]);
+        else return acc;
+    };
         // ================= endpoint network: row r = block r of the unit
         {
             const TcNet& net = args.net[1];
@@ -521,17 +640,18 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             int b = valid ? (args.ids ? args.ids[k] : k) : 0;
             int bx, by;
             block_xy(b, mv.bw, args.inv_bw, bx, by);
-            gather_row<SPLIT>(mv.endpoint, esrc, lvl + NTBC_MAX_LEVELS, ((float)bx + 0.5f) * args.inv_bw,
-                              ((float)by + 0.5f) * args.inv_bh, net.layer[0].K, A, Alo, r, valid);
+            gather_row<ACT>(mv.endpoint, esrc, lvl + NTBC_MAX_LEVELS, fs[1], ((float)bx + 0.5f) * args.inv_bw,
+                            ((float)by + 0.5f) * args.inv_bh, net.layer[0].K, A, Alo, r, valid);
             uint32_t orow = 0;
-            ok = run_mlp<SPLIT>(net, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
+            ok = run_mlp<ACT>(net, 1, args.ftab, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
             for (int l = net.n_layers - 1; l < net.n_layers && ok; ++l) {
                 const uint32_t tmem_row = orow;
                 if (args.mode == 1) {
                     int out = net.layer[l].out;
                     for (int o = 0; o < out; ++o) {
-                        float e = sigmoid_l2(tmem_ld1(tmem_row + o));
-                        tmem_wait_ld();
+                        float e = tmem_ld1(tmem_row + o);
+                        tmem_wait_ld_regs<1>(&e);
+                        e = sigmoid_l2(zl(1, e, o));
                         if (valid) e_out[(long long)k * out + o] = e;
                     }
                     continue;
@@ -545,7 +665,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                         for (int q = 0; q < 6; ++q) e[q] = tmem_ld1(tmem_row + eo + q);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) e[q] = sigmoid_l2(e[q]);
+                        for (int q = 0; q < 6; ++q) e[q] = sigmoid_l2(zl(1, e[q], eo + q));
                         uint32_t c0 = (quant_channel(e[0], 31.f, 31) << 11) | (quant_channel(e[1], 63.f, 63) << 5) |
                                       quant_channel(e[2], 31.f, 31);
                         uint32_t c1 = (quant_channel(e[3], 31.f, 31) << 11) | (quant_channel(e[4], 63.f, 63) << 5) |
@@ -566,8 +686,8 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                         e[0] = tmem_ld1(tmem_row + eo);
                         e[1] = tmem_ld1(tmem_row + eo + 1);
                         tmem_wait_ld();
-                        int r0 = quant_channel(sigmoid_l2(e[0]), 255.f, 255);
-                        int r1 = quant_channel(sigmoid_l2(e[1]), 255.f, 255);
+                        int r0 = quant_channel(sigmoid_l2(zl(1, e[0], eo)), 255.f, 255);
+                        int r1 = quant_channel(sigmoid_l2(zl(1, e[1], eo + 1)), 255.f, 255);
                         int p[8];
                         bc4_palette(r0, r1, p);
 #pragma unroll
@@ -587,17 +707,18 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             int bx, by;
             block_xy(b, mv.bw, args.inv_bw, bx, by);
             int x = 4 * bx + (i & 3), y = 4 * by + (i >> 2);
-            gather_row<SPLIT>(mv.color, csrc, lvl, ((float)x + 0.5f) * args.inv_w, ((float)y + 0.5f) * args.inv_h,
-                              net.layer[0].K, A, Alo, r, valid);
+            gather_row<ACT>(mv.color, csrc, lvl, fs[0], ((float)x + 0.5f) * args.inv_w, ((float)y + 0.5f) * args.inv_h,
+                            net.layer[0].K, A, Alo, r, valid);
             uint32_t orow = 0;
-            ok = run_mlp<SPLIT>(net, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
+            ok = run_mlp<ACT>(net, 0, args.ftab, mv.activation, smem, sl, G, phase, region, abort_flag, &orow);
             for (int l = net.n_layers - 1; l < net.n_layers && ok; ++l) {
                 const uint32_t tmem_row = orow;
                 if (args.mode == 1) {
                     int out = net.layer[l].out;
                     for (int o = 0; o < out; ++o) {
-                        float c = sigmoid_l2(tmem_ld1(tmem_row + o));
-                        tmem_wait_ld();
+                        float c = tmem_ld1(tmem_row + o);
+                        tmem_wait_ld_regs<1>(&c);
+                        c = sigmoid_l2(zl(0, c, o));
                         if (valid) c_out[((long long)k * 16 + i) * out + o] = c;
                     }
                     continue;
@@ -627,8 +748,10 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                                           *reinterpret_cast<const uint32_t*>(pb + 8)};
 #pragma unroll
                         for (int q = 0; q < 12; ++q) bp.pal[q / 3][q % 3] = tab[(wv[q / 4] >> (8 * (q % 4))) & 255];
-                        uint32_t w = (uint32_t)choose_code_bc1_x2(bp, sigmoid_l2(cv[t][0]), sigmoid_l2(cv[t][1]),
-                                                               sigmoid_l2(cv[t][2])) << (2 * i);
+                        const int co = mv.coff[t];
+                        uint32_t w = (uint32_t)choose_code_bc1_x2(bp, sigmoid_l2(zl(0, cv[t][0], co)),
+                                                                  sigmoid_l2(zl(0, cv[t][1], co + 1)),
+                                                                  sigmoid_l2(zl(0, cv[t][2], co + 2))) << (2 * i);
 #pragma unroll
                         for (int o = 8; o > 0; o >>= 1) w |= __shfl_xor_sync(0xffffffffu, w, o);
                         bits = w;
@@ -637,7 +760,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                         uint32_t w1 = *reinterpret_cast<const uint32_t*>(pb + 4);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) bp.pal[q][0] = tab[((q < 4 ? w0 : w1) >> (8 * (q % 4))) & 255];
-                        bits = (uint64_t)choose_code_bc4_x2(bp, sigmoid_l2(cv[t][0])) << (3 * i);
+                        bits = (uint64_t)choose_code_bc4_x2(bp, sigmoid_l2(zl(0, cv[t][0], mv.coff[t]))) << (3 * i);
 #pragma unroll
                         for (int o = 8; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
                     }
@@ -655,23 +778,34 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
     return ok;
 }
 
-template <bool SPLIT, int UB>
+// the grid-feature scales (colour, endpoint) of a weight image in global memory
+template <int ACT>
+__device__ __forceinline__ float2 feature_scales(const uint4* img, int ftab) {
+    if constexpr (ACT == kActE4M3) {
+        const TcLayerConst* t = reinterpret_cast<const TcLayerConst*>(reinterpret_cast<const unsigned char*>(img) + ftab);
+        return make_float2(t[0].fscale, t[NTBC_MAX_MLP_LAYERS].fscale);
+    }
+    return make_float2(kLog2e, kLog2e);
+}
+
+template <int ACT, int UB>
 __global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
 infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSrc esrc, TcOut outs,
                 float* __restrict__ e_out, float* __restrict__ c_out) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag[kTcMaxGroups];
-    const TcSmem sl = tc_smem_layout(args.img_bytes, args.mv.n_textures, SPLIT, UB);
+    const TcSmem sl = tc_smem_layout(args.img_bytes, args.mv.n_textures, ACT, UB);
     for (int i = threadIdx.x; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
     load_constants(smem, sl);
-    load_level_constants(args.mv, csrc, esrc, reinterpret_cast<float4*>(smem + sl.lvl_off));
+    const float2 fs = feature_scales<ACT>(img, args.ftab);
+    load_level_constants(args.mv, csrc, esrc, reinterpret_cast<float4*>(smem + sl.lvl_off), fs.x, fs.y);
     TcGroup G = setup_groups(smem, sl, args.groups, &tmem_slot, abort_flag);
     uint32_t phase = 0, region = 0;
     bool ok = true;
     const int n_units = (args.n + UB - 1) / UB;
     for (int unit = blockIdx.x * args.groups + G.g; unit < n_units && ok; unit += gridDim.x * args.groups)
-        ok = process_unit<SPLIT, UB>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, region, abort_flag);
+        ok = process_unit<ACT, UB>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, region, abort_flag);
     teardown_groups(G, args.groups, ok, phase, args.err, tmem_slot);
 }
 
@@ -712,7 +846,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // claim_limit of them the CTA records the error and stops, so a bad counter ends the launch
 // with NTBC_ETIMEOUT instead of spinning. A group that gave up keeps claiming with its CTA
 // (skipping the work) so that the CTA barriers stay uniform.
-template <bool SPLIT, int UB>
+template <int ACT, int UB>
 __global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
 infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -721,7 +855,7 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
     __shared__ TcMat cur;
     __shared__ int claim[2];
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr.stamps[0] = global_ns();
-    const TcSmem sl = tc_smem_layout(hdr.img_bytes, hdr.max_textures, SPLIT, UB);
+    const TcSmem sl = tc_smem_layout(hdr.img_bytes, hdr.max_textures, ACT, UB);
     load_constants(smem, sl);
     TcGroup G = setup_groups(smem, sl, hdr.groups, &tmem_slot, abort_flag);
     uint32_t phase = 0, region = 0;
@@ -751,7 +885,8 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
             __syncthreads();
             for (int i = threadIdx.x; i < cur.args.img_bytes / 16; i += blockDim.x)
                 reinterpret_cast<uint4*>(smem)[i] = cur.img[i];
-            load_level_constants(cur.args.mv, cur.csrc, cur.esrc, reinterpret_cast<float4*>(smem + sl.lvl_off));
+            const float2 fs = feature_scales<ACT>(cur.img, cur.args.ftab);
+            load_level_constants(cur.args.mv, cur.csrc, cur.esrc, reinterpret_cast<float4*>(smem + sl.lvl_off), fs.x, fs.y);
             proxy_fence();
             __syncthreads();
             tc_fence_after();
@@ -759,7 +894,7 @@ infer_tc_batch_kernel(TcBatchHeader hdr, const TcMat* __restrict__ mats) {
         }
         int unit = (j - cur.first_cta_unit) * hdr.groups + G.g;
         if (ok && unit < cur.units) {
-            ok = process_unit<SPLIT, UB>(cur.args, cur.csrc, cur.esrc, cur.outs, nullptr, nullptr, unit, smem, sl, G, phase,
+            ok = process_unit<ACT, UB>(cur.args, cur.csrc, cur.esrc, cur.outs, nullptr, nullptr, unit, smem, sl, G, phase,
                                      region, abort_flag);
             if (ok && G.r == 0) {
                 __threadfence();
@@ -845,10 +980,69 @@ __global__ void build_image_kernel(const float* __restrict__ params, TcArgs args
     }
 }
 
+// E4M3 weight image: every layer's B tile [N][K] of E4M3 codes (core-matrix layout, K = 32
+// for layer 0, 64 after it; no bias column), then per layer N FP32 values b L, then the
+// TcLayerConst table. Every byte up to the end of the table is written by the kernel.
+__global__ void build_image8_kernel(const uint8_t* __restrict__ codes, const float* __restrict__ params,
+                                    const int* __restrict__ wexp, const int* __restrict__ aexp, long long grid_floats,
+                                    TcArgs args, ModelView mv, uint8_t* __restrict__ img) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int used = args.ftab + 2 * NTBC_MAX_MLP_LAYERS * (int)sizeof(TcLayerConst);
+    for (int e = used + tid; e < args.img_bytes; e += nth) img[e] = 0;
+    for (int net = 0; net < 2; ++net) {
+        const NetView& nv = net ? mv.endpoint : mv.color;
+        const TcNet& tn = args.net[net];
+        for (int l = 0; l < tn.n_layers; ++l) {
+            const TcLayer& L = tn.layer[l];
+            const int in = nv.layer_in[l], out = nv.layer_out[l];
+            for (int e = tid; e < L.N * L.K; e += nth) {
+                const int n = e / L.K, k = e % L.K;
+                img[L.img + core_byte8(n, k, L.K)] = n < out && k < in ? codes[nv.w_off[l] - grid_floats + (long long)n * in + k] : 0;
+            }
+            // ReLU hidden layers work on z 2^-a' directly (bias b 2^-a', exact), every other
+            // layer on z L (bias b L)
+            const bool relu_hidden = mv.activation == NTBC_ACT_RELU && l + 1 < tn.n_layers;
+            const int i_next = net * tn.n_layers + l + 1;
+            float* b = reinterpret_cast<float*>(img + L.bias);
+            for (int n = tid; n < L.N; n += nth) {
+                const float bq = n < out ? params[nv.b_off[l] + n] : 0.f;
+                b[n] = relu_hidden ? ldexpf(bq, -aexp[i_next]) : bq * kLog2e;
+            }
+        }
+    }
+    // layer i = net * layers + l of the exponent lists (colour layers, then endpoint layers)
+    if (tid < 2 * NTBC_MAX_MLP_LAYERS) {
+        const int net = tid / NTBC_MAX_MLP_LAYERS, l = tid % NTBC_MAX_MLP_LAYERS, nl = args.net[net].n_layers;
+        TcLayerConst c{0.f, 0.f, 0.f, 0.f};
+        if (l < nl) {
+            const int i = net * nl + l;
+            c.s = ldexpf(kLog2e, aexp[i] + wexp[i]);
+            if (l == 0) c.fscale = ldexpf(1.f, -aexp[i]);
+            if (l + 1 < nl) {
+                if (mv.activation == NTBC_ACT_SELU) {
+                    c.c1 = ldexpf(kSeluLambda / kLog2e, -aexp[i + 1]);
+                    c.c2 = ldexpf(kSeluLA, -aexp[i + 1]);
+                } else {                 // ReLU: max(acc 2^(a + w - a') + b 2^-a', 0), all scalings exact
+                    c.s = ldexpf(1.f, aexp[i] + wexp[i] - aexp[i + 1]);
+                    c.c1 = 1.f;
+                }
+            }
+        }
+        reinterpret_cast<TcLayerConst*>(img + args.ftab)[tid] = c;
+    }
+}
+
+static int tc_act(const ntbc_model* m) {
+    if (m->weight_prec == NTBC_PREC_FP16_FAST) return kActF16;
+    return m->weight_prec == NTBC_PREC_FP8_MMA ? kActE4M3 : kActSplit;      // FP16 and FP8-storage: split
+}
+
 static TcArgs tc_args(const ntbc_model* m) {
     TcArgs a;
     memset(&a, 0, sizeof(a));
     a.mv = make_view(m->desc, m->layout);
+    a.act = tc_act(m);
+    const bool f8 = a.act == kActE4M3;
     int off = 0;
     for (int net = 0; net < 2; ++net) {
         const NetView& nv = net ? a.mv.endpoint : a.mv.color;
@@ -856,12 +1050,24 @@ static TcArgs tc_args(const ntbc_model* m) {
         tn.n_layers = nv.n_layers;
         for (int l = 0; l < nv.n_layers; ++l) {
             TcLayer& L = tn.layer[l];
-            L.K = l == 0 ? ((nv.in_dim + 1 + 15) / 16) * 16 : 64 + 16;
+            if (f8)
+                L.K = l == 0 ? 2 * NTBC_MAX_LEVELS : 64;             // in_dim <= 2 NTBC_MAX_LEVELS = 32
+            else
+                L.K = l == 0 ? ((nv.in_dim + 1 + 15) / 16) * 16 : 64 + 16;
             L.out = nv.layer_out[l];
             L.N = ((L.out + 15) / 16) * 16;
             L.img = off;
-            off += L.N * L.K * 2;
+            off += L.N * L.K * tc_a_bytes(a.act);
         }
+    }
+    if (f8) {
+        for (int net = 0; net < 2; ++net)
+            for (int l = 0; l < a.net[net].n_layers; ++l) {
+                a.net[net].layer[l].bias = off;
+                off += a.net[net].layer[l].N * 4;
+            }
+        a.ftab = off;
+        off += 2 * NTBC_MAX_MLP_LAYERS * (int)sizeof(TcLayerConst);
     }
     a.img_bytes = (off + 15) & ~15;
     a.inv_w = 1.f / (float)a.mv.width;
@@ -892,9 +1098,9 @@ static bool tc_coords_ok(const TcArgs& a) {
 // static_bytes: the kernel's static shared variables (the batch kernel keeps a copy of
 // the current material's launch description). Returns the warpgroups per CTA and sets the
 // work-unit size: 128 blocks, unless 64-block units (half the palette space) fit more groups.
-static int tc_groups_ub(const TcArgs& a, int n_tex, int split, int ub, size_t* smem_bytes, size_t static_bytes) {
+static int tc_groups_ub(const TcArgs& a, int n_tex, int act, int ub, size_t* smem_bytes, size_t static_bytes) {
     for (int groups = kTcMaxGroups; groups >= 1; --groups) {
-        TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, split, ub);
+        TcSmem sl = tc_smem_layout(a.img_bytes, n_tex, act, ub);
         size_t bytes = (size_t)sl.group_off + (size_t)groups * sl.group_bytes;
         if (bytes + static_bytes <= 227 * 1024) {
             // more than two groups allocate all 512 TMEM columns: ask for enough shared
@@ -907,10 +1113,10 @@ static int tc_groups_ub(const TcArgs& a, int n_tex, int split, int ub, size_t* s
     return 0;
 }
 
-static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, int* ub, size_t static_bytes = 256) {
+static int tc_groups(const TcArgs& a, int n_tex, int act, size_t* smem_bytes, int* ub, size_t static_bytes = 256) {
     size_t s128 = 0, s64 = 0;
-    const int g128 = tc_groups_ub(a, n_tex, split, kTcUnitBlocks, &s128, static_bytes);
-    const int g64 = g128 == kTcMaxGroups ? 0 : tc_groups_ub(a, n_tex, split, kTcUnitBlocks / 2, &s64, static_bytes);
+    const int g128 = tc_groups_ub(a, n_tex, act, kTcUnitBlocks, &s128, static_bytes);
+    const int g64 = g128 == kTcMaxGroups ? 0 : tc_groups_ub(a, n_tex, act, kTcUnitBlocks / 2, &s64, static_bytes);
     if (g64 > g128) {
         *smem_bytes = s64;
         *ub = kTcUnitBlocks / 2;
@@ -923,22 +1129,52 @@ static int tc_groups(const TcArgs& a, int n_tex, int split, size_t* smem_bytes, 
 
 ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s) {
     TcArgs a = tc_args(m);
+    const size_t need = (size_t)a.img_bytes + sizeof(int) * 4;
+    if (m->umma_img && m->umma_bytes < need) {          // an export with a larger image (FP16 after E4M3)
+        NTBC_CHECK_CUDA(cudaFree(m->umma_img));         // waits for work still reading it
+        m->umma_img = nullptr;
+    }
     if (!m->umma_img) {
-        ntbc_status st = device_alloc((void**)&m->umma_img, (size_t)a.img_bytes + sizeof(int) * 4, "tensor-core weight image");
+        ntbc_status st = device_alloc((void**)&m->umma_img, need, "tensor-core weight image");
         if (st != NTBC_OK) return st;
+        m->umma_bytes = need;
     }
     m->tc_err = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(m->umma_img) + a.img_bytes);
     NTBC_CHECK_CUDA(cudaMemsetAsync(m->tc_err, 0, sizeof(int), s));
-    build_image_kernel<<<32, 256, 0, s>>>(m->infer_params, a, a.mv, m->umma_img);
+    if (a.act == kActE4M3)
+        build_image8_kernel<<<32, 256, 0, s>>>(m->w8, m->infer_params, m->w8_exp, m->w8_aexp, (long long)m->layout.grid_floats,
+                                               a, a.mv, reinterpret_cast<uint8_t*>(m->umma_img));
+    else
+        build_image_kernel<<<32, 256, 0, s>>>(m->infer_params, a, a.mv, m->umma_img);
     NTBC_CHECK_LAUNCH("tensor-core weight image");
     return NTBC_OK;
+}
+
+using TcKernel = void (*)(TcArgs, const uint4*, GridSrc, GridSrc, TcOut, float*, float*);
+using TcBatchKernel = void (*)(TcBatchHeader, const TcMat*);
+
+// the kernel instance for an A-operand format and a work-unit size (128 or 64 blocks)
+static TcKernel tc_kernel(int act, int ub) {
+    const bool half = ub != kTcUnitBlocks;
+    if (act == kActE4M3) return half ? infer_tc_kernel<kActE4M3, kTcUnitBlocks / 2> : infer_tc_kernel<kActE4M3, kTcUnitBlocks>;
+    if (act == kActSplit) return half ? infer_tc_kernel<kActSplit, kTcUnitBlocks / 2> : infer_tc_kernel<kActSplit, kTcUnitBlocks>;
+    return half ? infer_tc_kernel<kActF16, kTcUnitBlocks / 2> : infer_tc_kernel<kActF16, kTcUnitBlocks>;
+}
+
+static TcBatchKernel tc_batch_kernel(int act, int ub) {
+    const bool half = ub != kTcUnitBlocks;
+    if (act == kActE4M3)
+        return half ? infer_tc_batch_kernel<kActE4M3, kTcUnitBlocks / 2> : infer_tc_batch_kernel<kActE4M3, kTcUnitBlocks>;
+    if (act == kActSplit)
+        return half ? infer_tc_batch_kernel<kActSplit, kTcUnitBlocks / 2> : infer_tc_batch_kernel<kActSplit, kTcUnitBlocks>;
+    return half ? infer_tc_batch_kernel<kActF16, kTcUnitBlocks / 2> : infer_tc_batch_kernel<kActF16, kTcUnitBlocks>;
 }
 
 int tc_units_in_flight(const ntbc_model* m, int* unit_blocks) {
     TcArgs a = tc_args(m);
     size_t smem = 0;
     int ub = kTcUnitBlocks;
-    const int groups = tc_groups(a, m->desc.n_textures, m->weight_prec != NTBC_PREC_FP16_FAST, &smem, &ub);
+    const int groups = tc_groups(a, m->desc.n_textures, a.act, &smem, &ub);
     if (unit_blocks) *unit_blocks = ub;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -950,8 +1186,7 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
                       float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
     TcArgs a = tc_args(m);
     size_t smem = 0;
-    const bool split = m->weight_prec != NTBC_PREC_FP16_FAST;     // FP16 and FP8 weights
-    a.groups = tc_groups(a, m->desc.n_textures, split, &smem, &a.ub);
+    a.groups = tc_groups(a, m->desc.n_textures, a.act, &smem, &a.ub);
     if (a.groups == 0) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: shared memory too small for this model");
     if (!tc_coords_ok(a)) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: a grid level is too fine for the texture extent");
     a.n = n;
@@ -972,14 +1207,9 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
     int grid = std::min(sms, (units + a.groups - 1) / a.groups);
     if (grid < 1) return NTBC_OK;
     const uint4* img = reinterpret_cast<const uint4*>(m->umma_img);
-    auto launch = [&](auto kernel) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) kernel<<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
-        return e;
-    };
-    const bool half = a.ub != kTcUnitBlocks;
-    NTBC_CHECK_CUDA(split ? (half ? launch(infer_tc_kernel<true, kTcUnitBlocks / 2>) : launch(infer_tc_kernel<true, kTcUnitBlocks>))
-                          : (half ? launch(infer_tc_kernel<false, kTcUnitBlocks / 2>) : launch(infer_tc_kernel<false, kTcUnitBlocks>)));
+    const TcKernel kernel = tc_kernel(a.act, a.ub);
+    NTBC_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kernel<<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
     NTBC_CHECK_LAUNCH("ntbc inference (tcgen05)");
     return NTBC_OK;
 }
@@ -988,7 +1218,7 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
 
 struct ntbc_batch {
     int n = 0, groups = 0, grid = 0;
-    bool split = true;
+    int act = ntbc::kActSplit;
     size_t smem = 0;
     ntbc::TcBatchHeader hdr{};
     ntbc::TcMat* d_mats = nullptr;
@@ -999,13 +1229,7 @@ struct ntbc_batch {
 namespace ntbc {
 
 static cudaError_t batch_set_smem(const ntbc_batch* b) {
-    const int bytes = (int)b->smem;
-    const bool half = b->hdr.ub != kTcUnitBlocks;
-    if (b->split)
-        return half ? cudaFuncSetAttribute(infer_tc_batch_kernel<true, kTcUnitBlocks / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-                    : cudaFuncSetAttribute(infer_tc_batch_kernel<true, kTcUnitBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return half ? cudaFuncSetAttribute(infer_tc_batch_kernel<false, kTcUnitBlocks / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-                : cudaFuncSetAttribute(infer_tc_batch_kernel<false, kTcUnitBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(tc_batch_kernel(b->act, b->hdr.ub), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
 }
 
 static ntbc_status batch_fail_free(ntbc_batch* b, ntbc_status st) {
@@ -1091,7 +1315,7 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         if (!m || !blocks_out[i]) return fail(NTBC_EINVAL, "material %d: null model or output list", i);
         if (m->weight_prec == NTBC_PREC_FP32 || m->grid_bits < 0 || !m->umma_img)
             return fail(NTBC_EINVAL, "material %d: export the model with a tensor-core precision first", i);
-        int kind = m->weight_prec == NTBC_PREC_FP16_FAST ? NTBC_PREC_FP16_FAST : NTBC_PREC_FP16;
+        const int kind = tc_act(m);
         if (prec >= 0 && kind != prec) return fail(NTBC_EINVAL, "all materials of a batch need the same tensor-core kernel");
         prec = kind;
         TcMat& t = mats[i];
@@ -1123,12 +1347,12 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
     ntbc_batch* b = new ntbc_batch();
     b->n = n;
     b->order = order;
-    b->split = prec == NTBC_PREC_FP16;
+    b->act = prec;
     TcArgs probe;
     memset(&probe, 0, sizeof(probe));
     probe.img_bytes = max_img;
     int ub = kTcUnitBlocks;
-    b->groups = tc_groups(probe, max_tex, b->split, &b->smem, &ub, sizeof(TcMat) + 256);
+    b->groups = tc_groups(probe, max_tex, b->act, &b->smem, &ub, sizeof(TcMat) + 256);
     if (b->groups == 0) return batch_fail_free(b, fail(NTBC_EUNSUPPORTED, "batch: shared memory too small"));
     for (int i = 0; i < n; ++i) {
         mats[i].args.ub = ub;
@@ -1179,15 +1403,8 @@ ntbc_status ntbc_batch_infer(ntbc_batch* b, void* stream) {
     // kernel's bounded claim loop turns into NTBC_ETIMEOUT
     NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.done, 0, (size_t)(b->n + 2) * sizeof(int), s));
     if (fault_injected("ticket")) NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.ticket, 0x80, sizeof(int), s));
-    const bool half = b->hdr.ub != kTcUnitBlocks;
-    const dim3 grid(b->grid), block(kTcRows * b->groups);
-    if (b->split) {
-        if (half) infer_tc_batch_kernel<true, kTcUnitBlocks / 2><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
-        else infer_tc_batch_kernel<true, kTcUnitBlocks><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
-    } else {
-        if (half) infer_tc_batch_kernel<false, kTcUnitBlocks / 2><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
-        else infer_tc_batch_kernel<false, kTcUnitBlocks><<<grid, block, b->smem, s>>>(b->hdr, b->d_mats);
-    }
+    const TcBatchKernel kernel = tc_batch_kernel(b->act, b->hdr.ub);
+    kernel<<<dim3(b->grid), dim3(kTcRows * b->groups), b->smem, s>>>(b->hdr, b->d_mats);
     NTBC_CHECK_LAUNCH("batched ntbc inference (tcgen05)");
     return NTBC_OK;
 }

@@ -78,9 +78,13 @@ struct ntbc_model {
     float* infer_params = nullptr;      // FP32 copy used by inference: FP32 grids (grid_bits 0)
                                         // and the MLP weights rounded to the export precision
     __half* w16 = nullptr;              // MLP part in FP16 (weight_prec FP16, and FP8 expanded)
-    uint8_t* w8 = nullptr;              // MLP part as E4M3 codes (weight_prec FP8), then
-    int* w8_exp = nullptr;              // the per-layer scale exponents (inside the w8 allocation)
-    __half* umma_img = nullptr;         // FP16 weights in the tensor-core shared-memory layout
+    uint8_t* w8 = nullptr;              // MLP part as E4M3 codes (weight_prec FP8 / FP8_MMA), then
+    int* w8_exp = nullptr;              // the per-layer weight scale exponents, the activation
+    int* w8_aexp = nullptr;             // scale exponents (FP8_MMA) and the calibration maxima
+    unsigned* w8_amax = nullptr;        // (all inside the w8 allocation)
+    __half* umma_img = nullptr;         // weights in the tensor-core shared-memory layout (FP16, or
+                                        // E4M3 codes followed by FP32 biases and layer constants)
+    size_t umma_bytes = 0;              // its allocation size
     int* tc_err = nullptr;              // set by the tensor-core kernel when a bounded wait gives up
     struct ntbc_train_state* train = nullptr;   // training scratch (allocated on first use)
     long long next_step = 0;            // the encode step a resumed ntbc_train_range starts at

@@ -107,7 +107,11 @@ void ntbc_train_release(ntbc_model* m);
 // grid sources of an exported model (codes + scale / zero, or FP32 grids)
 ntbc_status grid_sources(const ntbc_model* m, GridSrc& csrc, GridSrc& esrc);
 
-// tensor-core inference (FP16 weights): weight image preparation and launch
+// per-layer activation exponents of NTBC_PREC_FP8_MMA (into m->w8_aexp) from the calibration
+// sample of the exported model (grids and FP8 weights already in place)
+ntbc_status fp8_calibrate(ntbc_model* m, cudaStream_t s);
+
+// tensor-core inference (FP16 or FP8 weights): weight image preparation and launch
 ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s);
 // work units the tensor-core inference processes at once (groups x SMs; 0 on error) and the
 // blocks per work unit (unit_blocks, optional)

@@ -293,6 +293,13 @@ __global__ void __launch_bounds__(256) fp8_layers_kernel(const float* __restrict
     }
 }
 
+static bool is_fp8(int prec) { return prec == NTBC_PREC_FP8 || prec == NTBC_PREC_FP8_MMA; }
+
+// exponent bytes of an FP8 blob: the weight exponents, and for FP8_MMA the activation ones
+static size_t fp8_exp_bytes(int prec) {
+    return (prec == NTBC_PREC_FP8_MMA ? 4 : 2) * NTBC_MAX_MLP_LAYERS * sizeof(int);
+}
+
 static int grid_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 8); }
 
 }  // namespace ntbc
@@ -432,8 +439,12 @@ static ntbc_status ensure_export_buffers(ntbc_model* m) {
     if (st == NTBC_OK && !m->w16) st = device_alloc((void**)&m->w16, (L.total - L.grid_floats) * sizeof(__half), "half weights");
     if (st == NTBC_OK && !m->w8) {
         size_t codes = ((L.total - L.grid_floats) + 15) & ~(size_t)15;
-        st = device_alloc((void**)&m->w8, codes + 2 * NTBC_MAX_MLP_LAYERS * sizeof(int), "FP8 weights");
-        if (st == NTBC_OK) m->w8_exp = reinterpret_cast<int*>(m->w8 + codes);
+        st = device_alloc((void**)&m->w8, codes + 6 * NTBC_MAX_MLP_LAYERS * sizeof(int), "FP8 weights");
+        if (st == NTBC_OK) {
+            m->w8_exp = reinterpret_cast<int*>(m->w8 + codes);
+            m->w8_aexp = m->w8_exp + 2 * NTBC_MAX_MLP_LAYERS;
+            m->w8_amax = reinterpret_cast<unsigned*>(m->w8_aexp + 2 * NTBC_MAX_MLP_LAYERS);
+        }
     }
     return st;
 }
@@ -443,9 +454,9 @@ ntbc_status ntbc_model_export(ntbc_model* m, int grid_bits, int weight_prec, voi
     clear_error();
     if (!m) return fail(NTBC_EINVAL, "null model");
     if (grid_bits != 0 && grid_bits != 8 && grid_bits != 4) return fail(NTBC_EINVAL, "grid_bits must be 0, 4 or 8");
-    if (weight_prec != NTBC_PREC_FP32 && weight_prec != NTBC_PREC_FP16 && weight_prec != NTBC_PREC_FP16_FAST &&
-        weight_prec != NTBC_PREC_FP8)
-        return fail(NTBC_EINVAL, "weight precision must be NTBC_PREC_FP32, NTBC_PREC_FP16, NTBC_PREC_FP16_FAST or NTBC_PREC_FP8");
+    if (weight_prec < NTBC_PREC_FP32 || weight_prec > NTBC_PREC_FP8_MMA)
+        return fail(NTBC_EINVAL, "weight precision must be NTBC_PREC_FP32, NTBC_PREC_FP16, NTBC_PREC_FP16_FAST, "
+                                 "NTBC_PREC_FP8 or NTBC_PREC_FP8_MMA");
     ntbc_status st = ensure_export_buffers(m);
     if (st != NTBC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -465,11 +476,16 @@ ntbc_status ntbc_model_export(ntbc_model* m, int grid_bits, int weight_prec, voi
     // MLP weights
     long long nw = (long long)(L.total - L.grid_floats);
     m->weight_prec = weight_prec;
-    if (weight_prec == NTBC_PREC_FP8) {
+    if (is_fp8(weight_prec)) {
         Fp8Layers f = fp8_layers(m->desc, L);
         fp8_layers_kernel<<<f.n, 256, 0, s>>>(m->params, f, (long long)L.grid_floats, 1, m->w8, m->w8_exp,
                                               m->infer_params, m->w16);
         NTBC_CHECK_LAUNCH("quantise weights to FP8");
+        if (weight_prec == NTBC_PREC_FP8_MMA) {
+            m->grid_bits = grid_bits;          // the calibration reads the exported grids
+            st = fp8_calibrate(m, s);
+            if (st != NTBC_OK) return st;
+        }
         st = tc_prepare(m, s);
         if (st != NTBC_OK) return st;
     } else if (weight_prec != NTBC_PREC_FP32) {
@@ -513,8 +529,8 @@ static size_t blob_parts(const ntbc_model* m, size_t* grid_b, size_t* sz_b, size
     *grid_b = m->grid_bits == 4 ? (L.grid_floats + 1) / 2
                                 : (m->grid_bits > 0 ? L.grid_floats : L.grid_floats * sizeof(float));
     size_t nw = L.total - L.grid_floats;
-    if (m->weight_prec == NTBC_PREC_FP8)
-        *w_b = 2 * NTBC_MAX_MLP_LAYERS * sizeof(int) + nw;        // exponents, then codes
+    if (is_fp8(m->weight_prec))
+        *w_b = fp8_exp_bytes(m->weight_prec) + nw;                 // exponents, then codes
     else
         *w_b = nw * (m->weight_prec != NTBC_PREC_FP32 ? sizeof(__half) : sizeof(float));
     return sizeof(BlobHeader) + *sz_b + *grid_b + *w_b;
@@ -560,8 +576,9 @@ ntbc_status ntbc_model_save(const ntbc_model* m, uint8_t* blob, size_t size, voi
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb, m->infer_params, gb, cudaMemcpyDeviceToHost, s));
     }
     const ntbc_layout& L = m->layout;
-    if (m->weight_prec == NTBC_PREC_FP8) {
-        const size_t eb = 2 * NTBC_MAX_MLP_LAYERS * sizeof(int);
+    if (is_fp8(m->weight_prec)) {
+        // weight exponents, then (FP8_MMA) the activation exponents that follow them in w8
+        const size_t eb = fp8_exp_bytes(m->weight_prec);
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb, m->w8_exp, eb, cudaMemcpyDeviceToHost, s));
         NTBC_CHECK_CUDA(cudaMemcpyAsync(p + zb + gb + eb, m->w8, wb - eb, cudaMemcpyDeviceToHost, s));
     } else if (m->weight_prec != NTBC_PREC_FP32)
@@ -582,7 +599,7 @@ ntbc_status ntbc_model_load(ntbc_model* m, const uint8_t* blob, size_t size, voi
     if (memcmp(h.magic, "NTBC", 4) != 0 || h.version != ntbc_abi_version()) return fail(NTBC_EINVAL, "not an NTBC blob of this version");
     if (memcmp(&h.desc, &m->desc, sizeof(ntbc_model_desc)) != 0) return fail(NTBC_EINVAL, "blob describes a different model");
     if (h.grid_bits != 0 && h.grid_bits != 4 && h.grid_bits != 8) return fail(NTBC_EINVAL, "blob has grid_bits %d", h.grid_bits);
-    if (h.weight_prec < NTBC_PREC_FP32 || h.weight_prec > NTBC_PREC_FP8)
+    if (h.weight_prec < NTBC_PREC_FP32 || h.weight_prec > NTBC_PREC_FP8_MMA)
         return fail(NTBC_EINVAL, "blob has weight precision %d", h.weight_prec);
     ntbc_status st = ensure_export_buffers(m);
     if (st != NTBC_OK) return st;
@@ -607,8 +624,8 @@ ntbc_status ntbc_model_load(ntbc_model* m, const uint8_t* blob, size_t size, voi
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->infer_params, p + zb, gb, cudaMemcpyHostToDevice, s));
     }
     long long nw = (long long)(L.total - L.grid_floats);
-    if (m->weight_prec == NTBC_PREC_FP8) {
-        const size_t eb = 2 * NTBC_MAX_MLP_LAYERS * sizeof(int);
+    if (is_fp8(m->weight_prec)) {
+        const size_t eb = fp8_exp_bytes(m->weight_prec);
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->w8_exp, p + zb + gb, eb, cudaMemcpyHostToDevice, s));
         NTBC_CHECK_CUDA(cudaMemcpyAsync(m->w8, p + zb + gb + eb, wb - eb, cudaMemcpyHostToDevice, s));
         Fp8Layers f = fp8_layers(m->desc, L);

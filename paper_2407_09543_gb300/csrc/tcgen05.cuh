@@ -35,10 +35,21 @@ __host__ __device__ constexpr uint32_t umma_idesc_kind(int n, int bf16, int a_mn
            ((uint32_t)b_mn << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 __host__ __device__ constexpr uint32_t umma_idesc(int n) { return umma_idesc_kind(n, 0, 0, 0); }
+// kind::f8f6f4 with A and B both E4M3 (format code 0 in the same fields), D = F32, M = 128,
+// both operands K-major: the same bits as the FP16 descriptor
+__host__ __device__ constexpr uint32_t umma_idesc_e4m3(int n) { return umma_idesc_kind(n, 0, 0, 0); }
 
 __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// one MMA of kind::f8f6f4: K = 32 one-byte elements per row (the same 32 bytes per row as a
+// kind::f16 MMA's K = 16)
+__device__ __forceinline__ void umma_f8(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
                  "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
@@ -85,6 +96,12 @@ __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %
 // byte offset of element (r, k) in a tile of K columns (16-bit elements)
 __host__ __device__ __forceinline__ int core_byte(int r, int k, int K) {
     return (((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)) * 2;
+}
+
+// byte offset of element (r, k) in a tile of K columns (8-bit elements: a core matrix row
+// holds 16 of them)
+__host__ __device__ __forceinline__ int core_byte8(int r, int k, int K) {
+    return ((r >> 3) * (K >> 4) + (k >> 4)) * 128 + (r & 7) * 16 + (k & 15);
 }
 
 }  // namespace ntbc

@@ -32,6 +32,15 @@ def test_every_declared_symbol_is_exported():
         assert hasattr(nt.lib, n), n
 
 
+def test_enum_values_match_the_header():
+    with open(os.path.join(ROOT, "include", "ntbc.h")) as f:
+        text = f.read()
+    values = {k: int(v) for k, v in re.findall(r"\b(NTBC_(?:PREC|ACT|BC|TRAIN)_?\w*)\s*=\s*(\d+)", text)}
+    for name in ("PREC_FP32", "PREC_FP16", "PREC_FP16_FAST", "PREC_FP8", "PREC_FP8_MMA", "ACT_SELU", "ACT_RELU",
+                 "TRAIN_FP32", "TRAIN_BF16"):
+        assert values["NTBC_" + name] == getattr(nt, name), name
+
+
 def test_level_resolutions_agree_with_oracle():
     for L, lo, hi in ((8, 16, 2048), (12, 16, 2048), (4, 16, 128), (8, 16, 512), (5, 7, 333), (1, 16, 16)):
         assert nt.ntbc_level_resolutions(L, lo, hi) == ont.level_resolutions(L, lo, hi)

@@ -212,10 +212,13 @@ def test_blob_u4_packed_two_codes_per_byte():
         np.testing.assert_array_equal(a, b)
 
 
-def _blob_fp8_part(model, desc, n_layers):
+def _blob_fp8_part(model, desc, n_layers, mma=False, grid_bits=8):
     """(per-layer exponents, codes in parameter-layout order) from a saved FP8 blob: header
-    (magic, version, desc, grid_bits, weight_prec), (s, z) per level, grid codes, then the
-    MLP part as 2 * NTBC_MAX_MLP_LAYERS int32 exponents followed by one code per parameter."""
+    (magic, version, desc, grid_bits, weight_prec), (s, z) per level, the grid (one code per
+    byte, two per byte for 4-bit grids, FP32 for grid_bits 0), then the
+    MLP part as 2 * NTBC_MAX_MLP_LAYERS int32 weight exponents (for NTBC_PREC_FP8_MMA as many
+    activation exponents after them) followed by one code per parameter. With mma the
+    exponents are returned as (weight exponents, activation exponents)."""
     import ctypes
     blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
     model.save(blob)
@@ -223,10 +226,13 @@ def _blob_fp8_part(model, desc, n_layers):
     lay = model.layout
     levels = desc.color_levels + desc.endpoint_levels
     head = 8 + ctypes.sizeof(nt.ModelDesc) + 8
-    wpart = b[head + 8 * levels + lay.grid_floats:]
+    grid_bytes = {8: lay.grid_floats, 4: (lay.grid_floats + 1) // 2, 0: 4 * lay.grid_floats}[grid_bits]
+    wpart = b[head + 8 * levels + grid_bytes:]
     nw = lay.total - lay.grid_floats
-    exps = wpart[:4 * 2 * 4].view(np.int32)[:n_layers]
-    return exps, wpart[32:32 + nw]
+    n_exp = 2 * nt.MAX_MLP_LAYERS * (2 if mma else 1)
+    ints = wpart[:4 * n_exp].view(np.int32)
+    exps = (ints[:n_layers], ints[2 * nt.MAX_MLP_LAYERS:2 * nt.MAX_MLP_LAYERS + n_layers]) if mma else ints[:n_layers]
+    return exps, wpart[4 * n_exp:4 * n_exp + nw]
 
 
 def test_fp8_weights_codes_and_parity():
@@ -259,6 +265,112 @@ def test_fp8_weights_codes_and_parity():
     other.load(blob)
     for a, b in zip(before, gpu_blocks(other, desc)):
         np.testing.assert_array_equal(a, b)
+
+
+def _fp8_mma_case(mat, desc, odesc, params, bits=8):
+    """The FP8-arithmetic model on the GPU and the oracle's side of it: FP8 weights, its own
+    grid export and its own calibration of the activation exponents."""
+    model = gpu_model(desc, params, grid_bits=bits, weight_prec=nt.PREC_FP8_MMA)
+    p8, wexps, codes = ont.fp8_params(params)
+    if bits:
+        oc, os_, oz = ont.export_grid(params["color_grid"] + params["endpoint_grid"], bits)
+        deq = ont.dequantize_grid(oc, os_, oz)
+        nc = desc.color_levels
+        grids = dict(color_grid=deq[:nc], endpoint_grid=deq[nc:])
+    else:                                   # FP32 grids (the parameters as the library stores them)
+        p32 = descs.as_float32(params)
+        grids = dict(color_grid=p32["color_grid"], endpoint_grid=p32["endpoint_grid"])
+    aexps = ont.fp8_activation_exponents(odesc, p8, **grids)
+    return model, p8, wexps, codes, aexps, grids
+
+
+# FP8 arithmetic: the GPU and the oracle round every layer input to E4M3 from values that
+# differ only by FP32 arithmetic (~1e-6 relative), so they take the same rounding decisions
+# except where a value sits within that distance of an E4M3 rounding boundary (a "flip": one
+# input moves by one E4M3 spacing). Outputs without a flip agree like the split FP16 path
+# (1e-3 relative); flips are rare (expected well under 0.5 % of the outputs: ~10^-5 per
+# rounding, a few hundred roundings upstream of an output), and even a flipped output stays
+# within twice the propagated E4M3 error bound (both evaluations lie within that bound of the
+# exact-activation network). The decisions after quantisation then differ no more than the
+# split path allows.
+FP8_FLIP_FRACTION = 0.005
+
+
+def _fp8_error_bound(odesc, p8, aexps, ids, grids):
+    """Elementwise bound on |FP8 arithmetic - exact activations| for the outputs of the given
+    blocks: every E4M3 rounding of a layer input y at scale 2^a errs by at most
+    2^-4 |y| + 2^(a - 10), layer errors propagate through |W|, SELU (Lipschitz lambda alpha)
+    and the sigmoid (Lipschitz 1/4)."""
+    ids = np.asarray(ids, np.int64)
+    s, t = ont.block_coords(odesc.blocks_x, odesc.blocks_y, ids % odesc.blocks_x, ids // odesc.blocks_x)
+    xs, ys = ont.block_texel_xy(odesc, ids)
+    u, v = ont.texel_coords(odesc.width, odesc.height, xs.ravel(), ys.ravel())
+    nc = len(p8["color_mlp"])
+    out = []
+    for key, grid, (a, b), ex in (("endpoint_mlp", grids["endpoint_grid"], (s, t), aexps[nc:]),
+                                  ("color_mlp", grids["color_grid"], (u, v), aexps[:nc])):
+        x, _ = ont.grid_lookup([np.asarray(g, np.float64) for g in grid], a, b)
+        _, cache = ont.mlp_forward(p8[key], x, odesc.activation)
+        err = np.zeros_like(x)
+        for l, ((W, _), (h, _)) in enumerate(zip(p8[key], cache)):
+            zerr = (err + 2.0 ** -4 * (np.abs(h) + err) + 2.0 ** (ex[l] - 10)) @ np.abs(W).T
+            err = zerr * (ont.SELU_LAMBDA * ont.SELU_ALPHA if l + 1 < len(p8[key]) else 0.25)
+        out.append(err)
+    return out[0], out[1].reshape(len(ids), 16, -1)
+
+
+def check_fp8_mma_outputs(got, want, bound):
+    d = np.abs(got - want)
+    assert np.mean(d > RTOL * np.abs(want) + 1e-6) <= FP8_FLIP_FRACTION, float(np.mean(d > RTOL * np.abs(want) + 1e-6))
+    assert np.all(d <= 2 * bound + 1e-5), float(np.max(d - 2 * bound))
+
+
+def test_fp8_mma_exponents_codes_and_parity():
+    mat, desc, odesc, params = make_case(side=128, levels=4, lo=8, hi=64, hidden=3)
+    model, p8, wexps, codes, aexps, grids = _fp8_mma_case(mat, desc, odesc, params)
+    (gw, ga), gcodes = _blob_fp8_part(model, desc, len(wexps), mma=True)
+    np.testing.assert_array_equal(gw, np.array(wexps))
+    np.testing.assert_array_equal(ga, np.array(aexps))
+    code_params = dict(color_grid=params["color_grid"], endpoint_grid=params["endpoint_grid"],
+                       color_mlp=codes[:len(params["color_mlp"])], endpoint_mlp=codes[len(params["color_mlp"]):])
+    want = nt.configs.flatten(desc, code_params)[model.layout.grid_floats:].astype(np.uint8)
+    np.testing.assert_array_equal(gcodes, want)
+    ids = np.arange(odesc.n_blocks)
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p8, ids, fp8_act=aexps, **grids)
+    be, bc_ = _fp8_error_bound(odesc, p8, aexps, ids, grids)
+    check_fp8_mma_outputs(e, er, be)
+    check_fp8_mma_outputs(c, cr, bc_)
+    # the FP8 arithmetic is not the exact-activation network: outputs move by up to a few
+    # per cent (within the bound), which is what the mode costs in accuracy
+    ex, cx = ont.forward_blocks(odesc, p8, ids, **grids)
+    assert np.all(np.abs(c - cx) <= bc_ + 1e-5) and np.abs(c - cx).max() > 1e-3
+    got = gpu_blocks(model, desc)
+    check_blocks(mat, desc, odesc, got, ont.infer_blocks(odesc, p8, fp8_act=aexps, **grids))
+    # the stored blob (FP8 codes and both exponent lists) reproduces the blocks
+    blob = torch.empty(model.blob_size(), dtype=torch.uint8).pin_memory()
+    model.save(blob)
+    other = nt.Model(desc)
+    other.load(blob)
+    for a, b in zip(got, gpu_blocks(other, desc)):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("act,hidden,bits", [("relu", 2, 8), ("selu", 1, 4), ("selu", 3, 0)])
+def test_fp8_mma_activations_depths_and_grids(act, hidden, bits):
+    """ReLU and SELU, one to three hidden layers, 8-bit, 4-bit and FP32 grids; a non-square
+    material whose block count is not a multiple of the work unit."""
+    mat, desc, odesc, params = make_case(side=264, height=132, levels=4, lo=4, hi=32, hidden=hidden, act=act)
+    model, p8, _, _, aexps, grids = _fp8_mma_case(mat, desc, odesc, params, bits=bits)
+    (_, ga), _ = _blob_fp8_part(model, desc, len(aexps), mma=True, grid_bits=bits)
+    np.testing.assert_array_equal(ga, np.array(aexps))
+    ids = np.arange(odesc.n_blocks)
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p8, ids, fp8_act=aexps, **grids)
+    be, bc_ = _fp8_error_bound(odesc, p8, aexps, ids, grids)
+    check_fp8_mma_outputs(e, er, be)
+    check_fp8_mma_outputs(c, cr, bc_)
+    check_blocks(mat, desc, odesc, gpu_blocks(model, desc), ont.infer_blocks(odesc, p8, fp8_act=aexps, **grids))
 
 
 def test_full_size_4k_sampled():
