@@ -325,28 +325,40 @@ ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int 
 
 /*
  * Batched load-time inference (Sec. 4.4: inference runs once per material when it is
- * loaded): many materials, each with its own model, decoded to BC blocks in one
- * persistent launch. Every model must be exported for the same tensor-core kernel:
- * all NTBC_PREC_FP16 / NTBC_PREC_FP8 (split activations), all NTBC_PREC_FP16_FAST, or all
- * NTBC_PREC_FP8_MMA.
- *   ntbc_batch_create  models: host array of n models; blocks_out: host array of n host
- *                      arrays, each holding that material's per-texture DEVICE outputs.
- *                      Uploads the launch description (allocates; not capturable).
- *   ntbc_batch_infer   one reset of the launch's counters and one kernel launch on
- *                      `stream`; may be captured in a CUDA graph and replayed. The persistent
- *                      CTAs take work from a device queue of CTA-units (one 128-block work unit
- *                      per warpgroup), the materials queued largest first. A claim outside the
- *                      queue does no work; after 2^16 of them a CTA gives up and the launch
- *                      reports NTBC_ETIMEOUT through ntbc_batch_times (host-side fault
- *                      injection NTBC_FAULT=ticket starts the counter negative to test this).
+ * loaded): many materials, each with its own model, decoded to BC blocks by one call.
+ * Every model must be exported with a tensor-core precision (not NTBC_PREC_FP32), and the
+ * output ranges of all materials and textures must be disjoint (they are written
+ * concurrently; NTBC_EINVAL otherwise). Two modes:
+ *   NTBC_BATCH_CHAINED (ntbc_batch_create's mode) one launch of the single-material kernel
+ *                      per material, largest material first, each after the first a
+ *                      programmatic dependent launch: it may start as soon as every CTA of
+ *                      the previous launch is resident, so its CTAs take the SMs the previous
+ *                      material leaves at its tail. Materials may mix precisions.
+ *   NTBC_BATCH_QUEUE   one persistent launch whose CTAs take work from a device queue of
+ *                      CTA-units (one work unit per warpgroup), the materials queued largest
+ *                      first; all models must be exported for the same tensor-core kernel
+ *                      (NTBC_PREC_FP16 / NTBC_PREC_FP8, NTBC_PREC_FP16_FAST, or
+ *                      NTBC_PREC_FP8_MMA). A claim outside the queue does no work; after 2^16
+ *                      of them a CTA gives up and the launch reports NTBC_ETIMEOUT through
+ *                      ntbc_batch_times (host-side fault injection NTBC_FAULT=ticket starts
+ *                      the counter negative to test this).
+ *   ntbc_batch_create(_mode)  models: host array of n models; blocks_out: host array of n
+ *                      host arrays, each holding that material's per-texture DEVICE outputs
+ *                      (8-byte aligned, n_blocks * 8 bytes each). Plans the launches
+ *                      (allocates; not capturable). An unknown mode is NTBC_EINVAL.
+ *   ntbc_batch_infer   one reset of the batch's counters, then the launches on `stream`; may
+ *                      be captured in a CUDA graph and replayed.
  *   ntbc_batch_times   synchronises `stream`; ms (host double[n], in the order of `models`)
- *                      = each material's completion time after the start of the last launch
- *                      (device global timer); NTBC_ETIMEOUT if a bounded wait or the bounded
- *                      claim loop gave up.
+ *                      = each material's completion time after the start of the batch's first
+ *                      launch (device global timer); NTBC_ETIMEOUT if a bounded wait or the
+ *                      bounded claim loop gave up.
  */
+enum { NTBC_BATCH_CHAINED = 0, NTBC_BATCH_QUEUE = 1 };
 typedef struct ntbc_batch ntbc_batch;
 ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out,
                               ntbc_batch** out);
+ntbc_status ntbc_batch_create_mode(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out,
+                                   int mode, ntbc_batch** out);
 ntbc_status ntbc_batch_infer(ntbc_batch* batch, void* stream);
 ntbc_status ntbc_batch_times(const ntbc_batch* batch, double* ms, void* stream);
 void ntbc_batch_free(ntbc_batch* batch);

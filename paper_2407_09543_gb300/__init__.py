@@ -18,7 +18,7 @@ import os
 
 from ._abi import (  # noqa: F401
     BC1, BC3, BC4, BC5, ACT_RELU, ACT_SELU, PREC_FP16, PREC_FP16_FAST, PREC_FP32, PREC_FP8, PREC_FP8_MMA, TRAIN_FP32, TRAIN_BF16, MAX_LEVELS, MAX_TEXTURES,
-    MAX_MLP_LAYERS,
+    MAX_MLP_LAYERS, BATCH_CHAINED, BATCH_QUEUE,
     NTBCError, ModelDesc, Layout, Material, TrainConfig, lib, library_path,
     bc_reference_encode, bc_decode, ntbc_outputs_to_bc, ntbc_level_resolutions, ntbc_model_layout,
     ntbc_sample_blocks, ntbc_train_grads_noalloc, ntbc_wait_probe, ntbc_ex2_rate_probe, NOALLOC_MAX_BLOCKS, Model, Batch, STATUS_NAMES,

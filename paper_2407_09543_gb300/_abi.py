@@ -11,6 +11,7 @@ BC1, BC4 = 1, 4
 BC3, BC5 = 3, 5
 ACT_SELU, ACT_RELU = 0, 1
 PREC_FP32, PREC_FP16, PREC_FP16_FAST, PREC_FP8, PREC_FP8_MMA = 0, 1, 2, 3, 4
+BATCH_CHAINED, BATCH_QUEUE = 0, 1
 TRAIN_FP32, TRAIN_BF16 = 0, 1
 MAX_TEXTURES, MAX_LEVELS, MAX_MLP_LAYERS = 8, 16, 4
 STATUS_NAMES = {0: "NTBC_OK", 1: "NTBC_EINVAL", 2: "NTBC_ENOMEM", 3: "NTBC_ECUDA", 4: "NTBC_ETIMEOUT",
@@ -130,6 +131,8 @@ _SIGS = {
     "ntbc_adam_step": (c_int, [_P, _P, ctypes.c_long, ctypes.c_long, ctypes.POINTER(TrainConfig), _P]),
     "ntbc_sample_blocks": (c_int, [ctypes.c_uint64, ctypes.c_long, c_int, c_int, _P, _P]),
     "ntbc_batch_create": (c_int, [ctypes.POINTER(_P), c_int, ctypes.POINTER(ctypes.POINTER(_P)), ctypes.POINTER(_P)]),
+    "ntbc_batch_create_mode": (c_int, [ctypes.POINTER(_P), c_int, ctypes.POINTER(ctypes.POINTER(_P)), c_int,
+                                       ctypes.POINTER(_P)]),
     "ntbc_batch_infer": (c_int, [_P, _P]),
     "ntbc_batch_times": (c_int, [_P, ctypes.POINTER(ctypes.c_double), _P]),
     "ntbc_batch_free": (None, [_P]),
@@ -328,16 +331,21 @@ class Model:
 
 
 class Batch:
-    """Many materials (each its own exported Model) decoded to BC blocks in one launch."""
+    """Many materials (each its own exported Model) decoded to BC blocks by one call: chained
+    single-material launches (BATCH_CHAINED, the default) or one persistent work-queue launch
+    (BATCH_QUEUE)."""
 
-    def __init__(self, models, blocks_out):
+    def __init__(self, models, blocks_out, mode=None):
         self.models = list(models)
         self.n = len(self.models)
         self._outs = [(_P * len(o))(*[_ptr(b) for b in o]) for o in blocks_out]
         outer = (ctypes.POINTER(_P) * self.n)(*[ctypes.cast(o, ctypes.POINTER(_P)) for o in self._outs])
         handles = (_P * self.n)(*[m.handle for m in self.models])
         h = _P()
-        _check(lib.ntbc_batch_create(handles, self.n, outer, ctypes.byref(h)))
+        if mode is None:
+            _check(lib.ntbc_batch_create(handles, self.n, outer, ctypes.byref(h)))
+        else:
+            _check(lib.ntbc_batch_create_mode(handles, self.n, outer, mode, ctypes.byref(h)))
         self.handle = h
 
     def infer(self, stream=None):

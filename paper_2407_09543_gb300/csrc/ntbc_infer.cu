@@ -263,7 +263,7 @@ static ntbc_status launch_simt(const ntbc_model* m, const OutPtrs& outs, const i
     WeightImage wic = weight_image(mv.color), wie = weight_image(mv.endpoint);
     int threads = kSimtThreads;
     size_t smem = simt_smem_bytes(mv, wic, wie, threads);
-    NTBC_CHECK_CUDA(cudaFuncSetAttribute(infer_simt_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NTBC_CHECK_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(infer_simt_kernel<MODE>), smem));
     int grid = (n + threads - 1) / threads;
     infer_simt_kernel<MODE><<<grid, threads, smem, s>>>(mv, m->infer_params, csrc, esrc, wic, wie, outs, ids, n, e_out, c_out);
     NTBC_CHECK_LAUNCH("ntbc inference (SIMT)");

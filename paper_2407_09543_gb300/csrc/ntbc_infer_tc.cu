@@ -221,7 +221,18 @@ struct TcArgs {
     int ftab;                 // E4M3: byte offset of the TcLayerConst table in the weight image
     int* err;
     float inv_w, inv_h, inv_bw, inv_bh;   // reciprocals of the texel and block extents
+    // optional completion record (chained batches): units completed, the %globaltimer stamp of
+    // the last one, and (first launch of a chain) the stamp of the launch's start
+    int* done;
+    unsigned long long* done_stamp;
+    unsigned long long* start_stamp;
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // block index -> (bx, by) without an integer division: q = floor(b / bw) from the FP32
 // reciprocal (off by at most one for b < 2^24), then one correction step
@@ -796,6 +807,11 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag[kTcMaxGroups];
     const TcSmem sl = tc_smem_layout(args.img_bytes, args.mv.n_textures, ACT, UB);
+    // a launch chained after this one (programmatic dependent launch, chained batches) may start
+    // as soon as every CTA of this one is resident: it reads and writes none of this launch's
+    // data, and its CTAs take the SMs this launch's CTAs leave at its tail
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (args.start_stamp && blockIdx.x == 0 && threadIdx.x == 0) *args.start_stamp = global_ns();
     for (int i = threadIdx.x; i < args.img_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = img[i];
     load_constants(smem, sl);
     const float2 fs = feature_scales<ACT>(img, args.ftab);
@@ -804,8 +820,15 @@ infer_tc_kernel(TcArgs args, const uint4* __restrict__ img, GridSrc csrc, GridSr
     uint32_t phase = 0, region = 0;
     bool ok = true;
     const int n_units = (args.n + UB - 1) / UB;
-    for (int unit = blockIdx.x * args.groups + G.g; unit < n_units && ok; unit += gridDim.x * args.groups)
+    int units_done = 0;
+    for (int unit = blockIdx.x * args.groups + G.g; unit < n_units && ok; unit += gridDim.x * args.groups) {
         ok = process_unit<ACT, UB>(args, csrc, esrc, outs, e_out, c_out, unit, smem, sl, G, phase, region, abort_flag);
+        ++units_done;
+    }
+    if (args.done && ok && G.r == 0 && units_done > 0) {
+        __threadfence();
+        if (atomicAdd(args.done, units_done) + units_done == n_units) *args.done_stamp = global_ns();
+    }
     teardown_groups(G, args.groups, ok, phase, args.err, tmem_slot);
 }
 
@@ -830,12 +853,6 @@ struct TcBatchHeader {
     int* ticket;                 // work queue: the next CTA-unit to claim
     long long claim_limit;       // claims outside the queue a CTA makes before it gives up
 };
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // A device work queue of CTA-units (one work unit per warpgroup, all from one material; the
 // materials ordered largest first): thread 0 claims the next CTA-unit from the ticket counter
@@ -1182,8 +1199,21 @@ int tc_units_in_flight(const ntbc_model* m, int* unit_blocks) {
     return groups * sms;
 }
 
-ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
-                      float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
+// One planned launch of the single-material kernel (grid 0: nothing to do).
+struct TcLaunch {
+    TcKernel kernel;
+    TcArgs a;
+    const uint4* img;
+    GridSrc csrc, esrc;
+    TcOut outs;
+    float* e_out;
+    float* c_out;
+    int grid, block;
+    size_t smem;
+};
+
+static ntbc_status tc_plan(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
+                           float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, TcLaunch* L) {
     TcArgs a = tc_args(m);
     size_t smem = 0;
     a.groups = tc_groups(a, m->desc.n_textures, a.act, &smem, &a.ub);
@@ -1193,23 +1223,57 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
     a.ids = ids;
     a.mode = blocks_out ? 0 : 1;
     a.err = m->tc_err;
-    TcOut outs;
-    memset(&outs, 0, sizeof(outs));
+    memset(&L->outs, 0, sizeof(L->outs));
     if (blocks_out)
         for (int t = 0; t < m->desc.n_textures; ++t) {
-            outs.p[t] = blocks_out[t];
-            outs.stride[t] = strides ? strides[t] : 8;
+            L->outs.p[t] = blocks_out[t];
+            L->outs.stride[t] = strides ? strides[t] : 8;
         }
     int dev = 0, sms = 0;
     NTBC_CHECK_CUDA(cudaGetDevice(&dev));
     NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int units = (n + a.ub - 1) / a.ub;
-    int grid = std::min(sms, (units + a.groups - 1) / a.groups);
-    if (grid < 1) return NTBC_OK;
-    const uint4* img = reinterpret_cast<const uint4*>(m->umma_img);
-    const TcKernel kernel = tc_kernel(a.act, a.ub);
-    NTBC_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kernel<<<grid, kTcRows * a.groups, smem, s>>>(a, img, csrc, esrc, outs, e_out, c_out);
+    const int units = (n + a.ub - 1) / a.ub;
+    L->grid = std::max(0, std::min(sms, (units + a.groups - 1) / a.groups));
+    L->block = kTcRows * a.groups;
+    L->smem = smem;
+    L->kernel = tc_kernel(a.act, a.ub);
+    L->img = reinterpret_cast<const uint4*>(m->umma_img);
+    L->csrc = csrc;
+    L->esrc = esrc;
+    L->e_out = e_out;
+    L->c_out = c_out;
+    L->a = a;
+    if (L->grid > 0) NTBC_CHECK_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(L->kernel), smem));
+    return NTBC_OK;
+}
+
+// chained: a programmatic dependent launch, which may start while the previous kernel on the
+// stream (a launch of this kernel that reads and writes none of this one's data) is finishing
+static cudaError_t tc_enqueue(const TcLaunch& L, cudaStream_t s, bool chained) {
+    if (L.grid < 1) return cudaSuccess;
+    if (!chained) {
+        L.kernel<<<L.grid, L.block, L.smem, s>>>(L.a, L.img, L.csrc, L.esrc, L.outs, L.e_out, L.c_out);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L.grid);
+    cfg.blockDim = dim3(L.block);
+    cfg.dynamicSmemBytes = L.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, L.kernel, L.a, L.img, L.csrc, L.esrc, L.outs, L.e_out, L.c_out);
+}
+
+ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
+                      float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
+    TcLaunch L;
+    ntbc_status st = tc_plan(m, blocks_out, strides, ids, n, e_out, c_out, csrc, esrc, &L);
+    if (st != NTBC_OK) return st;
+    NTBC_CHECK_CUDA(tc_enqueue(L, s, false));
     NTBC_CHECK_LAUNCH("ntbc inference (tcgen05)");
     return NTBC_OK;
 }
@@ -1218,10 +1282,12 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
 
 struct ntbc_batch {
     int n = 0, groups = 0, grid = 0;
+    int mode = NTBC_BATCH_CHAINED;
     int act = ntbc::kActSplit;
     size_t smem = 0;
     ntbc::TcBatchHeader hdr{};
-    ntbc::TcMat* d_mats = nullptr;
+    ntbc::TcMat* d_mats = nullptr;      // work-queue mode: the materials' launch descriptions
+    std::vector<ntbc::TcLaunch> chain;  // chained mode: one planned launch per material
     unsigned char* d_mem = nullptr;     // stamps, done counters, error flag, ticket counter
     std::vector<int> order;             // queue position -> the caller's material index
 };
@@ -1229,7 +1295,7 @@ struct ntbc_batch {
 namespace ntbc {
 
 static cudaError_t batch_set_smem(const ntbc_batch* b) {
-    return cudaFuncSetAttribute(tc_batch_kernel(b->act, b->hdr.ub), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    return ensure_dynamic_smem(reinterpret_cast<const void*>(tc_batch_kernel(b->act, b->hdr.ub)), b->smem);
 }
 
 static ntbc_status batch_fail_free(ntbc_batch* b, ntbc_status st) {
@@ -1304,9 +1370,15 @@ ntbc_status ntbc_ex2_rate_probe(double* ex2_per_s, void* stream) {
 }
 
 ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out, ntbc_batch** out) {
+    return ntbc_batch_create_mode(models, n, blocks_out, NTBC_BATCH_CHAINED, out);
+}
+
+ntbc_status ntbc_batch_create_mode(const ntbc_model* const* models, int n, uint8_t* const* const* blocks_out, int mode,
+                                   ntbc_batch** out) {
     using namespace ntbc;
     clear_error();
     if (!models || !blocks_out || !out || n <= 0) return fail(NTBC_EINVAL, "need models, outputs and n > 0");
+    if (mode != NTBC_BATCH_CHAINED && mode != NTBC_BATCH_QUEUE) return fail(NTBC_EINVAL, "unknown batch mode %d", mode);
     *out = nullptr;
     int prec = -1, max_tex = 0, max_img = 0, total = 0;
     std::vector<TcMat> mats(n);
@@ -1316,7 +1388,8 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         if (m->weight_prec == NTBC_PREC_FP32 || m->grid_bits < 0 || !m->umma_img)
             return fail(NTBC_EINVAL, "material %d: export the model with a tensor-core precision first", i);
         const int kind = tc_act(m);
-        if (prec >= 0 && kind != prec) return fail(NTBC_EINVAL, "all materials of a batch need the same tensor-core kernel");
+        if (mode == NTBC_BATCH_QUEUE && prec >= 0 && kind != prec)
+            return fail(NTBC_EINVAL, "all materials of a work-queue batch need the same tensor-core kernel");
         prec = kind;
         TcMat& t = mats[i];
         memset(&t, 0, sizeof(t));
@@ -1336,8 +1409,20 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         max_tex = std::max(max_tex, m->desc.n_textures);
         max_img = std::max(max_img, t.args.img_bytes);
     }
-    // the queue holds the materials largest first, so the last claims are the small units of
-    // the small materials and the CTAs finish close together
+    // the materials of a batch are written concurrently: their output ranges must be disjoint
+    std::vector<std::pair<uintptr_t, uintptr_t>> ranges;
+    for (int i = 0; i < n; ++i) {
+        const size_t bytes = (size_t)mats[i].args.n * 8;
+        for (int k = 0; k < models[i]->desc.n_textures; ++k) {
+            const uintptr_t p0 = reinterpret_cast<uintptr_t>(blocks_out[i][k]);
+            ranges.push_back({p0, p0 + bytes});
+        }
+    }
+    std::sort(ranges.begin(), ranges.end());
+    for (size_t j = 1; j < ranges.size(); ++j)
+        if (ranges[j].first < ranges[j - 1].second) return fail(NTBC_EINVAL, "batch: two outputs overlap");
+    // materials largest first: the last work (queue claims, or chained launches) is the small
+    // materials', so the SMs finish close together
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mats[a].args.n > mats[b].args.n; });
@@ -1346,8 +1431,40 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
     mats.swap(sorted);
     ntbc_batch* b = new ntbc_batch();
     b->n = n;
+    b->mode = mode;
     b->order = order;
     b->act = prec;
+    // completion stamps (start, then one per material), done counters, error flag, ticket
+    size_t mem = (size_t)(n + 1) * sizeof(unsigned long long) + (size_t)(n + 2) * sizeof(int);
+    ntbc_status st = device_alloc((void**)&b->d_mem, mem, "batch counters");
+    if (st != NTBC_OK) return batch_fail_free(b, st);
+    b->hdr.n_mats = n;
+    b->hdr.stamps = reinterpret_cast<unsigned long long*>(b->d_mem);
+    b->hdr.done = reinterpret_cast<int*>(b->d_mem + (size_t)(n + 1) * sizeof(unsigned long long));
+    b->hdr.err = b->hdr.done + n;
+    b->hdr.ticket = b->hdr.err + 1;
+    b->hdr.claim_limit = 1 << 16;
+    cudaError_t e = cudaMemset(b->d_mem, 0, mem);
+    if (e != cudaSuccess) return batch_fail_free(b, cuda_fail(e, "batch set-up"));
+    if (mode == NTBC_BATCH_CHAINED) {
+        // one launch of the single-material kernel per material (each with its own unit size and
+        // warpgroup count), chained by programmatic dependent launch
+        b->chain.resize(n);
+        for (int k = 0; k < n; ++k) {
+            const int i = order[k];
+            GridSrc csrc, esrc;
+            st = grid_sources(models[i], csrc, esrc);
+            if (st == NTBC_OK) st = tc_plan(models[i], blocks_out[i], nullptr, nullptr, mats[k].args.n, nullptr, nullptr, csrc, esrc, &b->chain[k]);
+            if (st != NTBC_OK) return batch_fail_free(b, st);
+            TcArgs& a = b->chain[k].a;
+            a.err = b->hdr.err;
+            a.done = b->hdr.done + k;
+            a.done_stamp = b->hdr.stamps + k + 1;
+            a.start_stamp = k == 0 ? b->hdr.stamps : nullptr;
+        }
+        *out = b;
+        return NTBC_OK;
+    }
     TcArgs probe;
     memset(&probe, 0, sizeof(probe));
     probe.img_bytes = max_img;
@@ -1363,24 +1480,15 @@ ntbc_status ntbc_batch_create(const ntbc_model* const* models, int n, uint8_t* c
         mats[i].args.groups = b->groups;
         total += (mats[i].units + b->groups - 1) / b->groups;
     }
-    size_t mem = (size_t)(n + 1) * sizeof(unsigned long long) + (size_t)(n + 2) * sizeof(int);
-    ntbc_status st = device_alloc((void**)&b->d_mats, (size_t)n * sizeof(TcMat), "batch descriptors");
-    if (st == NTBC_OK) st = device_alloc((void**)&b->d_mem, mem, "batch counters");
+    st = device_alloc((void**)&b->d_mats, (size_t)n * sizeof(TcMat), "batch descriptors");
     if (st != NTBC_OK) return batch_fail_free(b, st);
-    b->hdr.n_mats = n;
     b->hdr.total_cta_units = total;
     b->hdr.groups = b->groups;
     b->hdr.img_bytes = max_img;
     b->hdr.max_textures = max_tex;
     b->hdr.ub = ub;
-    b->hdr.stamps = reinterpret_cast<unsigned long long*>(b->d_mem);
-    b->hdr.done = reinterpret_cast<int*>(b->d_mem + (size_t)(n + 1) * sizeof(unsigned long long));
-    b->hdr.err = b->hdr.done + n;
-    b->hdr.ticket = b->hdr.err + 1;
-    b->hdr.claim_limit = 1 << 16;
     for (int i = 0; i < n; ++i) mats[i].args.err = b->hdr.err;
-    cudaError_t e = cudaMemcpy(b->d_mats, mats.data(), (size_t)n * sizeof(TcMat), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(b->d_mem, 0, mem);
+    e = cudaMemcpy(b->d_mats, mats.data(), (size_t)n * sizeof(TcMat), cudaMemcpyHostToDevice);
     int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1402,6 +1510,13 @@ ntbc_status ntbc_batch_infer(ntbc_batch* b, void* stream) {
     // NTBC_FAULT=ticket corrupts the ticket counter instead (a negative start), which the
     // kernel's bounded claim loop turns into NTBC_ETIMEOUT
     NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.done, 0, (size_t)(b->n + 2) * sizeof(int), s));
+    if (b->mode == NTBC_BATCH_CHAINED) {
+        // the first launch follows the reset in stream order; each later one may start while its
+        // predecessor's last CTAs finish
+        for (int k = 0; k < b->n; ++k) NTBC_CHECK_CUDA(tc_enqueue(b->chain[k], s, k > 0));
+        NTBC_CHECK_LAUNCH("chained ntbc inference (tcgen05)");
+        return NTBC_OK;
+    }
     if (fault_injected("ticket")) NTBC_CHECK_CUDA(cudaMemsetAsync(b->hdr.ticket, 0x80, sizeof(int), s));
     const TcBatchKernel kernel = tc_batch_kernel(b->act, b->hdr.ub);
     kernel<<<dim3(b->grid), dim3(kTcRows * b->groups), b->smem, s>>>(b->hdr, b->d_mats);

@@ -8,7 +8,10 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 
 #include "../../include/ntbc.h"
 
@@ -41,6 +44,23 @@ ntbc_status device_alloc(void** ptr, size_t bytes, const char* what);
 
 // NVTX range over one C-ABI call (host timeline of a profiler; the NVTX v3 calls are no-ops
 // unless a tool is attached)
+// cudaFuncAttributeMaxDynamicSharedMemorySize belongs to a kernel instance, process-wide: it is
+// only ever raised (to the largest size any launch or batch of that instance has asked for on
+// this device), so a later, smaller request never invalidates a batch created earlier
+inline cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> granted;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = granted[{dev, fn}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 struct NvtxRange {
     explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
     ~NvtxRange() { nvtxRangePop(); }

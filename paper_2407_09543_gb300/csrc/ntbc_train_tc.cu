@@ -986,10 +986,10 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
     if (grid < 1) return NTBC_OK;
     grid = std::min(grid, max_rows / a.groups);
     if (color) {
-        NTBC_CHECK_CUDA(cudaFuncSetAttribute(train_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NTBC_CHECK_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(train_tc_kernel<true>), smem));
         train_tc_kernel<true><<<grid, kTrRows * a.groups, smem, s>>>(a);
     } else {
-        NTBC_CHECK_CUDA(cudaFuncSetAttribute(train_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NTBC_CHECK_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(train_tc_kernel<false>), smem));
         train_tc_kernel<false><<<grid, kTrEndpointThreads, smem, s>>>(a);
     }
     NTBC_CHECK_LAUNCH(color ? "tensor-core training (colour)" : "tensor-core training (endpoint)");

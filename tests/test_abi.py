@@ -35,9 +35,9 @@ def test_every_declared_symbol_is_exported():
 def test_enum_values_match_the_header():
     with open(os.path.join(ROOT, "include", "ntbc.h")) as f:
         text = f.read()
-    values = {k: int(v) for k, v in re.findall(r"\b(NTBC_(?:PREC|ACT|BC|TRAIN)_?\w*)\s*=\s*(\d+)", text)}
+    values = {k: int(v) for k, v in re.findall(r"\b(NTBC_(?:PREC|ACT|BC|TRAIN|BATCH)_?\w*)\s*=\s*(\d+)", text)}
     for name in ("PREC_FP32", "PREC_FP16", "PREC_FP16_FAST", "PREC_FP8", "PREC_FP8_MMA", "ACT_SELU", "ACT_RELU",
-                 "TRAIN_FP32", "TRAIN_BF16"):
+                 "TRAIN_FP32", "TRAIN_BF16", "BATCH_CHAINED", "BATCH_QUEUE"):
         assert values["NTBC_" + name] == getattr(nt, name), name
 
 

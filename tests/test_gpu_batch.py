@@ -1,9 +1,11 @@
 """Batched load-time inference: materials of uneven size and texture mix, each with its
-own model, in one persistent launch (replayed from a CUDA graph). Every material's blocks are
-checked against the FP64 oracle on the same stored model (u8 QAT grids, FP16 weights: at most
-0.1 % of fields differ with split activations) and must equal those of its own single-material
-launch (same kernels, same arithmetic). The launch's work queue gives up with NTBC_ETIMEOUT
-when its ticket counter is corrupted (host-side fault injection), and the next launch works."""
+own model, decoded by one call (replayed from a CUDA graph), in both batch modes: chained
+single-material launches (programmatic dependent launch) and one persistent work-queue launch.
+Every material's blocks are checked against the FP64 oracle on the same stored model (u8 QAT
+grids, FP16 weights: at most 0.1 % of fields differ with split activations) and must equal
+those of its own single-material launch (same arithmetic). The work queue gives up with
+NTBC_ETIMEOUT when its ticket counter is corrupted (host-side fault injection), and the next
+launch works; overlapping outputs and unknown modes are refused on the host."""
 import os
 
 import numpy as np
@@ -60,10 +62,14 @@ def _field_mismatch(formats, got, ref):
     return mism, total
 
 
+MODES = [nt.BATCH_CHAINED, nt.BATCH_QUEUE]
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("prec", [1, 2])
-def test_batch_equals_single_launches_and_replays(prec):
+def test_batch_equals_single_launches_and_replays(prec, mode):
     models, outs, dlist = _models(prec)
-    batch = nt.Batch(models, outs)
+    batch = nt.Batch(models, outs, mode=mode)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         batch.infer()
@@ -92,7 +98,7 @@ def test_batch_equals_single_launches_and_replays(prec):
 
 def test_batch_work_queue_timeout_and_recovery():
     models, outs, dlist = _models(1)
-    batch = nt.Batch(models, outs)
+    batch = nt.Batch(models, outs, mode=nt.BATCH_QUEUE)
     stream = torch.cuda.Stream()
     os.environ["NTBC_FAULT"] = "ticket"
     try:
@@ -120,8 +126,80 @@ def test_batch_work_queue_timeout_and_recovery():
     batch.close()
 
 
-def test_batch_rejects_fp32_models():
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_rejects_fp32_models_overlapping_outputs_and_unknown_modes(mode):
     models, outs, dlist = _models(1)
     models[1].export(grid_bits=8, weight_prec=nt.PREC_FP32)
     with pytest.raises(nt.NTBCError):
-        nt.Batch(models, outs)
+        nt.Batch(models, outs, mode=mode)
+    models, outs, dlist = _models(1)
+    shifted = [list(o) for o in outs]
+    shifted[3][1] = outs[0][0][8:]              # overlaps material 0's first texture
+    with pytest.raises(nt.NTBCError) as e:
+        nt.Batch(models, shifted, mode=mode)
+    assert e.value.status == 1 and "overlap" in str(e.value)
+    with pytest.raises(nt.NTBCError) as e:
+        nt.Batch(models, outs, mode=7)
+    assert e.value.status == 1
+
+
+def test_chained_batch_mixes_precisions():
+    """Chained launches run each material's own kernel: split FP16, pure FP16 and FP8
+    arithmetic in one batch, each equal to its single-material launch."""
+    models, outs, dlist = _models(1)
+    models[1].export(grid_bits=8, weight_prec=nt.PREC_FP16_FAST)
+    models[2].export(grid_bits=8, weight_prec=nt.PREC_FP8_MMA)
+    with pytest.raises(nt.NTBCError):
+        nt.Batch(models, outs, mode=nt.BATCH_QUEUE)
+    batch = nt.Batch(models, outs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.infer()
+    assert all(t > 0 for t in batch.times_ms(stream))
+    for m, mo in zip(models, outs):
+        single = [torch.empty_like(o) for o in mo]
+        m.infer_to_bc(single)
+        torch.cuda.synchronize()
+        for a, b in zip(single, mo):
+            assert torch.equal(a, b)
+    batch.close()
+
+
+def test_batches_and_single_launches_with_different_shared_memory_coexist():
+    """Two five-texture materials (64-block work units, the same kernel instance) whose weight
+    images differ in size (12 vs 4 grid levels): a single launch of the smaller one between two
+    launches of the larger one's batch must not shrink the shared-memory allowance the batch
+    was created with."""
+    made = []
+    for i, levels in enumerate((12, 4)):
+        formats = [1, 1, 4, 4, 4]
+        desc, odesc = descs.case_descs(nt, formats, 256, levels, 8, 128, 3, "selu")
+        params = descs.as_float32(synth.random_params_like(descs.init_params(odesc, 20 + i), seed=30 + i))
+        m = nt.Model(desc)
+        m.set_params(torch.from_numpy(nt.configs.flatten(desc, params)).to(DEV))
+        m.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+        made.append((m, [torch.empty((256 // 4) ** 2 * 8, dtype=torch.uint8, device=DEV) for _ in formats]))
+    (big, big_out), (small, small_out) = made
+    batch = nt.Batch([big], [big_out], mode=nt.BATCH_QUEUE)
+    batch.infer()
+    torch.cuda.synchronize()
+    first = [o.clone() for o in big_out]
+    small.infer_to_bc(small_out)
+    other = nt.Batch([small], [small_out], mode=nt.BATCH_QUEUE)
+    other.infer()
+    torch.cuda.synchronize()
+    for o in big_out:
+        o.fill_(0)
+    batch.infer()
+    torch.cuda.synchronize()
+    for a, b in zip(first, big_out):
+        assert torch.equal(a, b)
+    single = [torch.empty_like(o) for o in big_out]
+    big.infer_to_bc(single)
+    torch.cuda.synchronize()
+    for a, b in zip(single, big_out):
+        assert torch.equal(a, b)
+    batch.close()
+    other.close()
+    for m, _ in made:
+        m.close()
