@@ -75,12 +75,34 @@ __device__ __forceinline__ float tmem_ld1f(uint32_t taddr) {
 
 struct TrGroup {
     unsigned char* X;
+    unsigned char* X2;        // colour: the other input tile (tiles alternate between X and X2)
     unsigned char* A[3];
     unsigned char* D;
     uint64_t* bar;
     uint32_t tmem, row;       // group's TMEM base column; this thread's lane address
     int g, r;
 };
+
+// Colour pass: each tile warpgroup g has a helper warpgroup that gathers the group's next tile
+// into the other input tile (X / X2 alternate) and scatters the grid gradients of the group's
+// current tile (read from the group's delta tile, where the backward leaves them), so the group
+// itself runs only the forward, the loss and the backward. Named barriers over the pair's 256
+// threads hand the tiles over: XFULL (an input tile is gathered: the helper arrives, the group
+// waits), FULL (the tile's gradients are ready and its input tile is free: the group arrives,
+// the helper waits) and EMPTY (the helper has read its row of gradients into registers: it
+// arrives, then scatters; the group waits before its next loss writes the delta tile). Both
+// walk the same tile sequence and every arrival is matched by a wait, on the abort path too
+// (the group passes a stop flag and consumes the input tile gathered ahead).
+__device__ __forceinline__ int pair_full_id(int g) { return 4 + g; }
+__device__ __forceinline__ int pair_empty_id(int g) { return 6 + g; }
+__device__ __forceinline__ int pair_xfull_id(int g) { return 8 + g; }
+// bar.arrive releases the arriving thread's prior shared-memory writes to the threads that
+// complete the barrier with bar.sync; it takes no fence (a fence would also wait for the
+// helper's global gradient reductions still in flight)
+__device__ __forceinline__ void pair_arrive(int id) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(2 * kTrRows) : "memory");
+}
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(2 * kTrRows) : "memory"); }
 
 __device__ __forceinline__ bool tr_barrier(int g, volatile int* abort_flag) {
     proxy_fence();
@@ -453,16 +475,18 @@ __device__ __forceinline__ void gather_row_train(const NetView& nv, const GridSr
 constexpr int kTrEndpointThreads = 512;   // endpoint CTA: warpgroup 0 runs the tile, all 16 warps the loss
 
 template <bool COLOR>
-__global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointThreads, 1)
+__global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpointThreads, 1)
     train_tc_kernel(const __grid_constant__ TrArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag[kTrMaxGroups];
+    __shared__ int pair_stop[kTrMaxGroups];
     const TrNet& net = a.net;
     const TrSmem& sl = a.sl;
     const NetView& nv = COLOR ? a.mv.color : a.mv.endpoint;
     const int act = a.mv.activation;
     const bool tile_thread = threadIdx.x < a.groups * kTrRows;
+    const bool helper = COLOR && !tile_thread && threadIdx.x < 2 * a.groups * kTrRows;
 
     // weight image -> shared memory; tiles zeroed (no stale NaN bit patterns ever reach an MMA)
     for (int i = threadIdx.x; i < net.img_bytes / 16; i += blockDim.x)
@@ -472,10 +496,11 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
     __syncthreads();
 
     TrGroup G;
-    G.g = tile_thread ? threadIdx.x / kTrRows : 0;
+    G.g = tile_thread ? threadIdx.x / kTrRows : (helper ? threadIdx.x / kTrRows - a.groups : 0);
     G.r = threadIdx.x % kTrRows;
     unsigned char* gb = smem + sl.group_off + G.g * sl.group_bytes;
     G.X = gb + sl.x_off;
+    G.X2 = gb + sl.x2_off;
     for (int l = 0; l < 3; ++l) G.A[l] = gb + sl.a_off[l];
     G.D = gb + sl.d_off;
     G.bar = reinterpret_cast<uint64_t*>(gb + sl.bar_off);
@@ -491,6 +516,7 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
 #pragma unroll
             for (int j = 0; j < 8; ++j) v8[j] = kg * 8 + j == net.in_dim ? 1.f : 0.f;
             st_chunk_bf16(G.X, r, kg, net.K0, v8);
+            st_chunk_bf16(G.X2, r, kg, net.K0, v8);
         }
         if (r == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(G.bar)), "r"(1));
@@ -523,7 +549,44 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
     const int tile0 = COLOR ? blockIdx.x * a.groups + G.g : blockIdx.x;
     const int tstep = COLOR ? gridDim.x * a.groups : gridDim.x;
 
-    for (int tile = tile0; tile < a.tiles; tile += tstep) {
+    bool pending = false;                   // colour: a FULL arrival whose EMPTY is still owed
+    if (helper) {
+        // the grid scatter of the paired group's tiles (texels, warp-aggregated along the
+        // block's rows and columns), one tile behind the group
+        const int qat_bits = a.src.qat_bits;
+        const float* gs = reinterpret_cast<const float*>(G.D) + r * 33;
+        auto gather = [&](int t, unsigned char* X) {
+            const int sr = t * kTrRows + r;
+            float gu, gv2;
+            int x, y;
+            sample_coords(a.mv, true, a.ids, sr < a.B ? sr : a.B - 1, gu, gv2, x, y);
+            gather_row_train(nv, a.src, gu, gv2, X, r, net.K0);
+            proxy_fence();                            // the tensor core reads the tile
+            pair_arrive(pair_xfull_id(G.g));
+        };
+        if (tile0 < a.tiles) gather(tile0, G.X);
+        int k = 0;
+        for (int tile = tile0; tile < a.tiles; tile += tstep, ++k) {
+            // the next tile's input goes to the tile the group finished with one tile ago
+            if (tile + tstep < a.tiles) gather(tile + tstep, (k & 1) ? G.X : G.X2);
+            pair_sync(pair_full_id(G.g));
+            if (pair_stop[G.g]) break;
+            float gv[2 * NTBC_MAX_LEVELS];
+#pragma unroll
+            for (int j = 0; j < 2 * NTBC_MAX_LEVELS; ++j) gv[j] = gs[j];
+            pair_arrive(pair_empty_id(G.g));          // the delta tile is free again
+            const int s_raw = tile * kTrRows + r;
+            const bool valid = s_raw < a.B;
+            float su, sv;
+            int x, y;
+            sample_coords(a.mv, true, a.ids, valid ? s_raw : a.B - 1, su, sv, x, y);
+            const Neighbours nbr = neighbours(su, sv);
+#pragma unroll 1
+            for (int lv = 0; lv < nv.levels; ++lv)
+                scatter_level(nv, true, lv, su, sv, r, valid, gv[2 * lv], gv[2 * lv + 1], a.src, qat_bits, a.grads, nbr);
+        }
+    } else
+    for (int tile = tile0, kk = 0; tile < a.tiles; tile += tstep, ++kk) {
         const int s_raw = tile * kTrRows + r;
         const bool valid = s_raw < a.B;
         const int s = valid ? s_raw : a.B - 1;
@@ -543,14 +606,10 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
             proxy_fence();
             __syncthreads();
         }
-        float su = 0.f, sv = 0.f;                 // the colour sample's coordinates (gather, scatter)
+        unsigned char* Xt = (COLOR && (kk & 1)) ? G.X2 : G.X;    // this tile's input tile
         if (tile_thread && ok) {
-            // ---- gather
-            if (COLOR) {
-                int x, y;
-                sample_coords(a.mv, COLOR, a.ids, s, su, sv, x, y);
-                gather_row_train(nv, a.src, su, sv, G.X, r, net.K0);
-            }
+            // ---- gather (colour: gathered ahead by the helper)
+            if (COLOR) pair_sync(pair_xfull_id(G.g));
             // ---- forward
             for (int l = 0; l < L; ++l) {
                 const TrLayer& Ly = net.layer[l];
@@ -560,7 +619,7 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
                 }
                 if (r == 0) {
                     tc_fence_after();
-                    const unsigned char* src = l == 0 ? G.X : G.A[l - 1];
+                    const unsigned char* src = l == 0 ? Xt : G.A[l - 1];
                     const int C = l == 0 ? net.K0 : kTrHidCols;
                     const uint32_t idesc = umma_idesc_kind(Ly.N, 1, 0, 0);
                     for (int kc = 0; kc < Ly.K / 16; ++kc) {
@@ -585,8 +644,16 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
                     }
                 }
             }
+        }
+        // the helper is done with the delta tile (the previous tile's gradients) before the
+        // loss writes it
+        if (COLOR && tile_thread && pending) {
+            pair_sync(pair_empty_id(G.g));
+            pending = false;
+        }
+        if (tile_thread && ok) {
             // ---- outputs -> loss (colour) or staging (endpoint)
-            if (ok) {
+            {
                 if (COLOR) {
 #pragma unroll
                     for (int kg = 0; kg < 6; ++kg) {
@@ -659,7 +726,7 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
                             umma_f16(dw, ad, bd, idw, !(first && ks == 0));
                         }
                     } else {              // dW_0[o][i] += sum_s D_0[s][o] X[s][i]
-                        const uint32_t x_base = smem_u32(G.X);
+                        const uint32_t x_base = smem_u32(Xt);
                         const uint32_t xstride = (uint32_t)(net.K0 / 8) * 128;
                         const uint32_t idw = umma_idesc_kind(net.K0, 1, 1, 1);
                         for (int ks = 0; ks < kTrRows / 16; ++ks) {
@@ -706,17 +773,17 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
                     float* gs = reinterpret_cast<float*>(G.D) + r * 33;    // the delta tile is free now
 #pragma unroll
                     for (int j = 0; j < 32; ++j) gs[j] = gx[j];
-                    if (COLOR) {          // texels: warp-aggregated along the block's rows and columns
-                        const int qat_bits = a.src.qat_bits;
-                        const Neighbours nbr = neighbours(su, sv);
-#pragma unroll 1
-                        for (int lv = 0; lv < nv.levels; ++lv)
-                            scatter_level(nv, COLOR, lv, su, sv, r, valid, gs[2 * lv], gs[2 * lv + 1], a.src, qat_bits,
-                                          a.grads, nbr);
-                    }
+                    // (colour: the helper warpgroup scatters gs; endpoint: all warps, below)
                 }
             }
             if (ok) first = false;
+        }
+        if (COLOR && tile_thread) {         // hand the tile's gradients (or the stop) to the helper
+            if (r == 0) pair_stop[G.g] = ok ? 0 : 1;
+            __threadfence_block();
+            pair_arrive(pair_full_id(G.g));
+            pending = ok;
+            if (!ok && tile + tstep < a.tiles) pair_sync(pair_xfull_id(G.g));   // the tile gathered ahead
         }
         if (!COLOR) {
             // blocks: the (sample, level) scatter items spread over all 16 warps
@@ -736,6 +803,8 @@ __global__ void __launch_bounds__(COLOR ? kTrRows * kTrMaxGroups : kTrEndpointTh
             break;
         }
     }
+
+    if (COLOR && tile_thread && pending) pair_sync(pair_empty_id(G.g));
 
     // ---- losses: warp sums, then one double atomic per CTA and term
     {
@@ -921,6 +990,8 @@ static TrSmem train_tc_smem(const TrNet& n) {
     int o = 0;
     s.x_off = o;
     o += kTrRows * n.K0 * 2;
+    s.x2_off = o;
+    o += kTrRows * n.K0 * 2;
     for (int l = 0; l < 3; ++l) {
         s.a_off[l] = o;
         if (l < n.n_layers - 1) o += kTrRows * kTrHidCols * 2;
@@ -987,7 +1058,7 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
     grid = std::min(grid, max_rows / a.groups);
     if (color) {
         NTBC_CHECK_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(train_tc_kernel<true>), smem));
-        train_tc_kernel<true><<<grid, kTrRows * a.groups, smem, s>>>(a);
+        train_tc_kernel<true><<<grid, 2 * kTrRows * a.groups, smem, s>>>(a);   // tile groups + their helpers
     } else {
         NTBC_CHECK_CUDA(ensure_dynamic_smem(reinterpret_cast<const void*>(train_tc_kernel<false>), smem));
         train_tc_kernel<false><<<grid, kTrEndpointThreads, smem, s>>>(a);

@@ -28,6 +28,7 @@ struct TrNet {
 struct TrSmem {               // byte offsets: weight image at 0, then the groups
     int group_off, group_bytes;
     int x_off, a_off[3], d_off, bar_off;   // inside a group
+    int x2_off;               // colour network: the second input tile (the helper gathers ahead)
     int stage_off;            // endpoint network: FP32 outputs and summed L_cd gradients, [128][out]
 };
 
