@@ -609,7 +609,8 @@ static ntbc_status ensure_train_state(ntbc_model* m, int n_blocks) {
         NTBC_CHECK_CUDA(cudaMemset(ts->tc_err, 0, sizeof(int)));
         TrNet cn = train_tc_net_desc(mv, true), en = train_tc_net_desc(mv, false);
         ts->tc_part_rows = train_tc_max_partial_rows();
-        size_t part = (size_t)ts->tc_part_rows * std::max(cn.mlp_params, en.mlp_params) * sizeof(float);
+        // one scratch per network: both are reduced by one launch after the two passes
+        size_t part = (size_t)ts->tc_part_rows * ((size_t)cn.mlp_params + en.mlp_params) * sizeof(float);
         st = device_alloc((void**)&ts->tc_part, part, "weight-gradient partials");
         if (st != NTBC_OK) {
             ntbc_train_release(m);
@@ -769,13 +770,17 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
         TrNet cn = train_tc_net_desc(mv, true), en = train_tc_net_desc(mv, false);
         unsigned char* cimg = ts->tc_img;
         unsigned char* eimg = ts->tc_img + cn.img_bytes;
+        float* cpart = ts->tc_part;
+        float* epart = ts->tc_part + (size_t)ts->tc_part_rows * cn.mlp_params;
+        int crows = 0, erows = 0;
         st = train_tc_images(m->params, cn, cimg, en, eimg, s);
         if (st == NTBC_OK)
             st = train_tc_launch(mv, true, cn, cimg, csrc, tp, ids, nb * 16, T, grads, ts->loss_acc, ts->tc_err,
-                                 ts->tc_part, ts->tc_part_rows, s);
+                                 cpart, ts->tc_part_rows, &crows, s);
         if (st == NTBC_OK)
             st = train_tc_launch(mv, false, en, eimg, esrc, tp, ids, nb, T, grads, ts->loss_acc, ts->tc_err,
-                                 ts->tc_part, ts->tc_part_rows, s);
+                                 epart, ts->tc_part_rows, &erows, s);
+        if (st == NTBC_OK) st = train_tc_reduce(cn, cpart, crows, en, epart, erows, grads, s);
     } else {
         st = run_net(m, mv, true, tp, ids, nb * 16, csrc, T, grads, ts->loss_acc, s);
         if (st == NTBC_OK) st = run_net(m, mv, false, tp, ids, nb, esrc, T, grads, ts->loss_acc, s);

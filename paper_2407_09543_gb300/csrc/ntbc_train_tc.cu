@@ -902,28 +902,47 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
     if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(512));
 }
 
-// grads[mlp_base + j] += sum over the groups' partial rows. A CTA owns 32 columns (one per
-// lane, so every row read is one 128-byte line); its 8 warps split the rows, then warp 0
-// adds the 8 partial sums.
+// grads[base + j] += sum over a network's partial rows. blockIdx.x: 32 columns of the colour
+// network's parameters, then of the endpoint network's; blockIdx.y: a chunk of kReduceRows
+// rows, split over the 8 warps (each row read is one 128-byte line); the chunk's sum is added
+// atomically (the rows of a column are spread over several chunks).
 constexpr int kReduceWarps = 8;
-__global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(const float* __restrict__ part, int rows,
-                                                                            int n, float* __restrict__ grads) {
+constexpr int kReduceRows = 32;
+struct ReducePart {
+    const float* part;
+    float* grads;             // grads + the network's mlp_base
+    int rows, n, col_blocks;
+};
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(ReducePart c, ReducePart e) {
     __shared__ float sums[kReduceWarps][32];
+    const bool ep = (int)blockIdx.x >= c.col_blocks;
+    const ReducePart& q = ep ? e : c;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + lane;
+    const int j = ((int)blockIdx.x - (ep ? c.col_blocks : 0)) * 32 + lane;
+    const int r0 = blockIdx.y * kReduceRows, r1 = min(r0 + kReduceRows, q.rows);
+    if (r0 >= r1) return;                                  // CTA-uniform
     float acc = 0.f;
-    if (j < n) {
-#pragma unroll 4
-        for (int p = w; p < rows; p += kReduceWarps) acc += __ldcs(part + (long long)p * n + j);
-    }
+    if (j < q.n)
+        for (int p = r0 + w; p < r1; p += kReduceWarps) acc += __ldcs(q.part + (long long)p * q.n + j);
     sums[w][lane] = acc;
     __syncthreads();
-    if (w == 0 && j < n) {
+    if (w == 0 && j < q.n) {
         float t = 0.f;
 #pragma unroll
-        for (int q = 0; q < kReduceWarps; ++q) t += sums[q][lane];
-        grads[j] += t;
+        for (int k = 0; k < kReduceWarps; ++k) t += sums[k][lane];
+        atomicAdd(q.grads + j, t);
     }
+}
+
+ntbc_status train_tc_reduce(const TrNet& cnet, const float* cpart, int crows, const TrNet& enet, const float* epart,
+                            int erows, float* grads, cudaStream_t s) {
+    ReducePart c{cpart, grads + cnet.mlp_base, crows, cnet.mlp_params, (cnet.mlp_params + 31) / 32};
+    ReducePart e{epart, grads + enet.mlp_base, erows, enet.mlp_params, (enet.mlp_params + 31) / 32};
+    const int chunks = (std::max(crows, erows) + kReduceRows - 1) / kReduceRows;
+    if (chunks < 1) return NTBC_OK;
+    reduce_partials_kernel<<<dim3(c.col_blocks + e.col_blocks, chunks), 32 * kReduceWarps, 0, s>>>(c, e);
+    NTBC_CHECK_LAUNCH("weight-gradient partials");
+    return NTBC_OK;
 }
 
 // BF16 weight images of both networks (blockIdx.y: colour, endpoint): per layer the [N][K]
@@ -1017,7 +1036,8 @@ int train_tc_max_partial_rows() { return 2 * 152; }
 
 ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, const unsigned char* img,
                             const GridSrc& src, const TexPtrs& tp, const int32_t* ids, int B, float T, float* grads,
-                            double* acc, int* err, float* partials, int max_rows, cudaStream_t s) {
+                            double* acc, int* err, float* partials, int max_rows, int* rows, cudaStream_t s) {
+    *rows = 0;
     if (net.in_dim > 2 * NTBC_MAX_LEVELS || net.out_pad > 48)
         return fail(NTBC_EUNSUPPORTED, "tensor-core training: network shape outside the kernel's tiles");
     const int cols = train_tc_tmem_cols(net);
@@ -1064,9 +1084,7 @@ ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, c
         train_tc_kernel<false><<<grid, kTrEndpointThreads, smem, s>>>(a);
     }
     NTBC_CHECK_LAUNCH(color ? "tensor-core training (colour)" : "tensor-core training (endpoint)");
-    reduce_partials_kernel<<<(net.mlp_params + 31) / 32, 32 * kReduceWarps, 0, s>>>(partials, grid * a.groups, net.mlp_params,
-                                                                      grads + net.mlp_base);
-    NTBC_CHECK_LAUNCH("weight-gradient partials");
+    *rows = grid * a.groups;
     return NTBC_OK;
 }
 

@@ -57,10 +57,14 @@ ntbc_status train_tc_images(const float* params, const TrNet& cnet, unsigned cha
                             unsigned char* eimg, cudaStream_t s);
 // rows of the partial-sum scratch a launch may use (one per warpgroup)
 int train_tc_max_partial_rows();
-// forward + loss + backward of B samples; adds into grads and the loss accumulators;
-// partials: scratch of max_rows x mlp_params floats
+// forward + loss + backward of B samples; adds the grid gradients into grads and the losses
+// into the loss accumulators, and writes the MLP weight gradients as *rows partial rows of
+// mlp_params floats into partials (scratch of max_rows rows), to be added by train_tc_reduce
 ntbc_status train_tc_launch(const ModelView& mv, bool color, const TrNet& net, const unsigned char* img,
                             const GridSrc& src, const TexPtrs& tp, const int32_t* ids, int B, float T, float* grads,
-                            double* acc, int* err, float* partials, int max_rows, cudaStream_t s);
+                            double* acc, int* err, float* partials, int max_rows, int* rows, cudaStream_t s);
+// grads[mlp_base + j] += the sum of each network's partial rows (both networks, one launch)
+ntbc_status train_tc_reduce(const TrNet& cnet, const float* cpart, int crows, const TrNet& enet, const float* epart,
+                            int erows, float* grads, cudaStream_t s);
 
 }  // namespace ntbc
