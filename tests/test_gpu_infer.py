@@ -400,6 +400,33 @@ def test_full_size_4k_sampled():
     assert total_m <= 0.001 * total_f
 
 
+def test_full_size_4k_sampled_fp8_arithmetic():
+    """The 4096^2 four-texture workload in the FP8 arithmetic: the calibration exponents over
+    the whole material's sample equal the oracle's, and sampled blocks meet the FP8 bars."""
+    w = nt.configs.WORKLOADS["mat4k"]
+    formats = [1, 1, 4, 4]
+    desc, odesc = descs.case_descs(nt, formats, 4096, w.levels, w.min_res, w.max_res, 3, "selu")
+    params = synth.random_params_like(descs.init_params(odesc, 3), seed=4)
+    model, p8, wexps, _, aexps, grids = _fp8_mma_case(None, desc, odesc, params)
+    (gw, ga), _ = _blob_fp8_part(model, desc, len(wexps), mma=True)
+    np.testing.assert_array_equal(gw, np.array(wexps))
+    np.testing.assert_array_equal(ga, np.array(aexps))
+    ids = np.sort(np.random.default_rng(1).choice(odesc.n_blocks, 300, replace=False))
+    e, c = gpu_forward(model, ids)
+    er, cr = ont.forward_blocks(odesc, p8, ids, fp8_act=aexps, **grids)
+    be, bc_ = _fp8_error_bound(odesc, p8, aexps, ids, grids)
+    check_fp8_mma_outputs(e, er, be)
+    check_fp8_mma_outputs(c, cr, bc_)
+    got = gpu_blocks(model, desc)
+    ref = ont.infer_blocks(odesc, p8, block_ids=ids, fp8_act=aexps, **grids)
+    total_m = total_f = 0
+    for t, fmt in enumerate(formats):
+        m, f = field_mismatch(fmt, got[t][ids], ref[t])
+        total_m += m
+        total_f += f
+    assert total_m <= 0.005 * total_f
+
+
 def test_fp16_fast_mode_stated_tolerance():
     mat, desc, odesc, params = make_case(side=128, levels=4, lo=8, hi=64, hidden=3)
     model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16_FAST)
