@@ -111,6 +111,15 @@ __device__ __forceinline__ bool tr_barrier(int g, volatile int* abort_flag) {
     return abort_flag[g] == 0;
 }
 
+// the endpoint kernel's forward and backward run on all 16 warps (one tile per CTA): a CTA
+// barrier instead of the warpgroup's
+__device__ __forceinline__ bool tr_cta_barrier(volatile int* abort_flag) {
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    return abort_flag[0] == 0;
+}
+
 __device__ __forceinline__ void tr_wait(const TrGroup& G, uint32_t& phase, volatile int* abort_flag) {
     if (!mbar_wait(G.bar, phase)) abort_flag[G.g] = 1;
     phase ^= 1;
@@ -607,17 +616,22 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
             __syncthreads();
         }
         unsigned char* Xt = (COLOR && (kk & 1)) ? G.X2 : G.X;    // this tile's input tile
-        if (tile_thread && ok) {
+        // colour: the tile warpgroup; endpoint: all 16 warps, warpgroup qw taking accumulator
+        // columns [16 qw, 16 qw + 16) of every row in the epilogues (TMEM lane quarters are the
+        // warp's index mod 4, so every warp reaches its rows)
+        const bool mma_thread = COLOR ? tile_thread : true;
+        const int qw = COLOR ? 0 : (int)threadIdx.x / kTrRows;
+        if (mma_thread && ok) {
             // ---- gather (colour: gathered ahead by the helper)
             if (COLOR) pair_sync(pair_xfull_id(G.g));
             // ---- forward
             for (int l = 0; l < L; ++l) {
                 const TrLayer& Ly = net.layer[l];
-                if (!tr_barrier(G.g, abort)) {
+                if (!(COLOR ? tr_barrier(G.g, abort) : tr_cta_barrier(abort))) {
                     ok = false;
                     break;
                 }
-                if (r == 0) {
+                if (r == 0 && qw == 0) {
                     tc_fence_after();
                     const unsigned char* src = l == 0 ? Xt : G.A[l - 1];
                     const int C = l == 0 ? net.K0 : kTrHidCols;
@@ -631,16 +645,26 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                 }
                 tr_wait(G, phase, abort);
                 if (l + 1 < L) {
+                    if constexpr (COLOR) {
 #pragma unroll
-                    for (int c0 = 0; c0 < 64; c0 += 32) {
-                        float z[32];
-                        tmem_ld16(G.row + c0, z);
-                        tmem_ld16(G.row + c0 + 16, z + 16);
-                        tmem_wait_ld_regs<32>(z);
+                        for (int c0 = 0; c0 < 64; c0 += 32) {
+                            float z[32];
+                            tmem_ld16(G.row + c0, z);
+                            tmem_ld16(G.row + c0 + 16, z + 16);
+                            tmem_wait_ld_regs<32>(z);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) z[j] = act_fast(z[j], act);
+                            for (int j = 0; j < 32; ++j) z[j] = act_fast(z[j], act);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) st_chunk_bf16(G.A[l], r, c0 / 8 + q, kTrHidCols, z + 8 * q);
+                            for (int q = 0; q < 4; ++q) st_chunk_bf16(G.A[l], r, c0 / 8 + q, kTrHidCols, z + 8 * q);
+                        }
+                    } else {
+                        float z[16];
+                        tmem_ld16(G.row + 16 * qw, z);
+                        tmem_wait_ld_regs<16>(z);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) z[j] = act_fast(z[j], act);
+                        st_chunk_bf16(G.A[l], r, 2 * qw, kTrHidCols, z);
+                        st_chunk_bf16(G.A[l], r, 2 * qw + 1, kTrHidCols, z + 8);
                     }
                 }
             }
@@ -651,7 +675,7 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
             pair_sync(pair_empty_id(G.g));
             pending = false;
         }
-        if (tile_thread && ok) {
+        if (mma_thread && ok) {
             // ---- outputs -> loss (colour) or staging (endpoint)
             {
                 if (COLOR) {
@@ -663,7 +687,8 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                     }
                     color_loss_row(a, s, valid, G.row, G.D, r, loss0, loss1);
                 } else {
-                    for (int c0 = 0; c0 < net.out_pad; c0 += 16) {
+                    const int c0 = 16 * qw;                      // warp-uniform
+                    if (c0 < net.out_pad) {
                         float z[16];
                         tmem_ld16(G.row + c0, z);
                         tmem_wait_ld_regs<16>(z);
@@ -703,16 +728,16 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
             }
         }
 
-        if (tile_thread && ok) {
+        if (mma_thread && ok) {
             // ---- backward
             for (int l = L - 1; l >= 0; --l) {
                 const TrLayer& Ly = net.layer[l];
                 const int CD = l == L - 1 ? net.out_pad : 64;       // columns of the delta tile
-                if (!tr_barrier(G.g, abort)) {
+                if (!(COLOR ? tr_barrier(G.g, abort) : tr_cta_barrier(abort))) {
                     ok = false;
                     break;
                 }
-                if (r == 0) {
+                if (r == 0 && qw == 0) {
                     tc_fence_after();
                     const uint32_t dw = G.tmem + (uint32_t)Ly.dw_col;
                     const uint32_t d_base = smem_u32(G.D);
@@ -747,7 +772,30 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                     umma_commit(G.bar);
                 }
                 tr_wait(G, phase, abort);
-                if (l > 0) {              // D_{l-1} = dA_{l-1} * act'(A_{l-1})
+                if (!COLOR && l > 0) {    // quarter qw of D_{l-1} = dA_{l-1} * act'(A_{l-1})
+                    float dA[16];
+                    tmem_ld16(G.row + 16 * qw, dA);
+                    tmem_wait_ld_regs<16>(dA);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        float av[8];
+                        ld_chunk_bf16(G.A[l - 1], r, 2 * qw + q, kTrHidCols, av);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            dA[8 * q + j] = valid ? dA[8 * q + j] * act_grad_from_out(av[j], act) : 0.f;
+                    }
+                    st_chunk_bf16(G.D, r, 2 * qw, 64, dA);
+                    st_chunk_bf16(G.D, r, 2 * qw + 1, 64, dA + 8);
+                } else if (!COLOR) {      // quarters 0, 1: d loss / d features (32 columns)
+                    if (qw < 2) {
+                        float gx[16];
+                        tmem_ld16(G.row + 16 * qw, gx);
+                        tmem_wait_ld_regs<16>(gx);
+                        float* gs = reinterpret_cast<float*>(G.D) + r * 33 + 16 * qw;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) gs[j] = gx[j];
+                    }
+                } else if (l > 0) {       // D_{l-1} = dA_{l-1} * act'(A_{l-1})
 #pragma unroll
                     for (int c0 = 0; c0 < 64; c0 += 32) {
                         float dA[32];
