@@ -74,22 +74,22 @@ __device__ __forceinline__ float2 residual_f16x2(__half2 h, float2 x) {
 template <bool SPLIT>
 __device__ __forceinline__ void st_row8_split(unsigned char* hi_tile, unsigned char* lo_tile, int r, int kg, int K,
                                               const float* v) {
-    if (!SPLIT) {
+    if constexpr (!SPLIT) {
         st_row8(hi_tile, r, kg, K, v);
-        return;
-    }
-    uint32_t hw[4], lw[4];
+    } else {
+        uint32_t hw[4], lw[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        __half2 h = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-        float2 r = residual_f16x2(h, make_float2(v[2 * j], v[2 * j + 1]));
-        __half2 lo = __floats2half2_rn(r.x, r.y);
-        hw[j] = *reinterpret_cast<uint32_t*>(&h);
-        lw[j] = *reinterpret_cast<uint32_t*>(&lo);
+        for (int j = 0; j < 4; ++j) {
+            __half2 h = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+            float2 r = residual_f16x2(h, make_float2(v[2 * j], v[2 * j + 1]));
+            __half2 lo = __floats2half2_rn(r.x, r.y);
+            hw[j] = *reinterpret_cast<uint32_t*>(&h);
+            lw[j] = *reinterpret_cast<uint32_t*>(&lo);
+        }
+        int off = ((r >> 3) * (K >> 3) + kg) * 128 + (r & 7) * 16;
+        *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
-    int off = ((r >> 3) * (K >> 3) + kg) * 128 + (r & 7) * 16;
-    *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
 // two values as E4M3 codes (nearest even, saturating at +-448): lo in the low byte
@@ -356,19 +356,19 @@ __device__ __forceinline__ void gather_row(const NetView& nv, const GridSrc& src
     if constexpr (ACT == kActE4M3) {              // K0 = 32 = 2 NTBC_MAX_LEVELS
         st_row16_e4m3(A, r, 0, 32, f);
         st_row16_e4m3(A, r, 1, 32, f + 16);
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int kg = 0; kg < 6; ++kg) {
-        if (kg * 8 >= K0) break;
-        float v8[8];
+        for (int kg = 0; kg < 6; ++kg) {
+            if (kg * 8 >= K0) break;
+            float v8[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            int i = kg * 8 + j;
-            float x = i < 2 * NTBC_MAX_LEVELS ? f[i] : 0.f;
-            v8[j] = i == nv.in_dim ? kLog2e : x;
+            for (int j = 0; j < 8; ++j) {
+                int i = kg * 8 + j;
+                float x = i < 2 * NTBC_MAX_LEVELS ? f[i] : 0.f;
+                v8[j] = i == nv.in_dim ? kLog2e : x;
+            }
+            st_row8_split<ACT == kActSplit>(A, Alo, r, kg, K0, v8);
         }
-        st_row8_split<ACT == kActSplit>(A, Alo, r, kg, K0, v8);
     }
 }
 
@@ -542,17 +542,17 @@ __device__ __forceinline__ void epilogue_half(uint32_t src_row, int c0, unsigned
         }
         st_row16_e4m3(A, r, c0 / 16, 64, v);
         st_row16_e4m3(A, r, c0 / 16 + 1, 64, v + 16);
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < 32; j += 2) {
-        float2 y = act == NTBC_ACT_SELU ? selu2_l2(make_float2(v[j], v[j + 1]))
-                                        : make_float2(fmaxf(v[j], 0.f), fmaxf(v[j + 1], 0.f));
-        v[j] = y.x;
-        v[j + 1] = y.y;
-    }
+        for (int j = 0; j < 32; j += 2) {
+            float2 y = act == NTBC_ACT_SELU ? selu2_l2(make_float2(v[j], v[j + 1]))
+                                            : make_float2(fmaxf(v[j], 0.f), fmaxf(v[j + 1], 0.f));
+            v[j] = y.x;
+            v[j + 1] = y.y;
+        }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st_row8_split<ACT == kActSplit>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
+        for (int q = 0; q < 4; ++q) st_row8_split<ACT == kActSplit>(A, Alo, r, c0 / 8 + q, 64, v + 8 * q);
+    }
 }
 
 // E4M3: the constants of layer l of network `net` (0 colour, 1 endpoint) in the image copy
@@ -616,13 +616,11 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
                                           unsigned char* smem, const TcSmem& sl, const TcGroup& G, uint32_t& phase,
                                           uint32_t& region, volatile int* abort_flag) {
     const ModelView& mv = args.mv;
-    const int g = G.g, r = G.r;
+    const int r = G.r;
     unsigned char* A = G.A;
     unsigned char* Alo = G.Alo;
     uint8_t* palb = G.palb;
     uint32_t* eps = G.eps;
-    uint64_t* bar = G.bar;
-    const uint32_t tmem = G.tmem, tmem_row = G.tmem_row;
     const float* tab = reinterpret_cast<const float*>(smem + sl.table_off);
     const float4* lvl = reinterpret_cast<const float4*>(smem + sl.lvl_off);
     const int T = mv.n_textures;
