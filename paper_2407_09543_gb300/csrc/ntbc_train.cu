@@ -494,9 +494,17 @@ __device__ __forceinline__ void adam4(float4& P, float4 G, float4& M, float4& V,
 // dense Adam over all parameters, two float4 of every array in flight per thread; the
 // streams are touched once per step, so they bypass L2 retention (evict-first hints)
 // advance: a captured training step, whose last kernel this is, moves the step counter on
-__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+// gclear (the training step's own gradient buffer, = g): every gradient read is cleared for
+// the next step where it is nonzero, so the buffer stays zero without a dense clear (a step's
+// grid scatter touches a few million of the 16.8 M entries)
+__device__ __forceinline__ void clear_used(float* gclear, long long i4, float4 G) {
+    if (gclear && (G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f))
+        __stcs(reinterpret_cast<float4*>(gclear) + i4, make_float4(0.f, 0.f, 0.f, 0.f));
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* g, float* __restrict__ m,
                             float* __restrict__ v, long long n, long long grid_floats, StepState* __restrict__ st,
-                            int advance) {
+                            int advance, float* gclear) {
     const float inv_bc1 = 1.f / st->bc1, rsb2 = rsqrtf(st->bc2);
     const float step_g = st->lr_grid * inv_bc1, step_m = st->lr_mlp * inv_bc1;
     const long long n4 = n / 4;
@@ -512,6 +520,8 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
         float4 Pb = __ldcs(P4 + j), Gb = __ldcs(G4 + j), Mb = __ldcs(M4 + j), Vb = __ldcs(V4 + j);
         adam4(Pa, Ga, Ma, Va, 4 * i, grid_floats, step_g, step_m, rsb2);
         adam4(Pb, Gb, Mb, Vb, 4 * j, grid_floats, step_g, step_m, rsb2);
+        clear_used(gclear, i, Ga);
+        clear_used(gclear, j, Gb);
         __stcs(P4 + i, Pa);
         __stcs(M4 + i, Ma);
         __stcs(V4 + i, Va);
@@ -522,6 +532,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     if (i < n4) {
         float4 Pa = __ldcs(P4 + i), Ga = __ldcs(G4 + i), Ma = __ldcs(M4 + i), Va = __ldcs(V4 + i);
         adam4(Pa, Ga, Ma, Va, 4 * i, grid_floats, step_g, step_m, rsb2);
+        clear_used(gclear, i, Ga);
         __stcs(P4 + i, Pa);
         __stcs(M4 + i, Ma);
         __stcs(V4 + i, Va);
@@ -529,6 +540,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) {
         long long e = 4 * n4 + threadIdx.x;
         adam_one(p[e], g[e], m[e], v[e], e < grid_floats ? step_g : step_m, rsb2);
+        if (gclear) gclear[e] = 0.f;
     }
     if (advance && blockIdx.x == 0 && threadIdx.x == 0) st->step += 1;   // nothing of this kernel reads it
 }
@@ -763,7 +775,8 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
     GridSrc csrc, esrc;
     ntbc_status st0 = train_sources(m, qat_bits, csrc, esrc, s);
     if (st0 != NTBC_OK) return st0;
-    NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
+    // a captured step's gradients start at zero: the step's Adam clears every entry it used
+    if (!in_step) NTBC_CHECK_CUDA(cudaMemsetAsync(grads, 0, m->layout.total * sizeof(float), s));
     if (!in_step) NTBC_CHECK_CUDA(cudaMemsetAsync(ts->loss_acc, 0, 6 * sizeof(double), s));
     ntbc_status st;
     if (precision == NTBC_TRAIN_BF16) {
@@ -792,11 +805,12 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
     return NTBC_OK;
 }
 
-static ntbc_status adam_launch(ntbc_model* m, const float* grads, cudaStream_t s, int advance = 0) {
+static ntbc_status adam_launch(ntbc_model* m, const float* grads, cudaStream_t s, int advance = 0,
+                               float* clear = nullptr) {
     long long n = (long long)m->layout.total;
     unsigned g = (unsigned)std::min<long long>(blocks_for(n, 256), 152LL * 16);
     adam_kernel<<<g, 256, 0, s>>>(m->params, grads, m->adam_m, m->adam_v, n, (long long)m->layout.grid_floats, m->train->st,
-                                  advance);
+                                  advance, clear);
     NTBC_CHECK_LAUNCH("adam");
     return NTBC_OK;
 }
@@ -821,7 +835,7 @@ static ntbc_status capture_step(ntbc_model* m, const ntbc_material* mat, const n
     sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, ts->sched, total, 0, nb, n_blocks, ts->ids,
                                                         ts->loss_acc);
     ntbc_status st = grads_on_ids(m, mat, ts->ids, nb, qbits, cfg->temperature, cfg->precision, ts->grads, cap, true);
-    if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap, 1);
+    if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap, 1, ts->grads);   // clears what it used
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (st != NTBC_OK || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -957,6 +971,8 @@ ntbc_status ntbc_train_range(ntbc_model* m, const ntbc_material* mat, const ntbc
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), cap));
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), cap));
     }
+    // the captured steps' gradient buffer starts at zero (each step's Adam keeps it so)
+    NTBC_CHECK_CUDA(cudaMemsetAsync(ts->grads, 0, m->layout.total * sizeof(float), cap));
     {                               // the step counter the sampler, schedule and Adam read
         StepState st0;
         memset(&st0, 0, sizeof(st0));
