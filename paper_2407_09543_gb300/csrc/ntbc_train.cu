@@ -9,6 +9,8 @@
 // consecutive threads (samples) touch consecutive addresses. The colour network
 // runs on 16 samples per sampled block (all its texels), the endpoint network on
 // one sample per block.
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -17,6 +19,7 @@
 #include "ntbc_kernels.cuh"
 #include "ntbc_train_common.cuh"
 #include "ntbc_train_tc.cuh"
+#include "tcgen05.cuh"
 
 namespace ntbc {
 
@@ -497,6 +500,48 @@ __device__ __forceinline__ void adam4(float4& P, float4 G, float4& M, float4& V,
 // gclear (the training step's own gradient buffer, = g): every gradient read is cleared for
 // the next step where it is nonzero, so the buffer stays zero without a dense clear (a step's
 // grid scatter touches a few million of the 16.8 M entries)
+// the BF16 weight images of the tensor-core pass (both networks), rewritten by the training
+// step's Adam for the MLP parameters it updates, so no per-step image kernel is needed
+struct AdamImages {
+    TrNet net[2];
+    unsigned char* img[2];
+    long long lo, hi;         // the MLP parameters: [lo, hi) of the parameter buffer
+    int on;
+};
+
+// image element of parameter e (W[o][i] at row o, column i; b[o] at row o, column in)
+__device__ __forceinline__ void image_store(const AdamImages& im, long long e, float w) {
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+        const TrNet& n = im.net[k];
+#pragma unroll 1
+        for (int l = 0; l < n.n_layers; ++l) {
+            const TrLayer& L = n.layer[l];
+            long long d = e - L.w_off;
+            int row = -1, col = 0;
+            if (d >= 0 && d < (long long)L.out * L.in) {
+                row = (int)(d / L.in);
+                col = (int)(d % L.in);
+            } else if (e >= L.b_off && e < L.b_off + L.out) {
+                row = (int)(e - L.b_off);
+                col = L.in;
+            }
+            if (row >= 0) {
+                *reinterpret_cast<__nv_bfloat16*>(im.img[k] + L.img + core_byte(row, col, L.K)) = __float2bfloat16_rn(w);
+                return;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void image_update(const AdamImages& im, long long e, float4 P) {
+    if (!im.on || e + 3 < im.lo || e >= im.hi) return;
+    const float w[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j)
+        if (e + j >= im.lo && e + j < im.hi) image_store(im, e + j, w[j]);
+}
+
 __device__ __forceinline__ void clear_used(float* gclear, long long i4, float4 G) {
     if (gclear && (G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f))
         __stcs(reinterpret_cast<float4*>(gclear) + i4, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -504,7 +549,7 @@ __device__ __forceinline__ void clear_used(float* gclear, long long i4, float4 G
 
 __global__ void adam_kernel(float* __restrict__ p, const float* g, float* __restrict__ m,
                             float* __restrict__ v, long long n, long long grid_floats, StepState* __restrict__ st,
-                            int advance, float* gclear) {
+                            int advance, float* gclear, const __grid_constant__ AdamImages im) {
     const float inv_bc1 = 1.f / st->bc1, rsb2 = rsqrtf(st->bc2);
     const float step_g = st->lr_grid * inv_bc1, step_m = st->lr_mlp * inv_bc1;
     const long long n4 = n / 4;
@@ -522,6 +567,8 @@ __global__ void adam_kernel(float* __restrict__ p, const float* g, float* __rest
         adam4(Pb, Gb, Mb, Vb, 4 * j, grid_floats, step_g, step_m, rsb2);
         clear_used(gclear, i, Ga);
         clear_used(gclear, j, Gb);
+        image_update(im, 4 * i, Pa);
+        image_update(im, 4 * j, Pb);
         __stcs(P4 + i, Pa);
         __stcs(M4 + i, Ma);
         __stcs(V4 + i, Va);
@@ -533,6 +580,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* g, float* __rest
         float4 Pa = __ldcs(P4 + i), Ga = __ldcs(G4 + i), Ma = __ldcs(M4 + i), Va = __ldcs(V4 + i);
         adam4(Pa, Ga, Ma, Va, 4 * i, grid_floats, step_g, step_m, rsb2);
         clear_used(gclear, i, Ga);
+        image_update(im, 4 * i, Pa);
         __stcs(P4 + i, Pa);
         __stcs(M4 + i, Ma);
         __stcs(V4 + i, Va);
@@ -541,6 +589,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* g, float* __rest
         long long e = 4 * n4 + threadIdx.x;
         adam_one(p[e], g[e], m[e], v[e], e < grid_floats ? step_g : step_m, rsb2);
         if (gclear) gclear[e] = 0.f;
+        if (im.on && e >= im.lo && e < im.hi) image_store(im, e, p[e]);
     }
     if (advance && blockIdx.x == 0 && threadIdx.x == 0) st->step += 1;   // nothing of this kernel reads it
 }
@@ -786,7 +835,9 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
         float* cpart = ts->tc_part;
         float* epart = ts->tc_part + (size_t)ts->tc_part_rows * cn.mlp_params;
         int crows = 0, erows = 0;
-        st = train_tc_images(m->params, cn, cimg, en, eimg, s);
+        // a captured step reads the images its previous step's Adam rewrote (built once before
+        // the first step of a range)
+        st = in_step ? NTBC_OK : train_tc_images(m->params, cn, cimg, en, eimg, s);
         if (st == NTBC_OK)
             st = train_tc_launch(mv, true, cn, cimg, csrc, tp, ids, nb * 16, T, grads, ts->loss_acc, ts->tc_err,
                                  cpart, ts->tc_part_rows, &crows, s);
@@ -806,11 +857,14 @@ static ntbc_status grads_on_ids(ntbc_model* m, const ntbc_material* mat, const i
 }
 
 static ntbc_status adam_launch(ntbc_model* m, const float* grads, cudaStream_t s, int advance = 0,
-                               float* clear = nullptr) {
+                               float* clear = nullptr, const AdamImages* images = nullptr) {
     long long n = (long long)m->layout.total;
     unsigned g = (unsigned)std::min<long long>(blocks_for(n, 256), 152LL * 16);
+    AdamImages im;
+    memset(&im, 0, sizeof(im));
+    if (images) im = *images;
     adam_kernel<<<g, 256, 0, s>>>(m->params, grads, m->adam_m, m->adam_v, n, (long long)m->layout.grid_floats, m->train->st,
-                                  advance, clear);
+                                  advance, clear, im);
     NTBC_CHECK_LAUNCH("adam");
     return NTBC_OK;
 }
@@ -827,6 +881,21 @@ struct OwnedStream {
 };
 
 // Capture one training step (qbits > 0: a QAT-phase step) as a graph on `cap`.
+// the training step's weight images and their MLP parameter range (BF16 pass)
+static AdamImages step_images(const ntbc_model* m) {
+    AdamImages im;
+    memset(&im, 0, sizeof(im));
+    const ModelView mv = make_view(m->desc, m->layout);
+    im.net[0] = train_tc_net_desc(mv, true);
+    im.net[1] = train_tc_net_desc(mv, false);
+    im.img[0] = m->train->tc_img;
+    im.img[1] = m->train->tc_img + im.net[0].img_bytes;
+    im.lo = std::min(im.net[0].mlp_base, im.net[1].mlp_base);
+    im.hi = std::max(im.net[0].mlp_base + im.net[0].mlp_params, im.net[1].mlp_base + im.net[1].mlp_params);
+    im.on = 1;
+    return im;
+}
+
 static ntbc_status capture_step(ntbc_model* m, const ntbc_material* mat, const ntbc_train_config* cfg, int nb,
                                 int n_blocks, long long total, int qbits, cudaStream_t cap, cudaGraphExec_t* exec) {
     ntbc_train_state* ts = m->train;
@@ -835,7 +904,10 @@ static ntbc_status capture_step(ntbc_model* m, const ntbc_material* mat, const n
     sample_kernel<<<blocks_for(nb, 256), 256, 0, cap>>>(cfg->seed, ts->st, ts->sched, total, 0, nb, n_blocks, ts->ids,
                                                         ts->loss_acc);
     ntbc_status st = grads_on_ids(m, mat, ts->ids, nb, qbits, cfg->temperature, cfg->precision, ts->grads, cap, true);
-    if (st == NTBC_OK) st = adam_launch(m, ts->grads, cap, 1, ts->grads);   // clears what it used
+    // Adam clears the gradients it used and, for the BF16 pass, rewrites the weight images
+    const AdamImages im = step_images(m);
+    if (st == NTBC_OK)
+        st = adam_launch(m, ts->grads, cap, 1, ts->grads, cfg->precision == NTBC_TRAIN_BF16 ? &im : nullptr);
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (st != NTBC_OK || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -971,8 +1043,14 @@ ntbc_status ntbc_train_range(ntbc_model* m, const ntbc_material* mat, const ntbc
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_m, 0, m->layout.total * sizeof(float), cap));
         NTBC_CHECK_CUDA(cudaMemsetAsync(m->adam_v, 0, m->layout.total * sizeof(float), cap));
     }
-    // the captured steps' gradient buffer starts at zero (each step's Adam keeps it so)
+    // the captured steps' gradient buffer starts at zero (each step's Adam keeps it so), and
+    // the BF16 weight images start from the current parameters (each step's Adam keeps them)
     NTBC_CHECK_CUDA(cudaMemsetAsync(ts->grads, 0, m->layout.total * sizeof(float), cap));
+    if (cfg->precision == NTBC_TRAIN_BF16) {
+        const AdamImages im = step_images(m);
+        st = train_tc_images(m->params, im.net[0], im.img[0], im.net[1], im.img[1], cap);
+        if (st != NTBC_OK) return st;
+    }
     {                               // the step counter the sampler, schedule and Adam read
         StepState st0;
         memset(&st0, 0, sizeof(st0));
