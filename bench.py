@@ -517,13 +517,14 @@ def measured_peaks():
 def encode_roofline(nt, desc, ms_step):
     """Bounds of one encode step at BATCH_TEXELS: tensor time of the forward + backward MLP
     FLOPs (3x the forward, BF16 dense peak) and HBM time of the dense Adam pass (read p, g,
-    m, v; write p, m, v), the gradient clear and one read of both FP32 grids."""
+    m, v; write p, m, v) and one read of both FP32 grids. The gradients need no dense clear:
+    the step's Adam zeroes the entries it read, a few million of them."""
     lay = nt.ntbc_model_layout(desc)
     hl = desc.hidden_layers
     mac_c = lay.in_color * 64 + (hl - 1) * 64 * 64 + 64 * lay.out_color
     mac_e = lay.in_endpoint * 64 + (hl - 1) * 64 * 64 + 64 * lay.out_endpoint
     flops = 3 * 2.0 * (BATCH_TEXELS * mac_c + BATCH_TEXELS // 16 * mac_e)
-    bytes_ = lay.total * 4.0 * (7 + 1 + 1)
+    bytes_ = lay.total * 4.0 * (7 + 1)
     peaks = measured_peaks()
     t_tc = flops / (peaks["bf16_tflops"] * 1e12) * 1e3
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9) * 1e3

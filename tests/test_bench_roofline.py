@@ -41,9 +41,9 @@ def test_encode_counts_per_step():
     # forward + backward ~ 3x the forward MACs over 2^18 texels and 2^14 blocks
     terms = bench.encode_roofline(nt, _desc(), 0.4)
     assert terms["flop_per_step"] == 3 * 2 * ((1 << 18) * 10_240 + (1 << 14) * 10_496)
-    # dense Adam (read p, g, m, v; write p, m, v) + the gradient clear + one read of the grids
+    # dense Adam (read p, g, m, v; write p, m, v) + one read of the grids (no dense gradient clear)
     lay = nt.ntbc_model_layout(_desc())
-    assert terms["hbm_bytes_per_step"] == lay.total * 4 * 9
+    assert terms["hbm_bytes_per_step"] == lay.total * 4 * 8
 
 
 def test_job_throughput_is_whole_job():
