@@ -276,7 +276,9 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out
  * The same inference with the blocks delivered to HOST memory: the material's blocks are
  * produced in `chunks` (1..16) consecutive ranges of whole 128-block work units, and each
  * range is copied device -> host (one copy per texture, on a copy stream the model keeps)
- * while the next range is computed, so the transfer hides behind the inference.
+ * while the next range is computed, so the transfer hides behind the inference. On the
+ * tensor-core path each range after the first is a programmatic dependent launch, which may
+ * start while the previous range's last CTAs finish (the ranges write disjoint blocks).
  *   host_out  host array of n_textures HOST pointers, each (w/4)*(h/4)*8 bytes; pinned
  *             memory lets the copies overlap the compute (pageable memory still works)
  * Everything is ordered before later work on `stream`: the blocks are in host_out once
@@ -345,7 +347,9 @@ ntbc_status ntbc_forward(const ntbc_model* model, const int32_t* block_ids, int 
  *   ntbc_batch_create(_mode)  models: host array of n models; blocks_out: host array of n
  *                      host arrays, each holding that material's per-texture DEVICE outputs
  *                      (8-byte aligned, n_blocks * 8 bytes each). Plans the launches
- *                      (allocates; not capturable). An unknown mode is NTBC_EINVAL.
+ *                      (allocates; waits for all work on the device, so models exported on
+ *                      any stream are complete; not capturable). An unknown mode is
+ *                      NTBC_EINVAL.
  *   ntbc_batch_infer   one reset of the batch's counters, then the launches on `stream`; may
  *                      be captured in a CUDA graph and replayed.
  *   ntbc_batch_times   synchronises `stream`; ms (host double[n], in the order of `models`)

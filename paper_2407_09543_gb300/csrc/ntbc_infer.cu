@@ -502,7 +502,9 @@ ntbc_status ntbc_infer_to_host(ntbc_model* m, uint8_t* const* host_out, int chun
     for (int first = 0; first < n; first += per, ++c) {
         const int cnt = std::min(per, n - first);
         if (m->weight_prec != NTBC_PREC_FP32) {
-            st = tc_launch(m, stage, strides, io->ids + first, cnt, nullptr, nullptr, csrc, esrc, s);
+            // every range after the first is chained to the one before it (the ranges write
+            // disjoint blocks; a range's copy waits for its event, recorded after its launch)
+            st = tc_launch(m, stage, strides, io->ids + first, cnt, nullptr, nullptr, csrc, esrc, s, first > 0);
         } else {
             OutPtrs outs;
             memset(&outs, 0, sizeof(outs));

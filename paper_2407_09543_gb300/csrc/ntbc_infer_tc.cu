@@ -1267,11 +1267,12 @@ static cudaError_t tc_enqueue(const TcLaunch& L, cudaStream_t s, bool chained) {
 }
 
 ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
-                      float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s) {
+                      float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s,
+                      bool chained) {
     TcLaunch L;
     ntbc_status st = tc_plan(m, blocks_out, strides, ids, n, e_out, c_out, csrc, esrc, &L);
     if (st != NTBC_OK) return st;
-    NTBC_CHECK_CUDA(tc_enqueue(L, s, false));
+    NTBC_CHECK_CUDA(tc_enqueue(L, s, chained));
     NTBC_CHECK_LAUNCH("ntbc inference (tcgen05)");
     return NTBC_OK;
 }
@@ -1427,6 +1428,9 @@ ntbc_status ntbc_batch_create_mode(const ntbc_model* const* models, int n, uint8
     std::vector<TcMat> sorted(n);
     for (int i = 0; i < n; ++i) sorted[i] = mats[order[i]];
     mats.swap(sorted);
+    // the models may have been exported on any stream: their images and grids are complete
+    // before the batch exists (creation is a one-time set-up call)
+    NTBC_CHECK_CUDA(cudaDeviceSynchronize());
     ntbc_batch* b = new ntbc_batch();
     b->n = n;
     b->mode = mode;

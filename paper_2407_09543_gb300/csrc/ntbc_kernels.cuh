@@ -116,8 +116,11 @@ ntbc_status tc_prepare(ntbc_model* m, cudaStream_t s);
 // work units the tensor-core inference processes at once (groups x SMs; 0 on error) and the
 // blocks per work unit (unit_blocks, optional)
 int tc_units_in_flight(const ntbc_model* m, int* unit_blocks);
-// blocks_out: per texture the first block; strides: bytes between its blocks (NULL: 8)
+// blocks_out: per texture the first block; strides: bytes between its blocks (NULL: 8);
+// chained: a programmatic dependent launch, which may start while the previous launch on the
+// stream is finishing (only where the two share no data, e.g. the ranges of one material)
 ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
-                      float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s);
+                      float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s,
+                      bool chained = false);
 
 }  // namespace ntbc

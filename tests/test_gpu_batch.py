@@ -36,6 +36,7 @@ def _models(prec):
         models.append(m)
         outs.append([torch.full((nb * 8,), 0xAB, dtype=torch.uint8, device=DEV) for _ in formats])
         dlist.append((desc, odesc, params))
+    torch.cuda.synchronize()            # the exports ran on the current stream
     return models, outs, dlist
 
 
@@ -149,6 +150,7 @@ def test_chained_batch_mixes_precisions():
     models, outs, dlist = _models(1)
     models[1].export(grid_bits=8, weight_prec=nt.PREC_FP16_FAST)
     models[2].export(grid_bits=8, weight_prec=nt.PREC_FP8_MMA)
+    torch.cuda.synchronize()
     with pytest.raises(nt.NTBCError):
         nt.Batch(models, outs, mode=nt.BATCH_QUEUE)
     batch = nt.Batch(models, outs)
