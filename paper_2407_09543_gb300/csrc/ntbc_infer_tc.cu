@@ -214,7 +214,8 @@ struct TcArgs {
     int img_bytes;            // weight image size (multiple of 16)
     int groups;
     int n;                    // blocks to process
-    const int32_t* ids;       // optional block ids (else 0..n-1)
+    const int32_t* ids;       // optional block ids (else first .. first + n - 1)
+    int first;
     int mode;                 // 0 pack, 1 raw outputs
     int ub;                   // blocks per work unit (128, or 64)
     int act;                  // A-operand format (kActF16, kActSplit, kActE4M3)
@@ -646,7 +647,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             const TcNet& net = args.net[1];
             int k = unit * ub + r;
             bool valid = r < ub && k < args.n;
-            int b = valid ? (args.ids ? args.ids[k] : k) : 0;
+            int b = valid ? (args.ids ? args.ids[k] : args.first + k) : 0;
             int bx, by;
             block_xy(b, mv.bw, args.inv_bw, bx, by);
             gather_row<ACT>(mv.endpoint, esrc, lvl + NTBC_MAX_LEVELS, fs[1], ((float)bx + 0.5f) * args.inv_bw,
@@ -712,7 +713,7 @@ __device__ __forceinline__ bool process_unit(const TcArgs& args, const GridSrc& 
             int blk = tile * 8 + r / 16, i = r & 15;
             int k = unit * ub + blk;
             bool valid = k < args.n;
-            int b = valid ? (args.ids ? args.ids[k] : k) : 0;
+            int b = valid ? (args.ids ? args.ids[k] : args.first + k) : 0;
             int bx, by;
             block_xy(b, mv.bw, args.inv_bw, bx, by);
             int x = 4 * bx + (i & 3), y = 4 * by + (i >> 2);
@@ -1210,11 +1211,18 @@ struct TcLaunch {
     size_t smem;
 };
 
+// ub_force: 0 for the unit size tc_groups picks, or kTcUnitBlocks / 2
 static ntbc_status tc_plan(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
-                           float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, TcLaunch* L) {
+                           float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, TcLaunch* L,
+                           int ub_force = 0) {
     TcArgs a = tc_args(m);
     size_t smem = 0;
-    a.groups = tc_groups(a, m->desc.n_textures, a.act, &smem, &a.ub);
+    if (ub_force) {
+        a.ub = ub_force;
+        a.groups = tc_groups_ub(a, m->desc.n_textures, a.act, ub_force, &smem, 256);
+    } else {
+        a.groups = tc_groups(a, m->desc.n_textures, a.act, &smem, &a.ub);
+    }
     if (a.groups == 0) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: shared memory too small for this model");
     if (!tc_coords_ok(a)) return fail(NTBC_EUNSUPPORTED, "tensor-core inference: a grid level is too fine for the texture extent");
     a.n = n;
@@ -1266,13 +1274,37 @@ static cudaError_t tc_enqueue(const TcLaunch& L, cudaStream_t s, bool chained) {
     return cudaLaunchKernelEx(&cfg, L.kernel, L.a, L.img, L.csrc, L.esrc, L.outs, L.e_out, L.c_out);
 }
 
+// The units of one launch run in rounds of (grid x groups); when the grid is full and the last
+// round is partial, that round's blocks go to a second launch in half-size units (chained by
+// programmatic dependent launch, so its CTAs take the SMs the first launch's CTAs leave): the
+// tail then takes about half a unit's time at nearly full occupancy instead of a whole unit's
+// time on part of the SMs.
 ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int* strides, const int32_t* ids, int n,
                       float* e_out, float* c_out, const GridSrc& csrc, const GridSrc& esrc, cudaStream_t s,
                       bool chained) {
     TcLaunch L;
     ntbc_status st = tc_plan(m, blocks_out, strides, ids, n, e_out, c_out, csrc, esrc, &L);
     if (st != NTBC_OK) return st;
-    NTBC_CHECK_CUDA(tc_enqueue(L, s, chained));
+    int dev = 0, sms = 0;
+    NTBC_CHECK_CUDA(cudaGetDevice(&dev));
+    NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per_round = L.grid * L.a.groups;
+    const int units = (n + L.a.ub - 1) / L.a.ub;
+    const int head = L.grid == sms && L.a.ub == kTcUnitBlocks ? units / per_round * per_round * L.a.ub : n;
+    if (head > 0 && head < n) {
+        TcLaunch T;
+        const int rest = n - head;
+        st = tc_plan(m, blocks_out, strides, ids ? ids + head : nullptr, rest,
+                     e_out ? e_out + (size_t)head * L.a.mv.endpoint.out_dim : nullptr,
+                     c_out ? c_out + (size_t)head * 16 * L.a.mv.color.out_dim : nullptr, csrc, esrc, &T, kTcUnitBlocks / 2);
+        if (st != NTBC_OK) return st;
+        if (!ids) T.a.first = head;
+        L.a.n = head;
+        NTBC_CHECK_CUDA(tc_enqueue(L, s, chained));
+        NTBC_CHECK_CUDA(tc_enqueue(T, s, true));
+    } else {
+        NTBC_CHECK_CUDA(tc_enqueue(L, s, chained));
+    }
     NTBC_CHECK_LAUNCH("ntbc inference (tcgen05)");
     return NTBC_OK;
 }

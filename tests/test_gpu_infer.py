@@ -400,6 +400,34 @@ def test_full_size_4k_sampled():
     assert total_m <= 0.001 * total_f
 
 
+def test_split_tail_launch_equals_unsplit_launch():
+    """On a full grid the single-material launch sends its partial last round to a second,
+    chained launch of half-size work units. The 4096^2 material's blocks must equal those of
+    the work-queue batch launch (128-block units throughout, no split) and of the host
+    delivery (ranges, only the last one split), bit for bit: the units differ only in how
+    many rows their endpoint MMA holds."""
+    w = nt.configs.WORKLOADS["mat4k"]
+    formats = [1, 1, 4, 4]
+    desc, odesc = descs.case_descs(nt, formats, 4096, w.levels, w.min_res, w.max_res, 3, "selu")
+    params = synth.random_params_like(descs.init_params(odesc, 5), seed=6)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    torch.cuda.synchronize()
+    single = gpu_blocks(model, desc)
+    n = odesc.n_blocks
+    outs = [torch.zeros(n * 8, dtype=torch.uint8, device=DEV) for _ in formats]
+    batch = nt.Batch([model], [outs], mode=nt.BATCH_QUEUE)
+    batch.infer()
+    torch.cuda.synchronize()
+    host = [torch.empty(n * 8, dtype=torch.uint8).pin_memory() for _ in formats]
+    model.infer_to_host(host, chunks=3)
+    torch.cuda.synchronize()
+    for t in range(len(formats)):
+        q = outs[t].cpu().numpy().reshape(-1, 8)
+        np.testing.assert_array_equal(single[t], q)
+        np.testing.assert_array_equal(single[t], host[t].numpy().reshape(-1, 8))
+    batch.close()
+
+
 def test_full_size_4k_sampled_fp8_arithmetic():
     """The 4096^2 four-texture workload in the FP8 arithmetic: the calibration exponents over
     the whole material's sample equal the oracle's, and sampled blocks meet the FP8 bars."""
