@@ -498,10 +498,11 @@ def run_reference(args):
 # used only when no live measurement is given
 MUFU_PER_SM_PER_CLK = 32
 SM_COUNT = 152
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# infer_tc_kernel<SPLIT=true> on the 4096^2 four-texture material, from one ncu capture of the
-# current kernel; None for any other workload or precision
-INFER_TC_DRAM_BYTES_MAT4K = 16_961_536
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one inference pass of the split
+# FP16 kernel on the 4096^2 four-texture material (its full-rounds launch and its split tail
+# launch, summed), from one ncu capture of the current kernels; None for any other workload or
+# precision
+INFER_TC_DRAM_BYTES_MAT4K = 16_368_896 + 6_144 + 794_368     # full rounds (read + write), tail (read)
 SM_MAX_GHZ = 2.07
 
 
@@ -558,7 +559,7 @@ def inference_roofline(nt, desc, ms, traffic=None, mufu_peak=None):
             "MUFU exp2: 152 SM x 32/clk (measured per-SM rate) x 2.07 GHz")
     roofline = {"bound": "alu", "achieved": round(exps / sec / 1e12, 4), "peak": round(mufu_peak / 1e12, 4),
                 "unit": "Texp/s", "frac": round(t_xu / sec, 4), "traffic": traffic,
-                "kernel": "infer_tc_kernel<SPLIT=true>",
+                "kernel": "infer_tc_kernel<split FP16> (full rounds of 128-block units + a chained tail of 64-block units; per pass)",
                 "peak_kind": kind + "; tensor / HBM terms against MEASURED_PEAKS (of measured)"}
     terms = {"t_tensor_ms": round(t_tc * 1e3, 4), "t_mufu_ms": round(t_xu * 1e3, 4), "t_hbm_ms": round(t_hbm * 1e3, 4),
              "tensor_frac_of_measured": round(t_tc / sec, 4), "hbm_frac_of_measured": round(t_hbm / sec, 4),
@@ -764,6 +765,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     ms = max_over_ranks(float(np.mean(times)), world, dev)
+    launches_per_pass = model.infer_plan()[0]                  # the full rounds, and a split tail
     headline_blocks = [o.cpu().numpy() for o in outs]          # for the full-material oracle check
     ours_psnr = psnr_list(nt, torch, mat, outs, side)
     ours_ssim = ssim_list(nt, torch, mat, outs, side)
@@ -1009,7 +1011,7 @@ def main():
                 "h2d_bytes_per_step": int(blob.numel()), "d2h_bytes_per_step": int(nblk * 8 * len(FORMATS)),
                 **e2e_parts},
         "clocks": clk,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_pass,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

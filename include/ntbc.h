@@ -289,6 +289,16 @@ ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out
 ntbc_status ntbc_infer_to_host(ntbc_model* model, uint8_t* const* host_out, int chunks, void* stream);
 
 /*
+ * The launch plan of ntbc_infer_to_bc for an exported model (host-only query; no launch):
+ * launches = kernel launches per call (1; or 2 on the tensor-core path when a full grid's last
+ * round is partial: its blocks go to a chained launch of half-size work units),
+ * unit_blocks = blocks per work unit (128 or 64; 0 for the FP32 SIMT kernel),
+ * units_in_flight = work units one launch runs at once (warpgroups x CTAs; 0 for FP32).
+ * NTBC_EINVAL for a null argument or a model that has not been exported.
+ */
+ntbc_status ntbc_infer_plan(const ntbc_model* model, int* launches, int* unit_blocks, int* units_in_flight);
+
+/*
  * Failure-path check of the bounded device waits: one thread polls an mbarrier that nothing
  * will complete, with the wait loop of the tensor-core kernels limited to `polls` polls
  * (1 .. the kernels' own limit, 2^18, about one second). Returns NTBC_ETIMEOUT when the wait gave up (the

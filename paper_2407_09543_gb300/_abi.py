@@ -130,6 +130,7 @@ _SIGS = {
     "ntbc_vjp": (c_int, [_P, _P, c_int, c_int, _P, _P, _P, _P, _P, _P]),
     "ntbc_adam_step": (c_int, [_P, _P, ctypes.c_long, ctypes.c_long, ctypes.POINTER(TrainConfig), _P]),
     "ntbc_sample_blocks": (c_int, [ctypes.c_uint64, ctypes.c_long, c_int, c_int, _P, _P]),
+    "ntbc_infer_plan": (c_int, [_P, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "ntbc_batch_create": (c_int, [ctypes.POINTER(_P), c_int, ctypes.POINTER(ctypes.POINTER(_P)), ctypes.POINTER(_P)]),
     "ntbc_batch_create_mode": (c_int, [ctypes.POINTER(_P), c_int, ctypes.POINTER(ctypes.POINTER(_P)), c_int,
                                        ctypes.POINTER(_P)]),
@@ -286,6 +287,12 @@ class Model:
         block; the blocks are there once the stream has been synchronised."""
         arr = (_P * len(host_out))(*[_ptr(b) for b in host_out])
         _check(lib.ntbc_infer_to_host(self.handle, arr, chunks, _stream(stream)))
+
+    def infer_plan(self):
+        """(kernel launches per infer_to_bc call, blocks per work unit, work units in flight)."""
+        l, u, f = c_int(), c_int(), c_int()
+        _check(lib.ntbc_infer_plan(self.handle, ctypes.byref(l), ctypes.byref(u), ctypes.byref(f)))
+        return l.value, u.value, f.value
 
     def forward(self, block_ids, e_hat, c_hat, stream=None):
         _check(lib.ntbc_forward(self.handle, _ptr(block_ids), block_ids.numel(), _ptr(e_hat), _ptr(c_hat),

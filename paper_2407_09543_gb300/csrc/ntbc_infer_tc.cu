@@ -1274,6 +1274,13 @@ static cudaError_t tc_enqueue(const TcLaunch& L, cudaStream_t s, bool chained) {
     return cudaLaunchKernelEx(&cfg, L.kernel, L.a, L.img, L.csrc, L.esrc, L.outs, L.e_out, L.c_out);
 }
 
+// blocks of a planned launch that go to its full rounds (n when the launch is not split)
+static int tc_split_head(const TcLaunch& L, int n, int sms) {
+    const int per_round = L.grid * L.a.groups;
+    const int units = (n + L.a.ub - 1) / L.a.ub;
+    return L.grid == sms && L.a.ub == kTcUnitBlocks && per_round > 0 ? units / per_round * per_round * L.a.ub : n;
+}
+
 // The units of one launch run in rounds of (grid x groups); when the grid is full and the last
 // round is partial, that round's blocks go to a second launch in half-size units (chained by
 // programmatic dependent launch, so its CTAs take the SMs the first launch's CTAs leave): the
@@ -1288,9 +1295,7 @@ ntbc_status tc_launch(const ntbc_model* m, uint8_t* const* blocks_out, const int
     int dev = 0, sms = 0;
     NTBC_CHECK_CUDA(cudaGetDevice(&dev));
     NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int per_round = L.grid * L.a.groups;
-    const int units = (n + L.a.ub - 1) / L.a.ub;
-    const int head = L.grid == sms && L.a.ub == kTcUnitBlocks ? units / per_round * per_round * L.a.ub : n;
+    const int head = tc_split_head(L, n, sms);
     if (head > 0 && head < n) {
         TcLaunch T;
         const int rest = n - head;
@@ -1361,6 +1366,32 @@ ntbc_status ntbc_wait_probe(long long polls, double* seconds, void* stream) {
     if (seconds) *seconds = sec;
     const int gave_up = *reinterpret_cast<const int*>(&h[1]);
     if (gave_up) return fail(NTBC_ETIMEOUT, "bounded wait gave up after %lld polls (%.3f s)", polls, sec);
+    return NTBC_OK;
+}
+
+ntbc_status ntbc_infer_plan(const ntbc_model* m, int* launches, int* unit_blocks, int* units_in_flight) {
+    using namespace ntbc;
+    clear_error();
+    if (!m || !launches || !unit_blocks || !units_in_flight) return fail(NTBC_EINVAL, "null argument");
+    if (m->grid_bits < 0) return fail(NTBC_EINVAL, "model has not been exported (call ntbc_model_export or ntbc_model_load)");
+    *launches = 1;
+    *unit_blocks = 0;
+    *units_in_flight = 0;
+    if (m->weight_prec == NTBC_PREC_FP32) return NTBC_OK;             // the SIMT kernel: one launch
+    const int n = (m->desc.width / 4) * (m->desc.height / 4);
+    GridSrc csrc, esrc;
+    ntbc_status st = grid_sources(m, csrc, esrc);
+    if (st != NTBC_OK) return st;
+    TcLaunch L;
+    st = tc_plan(m, nullptr, nullptr, nullptr, n, nullptr, nullptr, csrc, esrc, &L);
+    if (st != NTBC_OK) return st;
+    int dev = 0, sms = 0;
+    NTBC_CHECK_CUDA(cudaGetDevice(&dev));
+    NTBC_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int head = tc_split_head(L, n, sms);
+    *launches = head > 0 && head < n ? 2 : 1;
+    *unit_blocks = L.a.ub;
+    *units_in_flight = L.grid * L.a.groups;
     return NTBC_OK;
 }
 
