@@ -428,6 +428,29 @@ def test_split_tail_launch_equals_unsplit_launch():
     batch.close()
 
 
+def test_infer_plan():
+    """The launch plan: a small material fits one partial round (one launch); the 4096^2
+    material runs full rounds plus a split tail (two launches); FP32 is the SIMT kernel."""
+    mat, desc, odesc, params = make_case(side=64)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    launches, ub, flight = model.infer_plan()
+    assert launches == 1 and ub == 128 and flight > 0
+    model.export(grid_bits=8, weight_prec=nt.PREC_FP32)
+    assert model.infer_plan() == (1, 0, 0)
+    w = nt.configs.WORKLOADS["mat4k"]
+    desc4, odesc4 = descs.case_descs(nt, [1, 1, 4, 4], 4096, w.levels, w.min_res, w.max_res, 3, "selu")
+    big = nt.Model(desc4)
+    big.export(grid_bits=8, weight_prec=nt.PREC_FP16)
+    launches, ub, flight = big.infer_plan()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ub == 128 and flight % sms == 0
+    units = odesc4.n_blocks // 128
+    assert launches == (2 if units % flight else 1)
+    unexported = nt.Model(desc)
+    with pytest.raises(nt.NTBCError):
+        unexported.infer_plan()
+
+
 def test_full_size_4k_sampled_fp8_arithmetic():
     """The 4096^2 four-texture workload in the FP8 arithmetic: the calibration exponents over
     the whole material's sample equal the oracle's, and sampled blocks meet the FP8 bars."""

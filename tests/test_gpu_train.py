@@ -128,8 +128,11 @@ def test_training_gains_over_untrained_network():
 def test_checkpoint_resume_matches_uninterrupted_encode(precision):
     """An encode split at a step, its checkpoint (FP32 master parameters, Adam moments, step)
     written out and loaded into a fresh model, then resumed, ends where an uninterrupted encode
-    ends, up to the rounding order of the grid scatter's floating-point atomics, which makes two
-    uninterrupted encodes differ too; the checkpoint round trip itself is exact."""
+    ends, up to the rounding order of the grid scatter's floating-point atomics, which makes
+    uninterrupted encodes differ too; the checkpoint round trip itself is exact. The spread of
+    uninterrupted encodes is chaotic (the argmax amplifies a rounding difference or not): two of
+    them were measured identical in one run and 0.9 % apart in another, so the noise reference is
+    the largest difference among three of them."""
     s = setup(grid_scale=0)
     desc, material = s["desc"], s["material"]
     flat0 = _dev(nt.configs.flatten(desc, s["params"]))
@@ -147,9 +150,10 @@ def test_checkpoint_resume_matches_uninterrupted_encode(precision):
         torch.cuda.synchronize()
         return out.cpu().numpy().astype(np.float64)
 
-    a, c = fresh(), fresh()
+    a, c, e = fresh(), fresh(), fresh()
     a.train(material, cfg)
     c.train(material, cfg)
+    e.train(material, cfg)
     first = fresh()
     first.train_range(material, cfg, 0, 20)
     ck = torch.empty(first.checkpoint_size(), dtype=torch.uint8)
@@ -161,10 +165,11 @@ def test_checkpoint_resume_matches_uninterrupted_encode(precision):
     assert torch.equal(ck, ck2)
     losses = b.train_range(material, cfg, 20, total)
     assert all(np.isfinite(losses))
-    pa, pb, pc = params(a), params(b), params(c)
-    noise = np.linalg.norm(pa - pc) / np.linalg.norm(pa)
-    resumed = np.linalg.norm(pa - pb) / np.linalg.norm(pa)
-    assert resumed <= 5 * noise + 1e-6, (resumed, noise)
+    pa, pb, pc, pe = params(a), params(b), params(c), params(e)
+    norm = np.linalg.norm(pa)
+    noise = max(np.linalg.norm(pa - pc), np.linalg.norm(pa - pe), np.linalg.norm(pc - pe)) / norm
+    resumed = min(np.linalg.norm(pb - q) for q in (pa, pc, pe)) / norm
+    assert resumed <= 3 * noise + 1e-6, (resumed, noise)
     # a checkpoint of another model, or with a damaged header, is refused
     other = nt.Model(nt.configs.model_desc(list(s["mat"].formats), 64, 3, 4, 9, 2, nt.ACT_SELU))
     with pytest.raises(nt.NTBCError):
