@@ -265,9 +265,12 @@ ntbc_status ntbc_model_load(ntbc_model* model, const uint8_t* blob, size_t size,
 
 /*
  * NTBC inference to BC blocks for every texture of the model's material, in one
- * fused launch: grid lookup + dequantisation, endpoint MLP per block, colour MLP
+ * fused kernel: grid lookup + dequantisation, endpoint MLP per block, colour MLP
  * per texel, endpoint quantisation, per-texel argmax of -||c_hat - p_n||, index
- * packing and 8-byte block stores. Uses the exported form (ntbc_model_export).
+ * packing and 8-byte block stores. Uses the exported form (ntbc_model_export). One
+ * launch, or on the tensor-core path two when a full grid's last round is partial (that
+ * round's blocks in half-size work units, chained by programmatic dependent launch;
+ * ntbc_infer_plan tells which). Enqueued on `stream`; asynchronous.
  *   blocks_out  host array of n_textures DEVICE pointers, each (w/4)*(h/4)*8 bytes
  */
 ntbc_status ntbc_infer_to_bc(const ntbc_model* model, uint8_t* const* blocks_out, void* stream);
