@@ -428,6 +428,28 @@ def test_split_tail_launch_equals_unsplit_launch():
     batch.close()
 
 
+def test_forward_split_tail_outputs_land_in_place():
+    """ntbc_forward over every block of the 4096^2 material runs as full rounds plus a split
+    tail whose raw outputs go to the tail's offset in e_hat / c_hat: they must equal a forward
+    of just the last 2000 blocks (one partial round, no split), bit for bit, and a sample of
+    the head must equal a forward of those blocks alone."""
+    w = nt.configs.WORKLOADS["mat4k"]
+    desc, odesc = descs.case_descs(nt, [1, 1, 4, 4], 4096, w.levels, w.min_res, w.max_res, 3, "selu")
+    params = synth.random_params_like(descs.init_params(odesc, 7), seed=8)
+    model = gpu_model(desc, params, grid_bits=8, weight_prec=nt.PREC_FP16)
+    n = odesc.n_blocks
+    assert model.infer_plan()[0] == 2
+    lay = model.layout
+    ids = torch.arange(n, dtype=torch.int32, device=DEV)
+    e = torch.empty(n, lay.out_endpoint, device=DEV)
+    c = torch.empty(n, 16, lay.out_color, device=DEV)
+    model.forward(ids, e, c)
+    for sel in (np.arange(n - 2000, n), np.sort(np.random.default_rng(2).choice(n - 2000, 500, replace=False))):
+        es, cs = gpu_forward(model, sel)
+        np.testing.assert_array_equal(e[torch.from_numpy(sel).to(DEV)].cpu().numpy().astype(np.float64), es)
+        np.testing.assert_array_equal(c[torch.from_numpy(sel).to(DEV)].cpu().numpy().astype(np.float64), cs)
+
+
 def test_infer_plan():
     """The launch plan: a small material fits one partial round (one launch); the 4096^2
     material runs full rounds plus a split tail (two launches); FP32 is the SIMT kernel."""
