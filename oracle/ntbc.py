@@ -274,21 +274,22 @@ def mlp_forward(layers, x, kind, rnd=None):
 
 def mlp_backward(layers, cache, y, g_y, kind, rnd=None):
     """Returns (g_x, [(gW, gb), ...]). With rnd, every matrix-product operand of the backward
-    (the deltas and the weights; the activations were rounded by the forward) is rounded,
-    and the activation derivative is taken from the rounded activation."""
+    (the deltas, the weights and the cached layer inputs) is rounded, and the activation
+    derivative is taken from the rounded activation; the forward may have run on exact
+    operands (a cached input the forward rounded already is unchanged by rounding again)."""
     grads = [None] * len(layers)
     r = rnd or (lambda v: v)
     g = r(g_y * y * (1.0 - y))                                # through the sigmoid
     for i in range(len(layers) - 1, -1, -1):
         W = r(np.asarray(layers[i][0], np.float64))
-        h, _ = cache[i]
+        h = r(cache[i][0])
         grads[i] = (g.T @ h, g.sum(axis=0))
         g_h = g @ W
         if i > 0:
             if rnd is None:
                 g = g_h * _act_grad(cache[i - 1][1], kind)
             else:
-                g = r(g_h * _act_grad_from_out(cache[i][0], kind))
+                g = r(g_h * _act_grad_from_out(h, kind))
         else:
             g = g_h
     return g, grads
@@ -655,7 +656,11 @@ def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_
     textures: list of uint8 arrays (H x W x 3 or H x W); ref_blocks: list of [nblocks, 8].
     soft=True evaluates the surrogate in which the forward decode is the softmax
     expectation itself (the backward is then that surrogate's exact gradient).
-    bf16=True rounds every MLP matrix-product operand to BF16 (forward and backward).
+    bf16=True takes the tensor-core training arithmetic: the colour MLP's matrix-product operands
+    rounded to BF16 in the forward and the backward; the endpoint MLP's forward on exact operands
+    (its outputs steer the straight-through softmax, which amplifies an output error 1/T; the
+    kernel splits each forward operand into BF16 hi + lo parts, ~2^-16 relative) and its backward
+    on BF16 operands.
     Returns (losses dict, grads dict shaped like params).
     """
     block_ids = np.asarray(block_ids, np.int64)
@@ -688,7 +693,7 @@ def losses_and_grads(desc, params, textures, ref_blocks, block_ids, T=0.01, qat_
     s, tt = block_coords(desc.blocks_x, desc.blocks_y, block_ids % desc.blocks_x, block_ids // desc.blocks_x)
     xe, ecache_g = grid_lookup(eg, s, tt)
     rnd = bf16_round if bf16 else None
-    e_hat, ecache = mlp_forward(params["endpoint_mlp"], xe, desc.activation, rnd)
+    e_hat, ecache = mlp_forward(params["endpoint_mlp"], xe, desc.activation)
     L_e = np.mean((e_hat - e_ref) ** 2)
     g_e = 2.0 * (e_hat - e_ref) / e_hat.size
     n_cd = nb * 16 * C_out

@@ -509,7 +509,8 @@ struct AdamImages {
     int on;
 };
 
-// image element of parameter e (W[o][i] at row o, column i; b[o] at row o, column in)
+// image element of parameter e (W[o][i] at row o, column i; b[o] at row o, column in), and its
+// lo part where the network has one
 __device__ __forceinline__ void image_store(const AdamImages& im, long long e, float w) {
 #pragma unroll 1
     for (int k = 0; k < 2; ++k) {
@@ -527,7 +528,11 @@ __device__ __forceinline__ void image_store(const AdamImages& im, long long e, f
                 col = L.in;
             }
             if (row >= 0) {
-                *reinterpret_cast<__nv_bfloat16*>(im.img[k] + L.img + core_byte(row, col, L.K)) = __float2bfloat16_rn(w);
+                unsigned char* t = im.img[k] + L.img + core_byte(row, col, L.K);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+                *reinterpret_cast<__nv_bfloat16*>(t) = hi;
+                if (n.lo_img)          // the endpoint network's lo parts
+                    *reinterpret_cast<__nv_bfloat16*>(t + n.lo_img) = __float2bfloat16_rn(w - __bfloat162float(hi));
                 return;
             }
         }

@@ -55,6 +55,26 @@ __device__ __forceinline__ void st_chunk_bf16(unsigned char* tile, int r, int kg
     *reinterpret_cast<uint4*>(tile + chunk_byte(r, kg, C)) = u;
 }
 
+// the BF16 pair nearest to what the BF16 pair `hi` leaves of (a, b): hi + lo carries about 16
+// significant bits of each value (the differences are exact in FP32)
+__device__ __forceinline__ uint32_t pack_bf16x2_lo(float a, float b, uint32_t hi) {
+    const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hi));
+    return pack_bf16x2(a - h.x, b - h.y);
+}
+
+// one chunk as a hi tile and a lo tile (the endpoint network's split forward operands)
+__device__ __forceinline__ void st_chunk_bf16_split(unsigned char* hi_tile, unsigned char* lo_tile, int r, int kg, int C,
+                                                    const float* v) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        h[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+        l[j] = pack_bf16x2_lo(v[2 * j], v[2 * j + 1], h[j]);
+    }
+    *reinterpret_cast<uint4*>(hi_tile + chunk_byte(r, kg, C)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo_tile + chunk_byte(r, kg, C)) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 __device__ __forceinline__ void ld_chunk_bf16(const unsigned char* tile, int r, int kg, int C, float* v) {
     uint4 u = *reinterpret_cast<const uint4*>(tile + chunk_byte(r, kg, C));
     uint32_t w[4] = {u.x, u.y, u.z, u.w};
@@ -443,9 +463,10 @@ __device__ __forceinline__ void endpoint_block_row(const TrArgs& a, int s, bool 
 // grid features of one sample (FP32 master grid, QAT fake quantisation while active)
 // straight into the BF16 X row: level l -> columns 2l, 2l + 1
 // the two features of level l at (u, v) (bilinear over the FP32 grid, fake-quantised in the
-// QAT phase) as one BF16 pair in row r of the X tile
+// QAT phase) as one BF16 pair in row r of the X tile (and, with Xlo, their lo parts in Xlo)
 __device__ __forceinline__ void gather_level_train(const NetView& nv, const GridSrc& src, int l, float u, float v,
-                                                   unsigned char* X, int r, int K0, int qat_bits) {
+                                                   unsigned char* X, int r, int K0, int qat_bits,
+                                                   unsigned char* Xlo = nullptr) {
     Bilinear bl = bilinear_at(nv.res[l], u, v);
     const float* gp = src.f32 + nv.grid_off[l] + bl.base;
     float2 p00 = __ldg(reinterpret_cast<const float2*>(gp));
@@ -461,7 +482,10 @@ __device__ __forceinline__ void gather_level_train(const NetView& nv, const Grid
     }
     float f0 = bl.w00 * p00.x + bl.w01 * p01.x + bl.w10 * p10.x + bl.w11 * p11.x;
     float f1 = bl.w00 * p00.y + bl.w01 * p01.y + bl.w10 * p10.y + bl.w11 * p11.y;
-    *reinterpret_cast<uint32_t*>(X + chunk_byte(r, (2 * l) >> 3, K0) + ((2 * l) & 7) * 2) = pack_bf16x2(f0, f1);
+    const int off = chunk_byte(r, (2 * l) >> 3, K0) + ((2 * l) & 7) * 2;
+    const uint32_t hi = pack_bf16x2(f0, f1);
+    *reinterpret_cast<uint32_t*>(X + off) = hi;
+    if (Xlo) *reinterpret_cast<uint32_t*>(Xlo + off) = pack_bf16x2_lo(f0, f1, hi);
 }
 
 __device__ __forceinline__ void gather_row_train(const NetView& nv, const GridSrc& src, float u, float v,
@@ -513,6 +537,7 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
     for (int l = 0; l < 3; ++l) G.A[l] = gb + sl.a_off[l];
     G.D = gb + sl.d_off;
     G.bar = reinterpret_cast<uint64_t*>(gb + sl.bar_off);
+    unsigned char* const Alo = gb + sl.alo_off;     // endpoint: lo parts of the hidden activations
     const int r = G.r;
     if (tile_thread) {
         // constant columns: the bias column of every hidden tile (64 = 1) and of X (in_dim = 1)
@@ -525,7 +550,7 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
 #pragma unroll
             for (int j = 0; j < 8; ++j) v8[j] = kg * 8 + j == net.in_dim ? 1.f : 0.f;
             st_chunk_bf16(G.X, r, kg, net.K0, v8);
-            st_chunk_bf16(G.X2, r, kg, net.K0, v8);
+            if (COLOR) st_chunk_bf16(G.X2, r, kg, net.K0, v8);   // endpoint: X2 holds lo parts (0 here)
         }
         if (r == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(G.bar)), "r"(1));
@@ -610,7 +635,7 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                 int x, y;
                 sample_coords(a.mv, false, a.ids, sb < a.B ? sb : a.B - 1, u, v, x, y);
                 if (lv == 0) UV[rr] = make_float2(u, v);
-                gather_level_train(nv, a.src, lv, u, v, G.X, rr, net.K0, qat_bits);
+                gather_level_train(nv, a.src, lv, u, v, G.X, rr, net.K0, qat_bits, G.X2);
             }
             proxy_fence();
             __syncthreads();
@@ -641,6 +666,20 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                         uint64_t bd = umma_desc(smem_u32(smem + Ly.img) + kc * 256, 128, (Ly.K / 8) * 128);
                         umma_f16(R, ad, bd, idesc, kc > 0);
                     }
+                    if constexpr (!COLOR) {
+                        // split operands: + A_lo W_hi + A_hi W_lo (the lo x lo term, ~2^-16 of the
+                        // product, is left out)
+                        const unsigned char* src_lo = l == 0 ? G.X2 : Alo;
+                        for (int kc = 0; kc < Ly.K / 16; ++kc) {
+                            uint64_t ad = umma_desc(smem_u32(src) + kc * 256, 128, (C / 8) * 128);
+                            uint64_t al = umma_desc(smem_u32(src_lo) + kc * 256, 128, (C / 8) * 128);
+                            uint64_t bd = umma_desc(smem_u32(smem + Ly.img) + kc * 256, 128, (Ly.K / 8) * 128);
+                            uint64_t bl = umma_desc(smem_u32(smem + net.lo_img + Ly.img) + kc * 256, 128,
+                                                    (Ly.K / 8) * 128);
+                            umma_f16(R, al, bd, idesc, 1);
+                            umma_f16(R, ad, bl, idesc, 1);
+                        }
+                    }
                     umma_commit(G.bar);
                 }
                 tr_wait(G, phase, abort);
@@ -663,8 +702,10 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                         tmem_wait_ld_regs<16>(z);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) z[j] = act_fast(z[j], act);
-                        st_chunk_bf16(G.A[l], r, 2 * qw, kTrHidCols, z);
-                        st_chunk_bf16(G.A[l], r, 2 * qw + 1, kTrHidCols, z + 8);
+                        // hi parts for the next layer and the backward, lo parts for the next layer
+                        // (layer l's MMAs, the last readers of the lo tile, have completed)
+                        st_chunk_bf16_split(G.A[l], Alo, r, 2 * qw, kTrHidCols, z);
+                        st_chunk_bf16_split(G.A[l], Alo, r, 2 * qw + 1, kTrHidCols, z + 8);
                     }
                 }
             }
@@ -995,7 +1036,7 @@ ntbc_status train_tc_reduce(const TrNet& cnet, const float* cpart, int crows, co
 
 // BF16 weight images of both networks (blockIdx.y: colour, endpoint): per layer the [N][K]
 // tile (W in columns 0..in-1, the bias in column `in`, zeros elsewhere), canonical K-major
-// core-matrix layout
+// core-matrix layout; a network with lo_img also gets the lo parts, w - bf16(w) in BF16
 __global__ void train_image_kernel(const float* __restrict__ params, TrNet net0, TrNet net1,
                                    __nv_bfloat16* __restrict__ img0, __nv_bfloat16* __restrict__ img1) {
     const TrNet& net = blockIdx.y ? net1 : net0;
@@ -1010,7 +1051,10 @@ __global__ void train_image_kernel(const float* __restrict__ params, TrNet net0,
                 if (k < Ly.in) w = params[Ly.w_off + (long long)n * Ly.in + k];
                 else if (k == Ly.in) w = params[Ly.b_off + n];
             }
-            t[core_byte(n, k, Ly.K) / 2] = __float2bfloat16_rn(w);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            t[core_byte(n, k, Ly.K) / 2] = hi;
+            if (net.lo_img)
+                t[(net.lo_img + core_byte(n, k, Ly.K)) / 2] = __float2bfloat16_rn(w - __bfloat162float(hi));
         }
     }
 }
@@ -1044,7 +1088,11 @@ TrNet train_tc_net_desc(const ModelView& mv, bool color) {
     }
     n.mlp_base = n.layer[0].w_off;
     n.mlp_params = (int)(n.layer[nv.n_layers - 1].b_off + n.layer[nv.n_layers - 1].out - n.mlp_base);
-    n.img_bytes = (img + 127) & ~127;
+    img = (img + 127) & ~127;
+    // the endpoint network's forward takes split operands (its outputs steer the straight-through
+    // softmax, where an output error is amplified 1/T): a second image of the weights' lo parts
+    n.lo_img = color ? 0 : img;
+    n.img_bytes = color ? img : 2 * img;
     return n;
 }
 
@@ -1063,6 +1111,8 @@ static TrSmem train_tc_smem(const TrNet& n) {
         s.a_off[l] = o;
         if (l < n.n_layers - 1) o += kTrRows * kTrHidCols * 2;
     }
+    s.alo_off = o;
+    if (n.lo_img) o += kTrRows * kTrHidCols * 2;
     s.d_off = o;
     o += kTrRows * 64 * 2 + kTrPad;
     s.bar_off = o;

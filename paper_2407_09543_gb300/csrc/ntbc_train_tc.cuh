@@ -20,7 +20,9 @@ struct TrLayer {
 struct TrNet {
     int n_layers, K0, in_dim, out_dim, out_pad;
     TrLayer layer[NTBC_MAX_MLP_LAYERS];
-    int img_bytes;
+    int img_bytes;            // hi tiles, then (lo_img > 0) the lo tiles at the same offsets + lo_img
+    int lo_img;               // endpoint network: byte offset of the weights' lo parts (w - bf16(w),
+                              // rounded to BF16; hi + lo carries ~16 bits), 0 for the colour network
     long long mlp_base;       // parameter offset of the network's first MLP weight
     int mlp_params;           // MLP parameters of the network (contiguous from mlp_base)
 };
@@ -28,7 +30,9 @@ struct TrNet {
 struct TrSmem {               // byte offsets: weight image at 0, then the groups
     int group_off, group_bytes;
     int x_off, a_off[3], d_off, bar_off;   // inside a group
-    int x2_off;               // colour network: the second input tile (the helper gathers ahead)
+    int x2_off;               // colour network: the second input tile (the helper gathers ahead);
+                              // endpoint network: the lo parts of the input tile
+    int alo_off;              // endpoint network: the lo parts of the hidden activations [128][80]
     int stage_off;            // endpoint network: FP32 outputs and summed L_cd gradients, [128][out]
 };
 

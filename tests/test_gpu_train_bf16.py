@@ -2,15 +2,18 @@
 gradients of one step on the same weights and batch, ragged tiles, several tiles per
 warpgroup, QAT, and a full encode that gains over the untrained network like the FP32 path.
 
-The comparison is with the oracle's BF16-operand mode (every matrix-product operand --
-features, weights, biases, activations, deltas -- rounded to BF16, products and sums exact):
-what is left is FP32 against FP64 arithmetic, so the bar is 5e-3 per tensor (2e-3 on the
-losses). Against the plain FP64 oracle the BF16 rounding itself shows, amplified by the
-straight-through argmax (1/T inside softmax(d / T)): a few percent at T = 1 and up to ~30 %
-on the endpoint network at T = 0.01 -- the oracle's BF16 mode reproduces those figures, so they
-are the arithmetic's, not the kernel's. They are asserted too, per network and temperature,
-at the bounds FP64_BOUND states (measured errors with margin), so a kernel change that makes the
-BF16 arithmetic worse than the oracle's BF16 mode predicts cannot pass unnoticed.
+The comparison is with the oracle's mode for this arithmetic: the colour network's
+matrix-product operands (features, weights, biases, activations, deltas) rounded to BF16; the
+endpoint network's forward on exact operands (the kernel splits each into BF16 hi + lo parts,
+~2^-16 relative) and its backward on BF16 operands; products and sums exact. What is left is
+FP32 against FP64 arithmetic, so the bar is 5e-3 per tensor (2e-3 on the losses). Against the
+plain FP64 oracle the BF16 rounding itself shows, amplified by the straight-through argmax
+(1/T inside softmax(d / T)) where it enters a forward: a few percent on the colour network at
+T = 0.01, about 1 % on the endpoint network, whose forward is split (with BF16 forward operands
+it reached ~30 % there). The oracle's mode reproduces those figures, so they are the
+arithmetic's, not the kernel's. They are asserted too, per network and temperature, at the
+bounds FP64_BOUND states (measured errors with margin), so a kernel change that makes the
+arithmetic worse than the oracle's mode predicts cannot pass unnoticed.
 """
 import numpy as np
 import pytest
@@ -27,8 +30,9 @@ TOL_GRAD = 5e-3
 TOL_LOSS = 2e-3
 # relative gradient error of the BF16 pass against the plain FP64 oracle, per tensor group and
 # temperature: the BF16 operand rounding (2^-9) amplified by the straight-through softmax
-FP64_BOUND = {1.0: {"color_grid": 0.06, "color_mlp": 0.06, "endpoint_grid": 0.06, "endpoint_mlp": 0.06},
-              0.01: {"color_grid": 0.15, "color_mlp": 0.15, "endpoint_grid": 0.45, "endpoint_mlp": 0.45}}
+# (the oracle's mode measures at most 0.034 on the colour network, 0.012 on the endpoint one)
+FP64_BOUND = {1.0: {"color_grid": 0.06, "color_mlp": 0.06, "endpoint_grid": 0.03, "endpoint_mlp": 0.03},
+              0.01: {"color_grid": 0.15, "color_mlp": 0.15, "endpoint_grid": 0.03, "endpoint_mlp": 0.03}}
 
 
 def _dev(a):
