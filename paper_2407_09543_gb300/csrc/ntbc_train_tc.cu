@@ -62,9 +62,10 @@ __device__ __forceinline__ uint32_t pack_bf16x2_lo(float a, float b, uint32_t hi
     return pack_bf16x2(a - h.x, b - h.y);
 }
 
-// one chunk as a hi tile and a lo tile (the endpoint network's split forward operands)
-__device__ __forceinline__ void st_chunk_bf16_split(unsigned char* hi_tile, unsigned char* lo_tile, int r, int kg, int C,
-                                                    const float* v) {
+// one chunk as a hi tile of C columns and a lo tile of Clo columns (the endpoint network's
+// split forward operands)
+__device__ __forceinline__ void st_chunk_bf16_split(unsigned char* hi_tile, int C, unsigned char* lo_tile, int Clo, int r,
+                                                    int kg, const float* v) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -72,7 +73,7 @@ __device__ __forceinline__ void st_chunk_bf16_split(unsigned char* hi_tile, unsi
         l[j] = pack_bf16x2_lo(v[2 * j], v[2 * j + 1], h[j]);
     }
     *reinterpret_cast<uint4*>(hi_tile + chunk_byte(r, kg, C)) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo_tile + chunk_byte(r, kg, C)) = make_uint4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<uint4*>(lo_tile + chunk_byte(r, kg, Clo)) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 __device__ __forceinline__ void ld_chunk_bf16(const unsigned char* tile, int r, int kg, int C, float* v) {
@@ -537,7 +538,9 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
     for (int l = 0; l < 3; ++l) G.A[l] = gb + sl.a_off[l];
     G.D = gb + sl.d_off;
     G.bar = reinterpret_cast<uint64_t*>(gb + sl.bar_off);
-    unsigned char* const Alo = gb + sl.alo_off;     // endpoint: lo parts of the hidden activations
+    // endpoint: lo parts of the hidden activations, [128][64] over the delta tile (dead during
+    // the forward: the loss writes it after the last forward MMA has completed)
+    unsigned char* const Alo = gb + sl.alo_off;
     const int r = G.r;
     if (tile_thread) {
         // constant columns: the bias column of every hidden tile (64 = 1) and of X (in_dim = 1)
@@ -667,16 +670,20 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                         umma_f16(R, ad, bd, idesc, kc > 0);
                     }
                     if constexpr (!COLOR) {
-                        // split operands: + A_lo W_hi + A_hi W_lo (the lo x lo term, ~2^-16 of the
-                        // product, is left out)
+                        // split operands: + A_lo W_hi (over the 64 units of a hidden tile: the
+                        // constant bias input has no lo part) + A_hi W_lo (the lo x lo term,
+                        // ~2^-16 of the product, is left out)
                         const unsigned char* src_lo = l == 0 ? G.X2 : Alo;
+                        const int Clo = l == 0 ? net.K0 : 64;
+                        for (int kc = 0; kc < Clo / 16; ++kc) {
+                            uint64_t al = umma_desc(smem_u32(src_lo) + kc * 256, 128, (Clo / 8) * 128);
+                            uint64_t bd = umma_desc(smem_u32(smem + Ly.img) + kc * 256, 128, (Ly.K / 8) * 128);
+                            umma_f16(R, al, bd, idesc, 1);
+                        }
                         for (int kc = 0; kc < Ly.K / 16; ++kc) {
                             uint64_t ad = umma_desc(smem_u32(src) + kc * 256, 128, (C / 8) * 128);
-                            uint64_t al = umma_desc(smem_u32(src_lo) + kc * 256, 128, (C / 8) * 128);
-                            uint64_t bd = umma_desc(smem_u32(smem + Ly.img) + kc * 256, 128, (Ly.K / 8) * 128);
                             uint64_t bl = umma_desc(smem_u32(smem + net.lo_img + Ly.img) + kc * 256, 128,
                                                     (Ly.K / 8) * 128);
-                            umma_f16(R, al, bd, idesc, 1);
                             umma_f16(R, ad, bl, idesc, 1);
                         }
                     }
@@ -704,8 +711,8 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                         for (int j = 0; j < 16; ++j) z[j] = act_fast(z[j], act);
                         // hi parts for the next layer and the backward, lo parts for the next layer
                         // (layer l's MMAs, the last readers of the lo tile, have completed)
-                        st_chunk_bf16_split(G.A[l], Alo, r, 2 * qw, kTrHidCols, z);
-                        st_chunk_bf16_split(G.A[l], Alo, r, 2 * qw + 1, kTrHidCols, z + 8);
+                        st_chunk_bf16_split(G.A[l], kTrHidCols, Alo, 64, r, 2 * qw, z);
+                        st_chunk_bf16_split(G.A[l], kTrHidCols, Alo, 64, r, 2 * qw + 1, z + 8);
                     }
                 }
             }
@@ -1111,9 +1118,8 @@ static TrSmem train_tc_smem(const TrNet& n) {
         s.a_off[l] = o;
         if (l < n.n_layers - 1) o += kTrRows * kTrHidCols * 2;
     }
-    s.alo_off = o;
-    if (n.lo_img) o += kTrRows * kTrHidCols * 2;
     s.d_off = o;
+    s.alo_off = o;      // split forward: the lo activations [128][64] share the delta tile
     o += kTrRows * 64 * 2 + kTrPad;
     s.bar_off = o;
     o += 16;

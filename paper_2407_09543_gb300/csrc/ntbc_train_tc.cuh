@@ -32,7 +32,8 @@ struct TrSmem {               // byte offsets: weight image at 0, then the group
     int x_off, a_off[3], d_off, bar_off;   // inside a group
     int x2_off;               // colour network: the second input tile (the helper gathers ahead);
                               // endpoint network: the lo parts of the input tile
-    int alo_off;              // endpoint network: the lo parts of the hidden activations [128][80]
+    int alo_off;              // endpoint network: the lo parts of the hidden activations [128][64]
+                              // (= d_off: the delta tile is dead during the forward)
     int stage_off;            // endpoint network: FP32 outputs and summed L_cd gradients, [128][out]
 };
 

@@ -1,6 +1,7 @@
-"""The largest model the kernels take (8 textures, 16 colour levels: 32 input features, 18
-colour and 36 endpoint outputs) and the degenerate cases of the method: every block solid
-(equal endpoints: BC1 all codes 0, BC4 six-value mode with r0 = r1), an empty block list."""
+"""The largest models the kernels take (8 textures, 16 colour levels: 32 input features, 18
+colour and 36 endpoint outputs; 8 BC1 textures with 16 endpoint levels: 32 endpoint inputs and
+48 outputs) and the degenerate cases of the method: every block solid (equal endpoints: BC1
+all codes 0, BC4 six-value mode with r0 = r1), an empty block list."""
 import numpy as np
 import pytest
 import torch
@@ -80,17 +81,13 @@ def test_largest_model_inference(prec):
     assert mm <= 0.001 * ff
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_largest_model_gradients(precision):
-    # BF16: the colour pass needs 272 TMEM columns here, so it runs one warpgroup per CTA
-    mat, desc, odesc, params = max_case(seed=2)
-    refs = [obc.encode(f, t, 64, 64) for f, t in zip(mat.formats, mat.textures)]
+def check_gradients(mat, desc, odesc, params, side, ids, precision):
+    refs = [obc.encode(f, t, side, side) for f, t in zip(mat.formats, mat.textures)]
     tex_d = [_dev(t) for t in mat.textures]
     ref_d = [_dev(r) for r in refs]
-    material = nt.Material.make(64, 64, mat.formats, tex_d, ref_d)
+    material = nt.Material.make(side, side, mat.formats, tex_d, ref_d)
     m = nt.Model(desc)
     m.set_params(_dev(nt.configs.flatten(desc, params)))
-    ids = np.array([0, 3, 7, 15, 100, 255, 128, 64, 3, 200], np.int64)
     grads = torch.empty(m.n_params, device=DEV)
     losses = torch.empty(6, device=DEV)
     m.train_grads(material, _dev(ids.astype(np.int32)), grads, losses, qat_bits=8, precision=precision)
@@ -107,6 +104,29 @@ def test_largest_model_gradients(precision):
         for (aW, ab), (bW, bb) in zip(gg[key], g[key]):
             assert np.linalg.norm(aW - bW) <= tol * np.linalg.norm(bW), key
             assert np.linalg.norm(ab - bb) <= tol * np.linalg.norm(bb), key
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_largest_model_gradients(precision):
+    # BF16: the colour pass needs 272 TMEM columns here, so it runs one warpgroup per CTA
+    mat, desc, odesc, params = max_case(seed=2)
+    ids = np.array([0, 3, 7, 15, 100, 255, 128, 64, 3, 200], np.int64)
+    check_gradients(mat, desc, odesc, params, 64, ids, precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_largest_endpoint_network_gradients(precision):
+    # the widest endpoint network: 16 endpoint levels (every colour level no finer than the 64
+    # blocks per side) and 8 BC1 textures, 32 inputs and 48 outputs; its BF16 pass, with the
+    # split forward's lo weight image, is the largest shared-memory footprint of the training
+    # kernels
+    side = 256
+    mat = synth.make_material("limits", side, ["sine_rgb"] * nt.MAX_TEXTURES, 4)
+    desc, odesc = descs.case_descs(nt, mat.formats, side, nt.MAX_LEVELS, 4, 64, 3, "selu")
+    assert len(odesc.endpoint_res) == nt.MAX_LEVELS and odesc.out_endpoint == 48
+    params = synth.random_params_like(descs.init_params(odesc, 4), seed=5)
+    ids = np.array([0, 3, 77, 1000, 4095, 2048, 513, 64, 3, 3000], np.int64)
+    check_gradients(mat, desc, odesc, params, side, ids, precision)
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
