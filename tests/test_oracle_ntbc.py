@@ -658,6 +658,35 @@ def test_backward_through_activation_output_equals_through_preactivation(act):
         np.testing.assert_allclose(b, d, rtol=1e-12, atol=1e-13)
 
 
+def test_bf16_mode_rounds_the_colour_forward_only():
+    # the training arithmetic's mode: the endpoint forward on exact operands, so its losses are
+    # the FP64 mode's to the last bit; the colour forward on BF16 operands, so its losses move
+    desc, p, mat, refs = _fd_setup("selu")
+    ids = np.array([0, 5, 17, 33, 63, 40])
+    L64, _ = ntbc.losses_and_grads(desc, p, mat.textures, refs, ids, T=0.01)
+    L16, _ = ntbc.losses_and_grads(desc, p, mat.textures, refs, ids, T=0.01, bf16=True)
+    assert L16["L_e"] == L64["L_e"] and L16["L_cd_endpoint"] == L64["L_cd_endpoint"]
+    assert L16["L_c"] != L64["L_c"]
+    assert L16["L_c"] == pytest.approx(L64["L_c"], rel=2e-2)
+
+
+def test_bf16_backward_rounds_an_exact_forward_input():
+    # one sigmoid unit y = s(3 x), x = 1 + 2^-10 (not a BF16 value: it rounds to 1), forward
+    # exact; by hand the rounded backward gives g = bf16(y (1 - y)), dL/dW = g * bf16(x) = g,
+    # dL/db = g, dL/dx = g * 3 (3 is a BF16 value)
+    x = np.array([[1.0 + 2.0 ** -10]])
+    layers = [(np.array([[3.0]]), np.array([0.0]))]
+    y, cache = ntbc.mlp_forward(layers, x, "selu")
+    y_exact = 1.0 / (1.0 + math.exp(-3.0 * (1.0 + 2.0 ** -10)))
+    assert y[0, 0] == pytest.approx(y_exact, rel=1e-15)
+    gx, grads = ntbc.mlp_backward(layers, cache, y, np.ones_like(y), "selu", rnd=ntbc.bf16_round)
+    g = float(ntbc.bf16_round(y_exact * (1.0 - y_exact)))
+    assert grads[0][0][0, 0] == g and grads[0][1][0] == g and gx[0, 0] == 3.0 * g
+    # without the rounding the weight gradient carries the input's 2^-10
+    _, grads64 = ntbc.mlp_backward(layers, cache, y, np.ones_like(y), "selu")
+    assert grads64[0][0][0, 0] == pytest.approx(y_exact * (1 - y_exact) * (1.0 + 2.0 ** -10), rel=1e-14)
+
+
 def test_params_from_flat_inverts_the_canonical_order():
     # the flat reader takes exactly the values of flatten_params, in that order, and its size is
     # the paper-pinned parameter count (4096^2 material, 8 levels 16..2048: the storage figure of
