@@ -410,8 +410,13 @@ typedef struct {
  *   NTBC_TRAIN_BF16  one fused tensor-core pass per network: BF16 MMA operands (features,
  *                    activations, weights, deltas) with FP32 accumulation in TMEM; losses,
  *                    sigmoid, straight-through argmax, grid gather / scatter and Adam in FP32.
- *                    Activations live on chip for one 128-sample tile, so device memory does
- *                    not grow with the batch. Gradients within about 2e-2 of FP64.
+ *                    The endpoint network's forward splits each operand into BF16 hi + lo
+ *                    parts (~16 significant bits): its outputs set the palettes that the
+ *                    straight-through softmax of App. A scores at temperature T, which
+ *                    amplifies an output error 1/T. Activations live on chip for one
+ *                    128-sample tile, so device memory does not grow with the batch.
+ *                    Gradients within about 4e-2 of FP64 at T = 0.01 (colour network), 1.5e-2
+ *                    (endpoint network).
  */
 enum { NTBC_TRAIN_FP32 = 0, NTBC_TRAIN_BF16 = 1 };
 
