@@ -129,15 +129,19 @@ def test_checkpoint_resume_matches_uninterrupted_encode(precision):
     """An encode split at a step, its checkpoint (FP32 master parameters, Adam moments, step)
     written out and loaded into a fresh model, then resumed, ends where an uninterrupted encode
     ends, up to the rounding order of the grid scatter's floating-point atomics, which makes
-    uninterrupted encodes differ too; the checkpoint round trip itself is exact. The spread of
-    uninterrupted encodes is chaotic (the argmax amplifies a rounding difference or not): two of
-    them were measured identical in one run and 0.9 % apart in another, so the noise reference is
-    the largest difference among three of them."""
+    uninterrupted encodes differ too; the checkpoint round trip itself is exact. Over a long
+    encode the argmax can amplify that rounding into a different trajectory (uninterrupted
+    encodes of 44 steps have measured from 0 to 0.9 % apart), so this encode is short: 4 steps
+    and 2 QAT steps, resumed after step 3, so the resumed range crosses into the QAT phase. The
+    bar is the larger of the spread of two uninterrupted encodes (x3) and a thousandth of the
+    distance the encode moves the parameters: a resume that lost the Adam moments, the step or
+    the phase lands a sizeable share of that distance away."""
     s = setup(grid_scale=0)
     desc, material = s["desc"], s["material"]
     flat0 = _dev(nt.configs.flatten(desc, s["params"]))
-    cfg = nt.TrainConfig.make(steps=40, batch_texels=512, qat_fraction=0.1, grid_bits=8, seed=5, precision=precision)
-    total = 44
+    cfg = nt.TrainConfig.make(steps=4, batch_texels=512, qat_fraction=0.5, grid_bits=8, warmup=2, seed=5,
+                              precision=precision)
+    split, total = 3, 6
 
     def fresh():
         m = nt.Model(desc)
@@ -150,26 +154,39 @@ def test_checkpoint_resume_matches_uninterrupted_encode(precision):
         torch.cuda.synchronize()
         return out.cpu().numpy().astype(np.float64)
 
-    a, c, e = fresh(), fresh(), fresh()
+    a, c = fresh(), fresh()
     a.train(material, cfg)
     c.train(material, cfg)
-    e.train(material, cfg)
     first = fresh()
-    first.train_range(material, cfg, 0, 20)
+    first.train_range(material, cfg, 0, split)
     ck = torch.empty(first.checkpoint_size(), dtype=torch.uint8)
     first.checkpoint_save(ck)
     b = nt.Model(desc)
-    assert b.checkpoint_load(ck) == 20
+    assert b.checkpoint_load(ck) == split
     ck2 = torch.empty_like(ck)
     b.checkpoint_save(ck2)
     assert torch.equal(ck, ck2)
-    losses = b.train_range(material, cfg, 20, total)
+    losses = b.train_range(material, cfg, split, total)
     assert all(np.isfinite(losses))
-    pa, pb, pc, pe = params(a), params(b), params(c), params(e)
-    norm = np.linalg.norm(pa)
-    noise = max(np.linalg.norm(pa - pc), np.linalg.norm(pa - pe), np.linalg.norm(pc - pe)) / norm
-    resumed = min(np.linalg.norm(pb - q) for q in (pa, pc, pe)) / norm
-    assert resumed <= 3 * noise + 1e-6, (resumed, noise)
+    p0 = flat0.cpu().numpy().astype(np.float64)
+    pa, pb, pc = params(a), params(b), params(c)
+    moved = np.linalg.norm(pa - p0)
+    assert moved > 0
+    noise = np.linalg.norm(pa - pc)
+    resumed = min(np.linalg.norm(pb - pa), np.linalg.norm(pb - pc))
+    bar = max(3 * noise, 1e-3 * moved)
+    assert resumed <= bar, (resumed, noise, moved)
+    # control: the split's parameters resumed with other Adam moments (those of a one-step
+    # history) land far outside the bar, so it tells a resume that lost the optimizer state
+    flat_split = torch.empty(first.n_params, device=DEV)
+    first.get_params(flat_split)
+    stale = fresh()
+    stale.train_range(material, cfg, 0, 1)
+    stale.set_params(flat_split)
+    stale.train_range(material, cfg, split, total)
+    lost = np.linalg.norm(params(stale) - pa)
+    print("resumed", resumed / moved, "noise", noise / moved, "other moments", lost / moved)
+    assert lost > 10 * bar, (lost, bar)
     # a checkpoint of another model, or with a damaged header, is refused
     other = nt.Model(nt.configs.model_desc(list(s["mat"].formats), 64, 3, 4, 9, 2, nt.ACT_SELU))
     with pytest.raises(nt.NTBCError):
