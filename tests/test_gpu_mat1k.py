@@ -57,6 +57,7 @@ def trained():
 def test_encode_fp32_and_bf16_gain_and_agree(trained):
     p32 = trained["psnrs"](trained["models"][nt.TRAIN_FP32], nt.PREC_FP32)[0]
     p16 = trained["psnrs"](trained["models"][nt.TRAIN_BF16], nt.PREC_FP32)[0]
+    print("PSNR FP32 encode", np.round(p32, 3), "BF16 encode", np.round(p16, 3))
     for u, a, b, r in zip(trained["untrained"], p32, p16, trained["ref"]):
         assert a > u + 8.0 and b > u + 8.0
         assert a < r and b < r
