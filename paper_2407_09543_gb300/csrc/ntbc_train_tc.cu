@@ -176,10 +176,16 @@ __device__ __forceinline__ float norm_and_inverse(float sq, float& inv) {
     inv = rsqrt_fast(fmaxf(sq, kNormGuard * kNormGuard));
     return sq * inv;
 }
-__device__ __forceinline__ float act_fast(float z, int act) {
-    if (act != NTBC_ACT_SELU) return fmaxf(z, 0.f);
-    float e = fmaf(kSeluLA, ex2_fast(fminf(z, 0.f) * kL2e), -kSeluLA);
-    return z > 0.f ? kSeluLambda * z : e;
+// the hidden activation on a pair with packed FP32 (two lanes per instruction): SELU as
+// lambda (z - m) + lambda alpha (2^(m log2 e) - 1) with m = min(z, 0), which is lambda z for z > 0
+// (the exponential term is exactly 0) and lambda alpha (e^z - 1) for z <= 0 (z - m is exactly 0)
+__device__ __forceinline__ float2 act_fast2(float2 z, int act) {
+    if (act != NTBC_ACT_SELU) return make_float2(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f));
+    const float2 m = make_float2(fminf(z.x, 0.f), fminf(z.y, 0.f));
+    const float2 ml = __fmul2_rn(m, make_float2(kL2e, kL2e));
+    const float2 e = make_float2(ex2_fast(ml.x), ex2_fast(ml.y));
+    const float2 t = __ffma2_rn(make_float2(kSeluLA, kSeluLA), e, make_float2(-kSeluLA, -kSeluLA));
+    return __ffma2_rn(make_float2(kSeluLambda, kSeluLambda), __ffma2_rn(m, make_float2(-1.f, -1.f), z), t);
 }
 __device__ __forceinline__ float sigmoid_fast(float z) { return rcp_fast(1.f + ex2_fast(-z * kL2e)); }
 
@@ -699,7 +705,11 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                             tmem_ld16(G.row + c0 + 16, z + 16);
                             tmem_wait_ld_regs<32>(z);
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) z[j] = act_fast(z[j], act);
+                            for (int j = 0; j < 32; j += 2) {
+                                const float2 y = act_fast2(make_float2(z[j], z[j + 1]), act);
+                                z[j] = y.x;
+                                z[j + 1] = y.y;
+                            }
 #pragma unroll
                             for (int q = 0; q < 4; ++q) st_chunk_bf16(G.A[l], r, c0 / 8 + q, kTrHidCols, z + 8 * q);
                         }
@@ -708,7 +718,11 @@ __global__ void __launch_bounds__(COLOR ? 2 * kTrRows * kTrMaxGroups : kTrEndpoi
                         tmem_ld16(G.row + 16 * qw, z);
                         tmem_wait_ld_regs<16>(z);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) z[j] = act_fast(z[j], act);
+                        for (int j = 0; j < 16; j += 2) {
+                            const float2 y = act_fast2(make_float2(z[j], z[j + 1]), act);
+                            z[j] = y.x;
+                            z[j + 1] = y.y;
+                        }
                         // hi parts for the next layer and the backward, lo parts for the next layer
                         // (layer l's MMAs, the last readers of the lo tile, have completed)
                         st_chunk_bf16_split(G.A[l], kTrHidCols, Alo, 64, r, 2 * qw, z);
